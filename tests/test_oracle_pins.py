@@ -1,0 +1,345 @@
+"""Pins for the FP64 oracle: facts fixed by the paper or by mathematics, not
+by the oracle itself.  Each test names the passage or theorem it relies on
+and the plausible mistakes it would catch.  CPU only."""
+import json
+import math
+import pathlib
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2305_13925_gb300 import channels as C
+
+GOLDEN = pathlib.Path(__file__).parent / "golden"
+
+
+def rand_h(M, K, seed, scales=None):
+    rng = np.random.default_rng(seed)
+    H = (rng.standard_normal((M, K)) + 1j * rng.standard_normal((M, K))) / math.sqrt(2)
+    if scales is not None:
+        H = H * np.asarray(scales)[None, :]
+    return H
+
+
+def dft_columns(M, K):
+    m = np.arange(M)[:, None]
+    k = np.arange(K)[None, :]
+    return np.exp(-2j * np.pi * m * k / M) / math.sqrt(M)
+
+
+# --------------------------------------------------------------------------
+# Gram matrix P = H^H H + xi I (Sec. II after Eq. 7)
+
+@pytest.mark.parametrize("M,K", [(7, 3), (64, 16), (100, 32)])
+def test_gram_quadratic_form_eq18(M, K):
+    """Eq. 18: q^H P q = ||H q||^2 + xi ||q||^2 for every q.  Catches a
+    conjugated/transposed operand (gives conj(P)), a dropped xi, a wrong index."""
+    H = rand_h(M, K, 1, scales=np.linspace(0.3, 3.0, K))
+    xi = 0.7
+    A = O.gram(H, xi)
+    rng = np.random.default_rng(2)
+    for _ in range(5):
+        q = rng.standard_normal(K) + 1j * rng.standard_normal(K)
+        lhs = np.vdot(q, A @ q)
+        rhs = np.linalg.norm(H @ q) ** 2 + xi * np.linalg.norm(q) ** 2
+        assert abs(lhs - rhs) <= 1e-12 * rhs
+
+
+def test_gram_hermitian_exact_and_hpd():
+    """P is Hermitian (entry by entry, exactly) and lambda_min(P) >= xi (Eq. 18)."""
+    inst = C.generate_instance(C.PRESETS["single_256x16"], 0, 0)
+    A = O.gram(inst.H, inst.xi)
+    assert np.array_equal(A, A.conj().T)
+    assert np.all(np.imag(np.diag(A)) == 0)
+    lam = np.linalg.eigvalsh(A)
+    assert lam.min() >= inst.xi * (1 - 1e-12)
+
+
+def test_gram_orthonormal_columns():
+    """Orthonormal columns (unitary DFT) give P = (1 + xi) I."""
+    H = dft_columns(64, 16)
+    A = O.gram(H, 0.25)
+    assert np.abs(A - 1.25 * np.eye(16)).max() < 1e-14
+
+
+def test_gram_single_user_and_trace():
+    """K = 1: P = ||h||^2 + xi.  Any K: tr P = ||H||_F^2 + K xi."""
+    h = rand_h(33, 1, 3)
+    A = O.gram(h, 0.5)
+    assert abs(A[0, 0] - (np.linalg.norm(h) ** 2 + 0.5)) < 1e-13
+    H = rand_h(50, 9, 4)
+    A = O.gram(H, 0.1)
+    assert abs(np.trace(A) - (np.linalg.norm(H) ** 2 + 0.9)) < 1e-11
+
+
+def test_gram_visibility_blocks_are_zero():
+    """Users that share no visible subarray have P[k, j] = 0 exactly (the
+    sparsity remark of Sec. III-B): disjoint supports give exact zeros."""
+    H = np.zeros((8, 2), dtype=complex)
+    H[:4, 0] = [1, 2j, 3, -1]
+    H[4:, 1] = [2, 1j, -1, 1]
+    A = O.gram(H, 0.1)
+    assert A[0, 1] == 0 and A[1, 0] == 0
+
+
+# --------------------------------------------------------------------------
+# Direct inversion (Appendix, Cholesky)
+
+def test_cholesky_matches_library_solve_and_rzf_identity():
+    """Direct RZF: numpy.linalg.solve agrees; and H^H W = I - xi X, which follows
+    from H^H H P^{-1} = I - xi P^{-1} (definition of P)."""
+    inst = C.generate_instance(C.PRESETS["single_256x16"], 0, 3)
+    W, X, st = O.rzf_direct(inst.H, inst.xi)
+    assert st == O.OK
+    A = inst.H.conj().T @ inst.H + inst.xi * np.eye(16)
+    Xn = np.linalg.solve(A, np.eye(16))
+    assert np.linalg.norm(X - Xn) / np.linalg.norm(Xn) < 1e-12
+    lhs = inst.H.conj().T @ W
+    assert np.abs(lhs - (np.eye(16) - inst.xi * X)).max() < 1e-12
+
+
+def test_cholesky_rejects_indefinite():
+    A = np.diag([1.0, -1.0, 2.0]).astype(complex)
+    _, st = O.cholesky_solve(A)
+    assert st == O.NOTHPD
+
+
+# --------------------------------------------------------------------------
+# (Preconditioned) conjugate gradients, Sec. III-B Steps 1-4, Eqs. 19-21
+
+def small_system(K=8, M=24, seed=5, spread=(0.5, 4.0), xi=0.3):
+    H = rand_h(M, K, seed, scales=np.geomspace(*spread, K))
+    return H, O.gram(H, xi)
+
+
+@pytest.mark.parametrize("K", [1, 2, 3, 5, 8])
+@pytest.mark.parametrize("variant", ["standard", "cg"])
+def test_exact_in_at_most_K_steps(K, variant):
+    """CG and PCG (Hermitian preconditioner) terminate in at most K steps in
+    exact arithmetic (finite termination theorem)."""
+    H, A = small_system(K=K, M=3 * K + 2, seed=10 + K)
+    X, it, rr, st = O.pcg(A, None, variant, max_iter=K)
+    Xs = np.linalg.solve(A, np.eye(K))
+    assert st == O.OK
+    assert np.linalg.norm(X - Xs) / np.linalg.norm(Xs) < 1e-9
+
+
+def krylov_minimiser(A, b, Minv, t):
+    """argmin over x in span{v, Minv A v, ..., (Minv A)^{t-1} v}, v = Minv b, of
+    ||x - A^{-1} b||_A: the Galerkin solution (Q^H A Q) y = Q^H b."""
+    v = Minv @ b
+    V = [v]
+    for _ in range(t - 1):
+        V.append(Minv @ (A @ V[-1]))
+    Q, _ = np.linalg.qr(np.stack(V, axis=1))
+    y = np.linalg.solve(Q.conj().T @ A @ Q, Q.conj().T @ b)
+    return Q @ y
+
+
+@pytest.mark.parametrize("variant", ["standard", "cg"])
+@pytest.mark.parametrize("T", [1, 2, 3, 4, 6])
+def test_fixed_T_iterate_is_krylov_minimiser(variant, T):
+    """The t-th (P)CG iterate minimises the energy-norm error over the t-th
+    Krylov space of the preconditioned operator (optimality of CG).  This
+    pins the fixed-T iterate itself; a wrong sign, a dropped preconditioner,
+    a wrong step or direction formula each break it."""
+    H, A = small_system(K=12, M=40, seed=21)
+    d = np.real(np.diag(A))
+    Minv = np.diag(1.0 / d) if variant == "standard" else np.eye(12)
+    rng = np.random.default_rng(7)
+    B = rng.standard_normal((12, 3)) + 1j * rng.standard_normal((12, 3))
+    X, it, rr, st = O.pcg(A, B, variant, max_iter=T)
+    for j in range(3):
+        xk = krylov_minimiser(A, B[:, j], Minv, T)
+        assert np.linalg.norm(X[:, j] - xk) / np.linalg.norm(xk) < 1e-9
+    assert np.all(it == T)
+
+
+@pytest.mark.parametrize("variant", ["standard", "alg1", "cg"])
+def test_recurrence_residual_equals_true_residual(variant):
+    """The updated residual equals s - P w (Eq. 13; for Algorithm 1, D r = s - P w).
+    Catches a mismatch between the solution and residual updates."""
+    H, A = small_system(K=10, M=30, seed=31, spread=(0.8, 1.5))
+    rng = np.random.default_rng(8)
+    B = rng.standard_normal((10, 2)) + 1j * rng.standard_normal((10, 2))
+    for T in (1, 3, 5):
+        X, it, rr, st = O.pcg(A, B, variant, max_iter=T)
+        true = np.linalg.norm(B - A @ X, axis=0) / np.linalg.norm(B, axis=0)
+        assert np.allclose(rr, true, rtol=1e-8, atol=1e-13)
+
+
+def test_jacobi_exact_in_one_step_for_diagonal_P():
+    """Orthogonal channels of unequal norms make P diagonal: with C = D both
+    Jac-PCG forms return D^{-1} s after one step; plain CG does not."""
+    H = dft_columns(32, 8) * np.geomspace(0.5, 5.0, 8)[None, :]
+    A = O.gram(H, 0.2)
+    assert np.abs(A - np.diag(np.diag(A))).max() < 1e-13
+    A = np.diag(np.diag(A))
+    exact = np.diag(1.0 / np.diag(A))
+    for v in ("standard", "alg1"):
+        X, it, rr, st = O.pcg(A, None, v, max_iter=1)
+        assert np.abs(X - exact).max() <= 1e-15 * np.abs(exact).max()
+        X3, _, _, st3 = O.pcg(A, None, v, max_iter=3)       # iterating further changes nothing
+        assert st3 == O.OK and np.array_equal(X3, X)
+    Xcg, _, _, _ = O.pcg(A, None, "cg", max_iter=1)
+    Bones = np.ones((8, 1), dtype=complex)
+    xcg, _, _, _ = O.pcg(A, Bones, "cg", max_iter=1)
+    assert np.linalg.norm(xcg[:, 0] - exact @ Bones[:, 0]) > 1e-3
+
+
+def test_equal_diagonal_all_forms_coincide():
+    """With D = cI the Jacobi preconditioner is a scalar: Jac-PCG (both forms)
+    and plain CG produce the same iterates."""
+    H = rand_h(30, 8, 41)
+    H = H / np.linalg.norm(H, axis=0)[None, :]          # equal column norms
+    A = O.gram(H, 0.4)
+    assert np.ptp(np.real(np.diag(A))) < 1e-14
+    for T in (1, 2, 4, 6):
+        Xs = [O.pcg(A, None, v, max_iter=T)[0] for v in ("standard", "alg1", "cg")]
+        assert np.linalg.norm(Xs[0] - Xs[2]) / np.linalg.norm(Xs[2]) < 1e-12
+        assert np.linalg.norm(Xs[1] - Xs[2]) / np.linalg.norm(Xs[2]) < 1e-12
+
+
+def test_brute_force_K1_K2():
+    """K = 1: x = s / (||h||^2 + xi) after one step.  K = 2: two steps of CG or
+    Jac-PCG give the closed-form 2 x 2 inverse."""
+    h = rand_h(9, 1, 51)
+    A = O.gram(h, 0.3)
+    for v in ("standard", "alg1", "cg"):
+        X, _, _, _ = O.pcg(A, None, v, max_iter=1)
+        assert abs(X[0, 0] - 1.0 / (np.linalg.norm(h) ** 2 + 0.3)) < 1e-15
+    H = rand_h(9, 2, 52)
+    A = O.gram(H, 0.3)
+    a, b, c, d = A[0, 0], A[0, 1], A[1, 0], A[1, 1]
+    inv = np.array([[d, -b], [-c, a]]) / (a * d - b * c)
+    for v in ("standard", "cg"):
+        X, _, _, _ = O.pcg(A, None, v, max_iter=2)
+        assert np.abs(X - inv).max() < 1e-13 * np.abs(inv).max()
+
+
+def test_tolerance_stops_at_first_small_residual():
+    """Step 2: a column stops at the first iterate with ||r|| <= tol ||s||;
+    one iteration fewer leaves it above the tolerance."""
+    inst = C.generate_instance(C.PRESETS["batched_1024x64"], 1, 0)
+    A = O.gram(inst.H, inst.xi)
+    tol = 1e-6
+    X, it, rr, st = O.pcg(A, None, "standard", max_iter=200, tol=tol)
+    assert np.all(rr <= tol) and np.all(it > 0)
+    for j in (0, 17, 63):
+        _, it2, rr2, _ = O.pcg(A, np.eye(64)[:, j], "standard", max_iter=int(it[j]) - 1)
+        assert rr2[0] > tol
+
+
+def test_converged_forms_reach_rzf():
+    """At tolerance, standard Jac-PCG and CG converge to the direct RZF solution."""
+    inst = C.generate_instance(C.PRESETS["single_256x16"], 0, 0)
+    A = O.gram(inst.H, inst.xi)
+    Xc, _ = O.cholesky_solve(A)
+    for v in ("standard", "cg"):
+        X, it, rr, st = O.pcg(A, None, v, max_iter=500, tol=1e-13)
+        assert np.linalg.norm(X - Xc) / np.linalg.norm(Xc) < 1e-10
+
+
+def test_alg1_converges_when_preconditioned_operator_is_mild():
+    """Algorithm 1 (Euclidean products on D^{-1} P) converges to P^{-1} s when
+    the diagonal is nearly constant."""
+    H, A = small_system(K=8, M=40, seed=61, spread=(0.95, 1.05), xi=0.5)
+    X, it, rr, st = O.pcg(A, None, "alg1", max_iter=400, tol=1e-12)
+    Xs = np.linalg.solve(A, np.eye(8))
+    assert np.linalg.norm(X - Xs) / np.linalg.norm(Xs) < 1e-9
+
+
+def test_column_independence():
+    """Each column of X depends only on its own column of B (Eq. 16 per column)."""
+    H, A = small_system(K=6, M=20, seed=71)
+    rng = np.random.default_rng(9)
+    B = rng.standard_normal((6, 4)) + 1j * rng.standard_normal((6, 4))
+    for v in ("standard", "alg1", "cg"):
+        X, _, _, _ = O.pcg(A, B, v, max_iter=3)
+        for j in range(4):
+            xj, _, _, _ = O.pcg(A, B[:, j], v, max_iter=3)
+            assert np.array_equal(X[:, j], xj[:, 0])
+
+
+# --------------------------------------------------------------------------
+# Precoder, power factor, SINR (Eqs. 7, 9, 15)
+
+def test_precoder_identity_and_power():
+    """Converged W satisfies H^H W = I - xi X, and ||beta W||_F^2 = P."""
+    inst = C.generate_instance(C.PRESETS["single_256x16"], 0, 1)
+    out = O.precode(inst.H, inst.xi, "standard", max_iter=300, tol=1e-14, power=3.0)
+    lhs = inst.H.conj().T @ out["W"]
+    assert np.abs(lhs - (np.eye(16) - inst.xi * out["X"])).max() < 1e-10
+    assert abs(np.linalg.norm(out["beta"] * out["W"]) ** 2 - 3.0) < 1e-12
+    W2 = inst.H @ out["X"]
+    assert np.abs(out["W"] - W2).max() < 1e-12 * np.abs(W2).max()
+
+
+def test_sinr_closed_form_orthogonal_channels():
+    """Orthogonal channels: RZF columns are h_k / (||h_k||^2 + xi), there is no
+    interference, and SINR_k = beta^2 (||h_k||^2 / (||h_k||^2 + xi))^2 / sigma^2
+    with beta^2 = P / sum_k ||h_k||^2 / (||h_k||^2 + xi)^2."""
+    norms = np.array([0.5, 1.0, 2.0, 3.5])
+    H = dft_columns(16, 4) * norms[None, :]
+    xi, P, s2 = 0.3, 2.0, 0.7
+    W, X, st = O.rzf_direct(H, xi)
+    beta = O.power_factor(W, P)
+    g = O.sinr(H, beta * W, s2)
+    n2 = norms ** 2
+    beta2 = P / np.sum(n2 / (n2 + xi) ** 2)
+    expect = beta2 * (n2 / (n2 + xi)) ** 2 / s2
+    assert np.allclose(g, expect, rtol=1e-12)
+
+
+def test_se_of_converged_pcg_matches_direct_rzf():
+    """Sum SE (argument of Eq. 10) from converged Jac-PCG equals direct RZF's."""
+    inst = C.generate_instance(C.PRESETS["single_256x16"], 0, 2)
+    Wd, _, _ = O.rzf_direct(inst.H, inst.xi)
+    out = O.precode(inst.H, inst.xi, "standard", max_iter=300, tol=1e-13)
+    se_d = O.sum_se(inst.H, O.power_factor(Wd, 10.0) * Wd)
+    se_p = O.sum_se(inst.H, out["beta"] * out["W"] * math.sqrt(10.0))
+    assert abs(se_d - se_p) < 1e-9 * se_d
+
+
+# --------------------------------------------------------------------------
+# Operation counts of the Appendix and the printed complexity claim
+
+def test_flop_formulas_and_54_percent_claim():
+    g = json.loads((GOLDEN / "paper_printed.json").read_text())
+    K = 30
+    T = g["iterations_to_convergence"]["value"]
+    # the CG iteration total is the sum of its listed parts (Appendix)
+    parts = (8 * K - 2) + (8 * K ** 2 - 2 * K) + (8 * K - 2) + 8 * K + 8 * K + (8 * K - 2) + 8 * K
+    assert parts == O.flops_cg_iteration(K)
+    red = 1 - O.flops_jacpcg(K, T) / O.flops_rzf_direct(K)
+    assert abs(red - 0.5693) < 5e-4
+    claim = g["complexity_reduction_jacpcg_vs_rzf"]
+    assert claim["K"] == K and abs(red - claim["value"]) < 0.04     # "about 54%"
+    # Fig. 6 discussion: CG and Jac-PCG fall below direct RZF as K grows; with
+    # the Appendix formulas at T = 5 the crossover is K = 15
+    for K in range(15, 129):
+        assert O.flops_cg(K, T) < O.flops_jacpcg(K, T) < O.flops_rzf_direct(K)
+    assert O.flops_jacpcg(14, T) > O.flops_rzf_direct(14)
+
+
+def test_table1_geometry():
+    """Table I: N = 23.0610 m at spacing 2 lambda and 2.6 GHz gives M = 100."""
+    g = json.loads((GOLDEN / "paper_printed.json").read_text())["table1"]
+    lam = 299792458.0 / g["carrier_hz"]
+    assert round(g["N_m"] / (g["antenna_spacing_lambda"] * lam)) == 100
+    inst = C.paper_table1(0, 0)
+    assert inst.H.shape == (100, 32)
+    A = O.gram(inst.H, inst.xi)
+    assert np.linalg.eigvalsh(A).min() >= inst.xi * (1 - 1e-9)
+
+
+def test_batch_equals_single_instances():
+    """The threaded batch entry computes each instance exactly as the single one."""
+    insts = C.generate_ragged(6, 3, k_set=(8, 16, 32), m_set=(256, 512))
+    Ws, beta, iters, relres, status = O.precode_batch([i.H for i in insts], [i.xi for i in insts],
+                                                      "standard", max_iter=6, nthreads=3)
+    for i, inst in enumerate(insts):
+        one = O.precode(inst.H, inst.xi, "standard", max_iter=6)
+        assert np.array_equal(Ws[i], one["W"]) and beta[i] == one["beta"]
+        assert iters[i] == 6 and status[i] == O.OK
