@@ -1,0 +1,167 @@
+/*
+ * jacpcg.h -- C ABI of the GB300 (sm_103a) Jac-PCG regularized zero-forcing
+ * precoder library.
+ *
+ * The operation (arXiv 2305.13925, Xu, Zhang, Li, Xiao, Ai):
+ *   for each channel H (M base-station antennas x K single-antenna users,
+ *   complex), form the regularised Gram matrix A = H^H H + xi I (Sec. II,
+ *   definition of P_i after Eq. 7), solve A X = I_K by Jacobi-preconditioned
+ *   conjugate gradients (Sec. III-B Steps 1-4, Eqs. 19-21, Algorithm 1),
+ *   and form the unnormalised precoder W = H X (Eq. 7; Eq. 15 per symbol)
+ *   with its power factor beta = sqrt(P / ||W||_F^2) (Sec. II after Eq. 7).
+ *
+ * Layout.  Complex values are complex64: two float32 (re, im) interleaved.
+ * Matrices are column-major: element (m, k) of H sits at H[m + k * ldh].
+ * W is M x K with leading dimension ldw; X and A are K x K with leading
+ * dimension K.  All H / W / X / A pointers are DEVICE pointers owned by the
+ * caller, 16-byte aligned, and must stay valid until the work enqueued on
+ * the stream has completed.  The library never frees or retains them.
+ *
+ * Errors.  Every call returns a jacpcg_status.  Call-level errors (invalid
+ * arguments, out of memory) leave all outputs untouched.  Per-instance
+ * outcomes (not converged, not Hermitian positive definite, non-finite
+ * values) are written to the caller's per-instance status array on the
+ * device.  No call aborts, traps or throws across this boundary.  A CUDA
+ * error reported by the runtime maps to JACPCG_ECUDA and leaves the context
+ * unusable (destroy it).
+ *
+ * Threading.  A context (and each plan made from it) may be used from one
+ * host thread at a time.  Work is enqueued asynchronously on the stream the
+ * caller passes (a cudaStream_t, passed as void*; NULL is the legacy
+ * default stream); the caller synchronises.
+ */
+#ifndef JACPCG_H
+#define JACPCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    JACPCG_OK = 0,
+    JACPCG_EINVAL = 1,      /* invalid argument (null pointer, size limit, alignment) */
+    JACPCG_ENOMEM = 2,      /* device or pinned host memory exhausted, or arena budget */
+    JACPCG_ECUDA = 3,       /* CUDA runtime error; the context is unusable afterwards */
+    JACPCG_ENOTCONV = 4,    /* per instance: tolerance not met within max_iter */
+    JACPCG_ENOTHPD = 5,     /* per instance: d^H A d <= 0 met, A is not positive definite */
+    JACPCG_ENONFINITE = 6,  /* per instance: NaN or Inf in W */
+    JACPCG_ETIMEOUT = 7,    /* a bounded wait ran out (serving) */
+    JACPCG_EBUSY = 8        /* serving queue full or ticket still in flight */
+} jacpcg_status;
+
+/* Iteration form (Sec. III-B).  STANDARD: Steps 1-4 with C = D (Eq. 21),
+ * written in residual form with the standard PCG step and direction ratios
+ * (the printed ratio of Eq. 20 is garbled).  ALG1: Algorithm 1 as printed
+ * (conjugate gradients with Euclidean inner products on the left-scaled
+ * system D^{-1} A X = D^{-1} B; its step alpha is complex).  CG: plain
+ * conjugate gradients (C = I). */
+enum { JACPCG_STANDARD = 0, JACPCG_ALG1 = 1, JACPCG_CG = 2 };
+
+/* Arithmetic of the Gram and W = H X contractions.
+ * FP32:   FP32 FMA on the SIMT pipes.
+ * TF32X3: tensor cores (tcgen05, kind::tf32) with each FP32 operand split
+ *         into a TF32 head and a TF32 tail, three products accumulated in
+ *         FP32 (about FP32 accuracy).
+ * The iteration always runs in FP32 with compensated dot products. */
+enum { JACPCG_FP32 = 0, JACPCG_TF32X3 = 1 };
+
+/* config flags */
+enum { JACPCG_FLAG_PROFILE = 1 };   /* record per-phase CUDA events on each execute */
+
+typedef struct {
+    int device;              /* CUDA device ordinal */
+    int max_instances;       /* most instances in one plan or precode call (>= 1) */
+    int max_M;               /* largest M accepted (>= 1) */
+    int max_K;               /* largest K accepted, 1 <= max_K <= 256 */
+    size_t arena_bytes;      /* device workspace arena; 0 = sized for one call at the limits */
+    int precision;           /* JACPCG_FP32 or JACPCG_TF32X3 */
+    int variant;             /* JACPCG_STANDARD, JACPCG_ALG1 or JACPCG_CG */
+    int flags;               /* JACPCG_FLAG_* */
+} jacpcg_config;
+
+typedef struct {
+    int M, K;                /* 1 <= K <= max_K, K <= M <= max_M (K > M needs xi > 0) */
+    int ldh;                 /* leading dimension of H, >= M, even */
+    const void *H;           /* device, complex64 M x K column-major, 16-byte aligned */
+    double xi;               /* regulariser, >= 0 (> 0 when K > M) */
+    double power;            /* total transmit power P for beta; <= 0 means 1 */
+    void *W;                 /* device out, complex64 M x K column-major */
+    int ldw;                 /* leading dimension of W, >= M, even */
+    void *X;                 /* optional device out, complex64 K x K (ld K): the iterate */
+    void *A;                 /* optional device out, complex64 K x K (ld K): H^H H + xi I */
+    int max_iter;            /* T, 0 <= T <= 4096 */
+    float tol;               /* > 0: stop a column once ||r|| <= tol ||b||; <= 0: exactly T steps */
+} jacpcg_instance;
+
+typedef struct jacpcg_ctx jacpcg_ctx;
+typedef struct jacpcg_plan jacpcg_plan;
+
+/* Create a context on cfg->device: validates the limits, reserves the
+ * device workspace arena and pinned staging memory.  *out receives the
+ * context.  Errors: EINVAL (bad limits), ENOMEM, ECUDA. */
+jacpcg_status jacpcg_create(const jacpcg_config *cfg, jacpcg_ctx **out);
+
+/* Precode n_inst independent channels in one batched launch sequence on
+ * `stream` (Eq. 7 for each instance, B = I_K).  inst[i] describes instance
+ * i (host array, read during the call).  Per-instance outputs are device
+ * arrays of n_inst entries (any may be NULL): status (jacpcg_status per
+ * instance), iters (largest per-column iteration count), resid (largest
+ * per-column recurrence residual ||r|| / ||b||), beta (power factor).
+ * The call waits, on the host, until the previous precode call of this
+ * context has finished reading its staging memory; it does not wait for
+ * the GPU work it enqueues.  Calls on one context must use one stream (or
+ * be ordered by the caller).  Errors: EINVAL, ENOMEM, ECUDA. */
+jacpcg_status jacpcg_precode(jacpcg_ctx *ctx, const jacpcg_instance *inst, int n_inst,
+                             int32_t *status_dev, int32_t *iters_dev, float *resid_dev,
+                             float *beta_dev, void *stream);
+
+/* Plans: the same work as jacpcg_precode, prepared once (instance table,
+ * tile lists and workspace resident on the device, carved from the context
+ * arena) and executed any number of times.  With use_graph != 0 the first
+ * execute captures the whole launch sequence into one CUDA graph and every
+ * execute replays it (graph replays are not profiled).  Plans of one context may
+ * execute concurrently on different streams (each owns its workspace).
+ * Errors: EINVAL, ENOMEM (arena budget), ECUDA. */
+jacpcg_status jacpcg_plan_create(jacpcg_ctx *ctx, const jacpcg_instance *inst, int n_inst,
+                                 int32_t *status_dev, int32_t *iters_dev, float *resid_dev,
+                                 float *beta_dev, int use_graph, jacpcg_plan **out);
+jacpcg_status jacpcg_plan_execute(jacpcg_plan *plan, void *stream);
+jacpcg_status jacpcg_plan_destroy(jacpcg_plan *plan);
+
+/* Bytes of arena workspace a plan for these instances needs, and bytes
+ * still free in the context arena (for admission control). */
+jacpcg_status jacpcg_plan_bytes(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n_inst,
+                                size_t *bytes);
+jacpcg_status jacpcg_arena_free_bytes(const jacpcg_ctx *ctx, size_t *bytes);
+
+/* Per-phase device time of the executes (plan executes and precode calls,
+ * not graph replays) made since the previous read, when the context was
+ * created with JACPCG_FLAG_PROFILE.  Events are recorded on the caller's
+ * stream around each phase; this call waits for the last of them.
+ * ms[0..3] = total milliseconds in Gram, iteration, W = H X, finalise
+ * (summed over K classes and executes); *n_executes = executes covered (at
+ * most 4096 are recorded between reads); *launches_per_execute = kernels
+ * the last execute launched.  Resets the record. */
+jacpcg_status jacpcg_profile_read(jacpcg_ctx *ctx, float ms[4], int *n_executes,
+                                  int *launches_per_execute);
+
+/* Kernels launched by this context since creation (all entry points). */
+int64_t jacpcg_launch_count(const jacpcg_ctx *ctx);
+
+/* Destroy a context (and any plans still alive).  Waits for the device. */
+jacpcg_status jacpcg_destroy(jacpcg_ctx *ctx);
+
+/* Static string for a status code. */
+const char *jacpcg_strerror(jacpcg_status s);
+
+/* Library version, "MAJOR.MINOR.PATCH". */
+const char *jacpcg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JACPCG_H */

@@ -1,0 +1,235 @@
+"""Thin ctypes binding of the C ABI in include/jacpcg.h.
+
+Names mirror the C entry points (jacpcg_create, jacpcg_precode, ...).  This
+module only marshals arguments: every step of the precoder runs in the CUDA
+kernels of libjacpcg.so.  There is no CPU fallback: if the library is not
+built, or the GPU is missing, the calls raise.
+
+``Precoder`` is a convenience wrapper for torch tensors (PyTorch supplies
+device memory and streams only).
+"""
+from __future__ import annotations
+
+import ctypes
+import pathlib
+import threading
+
+PKG = pathlib.Path(__file__).resolve().parent
+LIB_PATH = PKG / "_build" / "libjacpcg.so"
+
+JACPCG_OK, JACPCG_EINVAL, JACPCG_ENOMEM, JACPCG_ECUDA = 0, 1, 2, 3
+JACPCG_ENOTCONV, JACPCG_ENOTHPD, JACPCG_ENONFINITE, JACPCG_ETIMEOUT, JACPCG_EBUSY = 4, 5, 6, 7, 8
+JACPCG_STANDARD, JACPCG_ALG1, JACPCG_CG = 0, 1, 2
+JACPCG_FP32, JACPCG_TF32X3 = 0, 1
+JACPCG_FLAG_PROFILE = 1
+VARIANTS = {"standard": JACPCG_STANDARD, "alg1": JACPCG_ALG1, "cg": JACPCG_CG}
+PRECISIONS = {"fp32": JACPCG_FP32, "tf32x3": JACPCG_TF32X3}
+
+EXPORTS = ("jacpcg_create", "jacpcg_precode", "jacpcg_plan_create", "jacpcg_plan_execute",
+           "jacpcg_plan_destroy", "jacpcg_plan_bytes", "jacpcg_arena_free_bytes",
+           "jacpcg_profile_read", "jacpcg_launch_count", "jacpcg_destroy", "jacpcg_strerror",
+           "jacpcg_version")
+
+
+class jacpcg_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("max_instances", ctypes.c_int), ("max_M", ctypes.c_int),
+                ("max_K", ctypes.c_int), ("arena_bytes", ctypes.c_size_t),
+                ("precision", ctypes.c_int), ("variant", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+class jacpcg_instance(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int), ("K", ctypes.c_int), ("ldh", ctypes.c_int),
+                ("H", ctypes.c_void_p), ("xi", ctypes.c_double), ("power", ctypes.c_double),
+                ("W", ctypes.c_void_p), ("ldw", ctypes.c_int), ("X", ctypes.c_void_p),
+                ("A", ctypes.c_void_p), ("max_iter", ctypes.c_int), ("tol", ctypes.c_float)]
+
+
+class JacpcgError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {strerror(status)} (status {status})")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: pathlib.Path | str | None = None):
+    """Load libjacpcg.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = pathlib.Path(path) if path else LIB_PATH
+        if not p.exists():
+            raise RuntimeError(f"libjacpcg.so not built ({p}); run paper_2305_13925_gb300.build.build()")
+        L = ctypes.CDLL(str(p))
+        P, I, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        L.jacpcg_create.argtypes = [ctypes.POINTER(jacpcg_config), ctypes.POINTER(P)]
+        L.jacpcg_precode.argtypes = [P, ctypes.POINTER(jacpcg_instance), I, P, P, P, P, P]
+        L.jacpcg_plan_create.argtypes = [P, ctypes.POINTER(jacpcg_instance), I, P, P, P, P, I,
+                                         ctypes.POINTER(P)]
+        L.jacpcg_plan_execute.argtypes = [P, P]
+        L.jacpcg_plan_destroy.argtypes = [P]
+        L.jacpcg_plan_bytes.argtypes = [P, ctypes.POINTER(jacpcg_instance), I, ctypes.POINTER(S)]
+        L.jacpcg_arena_free_bytes.argtypes = [P, ctypes.POINTER(S)]
+        L.jacpcg_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(I),
+                                          ctypes.POINTER(I)]
+        L.jacpcg_launch_count.argtypes = [P]
+        L.jacpcg_launch_count.restype = ctypes.c_int64
+        L.jacpcg_destroy.argtypes = [P]
+        L.jacpcg_strerror.argtypes = [I]
+        L.jacpcg_strerror.restype = ctypes.c_char_p
+        L.jacpcg_version.restype = ctypes.c_char_p
+        for n in ("jacpcg_create", "jacpcg_precode", "jacpcg_plan_create", "jacpcg_plan_execute",
+                  "jacpcg_plan_destroy", "jacpcg_plan_bytes", "jacpcg_arena_free_bytes",
+                  "jacpcg_profile_read", "jacpcg_destroy"):
+            getattr(L, n).restype = I
+        _lib = L
+        return L
+
+
+def strerror(status: int) -> str:
+    try:
+        return load().jacpcg_strerror(int(status)).decode()
+    except RuntimeError:
+        return f"status {status}"
+
+
+def _check(st: int, what: str):
+    if st != JACPCG_OK:
+        raise JacpcgError(st, what)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+# --- C entry points, same names ------------------------------------------------
+
+def jacpcg_version() -> str:
+    return load().jacpcg_version().decode()
+
+
+def jacpcg_strerror(status: int) -> str:
+    return strerror(status)
+
+
+def jacpcg_create(cfg: jacpcg_config) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    _check(load().jacpcg_create(ctypes.byref(cfg), ctypes.byref(ctx)), "jacpcg_create")
+    return ctx
+
+
+def jacpcg_destroy(ctx) -> None:
+    _check(load().jacpcg_destroy(ctx), "jacpcg_destroy")
+
+
+def _array(insts):
+    if isinstance(insts, ctypes.Array):
+        return insts
+    return (jacpcg_instance * len(insts))(*insts)
+
+
+def jacpcg_precode(ctx, insts, status=None, iters=None, resid=None, beta=None, stream=0) -> None:
+    arr = _array(insts)
+    _check(load().jacpcg_precode(ctx, arr, len(insts), _ptr(status), _ptr(iters), _ptr(resid),
+                                 _ptr(beta), ctypes.c_void_p(stream)), "jacpcg_precode")
+
+
+def jacpcg_plan_create(ctx, insts, status=None, iters=None, resid=None, beta=None,
+                       use_graph: bool = False) -> ctypes.c_void_p:
+    arr = _array(insts)
+    plan = ctypes.c_void_p()
+    _check(load().jacpcg_plan_create(ctx, arr, len(insts), _ptr(status), _ptr(iters), _ptr(resid),
+                                     _ptr(beta), int(use_graph), ctypes.byref(plan)),
+           "jacpcg_plan_create")
+    return plan
+
+
+def jacpcg_plan_execute(plan, stream=0) -> None:
+    _check(load().jacpcg_plan_execute(plan, ctypes.c_void_p(stream)), "jacpcg_plan_execute")
+
+
+def jacpcg_plan_destroy(plan) -> None:
+    _check(load().jacpcg_plan_destroy(plan), "jacpcg_plan_destroy")
+
+
+def jacpcg_plan_bytes(ctx, insts) -> int:
+    arr = _array(insts)
+    b = ctypes.c_size_t()
+    _check(load().jacpcg_plan_bytes(ctx, arr, len(insts), ctypes.byref(b)), "jacpcg_plan_bytes")
+    return b.value
+
+
+def jacpcg_arena_free_bytes(ctx) -> int:
+    b = ctypes.c_size_t()
+    _check(load().jacpcg_arena_free_bytes(ctx, ctypes.byref(b)), "jacpcg_arena_free_bytes")
+    return b.value
+
+
+def jacpcg_profile_read(ctx):
+    """(ms per phase summed over executes, executes covered, launches per execute)."""
+    ms = (ctypes.c_float * 4)()
+    n = ctypes.c_int()
+    per = ctypes.c_int()
+    _check(load().jacpcg_profile_read(ctx, ms, ctypes.byref(n), ctypes.byref(per)),
+           "jacpcg_profile_read")
+    return list(ms), n.value, per.value
+
+
+def jacpcg_launch_count(ctx) -> int:
+    return int(load().jacpcg_launch_count(ctx))
+
+
+# --- torch convenience ---------------------------------------------------------
+
+def instance(H, W, xi: float, max_iter: int, tol: float = 0.0, power: float = 1.0, X=None,
+             A=None) -> jacpcg_instance:
+    """Describe one channel held in torch tensors of device storage layout:
+    H and W are complex64 tensors of shape (K, M) (column k of the matrix is
+    row k of the tensor, i.e. column-major storage of the M x K matrix)."""
+    K, M = H.shape[-2], H.shape[-1]
+    return jacpcg_instance(M=M, K=K, ldh=H.stride(-2), H=H.data_ptr(), xi=float(xi),
+                           power=float(power), W=W.data_ptr(), ldw=W.stride(-2),
+                           X=None if X is None else X.data_ptr(),
+                           A=None if A is None else A.data_ptr(), max_iter=int(max_iter),
+                           tol=float(tol))
+
+
+class Precoder:
+    """Owns a context; precodes batches of torch tensors on the current stream."""
+
+    def __init__(self, max_instances: int, max_M: int, max_K: int, variant="standard",
+                 precision="fp32", device: int = 0, arena_bytes: int = 0, profile: bool = False):
+        self.cfg = jacpcg_config(device=device, max_instances=max_instances, max_M=max_M,
+                                 max_K=max_K, arena_bytes=arena_bytes,
+                                 precision=PRECISIONS[precision] if isinstance(precision, str) else precision,
+                                 variant=VARIANTS[variant] if isinstance(variant, str) else variant,
+                                 flags=JACPCG_FLAG_PROFILE if profile else 0)
+        self.ctx = jacpcg_create(self.cfg)
+
+    def close(self):
+        if self.ctx:
+            jacpcg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def precode(self, insts, status=None, iters=None, resid=None, beta=None, stream=None):
+        import torch
+        s = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        jacpcg_precode(self.ctx, insts, status, iters, resid, beta, s)
+
+    def plan(self, insts, status=None, iters=None, resid=None, beta=None, use_graph=False):
+        return jacpcg_plan_create(self.ctx, insts, status, iters, resid, beta, use_graph)

@@ -307,3 +307,52 @@ def to_planar_bf16(H: np.ndarray) -> np.ndarray:
     """(M, K) complex -> (2, K, M) float32 planes (Re, Im) holding bf16-exact values."""
     Hc = np.ascontiguousarray(np.swapaxes(H, -1, -2))
     return np.stack([round_bf16(Hc.real.astype(np.float32)), round_bf16(Hc.imag.astype(np.float32))])
+
+
+def _fill_device_layout(args):
+    """Worker: instances [a, b) of a uniform batch into a shared (n, K, M) complex64 array."""
+    from multiprocessing import shared_memory
+    name, shape, preset, seed, first, a, b = args
+    shm = shared_memory.SharedMemory(name=name)
+    try:
+        out = np.ndarray(shape, dtype=np.complex64, buffer=shm.buf)
+        xi = np.empty(b - a)
+        spec = PRESETS[preset] if isinstance(preset, str) else preset
+        for i in range(a, b):
+            inst = generate_instance(spec, seed, first + i)
+            out[i] = inst.H.T.astype(np.complex64)
+            xi[i - a] = inst.xi
+        return a, xi
+    finally:
+        shm.close()
+
+
+def generate_batch_device_layout(preset: str | ChannelSpec, n: int, seed: int, first: int = 0,
+                                 workers: int | None = None):
+    """Uniform batch straight into the C-ABI storage layout: returns
+    (H (n, K, M) complex64, xi (n,)).  Same values as ``generate_batch``;
+    uses a pool of spawned worker processes (call before any GPU work)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+    from multiprocessing import shared_memory
+    spec = PRESETS[preset] if isinstance(preset, str) else preset
+    shape = (n, spec.K, spec.M)
+    workers = workers or min(16, os.cpu_count() or 1)
+    if workers <= 1 or n < 8:
+        H, xi = generate_batch(spec, n, seed, first)
+        return to_device_layout(H), xi
+    nbytes = int(np.prod(shape)) * 8
+    shm = shared_memory.SharedMemory(create=True, size=nbytes)
+    try:
+        chunks = [(i * n // (4 * workers), (i + 1) * n // (4 * workers)) for i in range(4 * workers)]
+        xi = np.empty(n)
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            jobs = [(shm.name, shape, preset, seed, first, a, b) for a, b in chunks if b > a]
+            for a, x in ex.map(_fill_device_layout, jobs):
+                xi[a:a + len(x)] = x
+        H = np.ndarray(shape, dtype=np.complex64, buffer=shm.buf).copy()
+    finally:
+        shm.close()
+        shm.unlink()
+    return H, xi

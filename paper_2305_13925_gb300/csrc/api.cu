@@ -1,0 +1,609 @@
+// api.cu -- the C ABI of include/jacpcg.h: contexts, the device workspace
+// arena, plans (instance tables + tile lists + workspace on the device),
+// CUDA-graph capture and the launch sequence Gram -> iteration -> W = H X
+// -> finalise for every K class of a (possibly ragged) batch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <array>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "../../include/jacpcg.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace jacpcg;
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+inline size_t align_up(size_t x, size_t a = ALIGN) { return (x + a - 1) / a * a; }
+
+int k_class(int K) {
+    int c = 8;
+    while (c < K) c <<= 1;
+    return c;
+}
+
+// ---------------------------------------------------------------------------
+// First-fit allocator over one device buffer, with stream-ordered release:
+// a block freed while kernels may still read it is parked with an event and
+// returned once the event has completed.
+struct Arena {
+    char *base = nullptr;
+    size_t size = 0;
+    std::map<size_t, size_t> free_;   // offset -> bytes
+    struct Pending {
+        size_t off, bytes;
+        cudaEvent_t ev;
+    };
+    std::vector<Pending> pending;
+
+    size_t free_bytes() const {
+        size_t s = 0;
+        for (auto &kv : free_) s += kv.second;
+        return s;
+    }
+    void insert_free(size_t off, size_t bytes) {
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    void reap(bool wait_one) {
+        for (size_t i = 0; i < pending.size();) {
+            cudaError_t q = wait_one && i == 0 ? cudaEventSynchronize(pending[i].ev)
+                                               : cudaEventQuery(pending[i].ev);
+            if (q == cudaSuccess) {
+                insert_free(pending[i].off, pending[i].bytes);
+                cudaEventDestroy(pending[i].ev);
+                pending.erase(pending.begin() + i);
+                wait_one = false;
+            } else {
+                if (q != cudaErrorNotReady) (void)cudaGetLastError();
+                ++i;
+            }
+        }
+    }
+    bool try_alloc(size_t bytes, size_t *off) {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes;
+                const size_t o = it->first;
+                free_.erase(it);
+                if (rest) free_.emplace(o + bytes, rest);
+                return true;
+            }
+        }
+        return false;
+    }
+    bool alloc(size_t bytes, size_t *off) {
+        bytes = align_up(bytes);
+        reap(false);
+        if (try_alloc(bytes, off)) return true;
+        while (!pending.empty()) {
+            reap(true);
+            if (try_alloc(bytes, off)) return true;
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes, cudaEvent_t ev) {
+        bytes = align_up(bytes);
+        if (ev) pending.push_back({off, bytes, ev});
+        else insert_free(off, bytes);
+    }
+};
+
+// What one kernel launch of a plan covers.
+struct Launch {
+    enum Kind { GRAM, PCG, HX } kind;
+    int param;        // TB (Gram), KC (iteration), TN (W = H X)
+    size_t list_off;  // byte offset of its work list inside the plan block
+    int count;        // CTAs
+};
+
+}  // namespace
+
+struct jacpcg_ctx {
+    jacpcg_config cfg{};
+    Arena arena;
+    bool broken = false;
+    int64_t launches = 0;
+    // pinned staging for asynchronous table uploads of jacpcg_precode
+    char *staging = nullptr;
+    size_t staging_bytes = 0;
+    cudaEvent_t staging_ev = nullptr;
+    bool staging_pending = false;
+    // per-phase events of the profiled executes since the last read
+    std::vector<std::array<cudaEvent_t, 5>> prof_pool;
+    size_t prof_used = 0;
+    int last_launches = 0;
+    std::vector<jacpcg_plan *> plans;
+};
+
+struct jacpcg_plan {
+    jacpcg_ctx *ctx = nullptr;
+    size_t off = 0, bytes = 0;
+    char *dev = nullptr;
+    int n_inst = 0;
+    DevInst *d_insts = nullptr;
+    DevAccum acc{};
+    DevOut out{};
+    std::vector<Launch> launches;
+    int use_graph = 0;
+    cudaGraphExec_t gexec = nullptr;
+    int graph_launches = 0;
+    cudaEvent_t done = nullptr;
+    bool executed = false;
+};
+
+namespace {
+
+jacpcg_status cuda_fail(jacpcg_ctx *ctx) {
+    if (ctx) ctx->broken = true;
+    return JACPCG_ECUDA;
+}
+#define CK(call)                                   \
+    do {                                           \
+        if ((call) != cudaSuccess) return cuda_fail(ctx); \
+    } while (0)
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+jacpcg_status validate(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n) {
+    if (!ctx || !inst || n < 1 || n > ctx->cfg.max_instances) return JACPCG_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        const jacpcg_instance &q = inst[i];
+        if (q.K < 1 || q.K > ctx->cfg.max_K || q.M < 1 || q.M > ctx->cfg.max_M) return JACPCG_EINVAL;
+        if (q.ldh < q.M || q.ldw < q.M || (q.ldh & 1) || (q.ldw & 1)) return JACPCG_EINVAL;
+        if (!q.H || !q.W || !aligned16(q.H) || !aligned16(q.W)) return JACPCG_EINVAL;
+        if ((q.X && !aligned16(q.X)) || (q.A && !aligned16(q.A))) return JACPCG_EINVAL;
+        if (!std::isfinite(q.xi) || q.xi < 0.0 || (q.K > q.M && !(q.xi > 0.0))) return JACPCG_EINVAL;
+        if (!std::isfinite(q.power) || !std::isfinite(q.tol)) return JACPCG_EINVAL;
+        if (q.max_iter < 0 || q.max_iter > 4096) return JACPCG_EINVAL;
+    }
+    return JACPCG_OK;
+}
+
+// Byte layout of one plan block.
+struct Layout {
+    size_t insts, gram, pcg, hx, accum, ws, total;
+    int n_gram, n_pcg, n_hx;
+    std::vector<size_t> ws_off;   // per instance
+};
+
+int n_wtiles(const jacpcg_instance &q) {
+    const int KC = k_class(q.K), TN = hx_tn(KC);
+    return ((q.M + HX_TM - 1) / HX_TM) * ((q.K + TN - 1) / TN);
+}
+int n_gtiles(const jacpcg_instance &q) {
+    const int KC = k_class(q.K), TB = gram_tb(KC);
+    const int nb = std::max(1, KC / TB);   // cover the zero padding up to KC as well
+    return nb * (nb + 1) / 2;
+}
+int n_pblocks(const jacpcg_instance &q) {
+    const PcgShape s = pcg_shape(k_class(q.K));
+    const int per = s.CW * s.NW;
+    return (q.K + per - 1) / per;
+}
+size_t inst_ws_bytes(const jacpcg_instance &q) {
+    const size_t KC = k_class(q.K);
+    return align_up(KC * KC * sizeof(float2)) * 2 + align_up(KC * sizeof(float)) +
+           align_up(n_wtiles(q) * sizeof(float));
+}
+
+Layout make_layout(const jacpcg_instance *inst, int n) {
+    Layout L{};
+    L.n_gram = L.n_pcg = L.n_hx = 0;
+    for (int i = 0; i < n; ++i) {
+        L.n_gram += n_gtiles(inst[i]);
+        L.n_pcg += n_pblocks(inst[i]);
+        L.n_hx += n_wtiles(inst[i]);
+    }
+    size_t o = 0;
+    L.insts = o;  o += align_up(sizeof(DevInst) * n);
+    L.gram = o;   o += align_up(sizeof(int4) * L.n_gram);
+    L.pcg = o;    o += align_up(sizeof(int2) * L.n_pcg);
+    L.hx = o;     o += align_up(sizeof(int4) * L.n_hx);
+    L.accum = o;  o += align_up(sizeof(int32_t) * n) * 3;
+    L.ws = o;
+    L.ws_off.resize(n);
+    for (int i = 0; i < n; ++i) {
+        L.ws_off[i] = o;
+        o += inst_ws_bytes(inst[i]);
+    }
+    L.total = o;
+    return L;
+}
+
+// Fill the host image of the table part ([0, L.accum)) for a block at `dev`
+// and the launch list of the plan.
+void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, const Layout &L,
+                  char *dev, char *host, std::vector<Launch> &launches) {
+    DevInst *hi = reinterpret_cast<DevInst *>(host + L.insts);
+    for (int i = 0; i < n; ++i) {
+        const jacpcg_instance &q = inst[i];
+        const int KC = k_class(q.K);
+        char *w = dev + L.ws_off[i];
+        DevInst d{};
+        d.H = static_cast<const float2 *>(q.H);
+        d.W = static_cast<float2 *>(q.W);
+        d.Xout = static_cast<float2 *>(q.X);
+        d.Aout = static_cast<float2 *>(q.A);
+        d.A = reinterpret_cast<float2 *>(w);
+        d.X = reinterpret_cast<float2 *>(w + align_up((size_t)KC * KC * sizeof(float2)));
+        d.dinv = reinterpret_cast<float *>(w + 2 * align_up((size_t)KC * KC * sizeof(float2)));
+        d.wpart = reinterpret_cast<float *>(w + 2 * align_up((size_t)KC * KC * sizeof(float2)) +
+                                            align_up(KC * sizeof(float)));
+        d.M = q.M; d.K = q.K; d.ldh = q.ldh; d.ldw = q.ldw; d.KC = KC;
+        d.max_iter = q.max_iter;
+        d.n_wpart = n_wtiles(q);
+        d.variant = ctx->cfg.variant;
+        d.xi = (float)q.xi;
+        d.power = q.power > 0.0 ? (float)q.power : 1.0f;
+        d.tol = q.tol;
+        hi[i] = d;
+    }
+    launches.clear();
+    // Gram tiles grouped by tile edge
+    int4 *gt = reinterpret_cast<int4 *>(host + L.gram);
+    int g = 0;
+    for (int TB : {16, 32, 64}) {
+        const int start = g;
+        for (int i = 0; i < n; ++i) {
+            const int KC = k_class(inst[i].K);
+            if (gram_tb(KC) != TB) continue;
+            const int nb = std::max(1, KC / TB);
+            for (int bi = 0; bi < nb; ++bi)
+                for (int bj = 0; bj <= bi; ++bj) gt[g++] = make_int4(i, bi, bj, 0);
+        }
+        if (g > start) launches.push_back({Launch::GRAM, TB, L.gram + start * sizeof(int4), g - start});
+    }
+    // iteration blocks grouped by K class
+    int2 *pb = reinterpret_cast<int2 *>(host + L.pcg);
+    int p = 0;
+    for (int KC : {8, 16, 32, 64, 128, 256}) {
+        const int start = p;
+        const PcgShape s = pcg_shape(KC);
+        for (int i = 0; i < n; ++i) {
+            if (k_class(inst[i].K) != KC) continue;
+            for (int c0 = 0; c0 < inst[i].K; c0 += s.CW * s.NW) pb[p++] = make_int2(i, c0);
+        }
+        if (p > start) launches.push_back({Launch::PCG, KC, L.pcg + start * sizeof(int2), p - start});
+    }
+    // W = H X tiles grouped by tile width; slot = index of the tile in its instance
+    int4 *ht = reinterpret_cast<int4 *>(host + L.hx);
+    int h = 0;
+    for (int TN : {16, 32, 64}) {
+        const int start = h;
+        for (int i = 0; i < n; ++i) {
+            const int KC = k_class(inst[i].K);
+            if (hx_tn(KC) != TN) continue;
+            const int nm = (inst[i].M + HX_TM - 1) / HX_TM, nn = (inst[i].K + TN - 1) / TN;
+            int slot = 0;
+            for (int nt = 0; nt < nn; ++nt)
+                for (int mt = 0; mt < nm; ++mt) ht[h++] = make_int4(i, mt, nt, slot++);
+        }
+        if (h > start) launches.push_back({Launch::HX, TN, L.hx + start * sizeof(int4), h - start});
+    }
+}
+
+constexpr size_t MAX_PROFILED = 4096;
+
+jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_launched) {
+    jacpcg_ctx *ctx = pl->ctx;
+    int nl = 0;
+    cudaEvent_t *ev = nullptr;
+    if (profile && ctx->prof_used < MAX_PROFILED) {
+        if (ctx->prof_used == ctx->prof_pool.size()) {
+            std::array<cudaEvent_t, 5> set{};
+            for (auto &e : set) CK(cudaEventCreate(&e));
+            ctx->prof_pool.push_back(set);
+        }
+        ev = ctx->prof_pool[ctx->prof_used++].data();
+    }
+    if (ev) CK(cudaEventRecord(ev[0], s));
+    for (int phase = 0; phase < 3; ++phase) {
+        for (const Launch &l : pl->launches) {
+            if ((int)l.kind != phase) continue;
+            cudaError_t e = cudaSuccess;
+            const void *list = pl->dev + l.list_off;
+            switch (l.kind) {
+                case Launch::GRAM:
+                    e = launch_gram_simt(l.param, pl->d_insts, static_cast<const int4 *>(list), l.count,
+                                         pl->acc, s);
+                    break;
+                case Launch::PCG:
+                    e = launch_pcg(l.param, ctx->cfg.variant, pl->d_insts,
+                                   static_cast<const int2 *>(list), l.count, pl->acc, s);
+                    break;
+                case Launch::HX:
+                    e = launch_hx_simt(l.param, pl->d_insts, static_cast<const int4 *>(list), l.count,
+                                       s);
+                    break;
+            }
+            if (e != cudaSuccess) return cuda_fail(ctx);
+            ++nl;
+        }
+        if (ev) CK(cudaEventRecord(ev[phase + 1], s));
+    }
+    if (launch_finalize(pl->d_insts, pl->n_inst, pl->acc, pl->out, s) != cudaSuccess)
+        return cuda_fail(ctx);
+    ++nl;
+    if (ev) CK(cudaEventRecord(ev[4], s));
+    *n_launched = nl;
+    return JACPCG_OK;
+}
+
+jacpcg_status make_plan(jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, int32_t *status_dev,
+                        int32_t *iters_dev, float *resid_dev, float *beta_dev, int use_graph,
+                        cudaStream_t async_stream, jacpcg_plan **out) {
+    if (!ctx || !out) return JACPCG_EINVAL;
+    if (ctx->broken) return JACPCG_ECUDA;
+    jacpcg_status st = validate(ctx, inst, n);
+    if (st != JACPCG_OK) return st;
+    Layout L = make_layout(inst, n);
+    size_t off;
+    if (!ctx->arena.alloc(L.total, &off)) return JACPCG_ENOMEM;
+    jacpcg_plan *pl = new (std::nothrow) jacpcg_plan();
+    if (!pl) {
+        ctx->arena.release(off, L.total, nullptr);
+        return JACPCG_ENOMEM;
+    }
+    pl->ctx = ctx;
+    pl->off = off;
+    pl->bytes = L.total;
+    pl->dev = ctx->arena.base + off;
+    pl->n_inst = n;
+    pl->d_insts = reinterpret_cast<DevInst *>(pl->dev + L.insts);
+    pl->acc.flags = reinterpret_cast<int32_t *>(pl->dev + L.accum);
+    pl->acc.iters = reinterpret_cast<int32_t *>(pl->dev + L.accum + align_up(sizeof(int32_t) * n));
+    pl->acc.resid_bits =
+        reinterpret_cast<uint32_t *>(pl->dev + L.accum + 2 * align_up(sizeof(int32_t) * n));
+    pl->out = DevOut{status_dev, iters_dev, resid_dev, beta_dev};
+    pl->use_graph = use_graph;
+    const size_t tbytes = L.accum;   // tables occupy [0, accum)
+    auto fail = [&](jacpcg_status s) {
+        ctx->arena.release(pl->off, pl->bytes, nullptr);
+        delete pl;
+        return s;
+    };
+    // host image in pinned staging, uploaded on the stream (or synchronously)
+    if (ctx->staging_pending) {
+        if (cudaEventSynchronize(ctx->staging_ev) != cudaSuccess) return fail(cuda_fail(ctx));
+        ctx->staging_pending = false;
+    }
+    if (ctx->staging_bytes < tbytes) {
+        if (ctx->staging) cudaFreeHost(ctx->staging);
+        ctx->staging = nullptr;
+        ctx->staging_bytes = 0;
+        if (cudaHostAlloc(reinterpret_cast<void **>(&ctx->staging), tbytes, cudaHostAllocDefault) !=
+            cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(JACPCG_ENOMEM);
+        }
+        ctx->staging_bytes = tbytes;
+    }
+    std::memset(ctx->staging, 0, tbytes);
+    build_tables(ctx, inst, n, L, pl->dev, ctx->staging, pl->launches);
+    if (async_stream) {
+        if (cudaMemcpyAsync(pl->dev, ctx->staging, tbytes, cudaMemcpyHostToDevice, async_stream) !=
+                cudaSuccess ||
+            cudaEventRecord(ctx->staging_ev, async_stream) != cudaSuccess)
+            return fail(cuda_fail(ctx));
+        ctx->staging_pending = true;
+    } else {
+        if (cudaMemcpy(pl->dev, ctx->staging, tbytes, cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(cuda_fail(ctx));
+    }
+    if (cudaEventCreateWithFlags(&pl->done, cudaEventDisableTiming) != cudaSuccess)
+        return fail(cuda_fail(ctx));
+    ctx->plans.push_back(pl);
+    *out = pl;
+    return JACPCG_OK;
+}
+
+void drop_plan(jacpcg_plan *pl) {
+    jacpcg_ctx *ctx = pl->ctx;
+    if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
+    // the block is reused only after the plan's last execute has finished
+    ctx->arena.release(pl->off, pl->bytes, pl->executed ? pl->done : nullptr);
+    if (!pl->executed && pl->done) cudaEventDestroy(pl->done);
+    ctx->plans.erase(std::remove(ctx->plans.begin(), ctx->plans.end(), pl), ctx->plans.end());
+    delete pl;
+}
+
+jacpcg_status execute(jacpcg_plan *pl, cudaStream_t s) {
+    jacpcg_ctx *ctx = pl->ctx;
+    if (ctx->broken) return JACPCG_ECUDA;
+    const bool profile = (ctx->cfg.flags & JACPCG_FLAG_PROFILE) && !pl->use_graph;
+    int nl = 0;
+    if (pl->use_graph) {
+        if (!pl->gexec) {
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            jacpcg_status st = enqueue(pl, s, false, &pl->graph_launches);
+            cudaError_t e = cudaStreamEndCapture(s, &g);
+            if (st != JACPCG_OK) return st;
+            if (e != cudaSuccess) return cuda_fail(ctx);
+            e = cudaGraphInstantiate(&pl->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(ctx);
+        }
+        CK(cudaGraphLaunch(pl->gexec, s));
+        nl = pl->graph_launches;
+    } else {
+        jacpcg_status st = enqueue(pl, s, profile, &nl);
+        if (st != JACPCG_OK) return st;
+    }
+    ctx->last_launches = nl;
+    ctx->launches += nl;
+    CK(cudaEventRecord(pl->done, s));
+    pl->executed = true;
+    return JACPCG_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *jacpcg_version(void) { return "0.1.0"; }
+
+const char *jacpcg_strerror(jacpcg_status s) {
+    switch (s) {
+        case JACPCG_OK: return "ok";
+        case JACPCG_EINVAL: return "invalid argument";
+        case JACPCG_ENOMEM: return "out of memory (device, pinned host or arena budget)";
+        case JACPCG_ECUDA: return "CUDA runtime error; context unusable";
+        case JACPCG_ENOTCONV: return "tolerance not met within max_iter";
+        case JACPCG_ENOTHPD: return "matrix not Hermitian positive definite";
+        case JACPCG_ENONFINITE: return "non-finite value in the precoder";
+        case JACPCG_ETIMEOUT: return "bounded wait ran out";
+        case JACPCG_EBUSY: return "busy";
+    }
+    return "unknown status";
+}
+
+jacpcg_status jacpcg_create(const jacpcg_config *cfg, jacpcg_ctx **out) {
+    if (!cfg || !out) return JACPCG_EINVAL;
+    if (cfg->max_K < 1 || cfg->max_K > 256 || cfg->max_M < 1 || cfg->max_instances < 1)
+        return JACPCG_EINVAL;
+    if (cfg->precision != JACPCG_FP32) return JACPCG_EINVAL;
+    if (cfg->variant < JACPCG_STANDARD || cfg->variant > JACPCG_CG) return JACPCG_EINVAL;
+    jacpcg_ctx *ctx = new (std::nothrow) jacpcg_ctx();
+    if (!ctx) return JACPCG_ENOMEM;
+    ctx->cfg = *cfg;
+    if (cudaSetDevice(cfg->device) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete ctx;
+        return JACPCG_EINVAL;
+    }
+    size_t bytes = cfg->arena_bytes;
+    if (bytes == 0) {
+        jacpcg_instance q{};
+        q.M = cfg->max_M;
+        q.K = cfg->max_K;
+        std::vector<jacpcg_instance> v(cfg->max_instances, q);
+        bytes = 2 * make_layout(v.data(), cfg->max_instances).total;
+    }
+    bytes = align_up(bytes);
+    if (cudaMalloc(reinterpret_cast<void **>(&ctx->arena.base), bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete ctx;
+        return JACPCG_ENOMEM;
+    }
+    ctx->arena.size = bytes;
+    ctx->arena.free_.emplace(0, bytes);
+    bool ok = cudaEventCreateWithFlags(&ctx->staging_ev, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        (void)cudaGetLastError();
+        jacpcg_destroy(ctx);
+        return JACPCG_ECUDA;
+    }
+    *out = ctx;
+    return JACPCG_OK;
+}
+
+jacpcg_status jacpcg_destroy(jacpcg_ctx *ctx) {
+    if (!ctx) return JACPCG_EINVAL;
+    cudaSetDevice(ctx->cfg.device);
+    cudaDeviceSynchronize();
+    while (!ctx->plans.empty()) drop_plan(ctx->plans.back());
+    ctx->arena.reap(false);
+    for (auto &p : ctx->arena.pending) cudaEventDestroy(p.ev);
+    if (ctx->arena.base) cudaFree(ctx->arena.base);
+    if (ctx->staging) cudaFreeHost(ctx->staging);
+    if (ctx->staging_ev) cudaEventDestroy(ctx->staging_ev);
+    for (auto &set : ctx->prof_pool)
+        for (auto &e : set) cudaEventDestroy(e);
+    (void)cudaGetLastError();
+    delete ctx;
+    return JACPCG_OK;
+}
+
+jacpcg_status jacpcg_plan_create(jacpcg_ctx *ctx, const jacpcg_instance *inst, int n_inst,
+                                 int32_t *status_dev, int32_t *iters_dev, float *resid_dev,
+                                 float *beta_dev, int use_graph, jacpcg_plan **out) {
+    return make_plan(ctx, inst, n_inst, status_dev, iters_dev, resid_dev, beta_dev, use_graph,
+                     nullptr, out);
+}
+
+jacpcg_status jacpcg_plan_execute(jacpcg_plan *plan, void *stream) {
+    if (!plan) return JACPCG_EINVAL;
+    return execute(plan, static_cast<cudaStream_t>(stream));
+}
+
+jacpcg_status jacpcg_plan_destroy(jacpcg_plan *plan) {
+    if (!plan) return JACPCG_EINVAL;
+    drop_plan(plan);
+    return JACPCG_OK;
+}
+
+jacpcg_status jacpcg_precode(jacpcg_ctx *ctx, const jacpcg_instance *inst, int n_inst,
+                             int32_t *status_dev, int32_t *iters_dev, float *resid_dev,
+                             float *beta_dev, void *stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    jacpcg_plan *pl = nullptr;
+    jacpcg_status st =
+        make_plan(ctx, inst, n_inst, status_dev, iters_dev, resid_dev, beta_dev, 0, s, &pl);
+    if (st != JACPCG_OK) return st;
+    st = execute(pl, s);
+    drop_plan(pl);
+    return st;
+}
+
+jacpcg_status jacpcg_plan_bytes(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n_inst,
+                                size_t *bytes) {
+    if (!bytes) return JACPCG_EINVAL;
+    jacpcg_status st = validate(ctx, inst, n_inst);
+    if (st != JACPCG_OK) return st;
+    *bytes = align_up(make_layout(inst, n_inst).total);
+    return JACPCG_OK;
+}
+
+jacpcg_status jacpcg_arena_free_bytes(const jacpcg_ctx *ctx, size_t *bytes) {
+    if (!ctx || !bytes) return JACPCG_EINVAL;
+    size_t s = ctx->arena.free_bytes();
+    for (auto &p : ctx->arena.pending) s += p.bytes;
+    *bytes = s;
+    return JACPCG_OK;
+}
+
+jacpcg_status jacpcg_profile_read(jacpcg_ctx *ctx, float ms[4], int *n_executes,
+                                  int *launches_per_execute) {
+    if (!ctx || !ms) return JACPCG_EINVAL;
+    for (int i = 0; i < 4; ++i) ms[i] = 0.f;
+    for (size_t k = 0; k < ctx->prof_used; ++k) {
+        auto &ev = ctx->prof_pool[k];
+        if (cudaEventSynchronize(ev[4]) != cudaSuccess) return cuda_fail(ctx);
+        for (int i = 0; i < 4; ++i) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, ev[i], ev[i + 1]) != cudaSuccess) return cuda_fail(ctx);
+            ms[i] += t;
+        }
+    }
+    if (n_executes) *n_executes = (int)ctx->prof_used;
+    if (launches_per_execute) *launches_per_execute = ctx->last_launches;
+    ctx->prof_used = 0;
+    return JACPCG_OK;
+}
+
+int64_t jacpcg_launch_count(const jacpcg_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,121 @@
+// common.cuh -- device-side data structures and helpers shared by the kernels
+// of the Jac-PCG RZF precoder (arXiv 2305.13925).  Host code in api.cu builds
+// the tables declared here; every kernel reads them.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace jacpcg {
+
+// Per-instance flags accumulated by the kernels, turned into a status by the
+// finalise kernel.
+enum : int32_t { FLAG_NOTHPD = 1, FLAG_NOTCONV = 2 };
+
+// One precoder instance as the kernels see it.  Workspace matrices (A, X)
+// are KC x KC with leading dimension KC, where KC is the instance's K class
+// (the next of 8, 16, 32, 64, 128, 256 at or above K); rows and columns
+// from K to KC are zero.
+struct DevInst {
+    const float2 *H;      // M x K, leading dimension ldh (caller)
+    float2 *W;            // M x K, leading dimension ldw (caller)
+    float2 *Xout;         // optional K x K, ld K (caller)
+    float2 *Aout;         // optional K x K, ld K (caller)
+    float2 *A;            // workspace KC x KC: H^H H + xi I
+    float *dinv;          // workspace KC: 1 / A_kk (0 beyond K)
+    float2 *X;            // workspace KC x KC: the iterate
+    float *wpart;         // workspace: one partial ||W||_F^2 per W = H X tile
+    int M, K, ldh, ldw;
+    int KC;               // K class
+    int max_iter;
+    int n_wpart;          // number of W = H X tiles of this instance
+    int variant;          // JACPCG_STANDARD / ALG1 / CG
+    float xi, power, tol;
+    int pad0;
+};
+
+// Per-instance results written by the kernels before finalisation.
+struct DevAccum {
+    int32_t *flags;       // FLAG_* bits
+    int32_t *iters;       // largest per-column iteration count
+    uint32_t *resid_bits; // largest per-column relative residual, float bits (>= 0)
+};
+
+// Caller-visible per-instance outputs (any may be null).
+struct DevOut {
+    int32_t *status;
+    int32_t *iters;
+    float *resid;
+    float *beta;
+};
+
+// ---------------------------------------------------------------------------
+// complex helpers (float2 = re, im)
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// acc += a * b
+__device__ __forceinline__ void cfma(float2 &acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+__device__ __forceinline__ void cfma_conj(float2 &acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(-a.y, b.x, acc.y);
+}
+
+// ---------------------------------------------------------------------------
+// Compensated summation (error-free transformations; Ogita, Rump and Oishi,
+// "Accurate sum and dot product", SIAM J. Sci. Comput. 26(6), 2005).
+// A value is carried as (s, c): the rounded sum and its accumulated error.
+struct Comp {
+    float s, c;
+};
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    float z = s - a;
+    e = (a - (s - z)) + (b - z);
+}
+// (s, c) += a * b exactly up to the final rounding of c (Dot2 step)
+__device__ __forceinline__ void comp_fma(Comp &v, float a, float b) {
+    float p = a * b;
+    float pe = fmaf(a, b, -p);
+    float s, e;
+    two_sum(v.s, p, s, e);
+    v.s = s;
+    v.c += pe + e;
+}
+__device__ __forceinline__ void comp_add(Comp &v, Comp w) {
+    float s, e;
+    two_sum(v.s, w.s, s, e);
+    v.s = s;
+    v.c += w.c + e;
+}
+// warp-wide all-reduce of a compensated value (fixed xor butterfly order)
+__device__ __forceinline__ Comp comp_warp_allreduce(Comp v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Comp w;
+        w.s = __shfl_xor_sync(0xffffffffu, v.s, o);
+        w.c = __shfl_xor_sync(0xffffffffu, v.c, o);
+        comp_add(v, w);
+    }
+    return v;
+}
+__device__ __forceinline__ float warp_allreduce_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ int warp_allreduce_max_i(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+}  // namespace jacpcg

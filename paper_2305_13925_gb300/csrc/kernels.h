@@ -1,0 +1,35 @@
+// kernels.h -- host-side launch wrappers for the device kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace jacpcg {
+
+// Launch shape of the iteration kernel for one K class.
+struct PcgShape {
+    int KC;   // K class
+    int CW;   // columns per warp
+    int NW;   // warps per CTA
+};
+PcgShape pcg_shape(int KC);
+
+// Gram tile edge and W = H X tile width for a K class (SIMT kernels).
+inline int gram_tb(int KC) { return KC <= 16 ? 16 : (KC >= 64 ? 64 : KC); }
+inline int hx_tn(int KC) { return KC <= 16 ? 16 : (KC >= 64 ? 64 : KC); }
+constexpr int HX_TM = 64;
+
+// tiles: (instance, bi, bj, 0) with bi >= bj
+cudaError_t launch_gram_simt(int TB, const DevInst *insts, const int4 *tiles, int n_tiles,
+                             DevAccum acc, cudaStream_t s);
+// blocks: (instance, first column)
+cudaError_t launch_pcg(int KC, int variant, const DevInst *insts, const int2 *blocks,
+                       int n_blocks, DevAccum acc, cudaStream_t s);
+// tiles: (instance, m tile, n tile, partial slot)
+cudaError_t launch_hx_simt(int TN, const DevInst *insts, const int4 *tiles, int n_tiles,
+                           cudaStream_t s);
+cudaError_t launch_finalize(const DevInst *insts, int n_inst, DevAccum acc, DevOut out,
+                            cudaStream_t s);
+
+}  // namespace jacpcg

@@ -1,0 +1,202 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs, element by element.  Bar: relative Frobenius error
+of W at most 1e-5 per instance (FP32 arithmetic); A, X and beta are checked
+alongside.  Marked gpu."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2305_13925_gb300 import channels as C
+
+from gpu_util import rel_fro, run
+
+pytestmark = pytest.mark.gpu
+
+TOL_W = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_13925_gb300 import build
+    build.build()
+
+
+def check_batch(Hs, xis, variant="standard", T=6, tol_w=TOL_W, **kw):
+    Hs = [C.round_complex64(h) for h in Hs]      # the oracle sees exactly what the GPU reads
+    out = run(Hs, xis, variant=variant, T=T, want_X=True, want_A=True, **kw)
+    errs = []
+    for i, (H, xi) in enumerate(zip(Hs, xis)):
+        ref = O.precode(H, xi, variant, max_iter=T)
+        e = rel_fro(out["W"][i], ref["W"])
+        errs.append(e)
+        assert e <= tol_w, (i, H.shape, e)
+        assert rel_fro(out["A"][i], ref["A"]) <= 1e-6
+        assert rel_fro(out["X"][i], ref["X"]) <= tol_w
+        assert abs(out["beta"][i] - ref["beta"]) <= 1e-5 * ref["beta"]
+        assert out["iters"][i] == ref["iters"]
+        assert out["status"][i] == 0
+    return out, errs
+
+
+def test_single_256x16_T8():
+    """Single instance: M = 256 (4 subarrays of 64), K = 16, r = 0.5, 2 of 4
+    subarrays visible, SNR 10 dB, xi = K / SNR, 8 iterations."""
+    inst = C.generate_instance(C.PRESETS["single_256x16"], 0, 0)
+    out, errs = check_batch([inst.H], [inst.xi], T=8)
+    # and close to the direct RZF
+    Wd, _, _ = O.rzf_direct(inst.H, inst.xi)
+    assert rel_fro(out["W"][0], Wd) < 1e-3
+
+
+@pytest.mark.parametrize("variant", ["standard", "cg"])
+def test_batched_1024x64_T6_subset(variant):
+    """Uniform batch shape M = 1024 (8 subarrays of 128), K = 64, T = 6, on 24 instances."""
+    H, xi = C.generate_batch("batched_1024x64", 24, 1)
+    check_batch(list(H), list(xi), variant=variant, T=6)
+
+
+def test_alg1_variant_parity():
+    """Algorithm 1 as printed, on channels with a mild diagonal spread
+    (equal column norms make D = cI, where it is well behaved)."""
+    H, xi = C.generate_batch("single_256x16", 6, 5)
+    Hn = [h / np.maximum(np.linalg.norm(h, axis=0), 1e-30)[None, :] for h in H]
+    check_batch(Hn, list(xi), variant="alg1", T=8)
+
+
+@pytest.mark.parametrize("K,M", [(1, 64), (2, 9), (3, 130), (8, 256), (17, 1000), (33, 96),
+                                 (64, 257), (100, 512), (128, 640), (200, 700), (256, 1024)])
+def test_ragged_shapes_and_tails(K, M):
+    """K classes 8..256 with K not a power of two, M not a multiple of the
+    64-row tile, and tiny K; standard variant, T = 5."""
+    spec = C.ChannelSpec(M=M, S=1, K=K, r=(0.5, 0.5), n_vis=(1, 1), snr_db=(10.0,))
+    inst = C.generate_instance(spec, 7, K + M)
+    check_batch([inst.H], [inst.xi], T=5)
+
+
+def test_ragged_batch_one_launch_sequence():
+    """A ragged batch (every K class, several M) in one call matches each
+    instance's oracle."""
+    insts = C.generate_ragged(12, 3, k_set=(8, 16, 32, 64, 128, 256), m_set=(256, 512, 1024))
+    check_batch([i.H for i in insts], [i.xi for i in insts], T=4)
+
+
+def test_more_users_than_antennas_with_regulariser():
+    """K > M is admissible when xi > 0 (A = H^H H + xi I stays HPD, Eq. 18)."""
+    rng = np.random.default_rng(3)
+    H = (rng.standard_normal((24, 40)) + 1j * rng.standard_normal((24, 40))) / math.sqrt(2)
+    H = C.round_complex64(H)
+    check_batch([H], [2.0], T=6)
+
+
+def test_diagonal_gram_exact_in_one_step():
+    """Orthogonal columns of unequal norm: A is diagonal and one Jac-PCG step
+    gives X = D^{-1} exactly (up to FP32 rounding)."""
+    M, K = 64, 8
+    m = np.arange(M)[:, None]
+    k = np.arange(K)[None, :]
+    H = np.exp(-2j * np.pi * m * k / M) / math.sqrt(M) * np.geomspace(0.5, 4.0, K)[None, :]
+    H = C.round_complex64(H)
+    out = run([H], [0.3], T=3, want_X=True)
+    ref = O.precode(H, 0.3, "standard", max_iter=1)
+    assert rel_fro(out["X"][0], ref["X"]) < 1e-6
+    assert out["iters"][0] == 3 and out["status"][0] == 0
+
+
+def test_tolerance_mode_reaches_direct_rzf():
+    """tol > 0: columns stop at ||r|| <= tol; the result is close to the
+    direct RZF, iteration counts are near the oracle's and status is OK."""
+    H, xi = C.generate_batch("batched_1024x64", 8, 11)
+    out = run(list(H), list(xi), T=200, tol=1e-6)
+    for i in range(8):
+        Wd, _, _ = O.rzf_direct(H[i], xi[i])
+        assert rel_fro(out["W"][i], Wd) < 2e-5
+        ref = O.precode(H[i], xi[i], "standard", max_iter=200, tol=1e-6)
+        assert abs(int(out["iters"][i]) - ref["iters"]) <= 2
+        assert out["status"][i] == 0 and out["resid"][i] <= 1e-6
+
+
+def test_not_converged_status():
+    """A tolerance that cannot be met in max_iter reports ENOTCONV, and the
+    result is still the max_iter iterate."""
+    H, xi = C.generate_batch("batched_1024x64", 2, 12)
+    out = run(list(H), list(xi), T=2, tol=1e-9)
+    assert list(out["status"]) == [4, 4]
+    for i in range(2):
+        ref = O.precode(H[i], xi[i], "standard", max_iter=2)
+        assert rel_fro(out["W"][i], ref["W"]) <= TOL_W
+
+
+def test_nonfinite_input_reported():
+    H, xi = C.generate_batch("single_256x16", 2, 13)
+    H = H.copy()
+    H[1][5, 3] = np.nan
+    out = run(list(H), list(xi), T=4)
+    assert out["status"][0] == 0 and out["status"][1] == 6
+
+
+def test_zero_user_channel():
+    """A user with no visible subarray (zero column): A_kk = xi, and that
+    user's column of X is e_k / xi."""
+    inst = C.generate_instance(C.PRESETS["single_256x16"], 0, 4)
+    H = inst.H.copy()
+    H[:, 5] = 0
+    out = run([H], [inst.xi], T=8, want_X=True)
+    ref = O.precode(H, inst.xi, "standard", max_iter=8)
+    assert rel_fro(out["W"][0], ref["W"]) <= TOL_W
+    assert abs(out["X"][0][5, 5] - 1.0 / inst.xi) < 1e-6 / inst.xi
+
+
+def test_plan_and_graph_replay_bitwise_equal():
+    """A plan executed directly, replayed from a CUDA graph, and a one-shot
+    precode call give bit-identical W."""
+    H, xi = C.generate_batch("batched_1024x64", 16, 21)
+    a = run(list(H), list(xi), T=6)
+    b = run(list(H), list(xi), T=6, plan=True, graph=False, repeats=2)
+    c = run(list(H), list(xi), T=6, plan=True, graph=True, repeats=3)
+    for i in range(16):
+        assert np.array_equal(a["W"][i], b["W"][i]) and np.array_equal(a["W"][i], c["W"][i])
+
+
+def test_result_alone_equals_result_in_mix():
+    """Batch composition does not change any instance's bits (fixed reduction
+    order per instance, no cross-instance arithmetic)."""
+    insts = C.generate_ragged(10, 31, k_set=(16, 64, 128), m_set=(256, 1024))
+    mix = run([i.H for i in insts], [i.xi for i in insts], T=5)
+    for j in (0, 3, 7):
+        alone = run([insts[j].H], [insts[j].xi], T=5)
+        assert np.array_equal(alone["W"][0], mix["W"][j])
+        assert alone["beta"][0] == mix["beta"][j]
+
+
+def test_invalid_arguments_rejected():
+    import torch
+    from paper_2305_13925_gb300 import binding
+    with pytest.raises(binding.JacpcgError):
+        binding.Precoder(max_instances=1, max_M=64, max_K=300)
+    prec = binding.Precoder(max_instances=2, max_M=128, max_K=16)
+    try:
+        H = torch.zeros((16, 128), dtype=torch.complex64, device="cuda")
+        W = torch.zeros_like(H)
+        good = binding.instance(H, W, 1.0, 4)
+        for field, val in (("K", 0), ("K", 17), ("M", 129), ("ldh", 64), ("xi", -1.0),
+                           ("max_iter", -1), ("ldw", 127)):
+            bad = binding.instance(H, W, 1.0, 4)
+            setattr(bad, field, val)
+            with pytest.raises(binding.JacpcgError) as e:
+                prec.precode([bad])
+            assert e.value.status == binding.JACPCG_EINVAL
+        bad = binding.instance(H, W, 1.0, 4)
+        bad.H = H.data_ptr() + 8
+        with pytest.raises(binding.JacpcgError):
+            prec.precode([bad])
+        with pytest.raises(binding.JacpcgError):
+            prec.precode([good, good, good])       # more than max_instances
+        prec.precode([good])                        # the context is still usable
+        torch.cuda.synchronize()
+    finally:
+        prec.close()
