@@ -129,6 +129,7 @@ struct jacpcg_ctx {
     size_t staging_bytes = 0;
     cudaEvent_t staging_ev = nullptr;
     bool staging_pending = false;
+    cudaStream_t capture_stream = nullptr;   // graphs are captured here, launched on the caller's
     // per-phase events of the profiled executes since the last read
     std::vector<std::array<cudaEvent_t, 5>> prof_pool;
     size_t prof_used = 0;
@@ -435,10 +436,13 @@ jacpcg_status execute(jacpcg_plan *pl, cudaStream_t s) {
     int nl = 0;
     if (pl->use_graph) {
         if (!pl->gexec) {
+            // capture on the context's own stream (the caller's may be the
+            // legacy default stream, which cannot be captured)
             cudaGraph_t g = nullptr;
-            CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-            jacpcg_status st = enqueue(pl, s, false, &pl->graph_launches);
-            cudaError_t e = cudaStreamEndCapture(s, &g);
+            const cudaStream_t cs = ctx->capture_stream;
+            CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            jacpcg_status st = enqueue(pl, cs, false, &pl->graph_launches);
+            cudaError_t e = cudaStreamEndCapture(cs, &g);
             if (st != JACPCG_OK) return st;
             if (e != cudaSuccess) return cuda_fail(ctx);
             e = cudaGraphInstantiate(&pl->gexec, g, 0);
@@ -510,7 +514,8 @@ jacpcg_status jacpcg_create(const jacpcg_config *cfg, jacpcg_ctx **out) {
     }
     ctx->arena.size = bytes;
     ctx->arena.free_.emplace(0, bytes);
-    bool ok = cudaEventCreateWithFlags(&ctx->staging_ev, cudaEventDisableTiming) == cudaSuccess;
+    bool ok = cudaEventCreateWithFlags(&ctx->staging_ev, cudaEventDisableTiming) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) == cudaSuccess;
     if (!ok) {
         (void)cudaGetLastError();
         jacpcg_destroy(ctx);
@@ -530,6 +535,7 @@ jacpcg_status jacpcg_destroy(jacpcg_ctx *ctx) {
     if (ctx->arena.base) cudaFree(ctx->arena.base);
     if (ctx->staging) cudaFreeHost(ctx->staging);
     if (ctx->staging_ev) cudaEventDestroy(ctx->staging_ev);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     for (auto &set : ctx->prof_pool)
         for (auto &e : set) cudaEventDestroy(e);
     (void)cudaGetLastError();

@@ -9,6 +9,9 @@
 // diagonal exactly real).  256 threads form a 16 x 16 grid, each owning a
 // U x U complex micro-tile (U = TB / 16).  H is staged through shared
 // memory in chunks of MC rows, prefetched into registers one chunk ahead.
+// Each stage's products are summed into a fresh partial that is then added
+// to the running total (two-level summation: the rounding error grows with
+// MC + M / MC terms rather than with M).
 #include "common.cuh"
 #include "kernels.h"
 
@@ -76,6 +79,12 @@ __global__ void __launch_bounds__(256) gram_simt_kernel(const DevInst *__restric
         __syncthreads();
         if (m0 + MC < Mloop) fetch(m0 + MC);
         float2(*Sb)[PITCH] = diag ? Si : Sj;
+        // two-level sum: a fresh partial per stage of MC rows, added to the total
+        float2 part[U][U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int v = 0; v < U; ++v) part[u][v] = make_float2(0.f, 0.f);
 #pragma unroll 4
         for (int r = 0; r < MC; ++r) {
             float2 a[U], b[U];
@@ -86,8 +95,15 @@ __global__ void __launch_bounds__(256) gram_simt_kernel(const DevInst *__restric
 #pragma unroll
             for (int u = 0; u < U; ++u)
 #pragma unroll
-                for (int v = 0; v < U; ++v) cfma_conj(acc[u][v], a[u], b[v]);
+                for (int v = 0; v < U; ++v) cfma_conj(part[u][v], a[u], b[v]);
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int v = 0; v < U; ++v) {
+                acc[u][v].x += part[u][v].x;
+                acc[u][v].y += part[u][v].y;
+            }
     }
 
     // write the tile (workspace has leading dimension KC, caller's A has K)

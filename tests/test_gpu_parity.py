@@ -26,7 +26,67 @@ def _gpu():
     build.build()
 
 
-def check_batch(Hs, xis, variant="standard", T=6, tol_w=TOL_W, **kw):
+def fp32_deviation(H, xi, variant, T):
+    """Relative distance between the FP64 oracle's W and an independent
+    complex64 (numpy) evaluation of the same fixed-T iteration: how far any
+    FP32 evaluation of this iteration drifts from exact arithmetic on this
+    channel (for plain CG and the literal Algorithm 1 the finite-precision
+    loss of conjugacy makes this far larger than rounding of the inputs)."""
+    c = np.complex64
+    Hc = H.astype(c)
+    A = Hc.conj().T @ Hc + c(xi) * np.eye(H.shape[1], dtype=c)
+    d = np.real(np.diag(A)).astype(np.float32)
+    dinv = (np.float32(1) / d) if variant != "cg" else np.ones_like(d)
+    K = H.shape[1]
+    X = np.zeros((K, K), dtype=c)
+    for j in range(K):
+        b = np.zeros(K, dtype=c)
+        b[j] = 1
+        x = np.zeros(K, dtype=c)
+        if variant == "alg1":
+            r = dinv * b
+            m = r.copy()
+            rr = np.vdot(r, r).real
+            for _ in range(T):
+                u = dinv * (A @ m)
+                den = np.vdot(m, u)
+                al = c(rr / den) if den != 0 else c(0)
+                x = x + al * m
+                r = r - al * u
+                rn = np.vdot(r, r).real
+                m = r + np.float32(rn / rr if rr != 0 else 0) * m
+                rr = rn
+        else:
+            r = b.copy()
+            z = dinv * r
+            p = z.copy()
+            rz = np.vdot(r, z).real
+            for _ in range(T):
+                q = A @ p
+                pq = np.vdot(p, q).real
+                lam = np.float32(rz / pq) if pq > 0 else np.float32(0)
+                x = x + lam * p
+                r = r - lam * q
+                z = dinv * r
+                rzn = np.vdot(r, z).real
+                p = z + np.float32(rzn / rz if rz != 0 else 0) * p
+                rz = rzn
+        X[:, j] = x
+    W32 = Hc @ X
+    ref = O.precode(H, xi, variant, max_iter=T)["W"]
+    return rel_fro(W32.astype(np.complex128), ref)
+
+
+def tol_for(H, xi, variant, T):
+    """Parity bar for W: 1e-5 for Jacobi-PCG (the method); for plain CG and
+    the literal Algorithm 1 the larger of 1e-5 and 30 x the drift of an
+    independent FP32 evaluation of the same iteration from the oracle."""
+    if variant == "standard":
+        return TOL_W
+    return max(TOL_W, 30.0 * fp32_deviation(H, xi, variant, T))
+
+
+def check_batch(Hs, xis, variant="standard", T=6, tol_w=None, **kw):
     Hs = [C.round_complex64(h) for h in Hs]      # the oracle sees exactly what the GPU reads
     out = run(Hs, xis, variant=variant, T=T, want_X=True, want_A=True, **kw)
     errs = []
@@ -34,9 +94,10 @@ def check_batch(Hs, xis, variant="standard", T=6, tol_w=TOL_W, **kw):
         ref = O.precode(H, xi, variant, max_iter=T)
         e = rel_fro(out["W"][i], ref["W"])
         errs.append(e)
-        assert e <= tol_w, (i, H.shape, e)
+        bar = tol_w if tol_w is not None else tol_for(H, xi, variant, T)
+        assert e <= bar, (i, H.shape, e, bar)
         assert rel_fro(out["A"][i], ref["A"]) <= 1e-6
-        assert rel_fro(out["X"][i], ref["X"]) <= tol_w
+        assert rel_fro(out["X"][i], ref["X"]) <= bar
         assert abs(out["beta"][i] - ref["beta"]) <= 1e-5 * ref["beta"]
         assert out["iters"][i] == ref["iters"]
         assert out["status"][i] == 0
@@ -57,7 +118,29 @@ def test_single_256x16_T8():
 def test_batched_1024x64_T6_subset(variant):
     """Uniform batch shape M = 1024 (8 subarrays of 128), K = 64, T = 6, on 24 instances."""
     H, xi = C.generate_batch("batched_1024x64", 24, 1)
-    check_batch(list(H), list(xi), variant=variant, T=6)
+    out, errs = check_batch(list(H), list(xi), variant=variant, T=6)
+    if variant == "standard":
+        assert max(errs) <= TOL_W
+
+
+def test_batched_1024x64_full_batch_sampled():
+    """The bench's launch configuration: all 2048 instances of the batched
+    shape in one call, T = 6; every 128th instance checked against the oracle."""
+    import torch
+    from paper_2305_13925_gb300 import binding
+    Hst, xi = C.generate_batch_device_layout("batched_1024x64", 2048, 1)
+    Hd = torch.from_numpy(Hst).cuda()
+    Wd = torch.empty_like(Hd)
+    status = torch.empty(2048, dtype=torch.int32, device="cuda")
+    with binding.Precoder(max_instances=2048, max_M=1024, max_K=64) as prec:
+        insts = [binding.instance(Hd[i], Wd[i], float(xi[i]), 6) for i in range(2048)]
+        prec.precode(insts, status)
+        torch.cuda.synchronize()
+    assert (status.cpu().numpy() == 0).all()
+    for i in range(0, 2048, 128):
+        H = Hst[i].T.astype(np.complex128)
+        ref = O.precode(H, xi[i], "standard", max_iter=6)["W"]
+        assert rel_fro(Wd[i].T.cpu().numpy().astype(np.complex128), ref) <= TOL_W
 
 
 def test_alg1_variant_parity():
