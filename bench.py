@@ -75,6 +75,27 @@ def workload_config(args, n):
     }
 
 
+def shard_range(rank, n):
+    """Channels owned by a rank under weak scaling: [rank n, (rank + 1) n)."""
+    return rank * n, (rank + 1) * n
+
+
+def reduce_max(value, dist, device=None):
+    """Max over ranks of a per-rank float (the job's wall time); no data-path
+    collective exists, only this timing reduction."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(n_per_rank, world, steps, t_max_ms):
+    """Whole-job precoders/s: every rank's channels over the slowest rank's time."""
+    return n_per_rank * world * steps / (t_max_ms / 1e3)
+
+
 def flops_per_instance(M, K, T):
     """Algorithmic flops: Hermitian Gram 4MK(K+1); iteration T*K*(8K^2+46K-6)
     plus the Jacobi preprocessing 4K^2+2K (Appendix); W = H X 8MK^2."""
@@ -249,7 +270,8 @@ def main():
     n = args.n_inst
     # inputs are generated before the first GPU call; rank r owns channels [r n, (r+1) n)
     t_gen = time.perf_counter()
-    Hst, xi = C.generate_batch_device_layout(WORKLOAD, n, args.seed, first=rank * n)
+    first, _ = shard_range(rank, n)
+    Hst, xi = C.generate_batch_device_layout(WORKLOAD, n, args.seed, first=first)
     t_gen = time.perf_counter() - t_gen
     K, M = Hst.shape[1], Hst.shape[2]
 
@@ -311,12 +333,8 @@ def main():
     phase_ms, n_exec, per_exec = (None, 0, 0)
     if plan is None or args.mode == "plan":
         phase_ms, n_exec, per_exec = binding.jacpcg_profile_read(prec.ctx)
-    t_max = total_ms
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = n * world * args.steps / (t_max / 1e3)
+    t_max = reduce_max(total_ms, dist, "cuda")
+    value = job_throughput(n, world, args.steps, t_max)
     st = status.cpu().numpy()
 
     # roofline of the dominant kernel (per launch, live event timing)
@@ -347,12 +365,8 @@ def main():
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, binding, prec, Hst, xi, M, K, torch)
-        if dist is not None:
-            t = torch.tensor([e2e.pop("_ms")], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e["value"] = n * world * args.e2e_steps / (float(t.item()) / 1e3)
-        else:
-            e2e.pop("_ms")
+        e2e["value"] = job_throughput(n, world, args.e2e_steps,
+                                      reduce_max(e2e.pop("_ms"), dist, "cuda"))
 
     cpu = acc = None
     if rank == 0 and not args.no_cpu:
