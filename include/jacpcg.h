@@ -151,6 +151,27 @@ jacpcg_status jacpcg_profile_read(jacpcg_ctx *ctx, float ms[4], int *n_executes,
 /* Kernels launched by this context since creation (all entry points). */
 int64_t jacpcg_launch_count(const jacpcg_ctx *ctx);
 
+/* Precode without allocating anything (no counterpart in the paper: this
+ * is an integration aid).  For callers that cannot call cudaMalloc or any
+ * allocating routine -- code running while someone else captures a CUDA
+ * graph, real-time slot loops that forbid allocator latency, integrations
+ * whose memory was fixed at start-up.  Same work, kernels and results as
+ * jacpcg_precode with a context of the given variant and FP32 precision,
+ * but no context: the tables, accumulators and Gram / iterate workspace
+ * live in one static device array of JACPCG_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading the library holds until the process exits.  Runs on
+ * the current device.  The first call on a device looks up the array's
+ * device address (make that first call before any stream capture).  All
+ * calls share the array: calls whose GPU work overlaps race, so serialise
+ * them (one stream, one thread).  Returns ENOMEM, and enqueues nothing,
+ * when the batch needs more scratch than the array holds (about 120
+ * instances of M = 1024, K = 64, or 7 of K = 256); EINVAL for invalid
+ * arguments as jacpcg_precode (K <= 256, no max_M limit). */
+#define JACPCG_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
+jacpcg_status jacpcg_precode_noalloc(const jacpcg_instance *inst, int n_inst, int variant,
+                                     int32_t *status_dev, int32_t *iters_dev, float *resid_dev,
+                                     float *beta_dev, void *stream);
+
 /* Destroy a context (and any plans still alive).  Waits for the device. */
 jacpcg_status jacpcg_destroy(jacpcg_ctx *ctx);
 

@@ -28,7 +28,7 @@ PRECISIONS = {"fp32": JACPCG_FP32, "tf32x3": JACPCG_TF32X3}
 EXPORTS = ("jacpcg_create", "jacpcg_precode", "jacpcg_plan_create", "jacpcg_plan_execute",
            "jacpcg_plan_destroy", "jacpcg_plan_bytes", "jacpcg_arena_free_bytes",
            "jacpcg_profile_read", "jacpcg_launch_count", "jacpcg_destroy", "jacpcg_strerror",
-           "jacpcg_version")
+           "jacpcg_version", "jacpcg_precode_noalloc")
 
 
 class jacpcg_config(ctypes.Structure):
@@ -78,12 +78,13 @@ def load(path: pathlib.Path | str | None = None):
         L.jacpcg_launch_count.argtypes = [P]
         L.jacpcg_launch_count.restype = ctypes.c_int64
         L.jacpcg_destroy.argtypes = [P]
+        L.jacpcg_precode_noalloc.argtypes = [ctypes.POINTER(jacpcg_instance), I, I, P, P, P, P, P]
         L.jacpcg_strerror.argtypes = [I]
         L.jacpcg_strerror.restype = ctypes.c_char_p
         L.jacpcg_version.restype = ctypes.c_char_p
         for n in ("jacpcg_create", "jacpcg_precode", "jacpcg_plan_create", "jacpcg_plan_execute",
                   "jacpcg_plan_destroy", "jacpcg_plan_bytes", "jacpcg_arena_free_bytes",
-                  "jacpcg_profile_read", "jacpcg_destroy"):
+                  "jacpcg_profile_read", "jacpcg_destroy", "jacpcg_precode_noalloc"):
             getattr(L, n).restype = I
         _lib = L
         return L
@@ -135,6 +136,16 @@ def jacpcg_precode(ctx, insts, status=None, iters=None, resid=None, beta=None, s
     arr = _array(insts)
     _check(load().jacpcg_precode(ctx, arr, len(insts), _ptr(status), _ptr(iters), _ptr(resid),
                                  _ptr(beta), ctypes.c_void_p(stream)), "jacpcg_precode")
+
+
+def jacpcg_precode_noalloc(insts, variant=JACPCG_STANDARD, status=None, iters=None, resid=None,
+                           beta=None, stream=0) -> None:
+    """Precode with no allocation at all (static device scratch; see the header)."""
+    arr = _array(insts)
+    v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    _check(load().jacpcg_precode_noalloc(arr, len(arr), v, _ptr(status), _ptr(iters), _ptr(resid),
+                                         _ptr(beta), ctypes.c_void_p(stream)),
+           "jacpcg_precode_noalloc")
 
 
 def jacpcg_plan_create(ctx, insts, status=None, iters=None, resid=None, beta=None,
