@@ -111,7 +111,8 @@ struct Arena {
 
 // What one kernel launch of a plan covers.
 struct Launch {
-    enum Kind { GRAM, PCG, HX } kind;
+    enum Kind { GRAM, PCG, HX, GRAM_TC, HX_TC } kind;
+    int phase;        // 0 Gram, 1 iteration, 2 W = H X
     int param;        // TB (Gram), KC (iteration), TN (W = H X)
     size_t list_off;  // byte offset of its work list inside the plan block
     int count;        // CTAs
@@ -183,7 +184,7 @@ jacpcg_status validate(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n
 
 // Byte layout of one plan block.
 struct Layout {
-    size_t insts, gram, pcg, hx, accum, ws, total;
+    size_t insts, gram, tcl, pcg, hx, hxl, accum, ws, total;
     int n_gram, n_pcg, n_hx;
     std::vector<size_t> ws_off;   // per instance
 };
@@ -208,6 +209,9 @@ size_t inst_ws_bytes(const jacpcg_instance &q) {
            align_up(n_wtiles(q) * sizeof(float));
 }
 
+// K classes whose Gram runs on the tensor cores at this precision
+bool gram_on_tc(int precision, int KC) { return precision == JACPCG_TF32X3 && KC == 64; }
+
 Layout make_layout(const jacpcg_instance *inst, int n) {
     Layout L{};
     L.n_gram = L.n_pcg = L.n_hx = 0;
@@ -219,8 +223,10 @@ Layout make_layout(const jacpcg_instance *inst, int n) {
     size_t o = 0;
     L.insts = o;  o += align_up(sizeof(DevInst) * n);
     L.gram = o;   o += align_up(sizeof(int4) * L.n_gram);
+    L.tcl = o;    o += align_up(sizeof(int) * n);
     L.pcg = o;    o += align_up(sizeof(int2) * L.n_pcg);
     L.hx = o;     o += align_up(sizeof(int4) * L.n_hx);
+    L.hxl = o;    o += align_up(sizeof(int) * n);
     L.accum = o;  o += align_up(sizeof(int32_t) * n) * 3;
     L.ws = o;
     L.ws_off.resize(n);
@@ -253,7 +259,7 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
                                             align_up(KC * sizeof(float)));
         d.M = q.M; d.K = q.K; d.ldh = q.ldh; d.ldw = q.ldw; d.KC = KC;
         d.max_iter = q.max_iter;
-        d.n_wpart = n_wtiles(q);
+        d.n_wpart = gram_on_tc(ctx->cfg.precision, KC) ? (q.M + 127) / 128 : n_wtiles(q);
         d.variant = ctx->cfg.variant;
         d.xi = (float)q.xi;
         d.power = q.power > 0.0 ? (float)q.power : 1.0f;
@@ -261,19 +267,26 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
         hi[i] = d;
     }
     launches.clear();
-    // Gram tiles grouped by tile edge
+    // Gram on the tensor cores: one CTA per instance
+    const int prec = ctx->cfg.precision;
+    int *tl = reinterpret_cast<int *>(host + L.tcl);
+    int nt = 0;
+    for (int i = 0; i < n; ++i)
+        if (gram_on_tc(prec, k_class(inst[i].K))) tl[nt++] = i;
+    if (nt) launches.push_back({Launch::GRAM_TC, 0, 0, L.tcl, nt});
+    // Gram tiles (SIMT) grouped by tile edge
     int4 *gt = reinterpret_cast<int4 *>(host + L.gram);
     int g = 0;
     for (int TB : {16, 32, 64}) {
         const int start = g;
         for (int i = 0; i < n; ++i) {
             const int KC = k_class(inst[i].K);
-            if (gram_tb(KC) != TB) continue;
+            if (gram_tb(KC) != TB || gram_on_tc(prec, KC)) continue;
             const int nb = std::max(1, KC / TB);
             for (int bi = 0; bi < nb; ++bi)
                 for (int bj = 0; bj <= bi; ++bj) gt[g++] = make_int4(i, bi, bj, 0);
         }
-        if (g > start) launches.push_back({Launch::GRAM, TB, L.gram + start * sizeof(int4), g - start});
+        if (g > start) launches.push_back({Launch::GRAM, 0, TB, L.gram + start * sizeof(int4), g - start});
     }
     // iteration blocks grouped by K class
     int2 *pb = reinterpret_cast<int2 *>(host + L.pcg);
@@ -285,22 +298,28 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
             if (k_class(inst[i].K) != KC) continue;
             for (int c0 = 0; c0 < inst[i].K; c0 += s.CW * s.NW) pb[p++] = make_int2(i, c0);
         }
-        if (p > start) launches.push_back({Launch::PCG, KC, L.pcg + start * sizeof(int2), p - start});
+        if (p > start) launches.push_back({Launch::PCG, 1, KC, L.pcg + start * sizeof(int2), p - start});
     }
-    // W = H X tiles grouped by tile width; slot = index of the tile in its instance
+    // W = H X on the tensor cores: instance list, one persistent launch
+    int *hl = reinterpret_cast<int *>(host + L.hxl);
+    int nh = 0;
+    for (int i = 0; i < n; ++i)
+        if (gram_on_tc(prec, k_class(inst[i].K))) hl[nh++] = i;
+    if (nh) launches.push_back({Launch::HX_TC, 2, 0, L.hxl, nh});
+    // W = H X tiles (SIMT) grouped by tile width; slot = index of the tile in its instance
     int4 *ht = reinterpret_cast<int4 *>(host + L.hx);
     int h = 0;
     for (int TN : {16, 32, 64}) {
         const int start = h;
         for (int i = 0; i < n; ++i) {
             const int KC = k_class(inst[i].K);
-            if (hx_tn(KC) != TN) continue;
+            if (hx_tn(KC) != TN || gram_on_tc(prec, KC)) continue;
             const int nm = (inst[i].M + HX_TM - 1) / HX_TM, nn = (inst[i].K + TN - 1) / TN;
             int slot = 0;
             for (int nt = 0; nt < nn; ++nt)
                 for (int mt = 0; mt < nm; ++mt) ht[h++] = make_int4(i, mt, nt, slot++);
         }
-        if (h > start) launches.push_back({Launch::HX, TN, L.hx + start * sizeof(int4), h - start});
+        if (h > start) launches.push_back({Launch::HX, 2, TN, L.hx + start * sizeof(int4), h - start});
     }
 }
 
@@ -321,7 +340,7 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
     if (ev) CK(cudaEventRecord(ev[0], s));
     for (int phase = 0; phase < 3; ++phase) {
         for (const Launch &l : pl->launches) {
-            if ((int)l.kind != phase) continue;
+            if (l.phase != phase) continue;
             cudaError_t e = cudaSuccess;
             const void *list = pl->dev + l.list_off;
             switch (l.kind) {
@@ -336,6 +355,12 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
                 case Launch::HX:
                     e = launch_hx_simt(l.param, pl->d_insts, static_cast<const int4 *>(list), l.count,
                                        s);
+                    break;
+                case Launch::GRAM_TC:
+                    e = launch_gram_tc64(pl->d_insts, static_cast<const int *>(list), l.count, pl->acc, s);
+                    break;
+                case Launch::HX_TC:
+                    e = launch_hx_tc64(pl->d_insts, static_cast<const int *>(list), l.count, pl->acc, s);
                     break;
             }
             if (e != cudaSuccess) return cuda_fail(ctx);
@@ -488,7 +513,7 @@ jacpcg_status jacpcg_create(const jacpcg_config *cfg, jacpcg_ctx **out) {
     if (!cfg || !out) return JACPCG_EINVAL;
     if (cfg->max_K < 1 || cfg->max_K > 256 || cfg->max_M < 1 || cfg->max_instances < 1)
         return JACPCG_EINVAL;
-    if (cfg->precision != JACPCG_FP32) return JACPCG_EINVAL;
+    if (cfg->precision != JACPCG_FP32 && cfg->precision != JACPCG_TF32X3) return JACPCG_EINVAL;
     if (cfg->variant < JACPCG_STANDARD || cfg->variant > JACPCG_CG) return JACPCG_EINVAL;
     jacpcg_ctx *ctx = new (std::nothrow) jacpcg_ctx();
     if (!ctx) return JACPCG_ENOMEM;

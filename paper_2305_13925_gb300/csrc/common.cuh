@@ -10,7 +10,7 @@ namespace jacpcg {
 
 // Per-instance flags accumulated by the kernels, turned into a status by the
 // finalise kernel.
-enum : int32_t { FLAG_NOTHPD = 1, FLAG_NOTCONV = 2 };
+enum : int32_t { FLAG_NOTHPD = 1, FLAG_NOTCONV = 2, FLAG_TIMEOUT = 4 };
 
 // One precoder instance as the kernels see it.  Workspace matrices (A, X)
 // are KC x KC with leading dimension KC, where KC is the instance's K class

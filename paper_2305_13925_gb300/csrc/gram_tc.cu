@@ -1,0 +1,313 @@
+// gram_tc.cu -- A = H^H H + xi I on the tcgen05 tensor cores for the K = 64
+// class (Sec. II, definition of P_i after Eq. 7; diag for Eq. 21).
+//
+// Complex arithmetic as one real GEMM: with Y = [Re H | Im H] (M x 2K real),
+// D = Y^T Y (2K x 2K) gives Re A = D11 + D22 and Im A = D12 - D21.  For
+// K = 64, D is one 128 x 128 tcgen05 tile (M = N = 128, FP32 in tensor memory).
+//
+// FP32 accuracy from TF32 units (3xTF32; Ootomo and Yokota, "Recovering
+// single precision accuracy from Tensor Cores while surpassing the FP32
+// theoretical peak performance", IJHPCA 2022): every staged value is split
+// x = hi + lo (hi = x rounded to TF32, lo = exact remainder) and the tile
+// accumulates hi*hi + hi*lo + lo*hi.  The tensor core's FP32 accumulation
+// rounds toward zero, so long accumulation chains drift: the reduction over
+// M is cut into groups of G stages, each accumulated into one of two TMEM
+// buffers from zero, and drain warps add the group results into FP32
+// registers while the next group accumulates into the other buffer.
+//
+// Persistent, warp-specialised: the CTA walks its share of the instances.
+//   warps 0-7   producers: H (global -> registers, one stage ahead), TF32
+//               split, Y^T stage tiles (hi, lo) in the canonical no-swizzle
+//               K-major layout;
+//   warps 8-15  drain/epilogue: TMEM -> registers per group; at the end of an
+//               instance D goes through shared memory into A (lower triangle
+//               mirrored, so A is exactly Hermitian) and 1/diag(A);
+//   warp 16     TMEM allocation; lane 0 issues the MMAs and commits.
+// Every wait is bounded; a timeout stops the CTA's pipeline, flags its
+// instances with FLAG_TIMEOUT, and the CTA still drains and frees its TMEM.
+#include "common.cuh"
+#include "kernels.h"
+#include "tc.cuh"
+
+namespace jacpcg {
+
+namespace {
+
+constexpr int ROWS = 128;                     // 2K rows of Y^T for K = 64
+constexpr int MCH = 32;                       // H rows (reduction values) per stage
+constexpr int STAGES = 4;
+constexpr int G = 4;                          // stages per accumulation group
+constexpr int PART = ROWS * MCH * 4;          // bytes of one part (hi or lo) of a stage
+constexpr uint32_t LBO = 128;                 // K-adjacent core matrices
+constexpr uint32_t SBO = (MCH / 4) * 128;     // 8-row groups
+constexpr uint32_t WAIT_LIMIT = 1u << 21;
+constexpr int DPITCH = ROWS + 1;              // floats per staged D row
+constexpr int NPW = 8, NDW = 8;               // producer and drain warps
+constexpr int MMA_WARP = NPW + NDW;
+constexpr int NTHREADS = (NPW + NDW + 1) * 32;
+constexpr int TMEM_COLS = 2 * ROWS;           // two accumulation buffers
+
+struct __align__(128) GramSmem {
+    unsigned char stage[STAGES][2 * PART];
+    float D[ROWS * DPITCH];
+    uint64_t full[STAGES];
+    uint64_t empty[STAGES];
+    uint64_t accf[2];
+    uint64_t acce[2];
+    uint64_t fin;
+    uint32_t tmem;
+    volatile int err;
+};
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, float a, float b, float c, float d) {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(addr), "f"(a), "f"(b), "f"(c),
+                 "f"(d)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1) gram_tc64_kernel(const DevInst *__restrict__ insts,
+                                                                const int *__restrict__ list, int n_list,
+                                                                DevAccum acc_out) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    GramSmem &S = *reinterpret_cast<GramSmem *>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            tc::mbar_init(&S.full[s], NPW);
+            tc::mbar_init(&S.empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&S.accf[b], 1);
+            tc::mbar_init(&S.acce[b], NDW);
+        }
+        tc::mbar_init(&S.fin, 1);
+        S.err = 0;
+        tc::mbar_init_fence();
+    }
+    if (warp == MMA_WARP) {
+        tc::tmem_alloc(&S.tmem, TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = S.tmem;
+
+    if (warp < NPW) {
+        // ---------------- producers ----------------
+        const int tid = threadIdx.x;   // 0 .. 255
+        uint32_t chunk = 0;
+        for (int j = blockIdx.x; j < n_list && !S.err; j += gridDim.x) {
+            const DevInst &in = insts[list[j]];
+            const int M = in.M, K = in.K, ldh = in.ldh;
+            const float2 *__restrict__ H = in.H;
+            const int nch = (M + MCH - 1) / MCH;
+            auto load = [&](int c, float4 (&buf)[2][2]) {
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int e = tid + 256 * q;
+                    const int k = (e & 7) + 8 * (e >> 6), mq = (e >> 3) & 7;
+                    const int m = c * MCH + 4 * mq;
+                    const float2 *p = H + (size_t)k * ldh + m;
+                    if (k < K && m + 3 < M) {
+                        buf[q][0] = __ldg(reinterpret_cast<const float4 *>(p));
+                        buf[q][1] = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+                    } else {
+                        float2 v[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            v[i] = (k < K && m + i < M) ? __ldg(p + i) : make_float2(0.f, 0.f);
+                        buf[q][0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+                        buf[q][1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+                    }
+                }
+            };
+            auto put = [&](const float4 (&buf)[2][2]) -> bool {
+                const int s = chunk % STAGES;
+                if (chunk >= STAGES &&
+                    !tc::mbar_wait(&S.empty[s], ((chunk / STAGES) - 1) & 1, WAIT_LIMIT)) {
+                    S.err = 1;
+                    return false;
+                }
+                const uint32_t base = tc::smem_u32(S.stage[s]);
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int e = tid + 256 * q;
+                    const int k = (e & 7) + 8 * (e >> 6), mq = (e >> 3) & 7;
+                    const float re[4] = {buf[q][0].x, buf[q][0].z, buf[q][1].x, buf[q][1].z};
+                    const float im[4] = {buf[q][0].y, buf[q][0].w, buf[q][1].y, buf[q][1].w};
+                    float rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        tc::split_tf32(re[i], rh[i], rl[i]);
+                        tc::split_tf32(im[i], ih[i], il[i]);
+                    }
+                    const uint32_t o_re = (uint32_t)(k >> 3) * SBO + mq * LBO + (k & 7) * 16;
+                    const uint32_t o_im = (uint32_t)((64 + k) >> 3) * SBO + mq * LBO + (k & 7) * 16;
+                    st_shared_v4(base + o_re, rh[0], rh[1], rh[2], rh[3]);
+                    st_shared_v4(base + o_im, ih[0], ih[1], ih[2], ih[3]);
+                    st_shared_v4(base + PART + o_re, rl[0], rl[1], rl[2], rl[3]);
+                    st_shared_v4(base + PART + o_im, il[0], il[1], il[2], il[3]);
+                }
+                tc::fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&S.full[s]);
+                ++chunk;
+                return true;
+            };
+            // loads run two stages ahead of the shared-memory stores
+            float4 bA[2][2], bB[2][2];
+            if (nch > 0) load(0, bA);
+            if (nch > 1) load(1, bB);
+            for (int c = 0; c < nch; c += 2) {
+                if (!put(bA)) break;
+                if (c + 2 < nch) load(c + 2, bA);
+                if (c + 1 < nch) {
+                    if (!put(bB)) break;
+                    if (c + 3 < nch) load(c + 3, bB);
+                }
+            }
+        }
+    } else if (warp < MMA_WARP) {
+        // ---------------- drain / epilogue ----------------
+        const int dw = warp - NPW;                 // 0 .. 7
+        const int quad = warp & 3;                 // TMEM lane quadrant of this warp
+        const int half = dw >> 2;                  // columns [64 half, 64 half + 64)
+        const int row = 32 * quad + lane;          // row of D owned by this thread
+        const int dtid = threadIdx.x - NPW * 32;   // 0 .. 255
+        uint32_t grp = 0;
+        for (int j = blockIdx.x; j < n_list; j += gridDim.x) {
+            const int id = list[j];
+            const DevInst &in = insts[id];
+            const int nch = (in.M + MCH - 1) / MCH;
+            const int ngrp = (nch + G - 1) / G;
+            float sum[64];
+#pragma unroll
+            for (int i = 0; i < 64; ++i) sum[i] = 0.f;
+            for (int g = 0; g < ngrp && !S.err; ++g, ++grp) {
+                const int b = grp & 1;
+                if (!tc::mbar_wait(&S.accf[b], (grp >> 1) & 1, WAIT_LIMIT)) {
+                    S.err = 1;
+                    break;
+                }
+                tc::tc_fence_after();
+                const uint32_t ta = tmem + ((uint32_t)(32 * quad) << 16) + b * ROWS + half * 64;
+#pragma unroll
+                for (int c0 = 0; c0 < 64; c0 += 16) {
+                    float v[16];
+                    tc::tmem_ld16(ta + c0, v);
+                    tc::tmem_ld_wait();
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) sum[c0 + i] += v[i];
+                }
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&S.acce[b]);
+            }
+#pragma unroll
+            for (int i = 0; i < 64; ++i) S.D[row * DPITCH + half * 64 + i] = sum[i];
+            asm volatile("bar.sync 1, 256;\n" ::: "memory");
+            const bool bad = S.err != 0;
+            const int K = in.K;
+            const float xi = in.xi;
+            float2 *__restrict__ A = in.A;
+            float2 *__restrict__ Aout = in.Aout;
+            for (int e = dtid; e < 64 * 64; e += 256) {
+                const int r = e & 63, c = e >> 6;
+                const int k = max(r, c), jj = min(r, c);
+                float re = S.D[k * DPITCH + jj] + S.D[(64 + k) * DPITCH + 64 + jj];
+                float im = S.D[k * DPITCH + 64 + jj] - S.D[(64 + k) * DPITCH + jj];
+                if (r < c) im = -im;
+                if (r == c) {
+                    im = 0.f;
+                    if (r < K) {
+                        re += xi;
+                        in.dinv[r] = 1.0f / re;
+                    } else {
+                        in.dinv[r] = 0.f;
+                    }
+                }
+                A[r + (size_t)c * 64] = make_float2(re, im);
+                if (Aout && r < K && c < K) Aout[r + (size_t)c * K] = make_float2(re, im);
+            }
+            if (dtid == 0) {
+                acc_out.flags[id] = bad ? FLAG_TIMEOUT : 0;
+                acc_out.iters[id] = 0;
+                acc_out.resid_bits[id] = 0u;
+            }
+            asm volatile("bar.sync 1, 256;\n" ::: "memory");   // D is rewritten by the next instance
+        }
+    } else if (lane == 0) {
+        // ---------------- MMA issuer ----------------
+        constexpr uint32_t idesc = tc::idesc_tf32(ROWS, ROWS);
+        uint32_t chunk = 0, grp = 0;
+        for (int j = blockIdx.x; j < n_list && !S.err; j += gridDim.x) {
+            const DevInst &in = insts[list[j]];
+            const int nch = (in.M + MCH - 1) / MCH;
+            for (int c = 0; c < nch; ++c, ++chunk) {
+                const int b = grp & 1;
+                if (c % G == 0 && grp >= 2) {
+                    if (!tc::mbar_wait(&S.acce[b], ((grp >> 1) - 1) & 1, WAIT_LIMIT)) {
+                        S.err = 1;
+                        break;
+                    }
+                    tc::tc_fence_after();
+                }
+                const int s = chunk % STAGES;
+                if (!tc::mbar_wait(&S.full[s], (chunk / STAGES) & 1, WAIT_LIMIT)) {
+                    S.err = 1;
+                    break;
+                }
+                tc::tc_fence_after();
+                const uint32_t hi = tc::smem_u32(S.stage[s]), lo = hi + PART;
+                const uint32_t d = tmem + b * ROWS;
+#pragma unroll
+                for (int kk = 0; kk < MCH / 8; ++kk) {
+                    const uint32_t off = kk * 2 * LBO;   // 8 TF32 values = 2 core matrices along K
+                    const uint64_t dh = tc::smem_desc(hi + off, LBO, SBO);
+                    const uint64_t dl = tc::smem_desc(lo + off, LBO, SBO);
+                    tc::mma_tf32(d, dh, dh, idesc, (c % G == 0 && kk == 0) ? 0u : 1u);
+                    tc::mma_tf32(d, dh, dl, idesc, 1u);
+                    tc::mma_tf32(d, dl, dh, idesc, 1u);
+                }
+                tc::mma_commit(&S.empty[s]);
+                if (c % G == G - 1 || c == nch - 1) {
+                    tc::mma_commit(&S.accf[b]);
+                    ++grp;
+                }
+            }
+        }
+        tc::mma_commit(&S.fin);
+        tc::mbar_wait(&S.fin, 0, WAIT_LIMIT);   // no MMA in flight past this point
+    }
+
+    tc::tc_fence_before();
+    __syncthreads();
+    if (S.err && threadIdx.x == 0) {
+        for (int j = blockIdx.x; j < n_list; j += gridDim.x) atomicOr(acc_out.flags + list[j], FLAG_TIMEOUT);
+    }
+    if (warp == MMA_WARP) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_gram_tc64(const DevInst *insts, const int *list, int n, DevAccum acc,
+                             cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const size_t smem = sizeof(GramSmem);
+    cudaError_t e = cudaFuncSetAttribute(gram_tc64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int grid = n < sms ? n : sms;
+    gram_tc64_kernel<<<grid, NTHREADS, smem, s>>>(insts, list, n, acc);
+    return cudaGetLastError();
+}
+
+}  // namespace jacpcg

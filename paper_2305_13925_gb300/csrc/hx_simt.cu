@@ -134,7 +134,8 @@ __global__ void finalize_kernel(const DevInst *__restrict__ insts, int n_inst, D
     if (lane != 0) return;
     const int f = acc.flags[inst];
     int32_t st = 0;                                  // JACPCG_OK
-    if (!isfinite(s)) st = 6;                        // JACPCG_ENONFINITE
+    if (f & FLAG_TIMEOUT) st = 7;                    // JACPCG_ETIMEOUT
+    else if (!isfinite(s)) st = 6;                   // JACPCG_ENONFINITE
     else if (f & FLAG_NOTHPD) st = 5;                // JACPCG_ENOTHPD
     else if (f & FLAG_NOTCONV) st = 4;               // JACPCG_ENOTCONV
     const double P = in.power > 0.f ? (double)in.power : 1.0;

@@ -1,0 +1,360 @@
+// hx_tc.cu -- the precoder W = H X on the tcgen05 tensor cores for the K = 64
+// class (Eq. 7 without the power factor; Eq. 15 per symbol), 3xTF32.
+//
+// Complex product as real MMAs over one 128-row tile of W (rows = antennas):
+//   Wr = Hr Xr - Hi Xi,   Wi = Hr Xi + Hi Xr.
+// With B = [Xr^T ; Xi^T] (128 rows of K values, K-major) resident in shared
+// memory per instance, each reduction step issues
+//   D[:, 0:128]  += Hr  . B^T            (N = 128: Hr Xr | Hr Xi)
+//   D[:, 0:64]   += -Hi . (Xi^T)^T       (N = 64, A negated)
+//   D[:, 64:128] +=  Hi . (Xr^T)^T       (N = 64)
+// each as hi*hi + hi*lo + lo*hi of the TF32 split (see gram_tc.cu).  The
+// reduction is only 2K long, so one TMEM accumulation per tile suffices.
+//
+// Persistent, warp-specialised, one CTA per SM walking its instances:
+//   warps 0-7   producers: per instance B (from the iterate X), then per tile
+//               H stage tiles [Hr | Hi] (16 users per stage) transposed into
+//               the canonical K-major layout;
+//   warps 8-15  drain: TMEM (two alternating 128-column accumulators) ->
+//               registers -> W (complex64, column-major, coalesced) and this
+//               tile's ||W||_F^2 partial in its own slot;
+//   warp 16     TMEM allocation; lane 0 issues MMAs and commits.
+// Every wait is bounded; a timeout flags the CTA's instances with FLAG_TIMEOUT.
+#include "common.cuh"
+#include "kernels.h"
+#include "tc.cuh"
+
+namespace jacpcg {
+
+namespace {
+
+constexpr int TMR = 128;                      // W rows per tile
+constexpr int KCH = 16;                       // users (reduction values) per stage
+constexpr int STAGES = 4;
+constexpr int APART = TMR * KCH * 4;          // one of Yr_hi, Yr_lo, Yi_hi, Yi_lo: 8 KB
+constexpr int BPART = 128 * 64 * 4;           // one of B_hi, B_lo: 32 KB
+constexpr uint32_t LBO = 128;
+constexpr uint32_t SBO_A = (KCH / 4) * 128;   // 512
+constexpr uint32_t SBO_B = (64 / 4) * 128;    // 2048
+constexpr uint32_t WAIT_LIMIT = 1u << 21;
+constexpr int NPW = 8, NDW = 8;
+constexpr int MMA_WARP = NPW + NDW;
+constexpr int NTHREADS = (NPW + NDW + 1) * 32;
+constexpr int TMEM_COLS = 256;
+
+struct __align__(128) HxSmem {
+    unsigned char B[2 * BPART];
+    unsigned char stage[STAGES][4 * APART];
+    float wsum[2][NDW];
+    uint64_t full[STAGES];
+    uint64_t empty[STAGES];
+    uint64_t bfull, bempty;
+    uint64_t accf[2];
+    uint64_t acce[2];
+    uint64_t fin;
+    uint32_t tmem;
+    volatile int err;
+};
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, float a, float b, float c, float d) {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(addr), "f"(a), "f"(b), "f"(c),
+                 "f"(d)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1) hx_tc64_kernel(const DevInst *__restrict__ insts,
+                                                              const int *__restrict__ list, int n_list,
+                                                              DevAccum acc_out) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    HxSmem &S = *reinterpret_cast<HxSmem *>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            tc::mbar_init(&S.full[s], NPW);
+            tc::mbar_init(&S.empty[s], 1);
+        }
+        tc::mbar_init(&S.bfull, NPW);
+        tc::mbar_init(&S.bempty, 1);
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&S.accf[b], 1);
+            tc::mbar_init(&S.acce[b], NDW);
+        }
+        tc::mbar_init(&S.fin, 1);
+        S.err = 0;
+        tc::mbar_init_fence();
+    }
+    if (warp == MMA_WARP) {
+        tc::tmem_alloc(&S.tmem, TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = S.tmem;
+
+    if (warp < NPW) {
+        // ---------------- producers ----------------
+        const int tid = threadIdx.x;   // 0 .. 255
+        uint32_t chunk = 0, ninst = 0;
+        const uint32_t bbase = tc::smem_u32(S.B);
+        for (int j = blockIdx.x; j < n_list && !S.err; j += gridDim.x, ++ninst) {
+            const DevInst &in = insts[list[j]];
+            const int M = in.M, K = in.K, ldh = in.ldh;
+            const float2 *__restrict__ H = in.H;
+            const float2 *__restrict__ X = in.X;   // ld 64
+            // B = [Xr^T ; Xi^T], rewritten once the previous instance's MMAs are done
+            if (ninst > 0 && !tc::mbar_wait(&S.bempty, (ninst - 1) & 1, WAIT_LIMIT)) {
+                S.err = 1;
+                break;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int e = tid + 256 * q;
+                const int n = (e & 7) + 8 * (e >> 7), rq = (e >> 3) & 15;
+                float2 v[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int r = 4 * rq + i;
+                    v[i] = (n < K && r < K) ? __ldg(X + r + (size_t)n * 64) : make_float2(0.f, 0.f);
+                }
+                float rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    tc::split_tf32(v[i].x, rh[i], rl[i]);
+                    tc::split_tf32(v[i].y, ih[i], il[i]);
+                }
+                const uint32_t o_r = (uint32_t)(n >> 3) * SBO_B + rq * LBO + (n & 7) * 16;
+                const uint32_t o_i = (uint32_t)((64 + n) >> 3) * SBO_B + rq * LBO + (n & 7) * 16;
+                st_shared_v4(bbase + o_r, rh[0], rh[1], rh[2], rh[3]);
+                st_shared_v4(bbase + o_i, ih[0], ih[1], ih[2], ih[3]);
+                st_shared_v4(bbase + BPART + o_r, rl[0], rl[1], rl[2], rl[3]);
+                st_shared_v4(bbase + BPART + o_i, il[0], il[1], il[2], il[3]);
+            }
+            tc::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&S.bfull);
+            // H tiles: stage t = (tile t / nks, users 16 (t % nks) ...); loads run two stages ahead
+            const int nmt = (M + TMR - 1) / TMR;
+            const int nks = (K + KCH - 1) / KCH;
+            const int T = nmt * nks;
+            auto load = [&](int t, float2 (&h)[2][4]) {
+                const int mt = t / nks, ks = t % nks;
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int e = tid + 256 * q;
+                    const int m = e & 127, kq = e >> 7;
+                    const int gm = mt * TMR + m;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int k = ks * KCH + 4 * kq + i;
+                        h[q][i] = (gm < M && k < K) ? __ldg(H + gm + (size_t)k * ldh)
+                                                    : make_float2(0.f, 0.f);
+                    }
+                }
+            };
+            auto put = [&](const float2 (&h)[2][4]) -> bool {
+                const int s = chunk % STAGES;
+                if (chunk >= STAGES &&
+                    !tc::mbar_wait(&S.empty[s], ((chunk / STAGES) - 1) & 1, WAIT_LIMIT)) {
+                    S.err = 1;
+                    return false;
+                }
+                const uint32_t base = tc::smem_u32(S.stage[s]);
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int e = tid + 256 * q;
+                    const int m = e & 127, kq = e >> 7;
+                    float rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        tc::split_tf32(h[q][i].x, rh[i], rl[i]);
+                        tc::split_tf32(h[q][i].y, ih[i], il[i]);
+                    }
+                    const uint32_t o = (uint32_t)(m >> 3) * SBO_A + kq * LBO + (m & 7) * 16;
+                    st_shared_v4(base + o, rh[0], rh[1], rh[2], rh[3]);                 // Yr hi
+                    st_shared_v4(base + APART + o, rl[0], rl[1], rl[2], rl[3]);         // Yr lo
+                    st_shared_v4(base + 2 * APART + o, ih[0], ih[1], ih[2], ih[3]);     // Yi hi
+                    st_shared_v4(base + 3 * APART + o, il[0], il[1], il[2], il[3]);     // Yi lo
+                }
+                tc::fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&S.full[s]);
+                ++chunk;
+                return true;
+            };
+            float2 hA[2][4], hB[2][4];
+            if (T > 0) load(0, hA);
+            if (T > 1) load(1, hB);
+            for (int t = 0; t < T; t += 2) {
+                if (!put(hA)) break;
+                if (t + 2 < T) load(t + 2, hA);
+                if (t + 1 < T) {
+                    if (!put(hB)) break;
+                    if (t + 3 < T) load(t + 3, hB);
+                }
+            }
+        }
+    } else if (warp < MMA_WARP) {
+        // ---------------- drain ----------------
+        const int dw = warp - NPW;
+        const int quad = warp & 3;
+        const int half = dw >> 2;                  // users [32 half, 32 half + 32)
+        const int row = 32 * quad + lane;
+        uint32_t tile = 0;
+        for (int j = blockIdx.x; j < n_list; j += gridDim.x) {
+            const DevInst &in = insts[list[j]];
+            const int M = in.M, K = in.K, ldw = in.ldw;
+            float2 *__restrict__ W = in.W;
+            const int nmt = (M + TMR - 1) / TMR;
+            for (int mt = 0; mt < nmt; ++mt, ++tile) {
+                const int b = tile & 1;
+                float wr[32], wi[32];
+                bool ok = !S.err && tc::mbar_wait(&S.accf[b], (tile >> 1) & 1, WAIT_LIMIT);
+                if (!ok) S.err = 1;
+                tc::tc_fence_after();
+                if (ok) {
+                    const uint32_t ta = tmem + ((uint32_t)(32 * quad) << 16) + b * 128 + 32 * half;
+                    float v[16];
+                    tc::tmem_ld16(ta, v);
+                    tc::tmem_ld_wait();
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) wr[i] = v[i];
+                    tc::tmem_ld16(ta + 16, v);
+                    tc::tmem_ld_wait();
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) wr[16 + i] = v[i];
+                    tc::tmem_ld16(ta + 64, v);
+                    tc::tmem_ld_wait();
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) wi[i] = v[i];
+                    tc::tmem_ld16(ta + 80, v);
+                    tc::tmem_ld_wait();
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) wi[16 + i] = v[i];
+                }
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&S.acce[b]);
+                float nrm = 0.f;
+                const int gm = mt * TMR + row;
+                if (ok && gm < M) {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const int jj = 32 * half + i;
+                        if (jj < K) {
+                            W[gm + (size_t)jj * ldw] = make_float2(wr[i], wi[i]);
+                            nrm = fmaf(wr[i], wr[i], nrm);
+                            nrm = fmaf(wi[i], wi[i], nrm);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+                if (lane == 0) S.wsum[b][dw] = nrm;
+                asm volatile("bar.sync 1, 256;\n" ::: "memory");
+                if (dw == 0 && lane == 0) {
+                    float s = 0.f;
+#pragma unroll
+                    for (int w = 0; w < NDW; ++w) s += S.wsum[b][w];
+                    in.wpart[mt] = s;
+                }
+            }
+        }
+    } else if (lane == 0) {
+        // ---------------- MMA issuer ----------------
+        constexpr uint32_t id128 = tc::idesc_tf32(TMR, 128);
+        constexpr uint32_t id64n = tc::idesc_tf32(TMR, 64, true);
+        constexpr uint32_t id64 = tc::idesc_tf32(TMR, 64);
+        const uint32_t bhi = tc::smem_u32(S.B), blo = bhi + BPART;
+        uint32_t chunk = 0, tile = 0, ninst = 0;
+        for (int j = blockIdx.x; j < n_list && !S.err; j += gridDim.x, ++ninst) {
+            const DevInst &in = insts[list[j]];
+            const int nmt = (in.M + TMR - 1) / TMR;
+            const int nks = (in.K + KCH - 1) / KCH;
+            if (!tc::mbar_wait(&S.bfull, ninst & 1, WAIT_LIMIT)) {
+                S.err = 1;
+                break;
+            }
+            tc::tc_fence_after();
+            for (int mt = 0; mt < nmt && !S.err; ++mt, ++tile) {
+                const int b = tile & 1;
+                if (tile >= 2) {
+                    if (!tc::mbar_wait(&S.acce[b], ((tile >> 1) - 1) & 1, WAIT_LIMIT)) {
+                        S.err = 1;
+                        break;
+                    }
+                    tc::tc_fence_after();
+                }
+                const uint32_t d = tmem + b * 128;
+                for (int ks = 0; ks < nks; ++ks, ++chunk) {
+                    const int s = chunk % STAGES;
+                    if (!tc::mbar_wait(&S.full[s], (chunk / STAGES) & 1, WAIT_LIMIT)) {
+                        S.err = 1;
+                        break;
+                    }
+                    tc::tc_fence_after();
+                    const uint32_t a = tc::smem_u32(S.stage[s]);
+#pragma unroll
+                    for (int kk = 0; kk < KCH / 8; ++kk) {
+                        const uint32_t ao = kk * 2 * LBO;
+                        const uint32_t bo = (uint32_t)(ks * KCH / 4 + 2 * kk) * LBO;
+                        const uint64_t arh = tc::smem_desc(a + ao, LBO, SBO_A);
+                        const uint64_t arl = tc::smem_desc(a + APART + ao, LBO, SBO_A);
+                        const uint64_t aih = tc::smem_desc(a + 2 * APART + ao, LBO, SBO_A);
+                        const uint64_t ail = tc::smem_desc(a + 3 * APART + ao, LBO, SBO_A);
+                        const uint64_t bh = tc::smem_desc(bhi + bo, LBO, SBO_B);           // rows 0..127
+                        const uint64_t bl = tc::smem_desc(blo + bo, LBO, SBO_B);
+                        const uint64_t bhr = bh, blr = bl;                                  // Xr^T rows 0..63
+                        const uint64_t bhi_i = tc::smem_desc(bhi + bo + 8 * SBO_B, LBO, SBO_B);  // Xi^T
+                        const uint64_t blo_i = tc::smem_desc(blo + bo + 8 * SBO_B, LBO, SBO_B);
+                        const uint32_t first = (ks == 0 && kk == 0) ? 0u : 1u;
+                        tc::mma_tf32(d, arh, bh, id128, first);
+                        tc::mma_tf32(d, arh, bl, id128, 1u);
+                        tc::mma_tf32(d, arl, bh, id128, 1u);
+                        tc::mma_tf32(d, aih, bhi_i, id64n, 1u);
+                        tc::mma_tf32(d, aih, blo_i, id64n, 1u);
+                        tc::mma_tf32(d, ail, bhi_i, id64n, 1u);
+                        tc::mma_tf32(d + 64, aih, bhr, id64, 1u);
+                        tc::mma_tf32(d + 64, aih, blr, id64, 1u);
+                        tc::mma_tf32(d + 64, ail, bhr, id64, 1u);
+                    }
+                    tc::mma_commit(&S.empty[s]);
+                }
+                tc::mma_commit(&S.accf[b]);
+            }
+            tc::mma_commit(&S.bempty);
+        }
+        tc::mma_commit(&S.fin);
+        tc::mbar_wait(&S.fin, 0, WAIT_LIMIT);
+    }
+
+    tc::tc_fence_before();
+    __syncthreads();
+    if (S.err && threadIdx.x == 0) {
+        for (int j = blockIdx.x; j < n_list; j += gridDim.x) atomicOr(acc_out.flags + list[j], FLAG_TIMEOUT);
+    }
+    if (warp == MMA_WARP) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_hx_tc64(const DevInst *insts, const int *list, int n, DevAccum acc,
+                           cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const size_t smem = sizeof(HxSmem);
+    cudaError_t e = cudaFuncSetAttribute(hx_tc64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int grid = n < sms ? n : sms;
+    hx_tc64_kernel<<<grid, NTHREADS, smem, s>>>(insts, list, n, acc);
+    return cudaGetLastError();
+}
+
+}  // namespace jacpcg

@@ -23,6 +23,12 @@ constexpr int HX_TM = 64;
 // tiles: (instance, bi, bj, 0) with bi >= bj
 cudaError_t launch_gram_simt(int TB, const DevInst *insts, const int4 *tiles, int n_tiles,
                              DevAccum acc, cudaStream_t s);
+// tensor-core Gram for the K = 64 class (3xTF32); list: instance ids, one CTA each
+cudaError_t launch_gram_tc64(const DevInst *insts, const int *list, int n, DevAccum acc,
+                             cudaStream_t s);
+// tensor-core W = H X for the K = 64 class (3xTF32); list: instance ids
+cudaError_t launch_hx_tc64(const DevInst *insts, const int *list, int n, DevAccum acc,
+                           cudaStream_t s);
 // blocks: (instance, first column)
 cudaError_t launch_pcg(int KC, int variant, const DevInst *insts, const int2 *blocks,
                        int n_blocks, DevAccum acc, cudaStream_t s);

@@ -1,0 +1,59 @@
+"""GPU parity of the tensor-core (tcgen05, 3xTF32) path against the FP64
+oracle, through the C ABI.  Same bar as the FP32 SIMT path: relative
+Frobenius error of W at most 1e-5 per instance."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2305_13925_gb300 import channels as C
+
+from gpu_util import rel_fro, run
+
+pytestmark = pytest.mark.gpu
+
+TOL_W = 1e-5
+TOL_A = 4e-6      # FP32 accumulation of 2M terms inside the tensor core
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_13925_gb300 import build
+    build.build()
+
+
+def check(Hs, xis, T=6, variant="standard"):
+    Hs = [C.round_complex64(h) for h in Hs]
+    out = run(Hs, xis, variant=variant, T=T, want_X=True, want_A=True, precision="tf32x3")
+    errs = []
+    for i, (H, xi) in enumerate(zip(Hs, xis)):
+        ref = O.precode(H, xi, variant, max_iter=T)
+        e = rel_fro(out["W"][i], ref["W"])
+        errs.append(e)
+        assert out["status"][i] == 0, (i, out["status"][i])
+        assert rel_fro(out["A"][i], ref["A"]) <= TOL_A, (i, rel_fro(out["A"][i], ref["A"]))
+        assert np.array_equal(out["A"][i], out["A"][i].conj().T)
+        assert e <= TOL_W, (i, H.shape, e)
+        assert abs(out["beta"][i] - ref["beta"]) <= 1e-5 * ref["beta"]
+    return out, errs
+
+
+def test_tensor_batched_1024x64_subset():
+    H, xi = C.generate_batch("batched_1024x64", 24, 1)
+    check(list(H), list(xi), T=6)
+
+
+@pytest.mark.parametrize("K,M", [(64, 1024), (64, 257), (40, 1000), (33, 96), (64, 4096)])
+def test_tensor_gram_shapes(K, M):
+    spec = C.ChannelSpec(M=M, S=1, K=K, r=(0.5, 0.5), n_vis=(1, 1), snr_db=(10.0,))
+    inst = C.generate_instance(spec, 9, K * 7 + M)
+    check([inst.H], [inst.xi], T=5)
+
+
+def test_tensor_ragged_mix_with_simt_classes():
+    insts = C.generate_ragged(12, 8, k_set=(16, 64, 128), m_set=(256, 1024))
+    check([i.H for i in insts], [i.xi for i in insts], T=4)
