@@ -59,6 +59,11 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--plain-sample", type=int, default=64)
+    ap.add_argument("--workload", default="batched", choices=["batched", "serving"])
+    ap.add_argument("--rates", default="5000,20000,50000,100000,200000")
+    ap.add_argument("--trace-seconds", type=float, default=0.5)
+    ap.add_argument("--pool", type=int, default=512)
     return ap.parse_args()
 
 
@@ -229,6 +234,92 @@ def cpu_baseline_leg(Hst, xi, T, variant, seconds, Wd=None):
     return out, acc
 
 
+def plain_leg(binding, torch, Hd, Wd, xi, T, variant, sample):
+    """The plain FP32 per-instance comparator on the first `sample` channels
+    of the same batch: one jacpcg_precode_plain call per channel, each timed
+    with CUDA events; precoders/s and per-channel latency."""
+    n = min(sample, Hd.shape[0])
+    K = Hd.shape[1]
+    ws = torch.empty(binding.plain_workspace_bytes(K), dtype=torch.uint8, device="cuda")
+    st = torch.empty(n, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    Wp = torch.empty_like(Hd[:n])      # the batched result in Wd stays untouched
+    descs = [binding.instance(Hd[i], Wp[i], float(xi[i]), T) for i in range(n)]
+    for i in range(min(3, n)):   # warm-up
+        binding.jacpcg_precode_plain([descs[i]], ws, variant, st[i:i + 1], stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1)]
+    ev[0].record(stream)
+    for i in range(n):
+        binding.jacpcg_precode_plain([descs[i]], ws, variant, st[i:i + 1], stream=stream.cuda_stream)
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    lat = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(n))
+    total = ev[0].elapsed_time(ev[-1])
+    return {"value": n / (total / 1e3), "unit": UNIT, "sample": n,
+            "latency_ms": {"p50": statistics.median(lat), "p99": lat[min(n - 1, int(0.99 * n))]},
+            "what": "jacpcg_precode_plain: one channel at a time, simple SIMT kernels, one launch "
+                    "per step and per iteration, plain FP32, no batching / graphs / tensor cores",
+            "status_ok": int((st.cpu().numpy() == 0).sum())}
+
+
+def run_serving(args):
+    """Open-loop Poisson traces over the ragged mix (K in {8..256}, M in
+    {256..4096}, tolerance 1e-5), replayed against the continuous-batching
+    server; p50/p99 latency and the share of requests over the 1 ms slot."""
+    import numpy as np
+    import torch
+    from paper_2305_13925_gb300 import binding, build, channels as C
+    insts = C.generate_ragged(args.pool, 3)
+    build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    Hd, Wd, descs = [], [], []
+    for i in insts:
+        M, K = i.H.shape
+        h = torch.from_numpy(np.ascontiguousarray(i.H.T).astype(np.complex64)).cuda()
+        w = torch.empty_like(h)
+        Hd.append(h)
+        Wd.append(w)
+        descs.append(binding.instance(h, w, i.xi, 64, 1e-5))
+    rates = [float(r) for r in args.rates.split(",")]
+    rng = np.random.default_rng(4)
+    out = []
+    for plain in (False, True):
+        prec = binding.Precoder(max_instances=1024, max_M=4096, max_K=256, precision=args.precision,
+                                arena_bytes=16 << 30)
+        srv = binding.jacpcg_server_create(prec.ctx, max_batch=1024, max_inflight=4, plain=plain)
+        try:
+            binding.jacpcg_server_replay(srv, descs, np.arange(len(descs)) % len(descs),
+                                         np.zeros(len(descs)))          # warm-up
+            for lam in (rates if not plain else rates[:1]):
+                n_req = int(min(40000, lam * args.trace_seconds)) if not plain else 200
+                arr = np.cumsum(rng.exponential(1e6 / lam, n_req))
+                which = rng.integers(0, len(descs), n_req)
+                t0 = time.perf_counter()
+                lat, st = binding.jacpcg_server_replay(srv, descs, which, arr)
+                wall = time.perf_counter() - t0
+                ok = st == 0
+                l = np.sort(lat[ok])
+                out.append({"path": "plain_fp32" if plain else "batched", "offered_req_s": lam,
+                            "requests": n_req, "completed_per_s": float(ok.sum() / wall),
+                            "p50_us": float(np.median(l)) if len(l) else None,
+                            "p99_us": float(l[min(len(l) - 1, int(0.99 * len(l)))]) if len(l) else None,
+                            "deadline_miss_rate": float(np.mean(lat > 1000.0)),
+                            "status_ok": int(ok.sum())})
+        finally:
+            binding.jacpcg_server_destroy(srv)
+            prec.close()
+    best = [o for o in out if o["path"] == "batched"]
+    line = {"metric": METRIC, "value": max(o["completed_per_s"] for o in best), "unit": UNIT,
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"serving: Poisson arrivals, ragged mix K in {{8..256}}, "
+                                   f"M in {{256..4096}}, tol 1e-5, pool of {len(descs)} channels, "
+                                   f"1 ms deadline", "precision": args.precision},
+            "traces": out}
+    print(json.dumps(line))
+    return 0
+
+
 def run_reference(args):
     """--impl reference: the FP64 oracle timed on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
@@ -265,6 +356,8 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
 
     import numpy as np
     from paper_2305_13925_gb300 import channels as C
@@ -383,6 +476,11 @@ def main():
         e2e["value"] = job_throughput(n, world, args.e2e_steps,
                                       reduce_max(e2e.pop("_ms"), dist, "cuda"))
 
+    plain = None
+    if rank == 0 and args.plain_sample > 0:
+        plain = plain_leg(binding, torch, Hd, Wd, xi, args.iters, args.variant, args.plain_sample)
+        plain["speedup"] = value / world / plain["value"] if plain["value"] > 0 else None
+
     cpu = acc = None
     if rank == 0 and not args.no_cpu:
         cpu, acc = cpu_baseline_leg(Hst, xi, args.iters, args.variant, args.cpu_seconds, Wd)
@@ -397,7 +495,8 @@ def main():
             "latency_ms": {"p50": statistics.median(step_ms),
                            "p99": sorted(step_ms)[min(len(step_ms) - 1, int(0.99 * len(step_ms)))],
                            "what": "device time of one whole batch step"},
-            "roofline": roofline, "phase_ms": phases, "cpu_baseline": cpu, "accuracy": acc,
+            "roofline": roofline, "phase_ms": phases, "plain_fp32": plain, "cpu_baseline": cpu,
+            "accuracy": acc,
             "e2e": e2e, "gpu_launches": int(launches), "launches_per_step": per_exec or None,
             "clocks": clocks, "status_ok": int((st == 0).sum()), "input_gen_s": round(t_gen, 2),
         }

@@ -151,6 +151,65 @@ jacpcg_status jacpcg_profile_read(jacpcg_ctx *ctx, float ms[4], int *n_executes,
 /* Kernels launched by this context since creation (all entry points). */
 int64_t jacpcg_launch_count(const jacpcg_ctx *ctx);
 
+/* ---- serving: continuous batching of precoding requests -----------------
+ * A server owns a context (do not use that context elsewhere while the
+ * server lives) and a scheduler thread.  Each request is one instance whose
+ * H and W are device buffers that stay valid until the request completes.
+ * While fewer than max_inflight batches are on the GPU, the scheduler takes
+ * every waiting request (at most max_batch), admits them if the context
+ * arena has room for their plan (else it waits for a running batch to
+ * retire, or launches fewer), and runs them as one ragged batch on its own
+ * stream: requests that arrive while others run join the next batch and
+ * their work overlaps on the device.  Results are bitwise the same as the
+ * request's result alone.  Latency = host time from submit to the end of
+ * its batch on the GPU (a host callback on the batch's stream). */
+typedef struct jacpcg_server jacpcg_server;
+typedef struct {
+    int max_batch;          /* most requests per launched batch (>= 1) */
+    int max_inflight;       /* batches on the GPU at once, 1..64 (one stream each) */
+    int max_queue;          /* waiting requests before submit returns EBUSY; <= 0: unbounded */
+    int plain;              /* 1: run each batch with the plain per-instance comparator
+                               (jacpcg_precode_plain) instead of the batched path */
+    int plain_variant;      /* iteration form for plain = 1 */
+} jacpcg_server_config;
+
+jacpcg_status jacpcg_server_create(jacpcg_ctx *ctx, const jacpcg_server_config *cfg,
+                                   jacpcg_server **out);
+/* Queue one request; *ticket identifies it.  Thread-safe.  Errors: EINVAL
+ * (invalid instance), EBUSY (queue full or shutting down), ECUDA. */
+jacpcg_status jacpcg_submit(jacpcg_server *srv, const jacpcg_instance *inst, uint64_t *ticket);
+/* Result of a request: returns EBUSY while it runs (blocking == 0), or waits
+ * (at most 60 s, then ETIMEOUT).  On JACPCG_OK, *result is the request's
+ * status (as jacpcg_precode's per-instance status) and *latency_us (may be
+ * NULL) its latency; the ticket is then forgotten.  Thread-safe. */
+jacpcg_status jacpcg_poll(jacpcg_server *srv, uint64_t ticket, jacpcg_status *result,
+                          double *latency_us, int blocking);
+/* Load driver: submit request i (instance pool[which[i]]) at arrival_us[i]
+ * microseconds after the call starts (open loop, busy-waiting on a steady
+ * clock), then collect every result.  latency_us / status (may be NULL)
+ * receive n_req values (latency -1 when a request was refused). */
+jacpcg_status jacpcg_server_replay(jacpcg_server *srv, const jacpcg_instance *pool, int n_pool,
+                                   const int *which, const double *arrival_us, int n_req,
+                                   double *latency_us, int32_t *status);
+/* Requests completed, batches launched and the mean batch size so far. */
+jacpcg_status jacpcg_server_stats(jacpcg_server *srv, uint64_t *n_done, uint64_t *n_batches,
+                                  double *mean_batch);
+/* Drain the queue, wait for running batches, free the server (not the context). */
+jacpcg_status jacpcg_server_destroy(jacpcg_server *srv);
+
+/* The plain FP32 per-instance comparator: the same precoder (same variant
+ * semantics, Eq. 7 with B = I) computed one instance at a time with simple
+ * one-thread-per-entry SIMT kernels, one launch per step and per iteration,
+ * plain FP32 sums, no batching, no CUDA graphs, no tensor cores.  It is the
+ * baseline the batched path is measured against.  No context: the caller
+ * passes a device workspace of at least 5 K^2 * 8 + 16 K + 256 bytes for the
+ * largest K of the batch (ENOMEM otherwise).  Per-instance outputs as in
+ * jacpcg_precode.  Errors: EINVAL, ENOMEM, ECUDA. */
+jacpcg_status jacpcg_precode_plain(const jacpcg_instance *inst, int n_inst, int variant,
+                                   void *workspace, size_t workspace_bytes, int32_t *status_dev,
+                                   int32_t *iters_dev, float *resid_dev, float *beta_dev,
+                                   void *stream);
+
 /* Precode without allocating anything (no counterpart in the paper: this
  * is an integration aid).  For callers that cannot call cudaMalloc or any
  * allocating routine -- code running while someone else captures a CUDA

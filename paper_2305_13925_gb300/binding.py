@@ -28,7 +28,9 @@ PRECISIONS = {"fp32": JACPCG_FP32, "tf32x3": JACPCG_TF32X3}
 EXPORTS = ("jacpcg_create", "jacpcg_precode", "jacpcg_plan_create", "jacpcg_plan_execute",
            "jacpcg_plan_destroy", "jacpcg_plan_bytes", "jacpcg_arena_free_bytes",
            "jacpcg_profile_read", "jacpcg_launch_count", "jacpcg_destroy", "jacpcg_strerror",
-           "jacpcg_version", "jacpcg_precode_noalloc")
+           "jacpcg_version", "jacpcg_precode_noalloc", "jacpcg_precode_plain",
+           "jacpcg_server_create", "jacpcg_submit", "jacpcg_poll", "jacpcg_server_replay",
+           "jacpcg_server_stats", "jacpcg_server_destroy")
 
 
 class jacpcg_config(ctypes.Structure):
@@ -42,6 +44,11 @@ class jacpcg_instance(ctypes.Structure):
                 ("H", ctypes.c_void_p), ("xi", ctypes.c_double), ("power", ctypes.c_double),
                 ("W", ctypes.c_void_p), ("ldw", ctypes.c_int), ("X", ctypes.c_void_p),
                 ("A", ctypes.c_void_p), ("max_iter", ctypes.c_int), ("tol", ctypes.c_float)]
+
+
+class jacpcg_server_config(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_int), ("max_inflight", ctypes.c_int),
+                ("max_queue", ctypes.c_int), ("plain", ctypes.c_int), ("plain_variant", ctypes.c_int)]
 
 
 class JacpcgError(RuntimeError):
@@ -79,12 +86,22 @@ def load(path: pathlib.Path | str | None = None):
         L.jacpcg_launch_count.restype = ctypes.c_int64
         L.jacpcg_destroy.argtypes = [P]
         L.jacpcg_precode_noalloc.argtypes = [ctypes.POINTER(jacpcg_instance), I, I, P, P, P, P, P]
+        L.jacpcg_precode_plain.argtypes = [ctypes.POINTER(jacpcg_instance), I, I, P, S, P, P, P, P, P]
+        U64, D = ctypes.c_uint64, ctypes.c_double
+        L.jacpcg_server_create.argtypes = [P, ctypes.POINTER(jacpcg_server_config), ctypes.POINTER(P)]
+        L.jacpcg_submit.argtypes = [P, ctypes.POINTER(jacpcg_instance), ctypes.POINTER(U64)]
+        L.jacpcg_poll.argtypes = [P, U64, ctypes.POINTER(I), ctypes.POINTER(D), I]
+        L.jacpcg_server_replay.argtypes = [P, ctypes.POINTER(jacpcg_instance), I, P, P, I, P, P]
+        L.jacpcg_server_stats.argtypes = [P, ctypes.POINTER(U64), ctypes.POINTER(U64), ctypes.POINTER(D)]
+        L.jacpcg_server_destroy.argtypes = [P]
         L.jacpcg_strerror.argtypes = [I]
         L.jacpcg_strerror.restype = ctypes.c_char_p
         L.jacpcg_version.restype = ctypes.c_char_p
         for n in ("jacpcg_create", "jacpcg_precode", "jacpcg_plan_create", "jacpcg_plan_execute",
                   "jacpcg_plan_destroy", "jacpcg_plan_bytes", "jacpcg_arena_free_bytes",
-                  "jacpcg_profile_read", "jacpcg_destroy", "jacpcg_precode_noalloc"):
+                  "jacpcg_profile_read", "jacpcg_destroy", "jacpcg_precode_noalloc",
+                  "jacpcg_precode_plain", "jacpcg_server_create", "jacpcg_submit", "jacpcg_poll",
+                  "jacpcg_server_replay", "jacpcg_server_stats", "jacpcg_server_destroy"):
             getattr(L, n).restype = I
         _lib = L
         return L
@@ -148,6 +165,21 @@ def jacpcg_precode_noalloc(insts, variant=JACPCG_STANDARD, status=None, iters=No
            "jacpcg_precode_noalloc")
 
 
+def plain_workspace_bytes(max_K: int) -> int:
+    return 5 * max_K * max_K * 8 + 16 * max_K + 256
+
+
+def jacpcg_precode_plain(insts, workspace, variant=JACPCG_STANDARD, status=None, iters=None,
+                         resid=None, beta=None, stream=0) -> None:
+    """The plain FP32 per-instance comparator (see the header)."""
+    arr = _array(insts)
+    v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    _check(load().jacpcg_precode_plain(arr, len(arr), v, ctypes.c_void_p(workspace.data_ptr()),
+                                       workspace.numel() * workspace.element_size(), _ptr(status),
+                                       _ptr(iters), _ptr(resid), _ptr(beta), ctypes.c_void_p(stream)),
+           "jacpcg_precode_plain")
+
+
 def jacpcg_plan_create(ctx, insts, status=None, iters=None, resid=None, beta=None,
                        use_graph: bool = False) -> ctypes.c_void_p:
     arr = _array(insts)
@@ -191,6 +223,57 @@ def jacpcg_profile_read(ctx):
 
 def jacpcg_launch_count(ctx) -> int:
     return int(load().jacpcg_launch_count(ctx))
+
+
+def jacpcg_server_create(ctx, max_batch=256, max_inflight=4, max_queue=0, plain=False,
+                         plain_variant=JACPCG_STANDARD):
+    cfg = jacpcg_server_config(max_batch=max_batch, max_inflight=max_inflight, max_queue=max_queue,
+                               plain=int(plain), plain_variant=int(plain_variant))
+    srv = ctypes.c_void_p()
+    _check(load().jacpcg_server_create(ctx, ctypes.byref(cfg), ctypes.byref(srv)), "jacpcg_server_create")
+    return srv
+
+
+def jacpcg_submit(srv, inst: jacpcg_instance) -> int:
+    t = ctypes.c_uint64()
+    _check(load().jacpcg_submit(srv, ctypes.byref(inst), ctypes.byref(t)), "jacpcg_submit")
+    return t.value
+
+
+def jacpcg_poll(srv, ticket: int, blocking: bool = True):
+    """(request status, latency in microseconds); raises on EBUSY / ETIMEOUT."""
+    r = ctypes.c_int()
+    lat = ctypes.c_double()
+    _check(load().jacpcg_poll(srv, ctypes.c_uint64(ticket), ctypes.byref(r), ctypes.byref(lat),
+                              int(blocking)), "jacpcg_poll")
+    return r.value, lat.value
+
+
+def jacpcg_server_replay(srv, pool, which, arrival_us):
+    """Open-loop replay; returns (latency_us array, status array) as numpy."""
+    import numpy as np
+    arr = _array(pool)
+    which = np.ascontiguousarray(which, dtype=np.int32)
+    arrival = np.ascontiguousarray(arrival_us, dtype=np.float64)
+    n = len(which)
+    lat = np.zeros(n, dtype=np.float64)
+    st = np.zeros(n, dtype=np.int32)
+    _check(load().jacpcg_server_replay(srv, arr, len(arr), which.ctypes.data_as(ctypes.c_void_p),
+                                       arrival.ctypes.data_as(ctypes.c_void_p), n,
+                                       lat.ctypes.data_as(ctypes.c_void_p),
+                                       st.ctypes.data_as(ctypes.c_void_p)), "jacpcg_server_replay")
+    return lat, st
+
+
+def jacpcg_server_stats(srv):
+    a, b, m = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_double()
+    _check(load().jacpcg_server_stats(srv, ctypes.byref(a), ctypes.byref(b), ctypes.byref(m)),
+           "jacpcg_server_stats")
+    return a.value, b.value, m.value
+
+
+def jacpcg_server_destroy(srv) -> None:
+    _check(load().jacpcg_server_destroy(srv), "jacpcg_server_destroy")
 
 
 # --- torch convenience ---------------------------------------------------------
