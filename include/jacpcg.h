@@ -68,6 +68,12 @@ enum { JACPCG_STANDARD = 0, JACPCG_ALG1 = 1, JACPCG_CG = 2 };
  * The iteration always runs in FP32 with compensated dot products. */
 enum { JACPCG_FP32 = 0, JACPCG_TF32X3 = 1 };
 
+/* Storage type of H (jacpcg_instance.h_dtype).  BF16: each complex entry is
+ * two bfloat16 (re, im), 4 bytes, column-major with leading dimension ldh
+ * (entries); the values are used exactly (bfloat16 converts to FP32 and
+ * TF32 without rounding).  W, X and A are complex64 in both cases. */
+enum { JACPCG_H_C64 = 0, JACPCG_H_BF16 = 1 };
+
 /* config flags */
 enum { JACPCG_FLAG_PROFILE = 1 };   /* record per-phase CUDA events on each execute */
 
@@ -80,6 +86,10 @@ typedef struct {
     int precision;           /* JACPCG_FP32 or JACPCG_TF32X3 */
     int variant;             /* JACPCG_STANDARD, JACPCG_ALG1 or JACPCG_CG */
     int flags;               /* JACPCG_FLAG_* */
+    int refine_sweeps;       /* 0..3 iterative-refinement sweeps after the solve: R = I - A X
+                                with products and sums in FP64 on the GPU, A dX = R solved by
+                                the same FP32 iteration (the instance's max_iter and tol,
+                                relative to ||R||), X += dX */
 } jacpcg_config;
 
 typedef struct {
@@ -94,6 +104,9 @@ typedef struct {
     void *A;                 /* optional device out, complex64 K x K (ld K): H^H H + xi I */
     int max_iter;            /* T, 0 <= T <= 4096 */
     float tol;               /* > 0: stop a column once ||r|| <= tol ||b||; <= 0: exactly T steps */
+    int h_dtype;             /* JACPCG_H_C64 (0) or JACPCG_H_BF16 */
+    float *resid_hist;       /* optional device out, refine_sweeps + 1 floats: ||I - A X||_F / sqrt(K)
+                                (FP64-evaluated) before each sweep and after the last */
 } jacpcg_instance;
 
 typedef struct jacpcg_ctx jacpcg_ctx;

@@ -22,6 +22,7 @@ JACPCG_ENOTCONV, JACPCG_ENOTHPD, JACPCG_ENONFINITE, JACPCG_ETIMEOUT, JACPCG_EBUS
 JACPCG_STANDARD, JACPCG_ALG1, JACPCG_CG = 0, 1, 2
 JACPCG_FP32, JACPCG_TF32X3 = 0, 1
 JACPCG_FLAG_PROFILE = 1
+JACPCG_H_C64, JACPCG_H_BF16 = 0, 1
 VARIANTS = {"standard": JACPCG_STANDARD, "alg1": JACPCG_ALG1, "cg": JACPCG_CG}
 PRECISIONS = {"fp32": JACPCG_FP32, "tf32x3": JACPCG_TF32X3}
 
@@ -36,14 +37,16 @@ EXPORTS = ("jacpcg_create", "jacpcg_precode", "jacpcg_plan_create", "jacpcg_plan
 class jacpcg_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("max_instances", ctypes.c_int), ("max_M", ctypes.c_int),
                 ("max_K", ctypes.c_int), ("arena_bytes", ctypes.c_size_t),
-                ("precision", ctypes.c_int), ("variant", ctypes.c_int), ("flags", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("variant", ctypes.c_int), ("flags", ctypes.c_int),
+                ("refine_sweeps", ctypes.c_int)]
 
 
 class jacpcg_instance(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("K", ctypes.c_int), ("ldh", ctypes.c_int),
                 ("H", ctypes.c_void_p), ("xi", ctypes.c_double), ("power", ctypes.c_double),
                 ("W", ctypes.c_void_p), ("ldw", ctypes.c_int), ("X", ctypes.c_void_p),
-                ("A", ctypes.c_void_p), ("max_iter", ctypes.c_int), ("tol", ctypes.c_float)]
+                ("A", ctypes.c_void_p), ("max_iter", ctypes.c_int), ("tol", ctypes.c_float),
+                ("h_dtype", ctypes.c_int), ("resid_hist", ctypes.c_void_p)]
 
 
 class jacpcg_server_config(ctypes.Structure):
@@ -279,28 +282,38 @@ def jacpcg_server_destroy(srv) -> None:
 # --- torch convenience ---------------------------------------------------------
 
 def instance(H, W, xi: float, max_iter: int, tol: float = 0.0, power: float = 1.0, X=None,
-             A=None) -> jacpcg_instance:
+             A=None, resid_hist=None) -> jacpcg_instance:
     """Describe one channel held in torch tensors of device storage layout:
-    H and W are complex64 tensors of shape (K, M) (column k of the matrix is
-    row k of the tensor, i.e. column-major storage of the M x K matrix)."""
-    K, M = H.shape[-2], H.shape[-1]
-    return jacpcg_instance(M=M, K=K, ldh=H.stride(-2), H=H.data_ptr(), xi=float(xi),
+    H (complex64, or bfloat16 with a trailing (re, im) axis) and W
+    (complex64) have shape (K, M) (column k of the matrix is row k of the
+    tensor, i.e. column-major storage of the M x K matrix)."""
+    import torch
+    bf16 = H.dtype == torch.bfloat16
+    if bf16:
+        assert H.shape[-1] == 2 and H.stride(-1) == 1
+        K, M, ldh = H.shape[-3], H.shape[-2], H.stride(-3) // 2
+    else:
+        K, M, ldh = H.shape[-2], H.shape[-1], H.stride(-2)
+    return jacpcg_instance(M=M, K=K, ldh=ldh, H=H.data_ptr(), xi=float(xi),
                            power=float(power), W=W.data_ptr(), ldw=W.stride(-2),
                            X=None if X is None else X.data_ptr(),
                            A=None if A is None else A.data_ptr(), max_iter=int(max_iter),
-                           tol=float(tol))
+                           tol=float(tol), h_dtype=JACPCG_H_BF16 if bf16 else JACPCG_H_C64,
+                           resid_hist=None if resid_hist is None else resid_hist.data_ptr())
 
 
 class Precoder:
     """Owns a context; precodes batches of torch tensors on the current stream."""
 
     def __init__(self, max_instances: int, max_M: int, max_K: int, variant="standard",
-                 precision="fp32", device: int = 0, arena_bytes: int = 0, profile: bool = False):
+                 precision="fp32", device: int = 0, arena_bytes: int = 0, profile: bool = False,
+                 refine_sweeps: int = 0):
         self.cfg = jacpcg_config(device=device, max_instances=max_instances, max_M=max_M,
                                  max_K=max_K, arena_bytes=arena_bytes,
                                  precision=PRECISIONS[precision] if isinstance(precision, str) else precision,
                                  variant=VARIANTS[variant] if isinstance(variant, str) else variant,
-                                 flags=JACPCG_FLAG_PROFILE if profile else 0)
+                                 flags=JACPCG_FLAG_PROFILE if profile else 0,
+                                 refine_sweeps=int(refine_sweeps))
         self.ctx = jacpcg_create(self.cfg)
 
     def close(self):

@@ -152,6 +152,9 @@ struct jacpcg_plan {
     int graph_launches = 0;
     cudaEvent_t done = nullptr;
     bool executed = false;
+    int refine_sweeps = 0;
+    size_t res_off = 0;
+    int n_res = 0;
 };
 
 namespace {
@@ -178,14 +181,17 @@ jacpcg_status validate(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n
         if (!std::isfinite(q.xi) || q.xi < 0.0 || (q.K > q.M && !(q.xi > 0.0))) return JACPCG_EINVAL;
         if (!std::isfinite(q.power) || !std::isfinite(q.tol)) return JACPCG_EINVAL;
         if (q.max_iter < 0 || q.max_iter > 4096) return JACPCG_EINVAL;
+        if (q.h_dtype != JACPCG_H_C64 && q.h_dtype != JACPCG_H_BF16) return JACPCG_EINVAL;
+        if (q.h_dtype == JACPCG_H_BF16 && (q.ldh & 3)) return JACPCG_EINVAL;   // 16-byte columns
     }
     return JACPCG_OK;
 }
 
 // Byte layout of one plan block.
 struct Layout {
-    size_t insts, gram, tcl, pcg, hx, hxl, accum, ws, total;
-    int n_gram, n_pcg, n_hx;
+    size_t insts, gram, tcl, pcg, hx, hxl, res, accum, ws, total;
+    int n_gram, n_pcg, n_hx, n_res;
+    bool refine;
     std::vector<size_t> ws_off;   // per instance
 };
 
@@ -203,19 +209,23 @@ int n_pblocks(const jacpcg_instance &q) {
     const int per = s.CW * s.NW;
     return (q.K + per - 1) / per;
 }
-size_t inst_ws_bytes(const jacpcg_instance &q) {
+size_t inst_ws_bytes(const jacpcg_instance &q, bool refine) {
     const size_t KC = k_class(q.K);
-    return align_up(KC * KC * sizeof(float2)) * 2 + align_up(KC * sizeof(float)) +
-           align_up(n_wtiles(q) * sizeof(float));
+    size_t b = align_up(KC * KC * sizeof(float2)) * 2 + align_up(KC * sizeof(float)) +
+               align_up(n_wtiles(q) * sizeof(float));
+    if (refine) b += align_up(KC * KC * sizeof(float2)) + align_up(KC * sizeof(float));
+    return b;
 }
 
 // K classes whose Gram runs on the tensor cores at this precision
 bool gram_on_tc(int precision, int KC) { return precision == JACPCG_TF32X3 && KC == 64; }
 
-Layout make_layout(const jacpcg_instance *inst, int n) {
+Layout make_layout(const jacpcg_instance *inst, int n, bool refine) {
     Layout L{};
-    L.n_gram = L.n_pcg = L.n_hx = 0;
+    L.n_gram = L.n_pcg = L.n_hx = L.n_res = 0;
+    L.refine = refine;
     for (int i = 0; i < n; ++i) {
+        if (refine) L.n_res += inst[i].K;
         L.n_gram += n_gtiles(inst[i]);
         L.n_pcg += n_pblocks(inst[i]);
         L.n_hx += n_wtiles(inst[i]);
@@ -227,12 +237,13 @@ Layout make_layout(const jacpcg_instance *inst, int n) {
     L.pcg = o;    o += align_up(sizeof(int2) * L.n_pcg);
     L.hx = o;     o += align_up(sizeof(int4) * L.n_hx);
     L.hxl = o;    o += align_up(sizeof(int) * n);
+    L.res = o;    o += align_up(sizeof(int2) * L.n_res);
     L.accum = o;  o += align_up(sizeof(int32_t) * n) * 3;
     L.ws = o;
     L.ws_off.resize(n);
     for (int i = 0; i < n; ++i) {
         L.ws_off[i] = o;
-        o += inst_ws_bytes(inst[i]);
+        o += inst_ws_bytes(inst[i], refine);
     }
     L.total = o;
     return L;
@@ -264,7 +275,21 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
         d.xi = (float)q.xi;
         d.power = q.power > 0.0 ? (float)q.power : 1.0f;
         d.tol = q.tol;
+        d.h_bf16 = q.h_dtype == JACPCG_H_BF16;
+        if (L.refine) {
+            const size_t base = 2 * align_up((size_t)KC * KC * sizeof(float2)) + align_up(KC * sizeof(float)) +
+                                align_up(n_wtiles(q) * sizeof(float));
+            d.R = reinterpret_cast<float2 *>(w + base);
+            d.rnorm = reinterpret_cast<float *>(w + base + align_up((size_t)KC * KC * sizeof(float2)));
+            d.resid_hist = q.resid_hist;
+        }
         hi[i] = d;
+    }
+    if (L.refine) {   // residual blocks: (instance, column)
+        int2 *rb = reinterpret_cast<int2 *>(host + L.res);
+        int r = 0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < inst[i].K; ++j) rb[r++] = make_int2(i, j);
     }
     launches.clear();
     // Gram on the tensor cores: one CTA per instance
@@ -350,7 +375,7 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
                     break;
                 case Launch::PCG:
                     e = launch_pcg(l.param, ctx->cfg.variant, pl->d_insts,
-                                   static_cast<const int2 *>(list), l.count, pl->acc, s);
+                                   static_cast<const int2 *>(list), l.count, pl->acc, s, 0);
                     break;
                 case Launch::HX:
                     e = launch_hx_simt(l.param, pl->d_insts, static_cast<const int4 *>(list), l.count,
@@ -365,6 +390,25 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
             }
             if (e != cudaSuccess) return cuda_fail(ctx);
             ++nl;
+        }
+        if (phase == 1 && pl->refine_sweeps > 0) {
+            // iterative refinement: R = I - A X (FP64), A dX = R (FP32 iteration), X += dX
+            const int2 *rb = reinterpret_cast<const int2 *>(pl->dev + pl->res_off);
+            for (int sw = 0; sw <= pl->refine_sweeps; ++sw) {
+                if (launch_residual(pl->d_insts, rb, pl->n_res, s) != cudaSuccess ||
+                    launch_resid_hist(pl->d_insts, pl->n_inst, sw, s) != cudaSuccess)
+                    return cuda_fail(ctx);
+                nl += 2;
+                if (sw == pl->refine_sweeps) break;
+                for (const Launch &l : pl->launches) {
+                    if (l.kind != Launch::PCG) continue;
+                    if (launch_pcg(l.param, ctx->cfg.variant, pl->d_insts,
+                                   reinterpret_cast<const int2 *>(pl->dev + l.list_off), l.count, pl->acc, s,
+                                   1) != cudaSuccess)
+                        return cuda_fail(ctx);
+                    ++nl;
+                }
+            }
         }
         if (ev) CK(cudaEventRecord(ev[phase + 1], s));
     }
@@ -383,7 +427,8 @@ jacpcg_status make_plan(jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, int
     if (ctx->broken) return JACPCG_ECUDA;
     jacpcg_status st = validate(ctx, inst, n);
     if (st != JACPCG_OK) return st;
-    Layout L = make_layout(inst, n);
+    const bool refine = ctx->cfg.refine_sweeps > 0;
+    Layout L = make_layout(inst, n, refine);
     size_t off;
     if (!ctx->arena.alloc(L.total, &off)) return JACPCG_ENOMEM;
     jacpcg_plan *pl = new (std::nothrow) jacpcg_plan();
@@ -403,6 +448,9 @@ jacpcg_status make_plan(jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, int
         reinterpret_cast<uint32_t *>(pl->dev + L.accum + 2 * align_up(sizeof(int32_t) * n));
     pl->out = DevOut{status_dev, iters_dev, resid_dev, beta_dev};
     pl->use_graph = use_graph;
+    pl->refine_sweeps = ctx->cfg.refine_sweeps;
+    pl->res_off = L.res;
+    pl->n_res = L.n_res;
     const size_t tbytes = L.accum;   // tables occupy [0, accum)
     auto fail = [&](jacpcg_status s) {
         ctx->arena.release(pl->off, pl->bytes, nullptr);
@@ -515,6 +563,7 @@ jacpcg_status jacpcg_create(const jacpcg_config *cfg, jacpcg_ctx **out) {
         return JACPCG_EINVAL;
     if (cfg->precision != JACPCG_FP32 && cfg->precision != JACPCG_TF32X3) return JACPCG_EINVAL;
     if (cfg->variant < JACPCG_STANDARD || cfg->variant > JACPCG_CG) return JACPCG_EINVAL;
+    if (cfg->refine_sweeps < 0 || cfg->refine_sweeps > 3) return JACPCG_EINVAL;
     jacpcg_ctx *ctx = new (std::nothrow) jacpcg_ctx();
     if (!ctx) return JACPCG_ENOMEM;
     ctx->cfg = *cfg;
@@ -529,7 +578,7 @@ jacpcg_status jacpcg_create(const jacpcg_config *cfg, jacpcg_ctx **out) {
         q.M = cfg->max_M;
         q.K = cfg->max_K;
         std::vector<jacpcg_instance> v(cfg->max_instances, q);
-        bytes = 2 * make_layout(v.data(), cfg->max_instances).total;
+        bytes = 2 * make_layout(v.data(), cfg->max_instances, cfg->refine_sweeps > 0).total;
     }
     bytes = align_up(bytes);
     if (cudaMalloc(reinterpret_cast<void **>(&ctx->arena.base), bytes) != cudaSuccess) {
@@ -604,7 +653,7 @@ jacpcg_status jacpcg_plan_bytes(const jacpcg_ctx *ctx, const jacpcg_instance *in
     if (!bytes) return JACPCG_EINVAL;
     jacpcg_status st = validate(ctx, inst, n_inst);
     if (st != JACPCG_OK) return st;
-    *bytes = align_up(make_layout(inst, n_inst).total);
+    *bytes = align_up(make_layout(inst, n_inst, ctx->cfg.refine_sweeps > 0).total);
     return JACPCG_OK;
 }
 

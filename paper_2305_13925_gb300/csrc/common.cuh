@@ -31,8 +31,20 @@ struct DevInst {
     int n_wpart;          // number of W = H X tiles of this instance
     int variant;          // JACPCG_STANDARD / ALG1 / CG
     float xi, power, tol;
-    int pad0;
+    int h_bf16;           // H holds bfloat16 (re, im) pairs instead of complex64
+    float2 *R;            // workspace KC x KC: refinement residual I - A X (null without refinement)
+    float *rnorm;         // workspace KC: per-column ||R_j||^2 of the last residual
+    float *resid_hist;    // caller's optional refinement history
 };
+
+// One entry of H as complex FP32 (bfloat16 converts exactly).
+__device__ __forceinline__ float2 bf16x2_to_float2(uint32_t u) {
+    return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xFFFF0000u));
+}
+__device__ __forceinline__ float2 load_h(const float2 *H, bool bf16, size_t idx) {
+    if (bf16) return bf16x2_to_float2(__ldg(reinterpret_cast<const uint32_t *>(H) + idx));
+    return __ldg(H + idx);
+}
 
 // Per-instance results written by the kernels before finalisation.
 struct DevAccum {

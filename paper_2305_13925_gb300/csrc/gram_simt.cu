@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(256) gram_simt_kernel(const DevInst *__restric
     const DevInst &in = insts[t.x];
     const int M = in.M, K = in.K, ldh = in.ldh, KC = in.KC;
     const float2 *__restrict__ H = in.H;
+    const bool bf16 = in.h_bf16 != 0;
     const int i0 = t.y * TB, j0 = t.z * TB;
     const bool diag = (t.y == t.z);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -60,9 +61,9 @@ __global__ void __launch_bounds__(256) gram_simt_kernel(const DevInst *__restric
             const int c = e / MC, r = e % MC;
             const int m = m0 + r;
             const int ci = i0 + c, cj = j0 + c;
-            ri[q] = (m < M && ci < K) ? __ldg(H + m + (size_t)ci * ldh) : make_float2(0.f, 0.f);
+            ri[q] = (m < M && ci < K) ? load_h(H, bf16, m + (size_t)ci * ldh) : make_float2(0.f, 0.f);
             if (!diag)
-                rj[q] = (m < M && cj < K) ? __ldg(H + m + (size_t)cj * ldh) : make_float2(0.f, 0.f);
+                rj[q] = (m < M && cj < K) ? load_h(H, bf16, m + (size_t)cj * ldh) : make_float2(0.f, 0.f);
         }
     };
     const int Mloop = (i0 < K) ? M : 0;   // tiles wholly in the zero padding skip the reduction

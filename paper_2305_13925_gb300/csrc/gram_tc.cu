@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc64_kernel(const DevInst *_
             const DevInst &in = insts[list[j]];
             const int M = in.M, K = in.K, ldh = in.ldh;
             const float2 *__restrict__ H = in.H;
+            const bool bf16 = in.h_bf16 != 0;
             const int nch = (M + MCH - 1) / MCH;
             auto load = [&](int c, float4 (&buf)[2][2]) {
 #pragma unroll
@@ -109,15 +110,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc64_kernel(const DevInst *_
                     const int e = tid + 256 * q;
                     const int k = (e & 7) + 8 * (e >> 6), mq = (e >> 3) & 7;
                     const int m = c * MCH + 4 * mq;
-                    const float2 *p = H + (size_t)k * ldh + m;
-                    if (k < K && m + 3 < M) {
+                    const size_t idx = (size_t)k * ldh + m;
+                    if (k < K && m + 3 < M && !bf16) {
+                        const float2 *p = H + idx;
                         buf[q][0] = __ldg(reinterpret_cast<const float4 *>(p));
                         buf[q][1] = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+                    } else if (k < K && m + 3 < M) {   // bfloat16 pairs, 16 bytes = 4 entries
+                        const uint4 u = __ldg(reinterpret_cast<const uint4 *>(
+                            reinterpret_cast<const uint32_t *>(H) + idx));
+                        const float2 a = bf16x2_to_float2(u.x), b = bf16x2_to_float2(u.y);
+                        const float2 c2 = bf16x2_to_float2(u.z), d = bf16x2_to_float2(u.w);
+                        buf[q][0] = make_float4(a.x, a.y, b.x, b.y);
+                        buf[q][1] = make_float4(c2.x, c2.y, d.x, d.y);
                     } else {
                         float2 v[4];
 #pragma unroll
                         for (int i = 0; i < 4; ++i)
-                            v[i] = (k < K && m + i < M) ? __ldg(p + i) : make_float2(0.f, 0.f);
+                            v[i] = (k < K && m + i < M) ? load_h(H, bf16, idx + i) : make_float2(0.f, 0.f);
                         buf[q][0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
                         buf[q][1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
                     }

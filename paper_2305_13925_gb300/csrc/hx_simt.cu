@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(256) hx_simt_kernel(const DevInst *__restrict_
     const int M = in.M, K = in.K, ldh = in.ldh, KC = in.KC;
     const float2 *__restrict__ H = in.H;
     const float2 *__restrict__ X = in.X;
+    const bool bf16 = in.h_bf16 != 0;
     const int m0 = t.y * TM, j0 = t.z * TN;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(256) hx_simt_kernel(const DevInst *__restrict_
             const int e = threadIdx.x + 256 * q;
             const int kk = e / TM, mm = e % TM;
             const int m = m0 + mm, k = k0 + kk;
-            rh[q] = (m < M && k < K) ? __ldg(H + m + (size_t)k * ldh) : make_float2(0.f, 0.f);
+            rh[q] = (m < M && k < K) ? load_h(H, bf16, m + (size_t)k * ldh) : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int q = 0; q < XL; ++q) {

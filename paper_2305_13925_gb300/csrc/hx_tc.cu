@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_tc64_kernel(const DevInst *__r
             const DevInst &in = insts[list[j]];
             const int M = in.M, K = in.K, ldh = in.ldh;
             const float2 *__restrict__ H = in.H;
+            const bool bf16 = in.h_bf16 != 0;
             const float2 *__restrict__ X = in.X;   // ld 64
             // B = [Xr^T ; Xi^T], rewritten once the previous instance's MMAs are done
             if (ninst > 0 && !tc::mbar_wait(&S.bempty, (ninst - 1) & 1, WAIT_LIMIT)) {
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_tc64_kernel(const DevInst *__r
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const int k = ks * KCH + 4 * kq + i;
-                        h[q][i] = (gm < M && k < K) ? __ldg(H + gm + (size_t)k * ldh)
+                        h[q][i] = (gm < M && k < K) ? load_h(H, bf16, gm + (size_t)k * ldh)
                                                     : make_float2(0.f, 0.f);
                     }
                 }

@@ -29,9 +29,13 @@ cudaError_t launch_gram_tc64(const DevInst *insts, const int *list, int n, DevAc
 // tensor-core W = H X for the K = 64 class (3xTF32); list: instance ids
 cudaError_t launch_hx_tc64(const DevInst *insts, const int *list, int n, DevAccum acc,
                            cudaStream_t s);
-// blocks: (instance, first column)
+// blocks: (instance, first column); mode 0: A X = I, mode 1: A dX = R, X += dX
 cudaError_t launch_pcg(int KC, int variant, const DevInst *insts, const int2 *blocks,
-                       int n_blocks, DevAccum acc, cudaStream_t s);
+                       int n_blocks, DevAccum acc, cudaStream_t s, int mode = 0);
+// refinement: R = I - A X in FP64 and per-column ||R_j||^2 (blocks: (instance, column)),
+// then hist[sweep] = ||R||_F / sqrt(K) per instance
+cudaError_t launch_residual(const DevInst *insts, const int2 *blocks, int n_blocks, cudaStream_t s);
+cudaError_t launch_resid_hist(const DevInst *insts, int n_inst, int sweep, cudaStream_t s);
 // tiles: (instance, m tile, n tile, partial slot)
 cudaError_t launch_hx_simt(int TN, const DevInst *insts, const int4 *tiles, int n_tiles,
                            cudaStream_t s);

@@ -88,6 +88,7 @@ extern "C" jacpcg_status jacpcg_precode_noalloc(const jacpcg_instance *inst, int
         if (!std::isfinite(q.xi) || q.xi < 0.0 || (q.K > q.M && !(q.xi > 0.0))) return JACPCG_EINVAL;
         if (!std::isfinite(q.power) || !std::isfinite(q.tol)) return JACPCG_EINVAL;
         if (q.max_iter < 0 || q.max_iter > 4096) return JACPCG_EINVAL;
+        if (q.h_dtype != JACPCG_H_C64) return JACPCG_EINVAL;   // complex64 H only
     }
     // sizes: tables, accumulators, workspace -- all must fit the static arrays
     size_t ng = 0, np = 0, nh = 0, ws = 0;

@@ -22,7 +22,11 @@
 //     m = r' + b m;
 //   2 plain CG (variant 0 with D = I).
 // Stopping (tol > 0): a column stops before an update once
-// ||r||^2 <= tol^2 ||b||^2 (Alg. 1: ||D r||^2), ||b|| = 1 for B = I.
+// ||r||^2 <= tol^2 ||b||^2 (Alg. 1: ||D r||^2).
+// Right-hand side (mode): 0 solves A X = I_K and writes X; 1 solves
+// A dX = R for the refinement residual R of the instance's workspace and
+// adds dX to X (iterative refinement); only mode 0 reports iterations,
+// residuals and non-convergence.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -33,7 +37,7 @@ namespace {
 template <int KC, int CW, int NW, bool RESIDENT, int VAR>
 __global__ void __launch_bounds__(NW * 32) pcg_kernel(const DevInst *__restrict__ insts,
                                                       const int2 *__restrict__ blocks,
-                                                      DevAccum acc_out) {
+                                                      DevAccum acc_out, int mode) {
     constexpr int RPL = KC >= 32 ? KC / 32 : 1;  // rows per lane
     constexpr int KCH = 32;                       // A columns per streamed chunk (K = 256)
     extern __shared__ __align__(16) float2 smem[];
@@ -78,17 +82,25 @@ __global__ void __launch_bounds__(NW * 32) pcg_kernel(const DevInst *__restrict_
     float2 x[RPL][CW], r[RPL][CW], p[RPL][CW];
     float rho[CW];      // r^H z (standard / CG) or r^H r (Alg. 1)
     float res2[CW];     // squared stopping residual
+    float btol[CW];     // tol^2 ||b||^2
     bool done[CW];
     int its[CW];
 #pragma unroll
     for (int c = 0; c < CW; ++c) {
-        Comp rz = {0.f, 0.f}, rs = {0.f, 0.f};
+        Comp rz = {0.f, 0.f}, rs = {0.f, 0.f}, bb = {0.f, 0.f};
 #pragma unroll
         for (int i = 0; i < RPL; ++i) {
-            const float b = (rvalid[i] && row[i] == col[c]) ? 1.f : 0.f;   // B = I
+            float2 b = make_float2(0.f, 0.f);
+            if (mode == 0) {
+                if (rvalid[i] && row[i] == col[c]) b.x = 1.f;               // B = I
+            } else if (rvalid[i] && cvalid[c]) {
+                b = in.R[row[i] + (size_t)col[c] * KC];                       // B = R
+            }
+            comp_fma(bb, b.x, b.x);
+            comp_fma(bb, b.y, b.y);
             x[i][c] = make_float2(0.f, 0.f);
-            r[i][c] = make_float2(VAR == 1 ? dv[i] * b : b, 0.f);
-            p[i][c] = make_float2(dv[i] * b, 0.f);     // z = D^{-1} r (standard, CG); m = r (Alg. 1)
+            r[i][c] = VAR == 1 ? make_float2(dv[i] * b.x, dv[i] * b.y) : b;
+            p[i][c] = make_float2(dv[i] * b.x, dv[i] * b.y);   // z = D^{-1} r (standard, CG); m = r (Alg. 1)
             const float2 z = make_float2(dv[i] * r[i][c].x, dv[i] * r[i][c].y);
             if (VAR == 1) {
                 comp_fma(rz, r[i][c].x, r[i][c].x);
@@ -104,8 +116,10 @@ __global__ void __launch_bounds__(NW * 32) pcg_kernel(const DevInst *__restrict_
         }
         rz = comp_warp_allreduce(rz);
         rs = comp_warp_allreduce(rs);
+        bb = comp_warp_allreduce(bb);
         rho[c] = rz.s + rz.c;
         res2[c] = rs.s + rs.c;
+        btol[c] = tol2 * (bb.s + bb.c);
         done[c] = !cvalid[c];
         its[c] = 0;
     }
@@ -119,7 +133,7 @@ __global__ void __launch_bounds__(NW * 32) pcg_kernel(const DevInst *__restrict_
         bool any = false;
 #pragma unroll
         for (int c = 0; c < CW; ++c) {
-            if (!done[c] && tol2 > 0.f && res2[c] <= tol2) done[c] = true;
+            if (!done[c] && tol2 > 0.f && res2[c] <= btol[c]) done[c] = true;
             any |= !done[c];
         }
         if (RESIDENT) {
@@ -303,10 +317,17 @@ __global__ void __launch_bounds__(NW * 32) pcg_kernel(const DevInst *__restrict_
         if (!cvalid[c]) continue;
 #pragma unroll
         for (int i = 0; i < RPL; ++i) {
-            if (row[i] < KC) in.X[row[i] + (size_t)col[c] * KC] = x[i][c];
-            if (in.Xout && rvalid[i]) in.Xout[row[i] + (size_t)col[c] * K] = x[i][c];
+            if (row[i] >= KC) continue;
+            float2 v = x[i][c];
+            if (mode == 1) {
+                const float2 o = in.X[row[i] + (size_t)col[c] * KC];
+                v = make_float2(o.x + v.x, o.y + v.y);
+            }
+            in.X[row[i] + (size_t)col[c] * KC] = v;
+            if (in.Xout && rvalid[i]) in.Xout[row[i] + (size_t)col[c] * K] = v;
         }
     }
+    if (mode != 0) return;
     int itmax = 0;
     float resmax = 0.f;
     bool notconv = false;
@@ -315,7 +336,7 @@ __global__ void __launch_bounds__(NW * 32) pcg_kernel(const DevInst *__restrict_
         if (!cvalid[c]) continue;
         itmax = max(itmax, its[c]);
         resmax = fmaxf(resmax, sqrtf(fmaxf(res2[c], 0.f)));
-        if (tol2 > 0.f && !(res2[c] <= tol2)) notconv = true;
+        if (tol2 > 0.f && !(res2[c] <= btol[c])) notconv = true;
     }
     if (lane == 0) {
         if (itmax > 0) atomicMax(acc_out.iters + blk.x, itmax);
@@ -327,7 +348,7 @@ __global__ void __launch_bounds__(NW * 32) pcg_kernel(const DevInst *__restrict_
 
 template <int KC, int CW, int NW, bool RES>
 cudaError_t launch_cfg(int variant, const DevInst *insts, const int2 *blocks, int n_blocks,
-                       DevAccum acc, cudaStream_t s) {
+                       DevAccum acc, cudaStream_t s, int mode) {
     constexpr int KCH = 32;
     const size_t smem = sizeof(float2) * ((RES ? KC * KC : 2 * KC * KCH) + (size_t)NW * KC * CW);
     cudaError_t e = cudaSuccess;
@@ -336,7 +357,7 @@ cudaError_t launch_cfg(int variant, const DevInst *insts, const int2 *blocks, in
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return;
         }
-        kern<<<n_blocks, NW * 32, smem, s>>>(insts, blocks, acc);
+        kern<<<n_blocks, NW * 32, smem, s>>>(insts, blocks, acc, mode);
         e = cudaGetLastError();
     };
     switch (variant) {
@@ -362,15 +383,15 @@ PcgShape pcg_shape(int KC) {
 }
 
 cudaError_t launch_pcg(int KC, int variant, const DevInst *insts, const int2 *blocks,
-                       int n_blocks, DevAccum acc, cudaStream_t s) {
+                       int n_blocks, DevAccum acc, cudaStream_t s, int mode) {
     if (n_blocks <= 0) return cudaSuccess;
     switch (KC) {
-        case 8: return launch_cfg<8, 4, 2, true>(variant, insts, blocks, n_blocks, acc, s);
-        case 16: return launch_cfg<16, 4, 4, true>(variant, insts, blocks, n_blocks, acc, s);
-        case 32: return launch_cfg<32, 4, 8, true>(variant, insts, blocks, n_blocks, acc, s);
-        case 64: return launch_cfg<64, 4, 16, true>(variant, insts, blocks, n_blocks, acc, s);
-        case 128: return launch_cfg<128, 4, 8, true>(variant, insts, blocks, n_blocks, acc, s);
-        case 256: return launch_cfg<256, 2, 8, false>(variant, insts, blocks, n_blocks, acc, s);
+        case 8: return launch_cfg<8, 4, 2, true>(variant, insts, blocks, n_blocks, acc, s, mode);
+        case 16: return launch_cfg<16, 4, 4, true>(variant, insts, blocks, n_blocks, acc, s, mode);
+        case 32: return launch_cfg<32, 4, 8, true>(variant, insts, blocks, n_blocks, acc, s, mode);
+        case 64: return launch_cfg<64, 4, 16, true>(variant, insts, blocks, n_blocks, acc, s, mode);
+        case 128: return launch_cfg<128, 4, 8, true>(variant, insts, blocks, n_blocks, acc, s, mode);
+        case 256: return launch_cfg<256, 2, 8, false>(variant, insts, blocks, n_blocks, acc, s, mode);
         default: return cudaErrorInvalidValue;
     }
 }

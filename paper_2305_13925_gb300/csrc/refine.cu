@@ -1,0 +1,73 @@
+// refine.cu -- the true residual of iterative refinement, R = I - A X, with
+// every product and sum in FP64 (A and X are FP32, so each product is exact
+// in FP64), and its per-instance norm history.  No passage of the paper: the
+// paper solves Eq. 16 by the iteration alone; refinement is the system
+// layer that wins back accuracy lost to FP32 and to bfloat16 inputs.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace jacpcg {
+
+namespace {
+
+// One block per (instance, column j), one thread per row i (K <= 256).
+__global__ void __launch_bounds__(256) residual_kernel(const DevInst *__restrict__ insts,
+                                                       const int2 *__restrict__ blocks) {
+    __shared__ double red[256];
+    const int2 b = blocks[blockIdx.x];
+    const DevInst &in = insts[b.x];
+    const int K = in.K, KC = in.KC, j = b.y, i = threadIdx.x;
+    const float2 *__restrict__ A = in.A;
+    const float2 *__restrict__ X = in.X;
+    double re = 0.0, im = 0.0;
+    if (i < K) {
+        for (int k = 0; k < K; ++k) {
+            const float2 a = A[i + (size_t)k * KC];
+            const float2 x = X[k + (size_t)j * KC];
+            re = fma((double)a.x, (double)x.x, re);
+            re = fma(-(double)a.y, (double)x.y, re);
+            im = fma((double)a.x, (double)x.y, im);
+            im = fma((double)a.y, (double)x.x, im);
+        }
+        re = (i == j ? 1.0 : 0.0) - re;
+        im = -im;
+    }
+    if (i < KC) in.R[i + (size_t)j * KC] = make_float2((float)re, (float)im);
+    red[i] = re * re + im * im;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (i < o) red[i] += red[i + o];
+        __syncthreads();
+    }
+    if (i == 0) in.rnorm[j] = (float)red[0];
+}
+
+// One warp per instance: fixed-order sum of the column norms.
+__global__ void resid_hist_kernel(const DevInst *__restrict__ insts, int n_inst, int sweep) {
+    const int inst = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (inst >= n_inst) return;
+    const DevInst &in = insts[inst];
+    if (!in.resid_hist) return;
+    double s = 0.0;
+    for (int j = lane; j < in.K; j += 32) s += (double)in.rnorm[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) in.resid_hist[sweep] = (float)sqrt(s / in.K);
+}
+
+}  // namespace
+
+cudaError_t launch_residual(const DevInst *insts, const int2 *blocks, int n_blocks, cudaStream_t s) {
+    if (n_blocks <= 0) return cudaSuccess;
+    residual_kernel<<<n_blocks, 256, 0, s>>>(insts, blocks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resid_hist(const DevInst *insts, int n_inst, int sweep, cudaStream_t s) {
+    if (n_inst <= 0) return cudaSuccess;
+    resid_hist_kernel<<<(n_inst + 7) / 8, 256, 0, s>>>(insts, n_inst, sweep);
+    return cudaGetLastError();
+}
+
+}  // namespace jacpcg

@@ -1,0 +1,59 @@
+"""Mixed precision on the GPU: H stored as bfloat16 (values used exactly),
+and iterative refinement with the true residual I - A X evaluated in FP64.
+The oracle always runs on the bfloat16-rounded channel (upcast exactly)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2305_13925_gb300 import channels as C
+
+from gpu_util import rel_fro, run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_13925_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tf32x3"])
+def test_bf16_storage_fixed_T_parity(precision):
+    """bfloat16 H, T = 6: W matches the oracle on the same rounded channel
+    within 1e-5 (K = 64 exercises the tensor path, K = 17 and 128 the SIMT one)."""
+    H, xi = C.generate_batch("batched_1024x64", 6, 1, dtype="bf16")
+    insts = list(zip(H, xi))
+    for spec_k, spec_m in ((17, 256), (128, 512)):
+        spec = C.ChannelSpec(M=spec_m, S=4, K=spec_k, r=(0.5, 0.5), n_vis=(2, 3), snr_db=(10.0,))
+        i = C.generate_instance(spec, 3, spec_k, dtype="bf16")
+        insts.append((i.H, i.xi))
+    out = run([h for h, _ in insts], [x for _, x in insts], T=6, precision=precision, bf16=True)
+    for k, (h, x) in enumerate(insts):
+        ref = O.precode(h, x, "standard", max_iter=6)
+        assert out["status"][k] == 0
+        assert rel_fro(out["W"][k], ref["W"]) <= 1e-5, (k, rel_fro(out["W"][k], ref["W"]))
+
+
+@pytest.mark.parametrize("shape", [("xl_4096x256", 2), ("batched_1024x64", 4)])
+def test_refinement_reaches_direct_rzf(shape):
+    """A loose first solve (tol 1e-3) then three refinement sweeps: the FP64
+    residual history decreases, and W ends within 1e-5 of the direct RZF of
+    the bfloat16 channel; without refinement it does not."""
+    preset, n = shape
+    H, xi = C.generate_batch(preset, n, 2, dtype="bf16")
+    before = run(list(H), list(xi), T=60, tol=1e-3, bf16=True, precision="tf32x3")
+    after = run(list(H), list(xi), T=60, tol=1e-3, bf16=True, precision="tf32x3", refine_sweeps=3,
+                want_hist=True)
+    for k in range(n):
+        Wd, _, st = O.rzf_direct(H[k], xi[k])
+        e0 = rel_fro(before["W"][k], Wd)
+        e1 = rel_fro(after["W"][k], Wd)
+        hist = after["hist"][k]
+        assert e0 > 1e-5 and e1 <= 1e-5, (k, e0, e1, hist)
+        # the first sweep removes most of the residual; later ones reach the FP32 floor of X
+        assert hist[1] < hist[0] / 10 and hist[-1] <= hist[1] * 1.5, hist
+        assert after["status"][k] == 0
