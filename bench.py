@@ -60,7 +60,7 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--plain-sample", type=int, default=64)
-    ap.add_argument("--workload", default="batched", choices=["batched", "serving"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "serving", "single", "xl", "ragged"])
     ap.add_argument("--rates", default="5000,20000,50000,100000,200000")
     ap.add_argument("--trace-seconds", type=float, default=0.5)
     ap.add_argument("--pool", type=int, default=512)
@@ -270,7 +270,7 @@ def run_serving(args):
     import numpy as np
     import torch
     from paper_2305_13925_gb300 import binding, build, channels as C
-    insts = C.generate_ragged(args.pool, 3)
+    insts = C.generate_ragged(args.pool, 3, workers=None)
     build.build()
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     Hd, Wd, descs = [], [], []
@@ -305,7 +305,9 @@ def run_serving(args):
                             "p50_us": float(np.median(l)) if len(l) else None,
                             "p99_us": float(l[min(len(l) - 1, int(0.99 * len(l)))]) if len(l) else None,
                             "deadline_miss_rate": float(np.mean(lat > 1000.0)),
-                            "status_ok": int(ok.sum())})
+                            "status_ok": int(ok.sum()),
+                            "status_counts": {int(k): int(v) for k, v in
+                                              zip(*np.unique(st, return_counts=True))}})
         finally:
             binding.jacpcg_server_destroy(srv)
             prec.close()
@@ -318,6 +320,179 @@ def run_serving(args):
             "traces": out}
     print(json.dumps(line))
     return 0
+
+
+def _line(cfg, value, extra):
+    d = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+         "dtype": "f32", "data": "synthetic", "config": cfg}
+    d.update(extra)
+    print(json.dumps(d))
+    return 0
+
+
+def run_single(args):
+    """One channel (M = 256 as 4 x 64, K = 16, 10 dB, T = 8): latency of one
+    precoder through jacpcg_precode, a plan replayed as a CUDA graph, and the
+    plain comparator; accuracy against the oracle and the direct RZF."""
+    import numpy as np
+    import torch
+    from oracle import oracle as O
+    from paper_2305_13925_gb300 import binding, build, channels as C
+    build.build()
+    inst = C.generate_instance(C.PRESETS["single_256x16"], 0, 0)
+    H = torch.from_numpy(np.ascontiguousarray(inst.H.T).astype(np.complex64)).cuda()
+    W = torch.empty_like(H)
+    st = torch.empty(1, dtype=torch.int32, device="cuda")
+    d = [binding.instance(H, W, inst.xi, 8)]
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    res = {}
+    with torch.cuda.stream(stream):
+        prec = binding.Precoder(max_instances=1, max_M=256, max_K=16, precision=args.precision)
+        plan = prec.plan(d, st, use_graph=True)
+        ws = torch.empty(binding.plain_workspace_bytes(16), dtype=torch.uint8, device="cuda")
+        calls = {"precode": lambda: binding.jacpcg_precode(prec.ctx, d, st, None, None, None, sh),
+                 "graph": lambda: binding.jacpcg_plan_execute(plan, sh),
+                 "plain": lambda: binding.jacpcg_precode_plain(d, ws, "standard", st, stream=sh)}
+        for name, fn in calls.items():
+            for _ in range(20):
+                fn()
+            torch.cuda.synchronize()
+            lat = []
+            for _ in range(args.steps):
+                t0 = time.perf_counter()
+                fn()
+                stream.synchronize()
+                lat.append((time.perf_counter() - t0) * 1e6)
+            lat.sort()
+            res[name] = {"p50_us": lat[len(lat) // 2], "p99_us": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                         "what": "host call to stream synchronised, one precoder"}
+        binding.jacpcg_plan_destroy(plan)
+        prec.close()
+    Wg = W.T.cpu().numpy().astype(np.complex128)
+    ref = O.precode(inst.H, inst.xi, "standard", max_iter=8)["W"]
+    Wd, _, _ = O.rzf_direct(inst.H, inst.xi)
+    err = float(np.linalg.norm(Wg - ref) / np.linalg.norm(ref))
+    cfg = {"workload": "single: M=256 (4x64), K=16, r=0.5, 2 of 4 subarrays visible, SNR 10 dB, "
+                       "xi=K/SNR, T=8, seed 0", "precision": args.precision}
+    return _line(cfg, 1e6 / res["graph"]["p50_us"], {
+        "latency": res, "accuracy": {"rel_err_W_vs_oracle": err,
+                                     "rel_err_W_vs_direct_rzf": float(np.linalg.norm(Wg - Wd) / np.linalg.norm(Wd))},
+        "speedup_vs_plain_p50": res["plain"]["p50_us"] / res["graph"]["p50_us"]})
+
+
+def run_xl(args):
+    """256 channels of M = 4096 (16 x 256), K = 256, H stored as bfloat16,
+    tolerance 1e-5, three refinement sweeps with the FP64 residual; error
+    against the direct RZF of the bfloat16 channel before and after."""
+    import numpy as np
+    import torch
+    from oracle import oracle as O
+    from paper_2305_13925_gb300 import binding, build, channels as C
+    n = min(args.n_inst, 256)
+    Hst, xi = C.generate_batch_device_layout("xl_4096x256", n, 2, dtype="bf16")
+    build.build()
+    K, M = Hst.shape[1], Hst.shape[2]
+    Hc = torch.from_numpy(Hst)
+    Hb = torch.view_as_real(Hc).to(torch.bfloat16).cuda()          # (n, K, M, 2), exact
+    out = {}
+    for sweeps, fp64 in ((0, False), (3, False), (3, True)):
+        W = torch.empty((n, K, M), dtype=torch.complex64, device="cuda")
+        st = torch.empty(n, dtype=torch.int32, device="cuda")
+        it = torch.empty(n, dtype=torch.int32, device="cuda")
+        hist = torch.full((n, sweeps + 1), -1.0, device="cuda")
+        prec = binding.Precoder(max_instances=n, max_M=M, max_K=K, precision=args.precision,
+                                refine_sweeps=sweeps, profile=True, refine_fp64=fp64)
+        d = [binding.instance(Hb[i], W[i], float(xi[i]), 100, 1e-5, resid_hist=hist[i]) for i in range(n)]
+        arr = (binding.jacpcg_instance * n)(*d)
+        s = torch.cuda.current_stream()
+        for _ in range(2):
+            binding.jacpcg_precode(prec.ctx, arr, st, it, None, None, s.cuda_stream)
+        torch.cuda.synchronize()
+        binding.jacpcg_profile_read(prec.ctx)
+        steps = max(3, min(args.steps, 10))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(steps):
+            binding.jacpcg_precode(prec.ctx, arr, st, it, None, None, s.cuda_stream)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        ph, nex, _ = binding.jacpcg_profile_read(prec.ctx)
+        prec.close()
+        out[(sweeps, fp64)] = {"ms_per_step": ms, "precoders_per_s": n / (ms / 1e3),
+                       "phase_ms": [round(v / max(nex, 1), 3) for v in ph],
+                       "iters_max": int(it.max().item()), "status_ok": int((st == 0).sum().item()),
+                       "resid_hist_median": np.median(hist.cpu().numpy(), axis=0).tolist(), "W": W}
+    sample = list(range(0, n, max(1, n // 4)))[:4]
+    keys = list(out.keys())
+    errs = {k: [] for k in keys}
+    for i in sample:
+        Hi = Hst[i].T.astype(np.complex128)
+        Wd, _, _ = O.rzf_direct(Hi, xi[i])
+        for k in keys:
+            Wg = out[k]["W"][i].T.cpu().numpy().astype(np.complex128)
+            errs[k].append(float(np.linalg.norm(Wg - Wd) / np.linalg.norm(Wd)))
+    for k in keys:
+        out[k].pop("W")
+    cfg = {"workload": f"xl: {n} channels, M=4096 (16x256), K=256, H bfloat16, tol 1e-5, max 100 "
+                       "iterations, refinement with FP64 residual", "precision": args.precision}
+    return _line(cfg, out[(3, False)]["precoders_per_s"], {
+        "no_refinement": out[(0, False)], "refine_3_sweeps_dot2": out[(3, False)],
+        "refine_3_sweeps_fp64": out[(3, True)],
+        "error_vs_direct_rzf": {"sample": sample, "before_refinement": errs[(0, False)],
+                                "after_refinement_dot2": errs[(3, False)],
+                                "after_refinement_fp64": errs[(3, True)], "bar": 1e-5}})
+
+
+def run_ragged(args):
+    """1024 channels with K uniform over {8..256} and M over {256..4096},
+    tolerance 1e-5: the whole ragged batch as one plan replayed as one CUDA
+    graph."""
+    import numpy as np
+    import torch
+    from paper_2305_13925_gb300 import binding, build, channels as C
+    n = min(args.n_inst, 1024)
+    insts = C.generate_ragged(n, 3, workers=None)
+    build.build()
+    Hd, Wd, d = [], [], []
+    for i in insts:
+        h = torch.from_numpy(np.ascontiguousarray(i.H.T).astype(np.complex64)).cuda()
+        w = torch.empty_like(h)
+        Hd.append(h)
+        Wd.append(w)
+        d.append(binding.instance(h, w, i.xi, 64, 1e-5))
+    st = torch.empty(n, dtype=torch.int32, device="cuda")
+    it = torch.empty(n, dtype=torch.int32, device="cuda")
+    prec = binding.Precoder(max_instances=n, max_M=4096, max_K=256, precision=args.precision)
+    s = torch.cuda.Stream()
+    t_tune = time.perf_counter()
+    tuning = binding.jacpcg_autotune(prec.ctx, d, s.cuda_stream)
+    t_tune = time.perf_counter() - t_tune
+    plan = prec.plan(d, st, it, use_graph=True)
+    for _ in range(3):
+        binding.jacpcg_plan_execute(plan, s.cuda_stream)
+    torch.cuda.synchronize()
+    steps = max(3, min(args.steps, 20))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(steps):
+        binding.jacpcg_plan_execute(plan, s.cuda_stream)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    launches = binding.jacpcg_launch_count(prec.ctx)
+    binding.jacpcg_plan_destroy(plan)
+    prec.close()
+    sv = st.cpu().numpy()
+    from collections import Counter
+    ks = Counter(i.H.shape[1] for i in insts)
+    cfg = {"workload": f"ragged: {n} channels, K uniform over {{8,...,256}}, M over {{256,...,4096}}, "
+                       "S=8, tol 1e-5, max 64 iterations, one plan replayed as one CUDA graph, seed 3",
+           "precision": args.precision, "k_mix": dict(sorted(ks.items()))}
+    return _line(cfg, n / (ms / 1e3), {"ms_per_step": ms, "status_counts": {int(k): int(v) for k, v in Counter(sv.tolist()).items()},
+                                      "iters_max": int(it.max().item()), "gpu_launches_total": launches,
+                                      "autotune": {"seconds": round(t_tune, 2), "table": tuning}})
 
 
 def run_reference(args):
@@ -358,6 +533,12 @@ def main():
         return run_reference(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "single":
+        return run_single(args)
+    if args.workload == "xl":
+        return run_xl(args)
+    if args.workload == "ragged":
+        return run_ragged(args)
 
     import numpy as np
     from paper_2305_13925_gb300 import channels as C

@@ -74,6 +74,13 @@ enum { JACPCG_FP32 = 0, JACPCG_TF32X3 = 1 };
  * TF32 without rounding).  W, X and A are complex64 in both cases. */
 enum { JACPCG_H_C64 = 0, JACPCG_H_BF16 = 1 };
 
+/* Evaluation of the refinement residual R = I - A X (jacpcg_config.refine_residual).
+ * DOT2: FP32 error-free transformations (TwoProduct by FMA + TwoSum, the
+ * compensated dot product of Ogita, Rump and Oishi, 2005), as accurate as
+ * twice the working precision, on the FP32 pipes.  FP64: products and sums
+ * in FP64 (exact products of the FP32 operands); slower on this GPU. */
+enum { JACPCG_RESID_DOT2 = 0, JACPCG_RESID_FP64 = 1 };
+
 /* config flags */
 enum { JACPCG_FLAG_PROFILE = 1 };   /* record per-phase CUDA events on each execute */
 
@@ -87,9 +94,10 @@ typedef struct {
     int variant;             /* JACPCG_STANDARD, JACPCG_ALG1 or JACPCG_CG */
     int flags;               /* JACPCG_FLAG_* */
     int refine_sweeps;       /* 0..3 iterative-refinement sweeps after the solve: R = I - A X
-                                with products and sums in FP64 on the GPU, A dX = R solved by
-                                the same FP32 iteration (the instance's max_iter and tol,
-                                relative to ||R||), X += dX */
+                                evaluated as refine_residual says, A dX = R solved by the same
+                                FP32 iteration (the instance's max_iter and tol, relative to
+                                ||R||), X += dX */
+    int refine_residual;     /* JACPCG_RESID_DOT2 (default) or JACPCG_RESID_FP64 */
 } jacpcg_config;
 
 typedef struct {
@@ -160,6 +168,26 @@ jacpcg_status jacpcg_arena_free_bytes(const jacpcg_ctx *ctx, size_t *bytes);
  * the last execute launched.  Resets the record. */
 jacpcg_status jacpcg_profile_read(jacpcg_ctx *ctx, float ms[4], int *n_executes,
                                   int *launches_per_execute);
+
+/* ---- autotuning --------------------------------------------------------
+ * The iteration kernel has several launch shapes per K class (columns per
+ * warp x warps per CTA; all give bit-identical results).  jacpcg_autotune
+ * times every candidate on the instances of each K class present in
+ * inst[0..n) (a plan of that class alone, 2 warm-up and 5 timed executes,
+ * CUDA events on `stream`, which it synchronises) and keeps the fastest in
+ * the context for later plans and calls.  If table is not NULL it receives a
+ * NUL-terminated JSON object (truncated to table_cap bytes):
+ *   {"<K class>": {"shape": i, "cols_per_warp": c, "warps_per_cta": w,
+ *                  "instances": n, "ms_per_candidate": [...]}, ...}
+ * which a caller can persist and replay with jacpcg_set_shape.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+jacpcg_status jacpcg_autotune(jacpcg_ctx *ctx, const jacpcg_instance *inst, int n_inst,
+                              void *stream, char *table, size_t table_cap);
+/* Choose candidate `shape` (0 = default) for K class k_class (8, 16, ..., 256). */
+jacpcg_status jacpcg_set_shape(jacpcg_ctx *ctx, int k_class, int shape);
+/* Current shape of a K class, the number of candidates, and its geometry. */
+jacpcg_status jacpcg_get_shape(const jacpcg_ctx *ctx, int k_class, int *shape, int *n_shapes,
+                               int *cols_per_warp, int *warps_per_cta);
 
 /* Kernels launched by this context since creation (all entry points). */
 int64_t jacpcg_launch_count(const jacpcg_ctx *ctx);

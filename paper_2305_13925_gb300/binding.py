@@ -23,6 +23,7 @@ JACPCG_STANDARD, JACPCG_ALG1, JACPCG_CG = 0, 1, 2
 JACPCG_FP32, JACPCG_TF32X3 = 0, 1
 JACPCG_FLAG_PROFILE = 1
 JACPCG_H_C64, JACPCG_H_BF16 = 0, 1
+JACPCG_RESID_DOT2, JACPCG_RESID_FP64 = 0, 1
 VARIANTS = {"standard": JACPCG_STANDARD, "alg1": JACPCG_ALG1, "cg": JACPCG_CG}
 PRECISIONS = {"fp32": JACPCG_FP32, "tf32x3": JACPCG_TF32X3}
 
@@ -31,14 +32,15 @@ EXPORTS = ("jacpcg_create", "jacpcg_precode", "jacpcg_plan_create", "jacpcg_plan
            "jacpcg_profile_read", "jacpcg_launch_count", "jacpcg_destroy", "jacpcg_strerror",
            "jacpcg_version", "jacpcg_precode_noalloc", "jacpcg_precode_plain",
            "jacpcg_server_create", "jacpcg_submit", "jacpcg_poll", "jacpcg_server_replay",
-           "jacpcg_server_stats", "jacpcg_server_destroy")
+           "jacpcg_server_stats", "jacpcg_server_destroy", "jacpcg_autotune", "jacpcg_set_shape",
+           "jacpcg_get_shape")
 
 
 class jacpcg_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("max_instances", ctypes.c_int), ("max_M", ctypes.c_int),
                 ("max_K", ctypes.c_int), ("arena_bytes", ctypes.c_size_t),
                 ("precision", ctypes.c_int), ("variant", ctypes.c_int), ("flags", ctypes.c_int),
-                ("refine_sweeps", ctypes.c_int)]
+                ("refine_sweeps", ctypes.c_int), ("refine_residual", ctypes.c_int)]
 
 
 class jacpcg_instance(ctypes.Structure):
@@ -97,6 +99,10 @@ def load(path: pathlib.Path | str | None = None):
         L.jacpcg_server_replay.argtypes = [P, ctypes.POINTER(jacpcg_instance), I, P, P, I, P, P]
         L.jacpcg_server_stats.argtypes = [P, ctypes.POINTER(U64), ctypes.POINTER(U64), ctypes.POINTER(D)]
         L.jacpcg_server_destroy.argtypes = [P]
+        L.jacpcg_autotune.argtypes = [P, ctypes.POINTER(jacpcg_instance), I, P, ctypes.c_char_p, S]
+        L.jacpcg_set_shape.argtypes = [P, I, I]
+        L.jacpcg_get_shape.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
+                                       ctypes.POINTER(I)]
         L.jacpcg_strerror.argtypes = [I]
         L.jacpcg_strerror.restype = ctypes.c_char_p
         L.jacpcg_version.restype = ctypes.c_char_p
@@ -104,7 +110,8 @@ def load(path: pathlib.Path | str | None = None):
                   "jacpcg_plan_destroy", "jacpcg_plan_bytes", "jacpcg_arena_free_bytes",
                   "jacpcg_profile_read", "jacpcg_destroy", "jacpcg_precode_noalloc",
                   "jacpcg_precode_plain", "jacpcg_server_create", "jacpcg_submit", "jacpcg_poll",
-                  "jacpcg_server_replay", "jacpcg_server_stats", "jacpcg_server_destroy"):
+                  "jacpcg_server_replay", "jacpcg_server_stats", "jacpcg_server_destroy",
+                  "jacpcg_autotune", "jacpcg_set_shape", "jacpcg_get_shape"):
             getattr(L, n).restype = I
         _lib = L
         return L
@@ -228,6 +235,42 @@ def jacpcg_launch_count(ctx) -> int:
     return int(load().jacpcg_launch_count(ctx))
 
 
+def jacpcg_autotune(ctx, insts, stream=0) -> dict:
+    """Tune the iteration launch shape per K class on these instances; returns the table."""
+    import json
+    arr = _array(insts)
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(load().jacpcg_autotune(ctx, arr, len(arr), ctypes.c_void_p(stream), buf, len(buf)),
+           "jacpcg_autotune")
+    return json.loads(buf.value.decode())
+
+
+def jacpcg_set_shape(ctx, k_class: int, shape: int) -> None:
+    _check(load().jacpcg_set_shape(ctx, int(k_class), int(shape)), "jacpcg_set_shape")
+
+
+def jacpcg_get_shape(ctx, k_class: int):
+    """(shape, number of candidates, columns per warp, warps per CTA)."""
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(load().jacpcg_get_shape(ctx, int(k_class), *[ctypes.byref(x) for x in v]), "jacpcg_get_shape")
+    return tuple(x.value for x in v)
+
+
+def save_tuning(ctx, path) -> None:
+    """Persist the context's chosen shapes as JSON {k_class: shape}."""
+    import json
+    table = {str(k): jacpcg_get_shape(ctx, k)[0] for k in (8, 16, 32, 64, 128, 256)}
+    with open(path, "w") as f:
+        json.dump(table, f)
+
+
+def load_tuning(ctx, path) -> None:
+    import json
+    with open(path) as f:
+        for k, v in json.load(f).items():
+            jacpcg_set_shape(ctx, int(k), int(v["shape"] if isinstance(v, dict) else v))
+
+
 def jacpcg_server_create(ctx, max_batch=256, max_inflight=4, max_queue=0, plain=False,
                          plain_variant=JACPCG_STANDARD):
     cfg = jacpcg_server_config(max_batch=max_batch, max_inflight=max_inflight, max_queue=max_queue,
@@ -307,13 +350,14 @@ class Precoder:
 
     def __init__(self, max_instances: int, max_M: int, max_K: int, variant="standard",
                  precision="fp32", device: int = 0, arena_bytes: int = 0, profile: bool = False,
-                 refine_sweeps: int = 0):
+                 refine_sweeps: int = 0, refine_fp64: bool = False):
         self.cfg = jacpcg_config(device=device, max_instances=max_instances, max_M=max_M,
                                  max_K=max_K, arena_bytes=arena_bytes,
                                  precision=PRECISIONS[precision] if isinstance(precision, str) else precision,
                                  variant=VARIANTS[variant] if isinstance(variant, str) else variant,
                                  flags=JACPCG_FLAG_PROFILE if profile else 0,
-                                 refine_sweeps=int(refine_sweeps))
+                                 refine_sweeps=int(refine_sweeps),
+                                 refine_residual=JACPCG_RESID_FP64 if refine_fp64 else JACPCG_RESID_DOT2)
         self.ctx = jacpcg_create(self.cfg)
 
     def close(self):

@@ -230,9 +230,28 @@ def ragged_spec(seed: int, inst: int) -> ChannelSpec:
     return ChannelSpec(M=M, S=8, K=K, r=(0.3, 0.9), n_vis=(2, 6), snr_db=(0.0, 10.0, 20.0))
 
 
+def _ragged_chunk(args):
+    seed, a, b, dtype, k_set, m_set = args
+    return generate_ragged(b - a, seed, a, dtype, k_set, m_set, workers=1)
+
+
 def generate_ragged(n: int, seed: int, first: int = 0, dtype: str = "complex64",
-                    k_set: Sequence[int] | None = None, m_set: Sequence[int] | None = None):
-    """Ragged batch: list of Instance with per-instance (M, K)."""
+                    k_set: Sequence[int] | None = None, m_set: Sequence[int] | None = None,
+                    workers: int | None = 1):
+    """Ragged batch: list of Instance with per-instance (M, K).  workers > 1
+    (or None for the core count) generates in spawned processes (call before
+    any GPU work); the result does not depend on the worker count."""
+    import os
+    if workers is None:
+        workers = min(16, os.cpu_count() or 1)
+    if workers > 1 and n >= 16:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        chunks = [(seed, first + i * n // (4 * workers), first + (i + 1) * n // (4 * workers), dtype,
+                   k_set, m_set) for i in range(4 * workers)]
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            parts = list(ex.map(_ragged_chunk, [c for c in chunks if c[2] > c[1]]))
+        return [inst for part in parts for inst in part]
     out = []
     for i in range(n):
         spec = ragged_spec(seed, first + i)
@@ -312,14 +331,14 @@ def to_planar_bf16(H: np.ndarray) -> np.ndarray:
 def _fill_device_layout(args):
     """Worker: instances [a, b) of a uniform batch into a shared (n, K, M) complex64 array."""
     from multiprocessing import shared_memory
-    name, shape, preset, seed, first, a, b = args
+    name, shape, preset, seed, first, a, b, dtype = args
     shm = shared_memory.SharedMemory(name=name)
     try:
         out = np.ndarray(shape, dtype=np.complex64, buffer=shm.buf)
         xi = np.empty(b - a)
         spec = PRESETS[preset] if isinstance(preset, str) else preset
         for i in range(a, b):
-            inst = generate_instance(spec, seed, first + i)
+            inst = generate_instance(spec, seed, first + i, dtype)
             out[i] = inst.H.T.astype(np.complex64)
             xi[i - a] = inst.xi
         return a, xi
@@ -328,7 +347,7 @@ def _fill_device_layout(args):
 
 
 def generate_batch_device_layout(preset: str | ChannelSpec, n: int, seed: int, first: int = 0,
-                                 workers: int | None = None):
+                                 workers: int | None = None, dtype: str = "complex64"):
     """Uniform batch straight into the C-ABI storage layout: returns
     (H (n, K, M) complex64, xi (n,)).  Same values as ``generate_batch``;
     uses a pool of spawned worker processes (call before any GPU work)."""
@@ -340,7 +359,7 @@ def generate_batch_device_layout(preset: str | ChannelSpec, n: int, seed: int, f
     shape = (n, spec.K, spec.M)
     workers = workers or min(16, os.cpu_count() or 1)
     if workers <= 1 or n < 8:
-        H, xi = generate_batch(spec, n, seed, first)
+        H, xi = generate_batch(spec, n, seed, first, dtype)
         return to_device_layout(H), xi
     nbytes = int(np.prod(shape)) * 8
     shm = shared_memory.SharedMemory(create=True, size=nbytes)
@@ -348,7 +367,7 @@ def generate_batch_device_layout(preset: str | ChannelSpec, n: int, seed: int, f
         chunks = [(i * n // (4 * workers), (i + 1) * n // (4 * workers)) for i in range(4 * workers)]
         xi = np.empty(n)
         with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
-            jobs = [(shm.name, shape, preset, seed, first, a, b) for a, b in chunks if b > a]
+            jobs = [(shm.name, shape, preset, seed, first, a, b, dtype) for a, b in chunks if b > a]
             for a, x in ex.map(_fill_device_layout, jobs):
                 xi[a:a + len(x)] = x
         H = np.ndarray(shape, dtype=np.complex64, buffer=shm.buf).copy()

@@ -11,6 +11,7 @@
 #include <array>
 #include <map>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "../../include/jacpcg.h"
@@ -116,6 +117,7 @@ struct Launch {
     int param;        // TB (Gram), KC (iteration), TN (W = H X)
     size_t list_off;  // byte offset of its work list inside the plan block
     int count;        // CTAs
+    int shape = 0;    // iteration launch shape (index into PCG_SHAPES)
 };
 
 }  // namespace
@@ -136,6 +138,7 @@ struct jacpcg_ctx {
     size_t prof_used = 0;
     int last_launches = 0;
     std::vector<jacpcg_plan *> plans;
+    int pcg_shape_idx[6] = {0, 0, 0, 0, 0, 0};   // chosen iteration shape per K class
 };
 
 struct jacpcg_plan {
@@ -204,8 +207,9 @@ int n_gtiles(const jacpcg_instance &q) {
     const int nb = std::max(1, KC / TB);   // cover the zero padding up to KC as well
     return nb * (nb + 1) / 2;
 }
-int n_pblocks(const jacpcg_instance &q) {
-    const PcgShape s = pcg_shape(k_class(q.K));
+int n_pblocks(const jacpcg_instance &q, const int *shape_idx) {
+    const int KC = k_class(q.K);
+    const PcgShape s = pcg_shape(KC, shape_idx[kc_index(KC)]);
     const int per = s.CW * s.NW;
     return (q.K + per - 1) / per;
 }
@@ -220,14 +224,14 @@ size_t inst_ws_bytes(const jacpcg_instance &q, bool refine) {
 // K classes whose Gram runs on the tensor cores at this precision
 bool gram_on_tc(int precision, int KC) { return precision == JACPCG_TF32X3 && KC == 64; }
 
-Layout make_layout(const jacpcg_instance *inst, int n, bool refine) {
+Layout make_layout(const jacpcg_instance *inst, int n, bool refine, const int *shape_idx) {
     Layout L{};
     L.n_gram = L.n_pcg = L.n_hx = L.n_res = 0;
     L.refine = refine;
     for (int i = 0; i < n; ++i) {
         if (refine) L.n_res += inst[i].K;
         L.n_gram += n_gtiles(inst[i]);
-        L.n_pcg += n_pblocks(inst[i]);
+        L.n_pcg += n_pblocks(inst[i], shape_idx);
         L.n_hx += n_wtiles(inst[i]);
     }
     size_t o = 0;
@@ -318,12 +322,13 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
     int p = 0;
     for (int KC : {8, 16, 32, 64, 128, 256}) {
         const int start = p;
-        const PcgShape s = pcg_shape(KC);
+        const int sh = ctx->pcg_shape_idx[kc_index(KC)];
+        const PcgShape s = pcg_shape(KC, sh);
         for (int i = 0; i < n; ++i) {
             if (k_class(inst[i].K) != KC) continue;
             for (int c0 = 0; c0 < inst[i].K; c0 += s.CW * s.NW) pb[p++] = make_int2(i, c0);
         }
-        if (p > start) launches.push_back({Launch::PCG, 1, KC, L.pcg + start * sizeof(int2), p - start});
+        if (p > start) launches.push_back({Launch::PCG, 1, KC, L.pcg + start * sizeof(int2), p - start, sh});
     }
     // W = H X on the tensor cores: instance list, one persistent launch
     int *hl = reinterpret_cast<int *>(host + L.hxl);
@@ -374,8 +379,8 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
                                          pl->acc, s);
                     break;
                 case Launch::PCG:
-                    e = launch_pcg(l.param, ctx->cfg.variant, pl->d_insts,
-                                   static_cast<const int2 *>(list), l.count, pl->acc, s, 0);
+                    e = launch_pcg_shape(l.param, l.shape, ctx->cfg.variant, pl->d_insts,
+                                         static_cast<const int2 *>(list), l.count, pl->acc, s, 0);
                     break;
                 case Launch::HX:
                     e = launch_hx_simt(l.param, pl->d_insts, static_cast<const int4 *>(list), l.count,
@@ -395,16 +400,17 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
             // iterative refinement: R = I - A X (FP64), A dX = R (FP32 iteration), X += dX
             const int2 *rb = reinterpret_cast<const int2 *>(pl->dev + pl->res_off);
             for (int sw = 0; sw <= pl->refine_sweeps; ++sw) {
-                if (launch_residual(pl->d_insts, rb, pl->n_res, s) != cudaSuccess ||
+                if (launch_residual(pl->d_insts, rb, pl->n_res, s,
+                                    ctx->cfg.refine_residual == JACPCG_RESID_FP64) != cudaSuccess ||
                     launch_resid_hist(pl->d_insts, pl->n_inst, sw, s) != cudaSuccess)
                     return cuda_fail(ctx);
                 nl += 2;
                 if (sw == pl->refine_sweeps) break;
                 for (const Launch &l : pl->launches) {
                     if (l.kind != Launch::PCG) continue;
-                    if (launch_pcg(l.param, ctx->cfg.variant, pl->d_insts,
-                                   reinterpret_cast<const int2 *>(pl->dev + l.list_off), l.count, pl->acc, s,
-                                   1) != cudaSuccess)
+                    if (launch_pcg_shape(l.param, l.shape, ctx->cfg.variant, pl->d_insts,
+                                         reinterpret_cast<const int2 *>(pl->dev + l.list_off), l.count,
+                                         pl->acc, s, 1) != cudaSuccess)
                         return cuda_fail(ctx);
                     ++nl;
                 }
@@ -428,7 +434,7 @@ jacpcg_status make_plan(jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, int
     jacpcg_status st = validate(ctx, inst, n);
     if (st != JACPCG_OK) return st;
     const bool refine = ctx->cfg.refine_sweeps > 0;
-    Layout L = make_layout(inst, n, refine);
+    Layout L = make_layout(inst, n, refine, ctx->pcg_shape_idx);
     size_t off;
     if (!ctx->arena.alloc(L.total, &off)) return JACPCG_ENOMEM;
     jacpcg_plan *pl = new (std::nothrow) jacpcg_plan();
@@ -564,6 +570,8 @@ jacpcg_status jacpcg_create(const jacpcg_config *cfg, jacpcg_ctx **out) {
     if (cfg->precision != JACPCG_FP32 && cfg->precision != JACPCG_TF32X3) return JACPCG_EINVAL;
     if (cfg->variant < JACPCG_STANDARD || cfg->variant > JACPCG_CG) return JACPCG_EINVAL;
     if (cfg->refine_sweeps < 0 || cfg->refine_sweeps > 3) return JACPCG_EINVAL;
+    if (cfg->refine_residual != JACPCG_RESID_DOT2 && cfg->refine_residual != JACPCG_RESID_FP64)
+        return JACPCG_EINVAL;
     jacpcg_ctx *ctx = new (std::nothrow) jacpcg_ctx();
     if (!ctx) return JACPCG_ENOMEM;
     ctx->cfg = *cfg;
@@ -578,7 +586,8 @@ jacpcg_status jacpcg_create(const jacpcg_config *cfg, jacpcg_ctx **out) {
         q.M = cfg->max_M;
         q.K = cfg->max_K;
         std::vector<jacpcg_instance> v(cfg->max_instances, q);
-        bytes = 2 * make_layout(v.data(), cfg->max_instances, cfg->refine_sweeps > 0).total;
+        const int zero[6] = {0, 0, 0, 0, 0, 0};
+        bytes = 2 * make_layout(v.data(), cfg->max_instances, cfg->refine_sweeps > 0, zero).total;
     }
     bytes = align_up(bytes);
     if (cudaMalloc(reinterpret_cast<void **>(&ctx->arena.base), bytes) != cudaSuccess) {
@@ -653,7 +662,7 @@ jacpcg_status jacpcg_plan_bytes(const jacpcg_ctx *ctx, const jacpcg_instance *in
     if (!bytes) return JACPCG_EINVAL;
     jacpcg_status st = validate(ctx, inst, n_inst);
     if (st != JACPCG_OK) return st;
-    *bytes = align_up(make_layout(inst, n_inst, ctx->cfg.refine_sweeps > 0).total);
+    *bytes = align_up(make_layout(inst, n_inst, ctx->cfg.refine_sweeps > 0, ctx->pcg_shape_idx).total);
     return JACPCG_OK;
 }
 
@@ -685,5 +694,83 @@ jacpcg_status jacpcg_profile_read(jacpcg_ctx *ctx, float ms[4], int *n_executes,
 }
 
 int64_t jacpcg_launch_count(const jacpcg_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+jacpcg_status jacpcg_set_shape(jacpcg_ctx *ctx, int k_class_, int shape) {
+    if (!ctx || k_class_ < 8 || k_class_ > 256 || (k_class_ & (k_class_ - 1))) return JACPCG_EINVAL;
+    const int c = kc_index(k_class_);
+    if (shape < 0 || shape >= PCG_NSHAPES[c]) return JACPCG_EINVAL;
+    ctx->pcg_shape_idx[c] = shape;
+    return JACPCG_OK;
+}
+
+jacpcg_status jacpcg_get_shape(const jacpcg_ctx *ctx, int k_class_, int *shape, int *n_shapes,
+                               int *cols_per_warp, int *warps_per_cta) {
+    if (!ctx || k_class_ < 8 || k_class_ > 256 || (k_class_ & (k_class_ - 1))) return JACPCG_EINVAL;
+    const int c = kc_index(k_class_);
+    const PcgShape s = pcg_shape(k_class_, ctx->pcg_shape_idx[c]);
+    if (shape) *shape = ctx->pcg_shape_idx[c];
+    if (n_shapes) *n_shapes = PCG_NSHAPES[c];
+    if (cols_per_warp) *cols_per_warp = s.CW;
+    if (warps_per_cta) *warps_per_cta = s.NW;
+    return JACPCG_OK;
+}
+
+jacpcg_status jacpcg_autotune(jacpcg_ctx *ctx, const jacpcg_instance *inst, int n_inst, void *stream,
+                              char *table, size_t table_cap) {
+    jacpcg_status st = validate(ctx, inst, n_inst);
+    if (st != JACPCG_OK) return st;
+    if (ctx->broken) return JACPCG_ECUDA;
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return cuda_fail(ctx);
+    std::string js = "{";
+    bool first = true;
+    for (int KC : {8, 16, 32, 64, 128, 256}) {
+        std::vector<jacpcg_instance> sub;
+        for (int i = 0; i < n_inst; ++i)
+            if (k_class(inst[i].K) == KC) sub.push_back(inst[i]);
+        if (sub.empty()) continue;
+        const int c = kc_index(KC);
+        float best_ms = 1e30f;
+        int best = 0;
+        std::string times;
+        for (int sh = 0; sh < PCG_NSHAPES[c] && st == JACPCG_OK; ++sh) {
+            ctx->pcg_shape_idx[c] = sh;
+            jacpcg_plan *pl = nullptr;
+            st = make_plan(ctx, sub.data(), (int)sub.size(), nullptr, nullptr, nullptr, nullptr, 0, nullptr, &pl);
+            if (st != JACPCG_OK) break;
+            float ms = 0.f;
+            for (int r = 0; r < 2 && st == JACPCG_OK; ++r) st = execute(pl, s);
+            if (st == JACPCG_OK && cudaEventRecord(e0, s) != cudaSuccess) st = cuda_fail(ctx);
+            for (int r = 0; r < 5 && st == JACPCG_OK; ++r) st = execute(pl, s);
+            if (st == JACPCG_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                st = cuda_fail(ctx);
+            drop_plan(pl);
+            ms /= 5.f;
+            if (st == JACPCG_OK && ms < best_ms) {
+                best_ms = ms;
+                best = sh;
+            }
+            times += (sh ? ", " : "") + std::to_string(ms);
+        }
+        ctx->pcg_shape_idx[c] = best;
+        const PcgShape b = pcg_shape(KC, best);
+        js += (first ? "" : ", ") + std::string("\"") + std::to_string(KC) + "\": {\"shape\": " + std::to_string(best) +
+              ", \"cols_per_warp\": " + std::to_string(b.CW) + ", \"warps_per_cta\": " + std::to_string(b.NW) +
+              ", \"instances\": " + std::to_string(sub.size()) + ", \"ms_per_candidate\": [" + times + "]}";
+        first = false;
+        if (st != JACPCG_OK) break;
+    }
+    js += "}";
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (table && table_cap > 0) {
+        const size_t n = js.size() < table_cap - 1 ? js.size() : table_cap - 1;
+        std::memcpy(table, js.data(), n);
+        table[n] = 0;
+    }
+    return st;
+}
 
 }  // extern "C"

@@ -13,7 +13,24 @@ struct PcgShape {
     int CW;   // columns per warp
     int NW;   // warps per CTA
 };
-PcgShape pcg_shape(int KC);
+// Candidate shapes per K class (8, 16, ..., 256), index 0 the default; the
+// autotuner picks among them.  Each pcg_k<KC>.cu instantiates exactly these.
+constexpr int PCG_MAX_SHAPES = 4;
+constexpr PcgShape PCG_SHAPES[6][PCG_MAX_SHAPES] = {
+    {{8, 4, 2}, {8, 8, 1}, {8, 2, 4}, {8, 4, 2}},
+    {{16, 4, 4}, {16, 8, 2}, {16, 2, 8}, {16, 4, 4}},
+    {{32, 4, 8}, {32, 8, 4}, {32, 2, 16}, {32, 4, 8}},
+    {{64, 4, 16}, {64, 8, 8}, {64, 4, 8}, {64, 2, 16}},
+    {{128, 4, 8}, {128, 2, 8}, {128, 2, 16}, {128, 4, 4}},
+    {{256, 2, 8}, {256, 1, 8}, {256, 2, 4}, {256, 1, 16}},
+};
+constexpr int PCG_NSHAPES[6] = {3, 3, 3, 4, 4, 4};
+inline int kc_index(int KC) {
+    int i = 0;
+    while ((8 << i) < KC) ++i;
+    return i;
+}
+PcgShape pcg_shape(int KC, int shape = 0);
 
 // Gram tile edge and W = H X tile width for a K class (SIMT kernels).
 inline int gram_tb(int KC) { return KC <= 16 ? 16 : (KC >= 64 ? 64 : KC); }
@@ -32,9 +49,22 @@ cudaError_t launch_hx_tc64(const DevInst *insts, const int *list, int n, DevAccu
 // blocks: (instance, first column); mode 0: A X = I, mode 1: A dX = R, X += dX
 cudaError_t launch_pcg(int KC, int variant, const DevInst *insts, const int2 *blocks,
                        int n_blocks, DevAccum acc, cudaStream_t s, int mode = 0);
+cudaError_t launch_pcg_shape(int KC, int shape, int variant, const DevInst *insts, const int2 *blocks,
+                             int n_blocks, DevAccum acc, cudaStream_t s, int mode);
+#define JACPCG_DECLARE_PCG_CLASS(KC)                                                              \
+    cudaError_t launch_pcg_k##KC(int shape, int variant, const DevInst *insts, const int2 *blocks, \
+                                 int n_blocks, DevAccum acc, cudaStream_t s, int mode);
+JACPCG_DECLARE_PCG_CLASS(8)
+JACPCG_DECLARE_PCG_CLASS(16)
+JACPCG_DECLARE_PCG_CLASS(32)
+JACPCG_DECLARE_PCG_CLASS(64)
+JACPCG_DECLARE_PCG_CLASS(128)
+JACPCG_DECLARE_PCG_CLASS(256)
+#undef JACPCG_DECLARE_PCG_CLASS
 // refinement: R = I - A X in FP64 and per-column ||R_j||^2 (blocks: (instance, column)),
 // then hist[sweep] = ||R||_F / sqrt(K) per instance
-cudaError_t launch_residual(const DevInst *insts, const int2 *blocks, int n_blocks, cudaStream_t s);
+cudaError_t launch_residual(const DevInst *insts, const int2 *blocks, int n_blocks, cudaStream_t s,
+                            bool fp64);
 cudaError_t launch_resid_hist(const DevInst *insts, int n_inst, int sweep, cudaStream_t s);
 // tiles: (instance, m tile, n tile, partial slot)
 cudaError_t launch_hx_simt(int TN, const DevInst *insts, const int4 *tiles, int n_tiles,

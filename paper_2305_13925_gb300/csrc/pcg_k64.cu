@@ -1,0 +1,22 @@
+// pcg_k64.cu -- the Jac-PCG iteration kernel instantiated for the K = 64
+// class in each candidate launch shape (see PCG_SHAPES in kernels.h).
+#include "pcg_kernel.cuh"
+
+namespace jacpcg {
+
+static_assert(PCG_SHAPES[3][0].CW == 4 && PCG_SHAPES[3][0].NW == 16, "shape table");
+static_assert(PCG_SHAPES[3][1].CW == 8 && PCG_SHAPES[3][1].NW == 8, "shape table");
+static_assert(PCG_SHAPES[3][2].CW == 4 && PCG_SHAPES[3][2].NW == 8, "shape table");
+static_assert(PCG_SHAPES[3][3].CW == 2 && PCG_SHAPES[3][3].NW == 16, "shape table");
+cudaError_t launch_pcg_k64(int shape, int variant, const DevInst *insts, const int2 *blocks,
+                            int n_blocks, DevAccum acc, cudaStream_t s, int mode) {
+    switch (shape) {
+        case 0: return pcgk::launch_cfg<64, 4, 16, true>(variant, insts, blocks, n_blocks, acc, s, mode);
+        case 1: return pcgk::launch_cfg<64, 8, 8, true>(variant, insts, blocks, n_blocks, acc, s, mode);
+        case 2: return pcgk::launch_cfg<64, 4, 8, true>(variant, insts, blocks, n_blocks, acc, s, mode);
+        case 3: return pcgk::launch_cfg<64, 2, 16, true>(variant, insts, blocks, n_blocks, acc, s, mode);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace jacpcg

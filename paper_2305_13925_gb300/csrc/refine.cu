@@ -1,8 +1,16 @@
-// refine.cu -- the true residual of iterative refinement, R = I - A X, with
-// every product and sum in FP64 (A and X are FP32, so each product is exact
-// in FP64), and its per-instance norm history.  No passage of the paper: the
-// paper solves Eq. 16 by the iteration alone; refinement is the system
-// layer that wins back accuracy lost to FP32 and to bfloat16 inputs.
+// refine.cu -- the true residual of iterative refinement, R = I - A X, and
+// its per-instance norm history.  Two evaluations, both far more accurate
+// than the FP32 iteration they correct:
+//   FP64: every product and sum in FP64 (A and X are FP32, so each product
+//         is exact in FP64);
+//   DOT2: FP32 error-free transformations (TwoProduct by FMA, TwoSum), the
+//         compensated dot product of Ogita, Rump and Oishi ("Accurate sum and
+//         dot product", SIAM J. Sci. Comput. 26(6), 2005), whose result is as
+//         accurate as if computed in twice the working precision; it runs on
+//         the FP32 pipes, which on this GPU are far faster than FP64.
+// No passage of the paper: the paper solves Eq. 16 by the iteration alone;
+// refinement is the system layer that wins back accuracy lost to FP32 and
+// to bfloat16 inputs.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -11,6 +19,7 @@ namespace jacpcg {
 namespace {
 
 // One block per (instance, column j), one thread per row i (K <= 256).
+template <bool FP64>
 __global__ void __launch_bounds__(256) residual_kernel(const DevInst *__restrict__ insts,
                                                        const int2 *__restrict__ blocks) {
     __shared__ double red[256];
@@ -21,16 +30,31 @@ __global__ void __launch_bounds__(256) residual_kernel(const DevInst *__restrict
     const float2 *__restrict__ X = in.X;
     double re = 0.0, im = 0.0;
     if (i < K) {
-        for (int k = 0; k < K; ++k) {
-            const float2 a = A[i + (size_t)k * KC];
-            const float2 x = X[k + (size_t)j * KC];
-            re = fma((double)a.x, (double)x.x, re);
-            re = fma(-(double)a.y, (double)x.y, re);
-            im = fma((double)a.x, (double)x.y, im);
-            im = fma((double)a.y, (double)x.x, im);
+        if (FP64) {
+            for (int k = 0; k < K; ++k) {
+                const float2 a = A[i + (size_t)k * KC];
+                const float2 x = X[k + (size_t)j * KC];
+                re = fma((double)a.x, (double)x.x, re);
+                re = fma(-(double)a.y, (double)x.y, re);
+                im = fma((double)a.x, (double)x.y, im);
+                im = fma((double)a.y, (double)x.x, im);
+            }
+            re = (i == j ? 1.0 : 0.0) - re;
+            im = -im;
+        } else {
+            // (s, c) pairs: s the rounded sum, c the accumulated error terms
+            Comp cr = {i == j ? 1.f : 0.f, 0.f}, ci = {0.f, 0.f};
+            for (int k = 0; k < K; ++k) {
+                const float2 a = A[i + (size_t)k * KC];
+                const float2 x = X[k + (size_t)j * KC];
+                comp_fma(cr, -a.x, x.x);
+                comp_fma(cr, a.y, x.y);
+                comp_fma(ci, -a.x, x.y);
+                comp_fma(ci, -a.y, x.x);
+            }
+            re = (double)cr.s + (double)cr.c;
+            im = (double)ci.s + (double)ci.c;
         }
-        re = (i == j ? 1.0 : 0.0) - re;
-        im = -im;
     }
     if (i < KC) in.R[i + (size_t)j * KC] = make_float2((float)re, (float)im);
     red[i] = re * re + im * im;
@@ -58,9 +82,13 @@ __global__ void resid_hist_kernel(const DevInst *__restrict__ insts, int n_inst,
 
 }  // namespace
 
-cudaError_t launch_residual(const DevInst *insts, const int2 *blocks, int n_blocks, cudaStream_t s) {
+cudaError_t launch_residual(const DevInst *insts, const int2 *blocks, int n_blocks, cudaStream_t s,
+                            bool fp64) {
     if (n_blocks <= 0) return cudaSuccess;
-    residual_kernel<<<n_blocks, 256, 0, s>>>(insts, blocks);
+    if (fp64)
+        residual_kernel<true><<<n_blocks, 256, 0, s>>>(insts, blocks);
+    else
+        residual_kernel<false><<<n_blocks, 256, 0, s>>>(insts, blocks);
     return cudaGetLastError();
 }
 

@@ -38,8 +38,9 @@ def test_bf16_storage_fixed_T_parity(precision):
         assert rel_fro(out["W"][k], ref["W"]) <= 1e-5, (k, rel_fro(out["W"][k], ref["W"]))
 
 
+@pytest.mark.parametrize("fp64", [False, True])
 @pytest.mark.parametrize("shape", [("xl_4096x256", 2), ("batched_1024x64", 4)])
-def test_refinement_reaches_direct_rzf(shape):
+def test_refinement_reaches_direct_rzf(shape, fp64):
     """A loose first solve (tol 1e-3) then three refinement sweeps: the FP64
     residual history decreases, and W ends within 1e-5 of the direct RZF of
     the bfloat16 channel; without refinement it does not."""
@@ -47,7 +48,7 @@ def test_refinement_reaches_direct_rzf(shape):
     H, xi = C.generate_batch(preset, n, 2, dtype="bf16")
     before = run(list(H), list(xi), T=60, tol=1e-3, bf16=True, precision="tf32x3")
     after = run(list(H), list(xi), T=60, tol=1e-3, bf16=True, precision="tf32x3", refine_sweeps=3,
-                want_hist=True)
+                want_hist=True, refine_fp64=fp64)
     for k in range(n):
         Wd, _, st = O.rzf_direct(H[k], xi[k])
         e0 = rel_fro(before["W"][k], Wd)

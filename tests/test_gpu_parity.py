@@ -283,3 +283,39 @@ def test_invalid_arguments_rejected():
         torch.cuda.synchronize()
     finally:
         prec.close()
+
+
+def test_every_launch_shape_bit_identical_and_autotune():
+    """Each candidate launch shape of the iteration kernel gives the same bits
+    (the per-column arithmetic does not depend on the shape); the autotuned
+    context keeps parity with the oracle."""
+    import torch
+    from paper_2305_13925_gb300 import binding
+    insts = C.generate_ragged(12, 91, k_set=(8, 16, 32, 64, 128, 256), m_set=(256, 512))
+    Hs = [C.round_complex64(i.H) for i in insts]
+    xis = [i.xi for i in insts]
+    base = run(Hs, xis, T=5)
+    prec = binding.Precoder(max_instances=12, max_M=512, max_K=256)
+    try:
+        for KC in (8, 16, 32, 64, 128, 256):
+            n_shapes = binding.jacpcg_get_shape(prec.ctx, KC)[1]
+            for sh in range(1, n_shapes):
+                binding.jacpcg_set_shape(prec.ctx, KC, sh)
+                out = run(Hs, xis, T=5, prec=prec)
+                for k in range(len(Hs)):
+                    assert np.array_equal(out["W"][k], base["W"][k]), (KC, sh, k)
+            binding.jacpcg_set_shape(prec.ctx, KC, 0)
+    except Exception:
+        prec.close()
+        raise
+    from gpu_util import to_dev
+    Hd = [to_dev(h, torch) for h in Hs]
+    Wd = [to_dev(np.zeros(h.shape), torch) for h in Hs]
+    table = binding.jacpcg_autotune(prec.ctx, [binding.instance(Hd[k], Wd[k], xis[k], 5)
+                                               for k in range(len(Hs))])
+    present = {str(1 << max(3, (int(h.shape[1]) - 1).bit_length())) for h in Hs}
+    assert set(table) == present
+    tuned = run(Hs, xis, T=5, prec=prec)
+    prec.close()
+    for k in range(len(Hs)):
+        assert np.array_equal(tuned["W"][k], base["W"][k])
