@@ -53,6 +53,7 @@ def parse_args():
     ap.add_argument("--variant", default="standard", choices=["standard", "alg1", "cg"])
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3"])
     ap.add_argument("--mode", default="precode", choices=["precode", "plan", "graph"])
+    ap.add_argument("--simt-iteration", action="store_true")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--e2e-chunks", type=int, default=8)
@@ -75,6 +76,8 @@ def workload_config(args, n):
                      f"K={spec.K}, complex64, T={args.iters} fixed, {args.variant} Jac-PCG, B=I_K"),
         "instances_per_gpu": n, "M": spec.M, "K": spec.K, "T": args.iters,
         "variant": args.variant, "precision": args.precision, "mode": args.mode,
+        "iteration": ("simt" if getattr(args, "simt_iteration", False) or args.precision != "tf32x3"
+                      else "tensor (K=64 class)"),
         "l2": "inputs larger than L2 (H is 1.07 GB per step), no flush needed",
         "seed": args.seed,
     }
@@ -109,9 +112,9 @@ def flops_per_instance(M, K, T):
             "hx": 8.0 * M * K * K}
 
 
-KERNEL_FILES = {("fp32", "gram"): ["gram_simt.cu"], ("fp32", "pcg"): ["pcg.cu"],
+KERNEL_FILES = {("fp32", "gram"): ["gram_simt.cu"], ("fp32", "pcg"): ["pcg_kernel.cuh"],
                 ("fp32", "hx"): ["hx_simt.cu"], ("tf32x3", "gram"): ["gram_tc.cu", "tc.cuh"],
-                ("tf32x3", "pcg"): ["pcg.cu"], ("tf32x3", "hx"): ["hx_tc.cu", "tc.cuh"]}
+                ("tf32x3", "pcg"): ["pcg_tc.cu", "tc.cuh"], ("tf32x3", "hx"): ["hx_tc.cu", "tc.cuh"]}
 
 
 def kernel_source_hash(phase, precision="fp32"):
@@ -574,7 +577,8 @@ def main():
     resid = torch.empty(n, dtype=torch.float32, device="cuda")
     beta = torch.empty(n, dtype=torch.float32, device="cuda")
     prec = binding.Precoder(max_instances=n, max_M=M, max_K=K, variant=args.variant,
-                            precision=args.precision, device=local, profile=True)
+                            precision=args.precision, device=local, profile=True,
+                            simt_iteration=args.simt_iteration)
     insts = [binding.instance(Hd[i], Wd[i], float(xi[i]), args.iters) for i in range(n)]
     arr = (binding.jacpcg_instance * n)(*insts)
     stream = torch.cuda.current_stream()
@@ -628,7 +632,7 @@ def main():
         per_phase = {}
         for ph in ("gram", "pcg", "hx"):
             achieved = f[ph] * n / (avg[ph] / 1e3) / 1e12
-            if args.precision == "fp32" or ph == "pcg":
+            if args.precision == "fp32" or (ph == "pcg" and args.simt_iteration):
                 peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
                 bound = "alu"
                 peak_note = "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, not measured)"

@@ -82,7 +82,12 @@ enum { JACPCG_H_C64 = 0, JACPCG_H_BF16 = 1 };
 enum { JACPCG_RESID_DOT2 = 0, JACPCG_RESID_FP64 = 1 };
 
 /* config flags */
-enum { JACPCG_FLAG_PROFILE = 1 };   /* record per-phase CUDA events on each execute */
+enum {
+    JACPCG_FLAG_PROFILE = 1,         /* record per-phase CUDA events on each execute */
+    JACPCG_FLAG_SIMT_ITERATION = 2   /* TF32X3, K = 64 class: keep the iteration on the FP32 SIMT
+                                        kernel (by default its A P product runs on the tensor
+                                        cores for the standard and CG forms) */
+};
 
 typedef struct {
     int device;              /* CUDA device ordinal */
@@ -188,6 +193,10 @@ jacpcg_status jacpcg_set_shape(jacpcg_ctx *ctx, int k_class, int shape);
 /* Current shape of a K class, the number of candidates, and its geometry. */
 jacpcg_status jacpcg_get_shape(const jacpcg_ctx *ctx, int k_class, int *shape, int *n_shapes,
                                int *cols_per_warp, int *warps_per_cta);
+
+/* Description of the CUDA error that made the context unusable (after an
+ * ECUDA), or "no error".  Static string. */
+const char *jacpcg_last_cuda_error(const jacpcg_ctx *ctx);
 
 /* Kernels launched by this context since creation (all entry points). */
 int64_t jacpcg_launch_count(const jacpcg_ctx *ctx);

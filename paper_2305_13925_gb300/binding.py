@@ -22,6 +22,7 @@ JACPCG_ENOTCONV, JACPCG_ENOTHPD, JACPCG_ENONFINITE, JACPCG_ETIMEOUT, JACPCG_EBUS
 JACPCG_STANDARD, JACPCG_ALG1, JACPCG_CG = 0, 1, 2
 JACPCG_FP32, JACPCG_TF32X3 = 0, 1
 JACPCG_FLAG_PROFILE = 1
+JACPCG_FLAG_SIMT_ITERATION = 2
 JACPCG_H_C64, JACPCG_H_BF16 = 0, 1
 JACPCG_RESID_DOT2, JACPCG_RESID_FP64 = 0, 1
 VARIANTS = {"standard": JACPCG_STANDARD, "alg1": JACPCG_ALG1, "cg": JACPCG_CG}
@@ -33,7 +34,7 @@ EXPORTS = ("jacpcg_create", "jacpcg_precode", "jacpcg_plan_create", "jacpcg_plan
            "jacpcg_version", "jacpcg_precode_noalloc", "jacpcg_precode_plain",
            "jacpcg_server_create", "jacpcg_submit", "jacpcg_poll", "jacpcg_server_replay",
            "jacpcg_server_stats", "jacpcg_server_destroy", "jacpcg_autotune", "jacpcg_set_shape",
-           "jacpcg_get_shape")
+           "jacpcg_get_shape", "jacpcg_last_cuda_error")
 
 
 class jacpcg_config(ctypes.Structure):
@@ -101,6 +102,8 @@ def load(path: pathlib.Path | str | None = None):
         L.jacpcg_server_destroy.argtypes = [P]
         L.jacpcg_autotune.argtypes = [P, ctypes.POINTER(jacpcg_instance), I, P, ctypes.c_char_p, S]
         L.jacpcg_set_shape.argtypes = [P, I, I]
+        L.jacpcg_last_cuda_error.argtypes = [P]
+        L.jacpcg_last_cuda_error.restype = ctypes.c_char_p
         L.jacpcg_get_shape.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                                        ctypes.POINTER(I)]
         L.jacpcg_strerror.argtypes = [I]
@@ -231,6 +234,10 @@ def jacpcg_profile_read(ctx):
     return list(ms), n.value, per.value
 
 
+def jacpcg_last_cuda_error(ctx) -> str:
+    return load().jacpcg_last_cuda_error(ctx).decode()
+
+
 def jacpcg_launch_count(ctx) -> int:
     return int(load().jacpcg_launch_count(ctx))
 
@@ -350,12 +357,13 @@ class Precoder:
 
     def __init__(self, max_instances: int, max_M: int, max_K: int, variant="standard",
                  precision="fp32", device: int = 0, arena_bytes: int = 0, profile: bool = False,
-                 refine_sweeps: int = 0, refine_fp64: bool = False):
+                 refine_sweeps: int = 0, refine_fp64: bool = False, simt_iteration: bool = False):
         self.cfg = jacpcg_config(device=device, max_instances=max_instances, max_M=max_M,
                                  max_K=max_K, arena_bytes=arena_bytes,
                                  precision=PRECISIONS[precision] if isinstance(precision, str) else precision,
                                  variant=VARIANTS[variant] if isinstance(variant, str) else variant,
-                                 flags=JACPCG_FLAG_PROFILE if profile else 0,
+                                 flags=(JACPCG_FLAG_PROFILE if profile else 0)
+                                 | (JACPCG_FLAG_SIMT_ITERATION if simt_iteration else 0),
                                  refine_sweeps=int(refine_sweeps),
                                  refine_residual=JACPCG_RESID_FP64 if refine_fp64 else JACPCG_RESID_DOT2)
         self.ctx = jacpcg_create(self.cfg)
@@ -380,7 +388,12 @@ class Precoder:
     def precode(self, insts, status=None, iters=None, resid=None, beta=None, stream=None):
         import torch
         s = torch.cuda.current_stream().cuda_stream if stream is None else stream
-        jacpcg_precode(self.ctx, insts, status, iters, resid, beta, s)
+        try:
+            jacpcg_precode(self.ctx, insts, status, iters, resid, beta, s)
+        except JacpcgError as e:
+            if e.status == JACPCG_ECUDA:
+                raise JacpcgError(e.status, f"jacpcg_precode ({jacpcg_last_cuda_error(self.ctx)})") from None
+            raise
 
     def plan(self, insts, status=None, iters=None, resid=None, beta=None, use_graph=False):
         return jacpcg_plan_create(self.ctx, insts, status, iters, resid, beta, use_graph)

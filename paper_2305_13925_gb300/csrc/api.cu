@@ -112,7 +112,7 @@ struct Arena {
 
 // What one kernel launch of a plan covers.
 struct Launch {
-    enum Kind { GRAM, PCG, HX, GRAM_TC, HX_TC } kind;
+    enum Kind { GRAM, PCG, HX, GRAM_TC, HX_TC, PCG_TC } kind;
     int phase;        // 0 Gram, 1 iteration, 2 W = H X
     int param;        // TB (Gram), KC (iteration), TN (W = H X)
     size_t list_off;  // byte offset of its work list inside the plan block
@@ -126,6 +126,7 @@ struct jacpcg_ctx {
     jacpcg_config cfg{};
     Arena arena;
     bool broken = false;
+    cudaError_t last_error = cudaSuccess;   // first CUDA error that broke the context
     int64_t launches = 0;
     // pinned staging for asynchronous table uploads of jacpcg_precode
     char *staging = nullptr;
@@ -162,13 +163,17 @@ struct jacpcg_plan {
 
 namespace {
 
-jacpcg_status cuda_fail(jacpcg_ctx *ctx) {
-    if (ctx) ctx->broken = true;
+jacpcg_status cuda_fail(jacpcg_ctx *ctx, cudaError_t e = cudaErrorUnknown) {
+    if (ctx) {
+        if (!ctx->broken) ctx->last_error = e;
+        ctx->broken = true;
+    }
     return JACPCG_ECUDA;
 }
 #define CK(call)                                   \
     do {                                           \
-        if ((call) != cudaSuccess) return cuda_fail(ctx); \
+        const cudaError_t ck_e = (call);           \
+        if (ck_e != cudaSuccess) return cuda_fail(ctx, ck_e); \
     } while (0)
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
@@ -221,8 +226,14 @@ size_t inst_ws_bytes(const jacpcg_instance &q, bool refine) {
     return b;
 }
 
-// K classes whose Gram runs on the tensor cores at this precision
+// K classes whose Gram and W = H X run on the tensor cores at this precision
 bool gram_on_tc(int precision, int KC) { return precision == JACPCG_TF32X3 && KC == 64; }
+// ... and whose iteration does, unless the SIMT kernel is asked for (Algorithm 1
+// always keeps the SIMT kernel)
+bool pcg_on_tc(const jacpcg_config &cfg, int KC) {
+    return !(cfg.flags & JACPCG_FLAG_SIMT_ITERATION) && gram_on_tc(cfg.precision, KC) &&
+           cfg.variant != JACPCG_ALG1;
+}
 
 Layout make_layout(const jacpcg_instance *inst, int n, bool refine, const int *shape_idx) {
     Layout L{};
@@ -320,12 +331,14 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
     // iteration blocks grouped by K class
     int2 *pb = reinterpret_cast<int2 *>(host + L.pcg);
     int p = 0;
+    if (nt && pcg_on_tc(ctx->cfg, 64))
+        launches.push_back({Launch::PCG_TC, 1, 64, L.tcl, nt});
     for (int KC : {8, 16, 32, 64, 128, 256}) {
         const int start = p;
         const int sh = ctx->pcg_shape_idx[kc_index(KC)];
         const PcgShape s = pcg_shape(KC, sh);
         for (int i = 0; i < n; ++i) {
-            if (k_class(inst[i].K) != KC) continue;
+            if (k_class(inst[i].K) != KC || pcg_on_tc(ctx->cfg, KC)) continue;
             for (int c0 = 0; c0 < inst[i].K; c0 += s.CW * s.NW) pb[p++] = make_int2(i, c0);
         }
         if (p > start) launches.push_back({Launch::PCG, 1, KC, L.pcg + start * sizeof(int2), p - start, sh});
@@ -392,8 +405,12 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
                 case Launch::HX_TC:
                     e = launch_hx_tc64(pl->d_insts, static_cast<const int *>(list), l.count, pl->acc, s);
                     break;
+                case Launch::PCG_TC:
+                    e = launch_pcg_tc64(ctx->cfg.variant, pl->d_insts, static_cast<const int *>(list), l.count,
+                                        pl->acc, s, 0);
+                    break;
             }
-            if (e != cudaSuccess) return cuda_fail(ctx);
+            if (e != cudaSuccess) return cuda_fail(ctx, e);
             ++nl;
         }
         if (phase == 1 && pl->refine_sweeps > 0) {
@@ -407,19 +424,28 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
                 nl += 2;
                 if (sw == pl->refine_sweeps) break;
                 for (const Launch &l : pl->launches) {
-                    if (l.kind != Launch::PCG) continue;
-                    if (launch_pcg_shape(l.param, l.shape, ctx->cfg.variant, pl->d_insts,
-                                         reinterpret_cast<const int2 *>(pl->dev + l.list_off), l.count,
-                                         pl->acc, s, 1) != cudaSuccess)
-                        return cuda_fail(ctx);
+                    cudaError_t e = cudaSuccess;
+                    if (l.kind == Launch::PCG)
+                        e = launch_pcg_shape(l.param, l.shape, ctx->cfg.variant, pl->d_insts,
+                                             reinterpret_cast<const int2 *>(pl->dev + l.list_off), l.count,
+                                             pl->acc, s, 1);
+                    else if (l.kind == Launch::PCG_TC)
+                        e = launch_pcg_tc64(ctx->cfg.variant, pl->d_insts,
+                                            reinterpret_cast<const int *>(pl->dev + l.list_off), l.count,
+                                            pl->acc, s, 1);
+                    else
+                        continue;
+                    if (e != cudaSuccess) return cuda_fail(ctx, e);
                     ++nl;
                 }
             }
         }
         if (ev) CK(cudaEventRecord(ev[phase + 1], s));
     }
-    if (launch_finalize(pl->d_insts, pl->n_inst, pl->acc, pl->out, s) != cudaSuccess)
-        return cuda_fail(ctx);
+    {
+        const cudaError_t e = launch_finalize(pl->d_insts, pl->n_inst, pl->acc, pl->out, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e);
+    }
     ++nl;
     if (ev) CK(cudaEventRecord(ev[4], s));
     *n_launched = nl;
@@ -694,6 +720,11 @@ jacpcg_status jacpcg_profile_read(jacpcg_ctx *ctx, float ms[4], int *n_executes,
 }
 
 int64_t jacpcg_launch_count(const jacpcg_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+const char *jacpcg_last_cuda_error(const jacpcg_ctx *ctx) {
+    if (!ctx) return "no context";
+    return ctx->broken ? cudaGetErrorString(ctx->last_error) : "no error";
+}
 
 jacpcg_status jacpcg_set_shape(jacpcg_ctx *ctx, int k_class_, int shape) {
     if (!ctx || k_class_ < 8 || k_class_ > 256 || (k_class_ & (k_class_ - 1))) return JACPCG_EINVAL;

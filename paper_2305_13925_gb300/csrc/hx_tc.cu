@@ -141,16 +141,32 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_tc64_kernel(const DevInst *__r
             const int T = nmt * nks;
             auto load = [&](int t, float2 (&h)[2][4]) {
                 const int mt = t / nks, ks = t % nks;
+                if (bf16) {   // storage type decided once per stage, not per element
+                    const uint32_t *__restrict__ Hb = reinterpret_cast<const uint32_t *>(H);
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int e = tid + 256 * q;
-                    const int m = e & 127, kq = e >> 7;
-                    const int gm = mt * TMR + m;
+                    for (int q = 0; q < 2; ++q) {
+                        const int e = tid + 256 * q;
+                        const int m = e & 127, kq = e >> 7;
+                        const int gm = mt * TMR + m;
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int k = ks * KCH + 4 * kq + i;
-                        h[q][i] = (gm < M && k < K) ? load_h(H, bf16, gm + (size_t)k * ldh)
-                                                    : make_float2(0.f, 0.f);
+                        for (int i = 0; i < 4; ++i) {
+                            const int k = ks * KCH + 4 * kq + i;
+                            h[q][i] = (gm < M && k < K) ? bf16x2_to_float2(__ldg(Hb + gm + (size_t)k * ldh))
+                                                        : make_float2(0.f, 0.f);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const int e = tid + 256 * q;
+                        const int m = e & 127, kq = e >> 7;
+                        const int gm = mt * TMR + m;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int k = ks * KCH + 4 * kq + i;
+                            h[q][i] = (gm < M && k < K) ? __ldg(H + gm + (size_t)k * ldh)
+                                                        : make_float2(0.f, 0.f);
+                        }
                     }
                 }
             };

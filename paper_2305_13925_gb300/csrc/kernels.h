@@ -46,6 +46,9 @@ cudaError_t launch_gram_tc64(const DevInst *insts, const int *list, int n, DevAc
 // tensor-core W = H X for the K = 64 class (3xTF32); list: instance ids
 cudaError_t launch_hx_tc64(const DevInst *insts, const int *list, int n, DevAccum acc,
                            cudaStream_t s);
+// tensor-core iteration for the K = 64 class (standard or plain CG); list: instance ids
+cudaError_t launch_pcg_tc64(int variant, const DevInst *insts, const int *list, int n, DevAccum acc,
+                            cudaStream_t s, int mode);
 // blocks: (instance, first column); mode 0: A X = I, mode 1: A dX = R, X += dX
 cudaError_t launch_pcg(int KC, int variant, const DevInst *insts, const int2 *blocks,
                        int n_blocks, DevAccum acc, cudaStream_t s, int mode = 0);

@@ -26,9 +26,10 @@ def _gpu():
     build.build()
 
 
-def check(Hs, xis, T=6, variant="standard"):
+def check(Hs, xis, T=6, variant="standard", simt_iteration=False):
     Hs = [C.round_complex64(h) for h in Hs]
-    out = run(Hs, xis, variant=variant, T=T, want_X=True, want_A=True, precision="tf32x3")
+    out = run(Hs, xis, variant=variant, T=T, want_X=True, want_A=True, precision="tf32x3",
+              simt_iteration=simt_iteration)
     errs = []
     for i, (H, xi) in enumerate(zip(Hs, xis)):
         ref = O.precode(H, xi, variant, max_iter=T)
@@ -42,9 +43,10 @@ def check(Hs, xis, T=6, variant="standard"):
     return out, errs
 
 
-def test_tensor_batched_1024x64_subset():
+@pytest.mark.parametrize("simt_iteration", [False, True])
+def test_tensor_batched_1024x64_subset(simt_iteration):
     H, xi = C.generate_batch("batched_1024x64", 24, 1)
-    check(list(H), list(xi), T=6)
+    check(list(H), list(xi), T=6, simt_iteration=simt_iteration)
 
 
 @pytest.mark.parametrize("K,M", [(64, 1024), (64, 257), (40, 1000), (33, 96), (64, 4096)])
@@ -57,3 +59,29 @@ def test_tensor_gram_shapes(K, M):
 def test_tensor_ragged_mix_with_simt_classes():
     insts = C.generate_ragged(12, 8, k_set=(16, 64, 128), m_set=(256, 1024))
     check([i.H for i in insts], [i.xi for i in insts], T=4)
+
+
+@pytest.mark.parametrize("simt_iteration", [False, True])
+def test_tensor_tolerance_mode_reaches_direct_rzf(simt_iteration):
+    """tf32x3 with tol 1e-6: each column stops at its tolerance and W lands
+    within 2e-5 of the direct RZF; iteration counts near the oracle's."""
+    H, xi = C.generate_batch("batched_1024x64", 8, 11)
+    out = run(list(H), list(xi), T=200, tol=1e-6, precision="tf32x3", simt_iteration=simt_iteration)
+    for i in range(8):
+        Wd, _, _ = O.rzf_direct(H[i], xi[i])
+        assert rel_fro(out["W"][i], Wd) < 2e-5
+        ref = O.precode(H[i], xi[i], "standard", max_iter=200, tol=1e-6)
+        assert abs(int(out["iters"][i]) - ref["iters"]) <= 2
+        assert out["status"][i] == 0
+
+
+@pytest.mark.parametrize("simt_iteration", [False, True])
+def test_tensor_plain_cg_variant(simt_iteration):
+    """Plain CG on the tensor path, against the oracle with the FP32-drift bar."""
+    from test_gpu_parity import tol_for
+    H, xi = C.generate_batch("batched_1024x64", 8, 1)
+    Hs = [C.round_complex64(h) for h in H]
+    out = run(Hs, list(xi), variant="cg", T=6, precision="tf32x3", simt_iteration=simt_iteration)
+    for i in range(8):
+        ref = O.precode(Hs[i], xi[i], "cg", max_iter=6)
+        assert rel_fro(out["W"][i], ref["W"]) <= tol_for(Hs[i], xi[i], "cg", 6)
