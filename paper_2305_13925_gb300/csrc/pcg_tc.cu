@@ -12,11 +12,10 @@
 // per half of the reduction) and the correction products in a third, so no
 // truncating accumulation chain is longer than 16 MMAs.
 //
-// One persistent CTA per SM walks its instances.  8 warps (two per SM
-// sub-partition, so each thread may use up to 255 registers) own the state:
-// thread (warp w, lane l) holds complex row i = 16 (w mod 4) + l / 2 and the
-// 16 columns starting at 32 (w / 4) + 16 (l mod 2) of x, r, p in registers
-// for all iterations.  Per iteration they write P (TF32 head and tail) into
+// One persistent CTA per SM walks its instances.  16 warps (four per SM
+// sub-partition, 128 registers each) own the state: thread (warp w, lane l)
+// holds complex row i = 16 (w mod 4) + l / 2 and the 8 columns starting at
+// 16 (w / 4) + 8 (l mod 2) of x, r, p in registers for all iterations.  Per iteration they write P (TF32 head and tail) into
 // shared memory, vote on continuing (a barrier reduction), thread 0 issues
 // 48 MMAs and commits, and all warps read
 // Q from TMEM, pair Re / Im with one shuffle, and reduce the per-column dot
@@ -38,8 +37,9 @@ constexpr uint32_t LBO = 144;               // K-adjacent core matrices (128 + 1
 constexpr uint32_t SBO = (RR / 4) * LBO;    // 8-row groups
 constexpr int APART = (RR / 8) * SBO;       // one of A_hi, A_lo
 constexpr int BPART = (NC / 8) * SBO;       // one of P_hi, P_lo
-constexpr int NSW = 8;                      // state warps (thread 0 also issues the MMAs)
+constexpr int NSW = 16;                     // state warps (thread 0 also issues the MMAs)
 constexpr int NTHREADS = NSW * 32;
+constexpr int CPT = 8;                      // columns owned per thread
 constexpr int TMEM_COLS = 256;              // [0,64) head*head k<64, [64,128) k>=64, [128,192) corrections
 constexpr uint32_t WAIT_LIMIT = 1u << 21;
 
@@ -63,24 +63,24 @@ __device__ __forceinline__ void st_shared_v2(uint32_t addr, float a, float b) {
     asm volatile("st.shared.v2.f32 [%0], {%1, %2};\n" ::"r"(addr), "f"(a), "f"(b) : "memory");
 }
 // Sum, over the 64 rows, of one compensated partial per column for the
-// thread's 16 columns, for NQ quantities at once.  Within a warp the 16
-// lanes of equal parity hold the 16 rows of a quarter: a butterfly
-// reduce-scatter (offsets 2, 4, 8, 16, halving the values each round)
-// leaves each lane the quarter sum of one column; the four quarters meet in
-// shared memory, one lane per column adds them, and every thread reads back
-// the totals of its 16 columns (fixed order throughout).
+// thread's 8 columns, for NQ quantities at once.  Within a warp the 16 lanes
+// of equal parity hold the 16 rows of a quarter: a butterfly
+// reduce-scatter (offsets 2, 4, 8, halving the values each round, then a
+// pairwise add at offset 16) leaves each lane the quarter sum of one column;
+// the four quarters meet in shared memory, one lane per column adds them,
+// and every thread reads back the totals of its 8 columns (fixed order).
 template <int NQ>
-__device__ __forceinline__ void column_sum(Comp (&v)[NQ][16], float2 (*red)[4][NC], float2 (*tot)[NC],
+__device__ __forceinline__ void column_sum(Comp (&v)[NQ][CPT], float2 (*red)[4][NC], float2 (*tot)[NC],
                                            int quad, int jb, int lane) {
     Comp d[NQ];
 #pragma unroll
     for (int qn = 0; qn < NQ; ++qn) {
-        Comp a[8], b[4], c2[2];
+        Comp a[4], b[2];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {   // offset 2: keep half by lane bit 1
+        for (int k = 0; k < 4; ++k) {   // offset 2: keep half by lane bit 1
             const bool hi = (lane >> 1) & 1;
-            const Comp send = hi ? v[qn][k] : v[qn][k + 8];
-            Comp keep = hi ? v[qn][k + 8] : v[qn][k];
+            const Comp send = hi ? v[qn][k] : v[qn][k + 4];
+            Comp keep = hi ? v[qn][k + 4] : v[qn][k];
             Comp got;
             got.s = __shfl_xor_sync(0xffffffffu, send.s, 2);
             got.c = __shfl_xor_sync(0xffffffffu, send.c, 2);
@@ -88,45 +88,45 @@ __device__ __forceinline__ void column_sum(Comp (&v)[NQ][16], float2 (*red)[4][N
             a[k] = keep;
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {   // offset 4: lane bit 2
+        for (int k = 0; k < 2; ++k) {   // offset 4: lane bit 2
             const bool hi = (lane >> 2) & 1;
-            const Comp send = hi ? a[k] : a[k + 4];
-            Comp keep = hi ? a[k + 4] : a[k];
+            const Comp send = hi ? a[k] : a[k + 2];
+            Comp keep = hi ? a[k + 2] : a[k];
             Comp got;
             got.s = __shfl_xor_sync(0xffffffffu, send.s, 4);
             got.c = __shfl_xor_sync(0xffffffffu, send.c, 4);
             comp_add(keep, got);
             b[k] = keep;
         }
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {   // offset 8: lane bit 3
+        Comp c1;
+        {                               // offset 8: lane bit 3
             const bool hi = (lane >> 3) & 1;
-            const Comp send = hi ? b[k] : b[k + 2];
-            Comp keep = hi ? b[k + 2] : b[k];
+            const Comp send = hi ? b[0] : b[1];
+            Comp keep = hi ? b[1] : b[0];
             Comp got;
             got.s = __shfl_xor_sync(0xffffffffu, send.s, 8);
             got.c = __shfl_xor_sync(0xffffffffu, send.c, 8);
             comp_add(keep, got);
-            c2[k] = keep;
+            c1 = keep;
         }
-        {                               // offset 16: lane bit 4
-            const bool hi = (lane >> 4) & 1;
-            const Comp send = hi ? c2[0] : c2[1];
-            Comp keep = hi ? c2[1] : c2[0];
+        {                               // offset 16: both lanes hold the same column
             Comp got;
-            got.s = __shfl_xor_sync(0xffffffffu, send.s, 16);
-            got.c = __shfl_xor_sync(0xffffffffu, send.c, 16);
-            comp_add(keep, got);
-            d[qn] = keep;
+            got.s = __shfl_xor_sync(0xffffffffu, c1.s, 16);
+            got.c = __shfl_xor_sync(0xffffffffu, c1.c, 16);
+            // fixed order: the lane with bit 4 clear adds its partner's value second
+            Comp lo = ((lane >> 4) & 1) ? got : c1, hi = ((lane >> 4) & 1) ? c1 : got;
+            comp_add(lo, hi);
+            d[qn] = lo;
         }
     }
-    // this lane now holds column jb + 8 b1 + 4 b2 + 2 b3 + b4 (b_n = lane bit n)
-    const int col = jb + 8 * ((lane >> 1) & 1) + 4 * ((lane >> 2) & 1) + 2 * ((lane >> 3) & 1) +
-                    ((lane >> 4) & 1);
+    // this lane now holds column jb + 4 b1 + 2 b2 + b3 (b_n = lane bit n)
+    const int col = jb + 4 * ((lane >> 1) & 1) + 2 * ((lane >> 2) & 1) + ((lane >> 3) & 1);
+    if (((lane >> 4) & 1) == 0) {
 #pragma unroll
-    for (int qn = 0; qn < NQ; ++qn) red[qn][quad][col] = make_float2(d[qn].s, d[qn].c);
-    asm volatile("bar.sync 2, 256;\n" ::: "memory");
-    if (quad == 0) {   // one lane per column adds the four quarters, in order
+        for (int qn = 0; qn < NQ; ++qn) red[qn][quad][col] = make_float2(d[qn].s, d[qn].c);
+    }
+    asm volatile("bar.sync 2, 512;\n" ::: "memory");
+    if (quad == 0 && ((lane >> 4) & 1) == 0) {   // one lane per column adds the four quarters
 #pragma unroll
         for (int qn = 0; qn < NQ; ++qn) {
             Comp t = {red[qn][0][col].x, red[qn][0][col].y};
@@ -135,11 +135,11 @@ __device__ __forceinline__ void column_sum(Comp (&v)[NQ][16], float2 (*red)[4][N
             tot[qn][col] = make_float2(t.s + t.c, 0.f);
         }
     }
-    asm volatile("bar.sync 2, 256;\n" ::: "memory");
+    asm volatile("bar.sync 2, 512;\n" ::: "memory");
 #pragma unroll
     for (int qn = 0; qn < NQ; ++qn)
 #pragma unroll
-        for (int c = 0; c < 16; ++c) v[qn][c] = Comp{tot[qn][jb + c].x, 0.f};
+        for (int c = 0; c < CPT; ++c) v[qn][c] = Comp{tot[qn][jb + c].x, 0.f};
 }
 
 template <int VAR>
@@ -168,10 +168,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
     const uint32_t b_hi = tc::smem_u32(S.B), b_lo = b_hi + BPART;
 
     // state-thread geometry
-    const int quad = warp & 3, half = (warp >> 2) & 1;
+    const int quad = warp & 3, part = warp >> 2;     // TMEM lane quarter, column quarter
     const int i = 16 * quad + (lane >> 1);          // complex row
     const int s = lane & 1;                          // 0: Re lane, 1: Im lane
-    const int jb = 32 * half + 16 * s;               // first of the 16 owned columns
+    const int jb = 16 * part + CPT * s;              // first of the owned columns
     uint32_t phase = 0;
     int err = 0;
 
@@ -181,8 +181,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
         const int K = in.K, T = in.max_iter;
         const float tol2 = in.tol > 0.f ? in.tol * in.tol : -1.f;
 
-        float2 x[16], r[16], p[16];
-        float rho[16], res2[16], btol[16];
+        float2 x[CPT], r[CPT], p[CPT];
+        float rho[CPT], res2[CPT], btol[CPT];
         uint32_t done = 0;                 // bit c: column jb + c stopped (or beyond K)
         int itmax = 0;                     // iterations in which an owned column updated
         float dv = 0.f;
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
         {
             // ---- A in the real 2 x 2-block layout, TF32 head and tail ----
             const float2 *__restrict__ Ag = in.A;   // ld 64, zero beyond K
-            for (int e = threadIdx.x; e < 64 * 32; e += 256) {
+            for (int e = threadIdx.x; e < 64 * 32; e += NTHREADS) {
                 const int ii = e & 63, kp = e >> 6;   // row, pair of columns (2 kp, 2 kp + 1)
                 const float2 a0 = Ag[ii + (size_t)(2 * kp) * 64];
                 const float2 a1 = Ag[ii + (size_t)(2 * kp + 1) * 64];
@@ -212,9 +212,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
             }
             // ---- state init (Step 1; x = 0, r = b, p = D^{-1} r) ----
             dv = (i < K) ? (VAR == 2 ? 1.f : in.dinv[i]) : 0.f;
-            Comp qv[3][16];
+            Comp qv[3][CPT];
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
+            for (int c = 0; c < CPT; ++c) {
                 const int j = jb + c;
                 float2 b = make_float2(0.f, 0.f);
                 if (mode == 0) {
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
             }
             column_sum<3>(qv, S.red, S.tot, quad, jb, lane);
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
+            for (int c = 0; c < CPT; ++c) {
                 rho[c] = qv[0][c].s;
                 res2[c] = qv[1][c].s;
                 btol[c] = tol2 * qv[2][c].s;
@@ -250,12 +250,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
             {
                 // Step 2: stopping test, then publish P = [Re p; Im p] (head, tail)
 #pragma unroll
-                for (int c = 0; c < 16; ++c)
+                for (int c = 0; c < CPT; ++c)
                     if (tol2 > 0.f && res2[c] <= btol[c]) done |= 1u << c;
-                any = done != 0xFFFFu;
+                any = done != (1u << CPT) - 1u;
                 if (t >= T) any = 0;
 #pragma unroll
-                for (int c = 0; c < 16; ++c) {
+                for (int c = 0; c < CPT; ++c) {
                     const int j = jb + c;
                     float ph, pl, qh, ql;
                     tc::split_tf32(p[c].x, ph, pl);
@@ -296,38 +296,35 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
             }
             ++phase;
             tc::tc_fence_after();
-            float v[32];
+            float v[16];
             {
-                const uint32_t ta = tmem + ((uint32_t)(32 * quad) << 16) + 32 * half;
+                const uint32_t ta = tmem + ((uint32_t)(32 * quad) << 16) + 16 * part;
                 float u0[16], u1[16], u2[16];
+                tc::tmem_ld16(ta, u0);
+                tc::tmem_ld16(ta + 64, u1);
+                tc::tmem_ld16(ta + 128, u2);
+                tc::tmem_ld_wait();
 #pragma unroll
-                for (int hlf = 0; hlf < 2; ++hlf) {
-                    tc::tmem_ld16(ta + 16 * hlf, u0);
-                    tc::tmem_ld16(ta + 64 + 16 * hlf, u1);
-                    tc::tmem_ld16(ta + 128 + 16 * hlf, u2);
-                    tc::tmem_ld_wait();
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) v[16 * hlf + e] = (u0[e] + u1[e]) + u2[e];
-                }
+                for (int e = 0; e < 16; ++e) v[e] = (u0[e] + u1[e]) + u2[e];
             }
             // pair Re (even lane) and Im (odd lane) of q[i][j] for the owned columns
-            float2 q[16];
+            float2 q[CPT];
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                const float mine_own = s ? v[16 + c] : v[c];     // my part of my column
-                const float send = s ? v[c] : v[16 + c];         // my part of the partner's column
+            for (int c = 0; c < CPT; ++c) {
+                const float mine_own = s ? v[CPT + c] : v[c];    // my part of my column
+                const float send = s ? v[c] : v[CPT + c];        // my part of the partner's column
                 const float got = __shfl_xor_sync(0xffffffffu, send, 1);
                 q[c] = s ? make_float2(got, mine_own) : make_float2(mine_own, got);
             }
             // lambda = r^H z / p^H A p
             // one row's term per column (plain FMA); the 64-row sums are compensated
-            Comp pq[2][16];
+            Comp pq[2][CPT];
 #pragma unroll
-            for (int c = 0; c < 16; ++c) pq[0][c] = {fmaf(p[c].x, q[c].x, p[c].y * q[c].y), 0.f};
-            column_sum<1>(*reinterpret_cast<Comp(*)[1][16]>(&pq[0]), S.red, S.tot, quad, jb, lane);
-            const bool upd = (done != 0xFFFFu);
+            for (int c = 0; c < CPT; ++c) pq[0][c] = {fmaf(p[c].x, q[c].x, p[c].y * q[c].y), 0.f};
+            column_sum<1>(*reinterpret_cast<Comp(*)[1][CPT]>(&pq[0]), S.red, S.tot, quad, jb, lane);
+            const bool upd = (done != (1u << CPT) - 1u);
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
+            for (int c = 0; c < CPT; ++c) {
                 const float pAp = pq[0][c].s;
                 const bool dn = (done >> c) & 1u;
                 float lam = 0.f;
@@ -344,7 +341,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
             }
             column_sum<2>(pq, S.red, S.tot, quad, jb, lane);
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
+            for (int c = 0; c < CPT; ++c) {
                 const float rz_new = pq[0][c].s;
                 const float beta = rho[c] != 0.f ? rz_new / rho[c] : 0.f;
                 if (!((done >> c) & 1u)) {
@@ -360,7 +357,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
         {
             // ---- outputs ----
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
+            for (int c = 0; c < CPT; ++c) {
                 const int j = jb + c;
                 if (j >= K) continue;
                 float2 val = x[c];
@@ -375,12 +372,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
                 float resmax = 0.f;
                 bool notconv = false;
 #pragma unroll
-                for (int c = 0; c < 16; ++c) {
+                for (int c = 0; c < CPT; ++c) {
                     if (jb + c >= K) continue;
                     resmax = fmaxf(resmax, sqrtf(fmaxf(res2[c], 0.f)));
                     if (tol2 > 0.f && !(res2[c] <= btol[c])) notconv = true;
                 }
-                if (i == 0) {   // one thread per 16 columns: warps 0 and 4, lanes 0 and 1
+                if (i == 0) {   // one thread per 8 columns: quarter-0 warps, lanes 0 and 1
                     if (itmax > 0) atomicMax(acc_out.iters + id, itmax);
                     if (resmax > 0.f) atomicMax(acc_out.resid_bits + id, __float_as_uint(resmax));
                 }
