@@ -8,20 +8,26 @@
 // FP32 accuracy from TF32 units (3xTF32; Ootomo and Yokota, "Recovering
 // single precision accuracy from Tensor Cores while surpassing the FP32
 // theoretical peak performance", IJHPCA 2022): every staged value is split
-// x = hi + lo (hi = x rounded to TF32, lo = exact remainder) and the tile
-// accumulates hi*hi + hi*lo + lo*hi.  The tensor core's FP32 accumulation
-// rounds toward zero, so long accumulation chains drift: the reduction over
-// M is cut into groups of G stages, each accumulated into one of two TMEM
-// buffers from zero, and drain warps add the group results into FP32
-// registers while the next group accumulates into the other buffer.
+// y = hi + lo (hi = y rounded to TF32, lo = exact remainder), and
+// D = Yh^T Yh + Yh^T Yl + Yl^T Yh.  D is symmetric, so the two correction
+// products are transposes of each other: the tile accumulates only
+// E = Yh^T Yl and the epilogue adds E + E^T, two MMAs per k-step instead of
+// three.  The tensor core's FP32 accumulation rounds toward zero, so long
+// accumulation chains drift: the head product's reduction over M is cut into
+// groups of G stages, each accumulated into one of two TMEM buffers from
+// zero, and drain warps add the group results into FP32 registers while the
+// next group accumulates into the other buffer.  E is about 2^-11 of D, so
+// its drift stays far below FP32 rounding of D: it accumulates over the whole
+// instance in a third buffer (two, alternating between instances).
 //
 // Persistent, warp-specialised: the CTA walks its share of the instances.
 //   warps 0-7   producers: H (global -> registers, one stage ahead), TF32
 //               split, Y^T stage tiles (hi, lo) in the canonical no-swizzle
 //               K-major layout;
 //   warps 8-15  drain/epilogue: TMEM -> registers per group; at the end of an
-//               instance D goes through shared memory into A (lower triangle
-//               mirrored, so A is exactly Hermitian) and 1/diag(A);
+//               instance head sums + E + E^T go through shared memory into A
+//               (lower triangle mirrored, so A is exactly Hermitian) and
+//               1/diag(A);
 //   warp 16     TMEM allocation; lane 0 issues the MMAs and commits.
 // Every wait is bounded; a timeout stops the CTA's pipeline, flags its
 // instances with FLAG_TIMEOUT, and the CTA still drains and frees its TMEM.
@@ -45,7 +51,7 @@ constexpr int DPITCH = ROWS + 1;              // floats per staged D row
 constexpr int NPW = 8, NDW = 8;               // producer and drain warps
 constexpr int MMA_WARP = NPW + NDW;
 constexpr int NTHREADS = (NPW + NDW + 1) * 32;
-constexpr int TMEM_COLS = 2 * ROWS;           // two accumulation buffers
+constexpr int TMEM_COLS = 4 * ROWS;           // two head-group buffers, two correction buffers
 
 struct __align__(128) GramSmem {
     unsigned char stage[STAGES][2 * PART];
@@ -54,6 +60,7 @@ struct __align__(128) GramSmem {
     uint64_t empty[STAGES];
     uint64_t accf[2];
     uint64_t acce[2];
+    uint64_t core[2];                          // correction buffer drained
     uint64_t fin;
     uint32_t tmem;
     volatile int err;
@@ -80,6 +87,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc64_kernel(const DevInst *_
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(&S.accf[b], 1);
             tc::mbar_init(&S.acce[b], NDW);
+            tc::mbar_init(&S.core[b], NDW);
         }
         tc::mbar_init(&S.fin, 1);
         S.err = 0;
@@ -185,8 +193,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc64_kernel(const DevInst *_
         const int half = dw >> 2;                  // columns [64 half, 64 half + 64)
         const int row = 32 * quad + lane;          // row of D owned by this thread
         const int dtid = threadIdx.x - NPW * 32;   // 0 .. 255
-        uint32_t grp = 0;
-        for (int j = blockIdx.x; j < n_list; j += gridDim.x) {
+        uint32_t grp = 0, ninst = 0;
+        for (int j = blockIdx.x; j < n_list; j += gridDim.x, ++ninst) {
             const int id = list[j];
             const DevInst &in = insts[id];
             const int nch = (in.M + MCH - 1) / MCH;
@@ -214,8 +222,29 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc64_kernel(const DevInst *_
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&S.acce[b]);
             }
+            // D = head sums + E + E^T (the last group's commit covers every
+            // correction MMA of the instance)
+            const uint32_t te = tmem + ((uint32_t)(32 * quad) << 16) + (2 + (ninst & 1)) * ROWS + half * 64;
 #pragma unroll
-            for (int i = 0; i < 64; ++i) S.D[row * DPITCH + half * 64 + i] = sum[i];
+            for (int c0 = 0; c0 < 64; c0 += 16) {
+                float v[16];
+                tc::tmem_ld16(te + c0, v);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int i = 0; i < 16; ++i) S.D[row * DPITCH + half * 64 + c0 + i] = sum[c0 + i] + v[i];
+            }
+            asm volatile("bar.sync 1, 256;\n" ::: "memory");
+#pragma unroll
+            for (int c0 = 0; c0 < 64; c0 += 16) {   // element (c, row) takes E[row][c]: one writer each
+                float v[16];
+                tc::tmem_ld16(te + c0, v);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int i = 0; i < 16; ++i) S.D[(half * 64 + c0 + i) * DPITCH + row] += v[i];
+            }
+            tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&S.core[ninst & 1]);
             asm volatile("bar.sync 1, 256;\n" ::: "memory");
             const bool bad = S.err != 0;
             const int K = in.K;
@@ -250,10 +279,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc64_kernel(const DevInst *_
     } else if (lane == 0) {
         // ---------------- MMA issuer ----------------
         constexpr uint32_t idesc = tc::idesc_tf32(ROWS, ROWS);
-        uint32_t chunk = 0, grp = 0;
-        for (int j = blockIdx.x; j < n_list && !S.err; j += gridDim.x) {
+        uint32_t chunk = 0, grp = 0, ninst = 0;
+        for (int j = blockIdx.x; j < n_list && !S.err; j += gridDim.x, ++ninst) {
             const DevInst &in = insts[list[j]];
             const int nch = (in.M + MCH - 1) / MCH;
+            const uint32_t e = tmem + (2 + (ninst & 1)) * ROWS;
+            if (ninst >= 2) {   // the correction buffer of two instances ago has been read
+                if (!tc::mbar_wait(&S.core[ninst & 1], ((ninst >> 1) - 1) & 1, WAIT_LIMIT)) {
+                    S.err = 1;
+                    break;
+                }
+                tc::tc_fence_after();
+            }
             for (int c = 0; c < nch; ++c, ++chunk) {
                 const int b = grp & 1;
                 if (c % G == 0 && grp >= 2) {
@@ -277,8 +314,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc64_kernel(const DevInst *_
                     const uint64_t dh = tc::smem_desc(hi + off, LBO, SBO);
                     const uint64_t dl = tc::smem_desc(lo + off, LBO, SBO);
                     tc::mma_tf32(d, dh, dh, idesc, (c % G == 0 && kk == 0) ? 0u : 1u);
-                    tc::mma_tf32(d, dh, dl, idesc, 1u);
-                    tc::mma_tf32(d, dl, dh, idesc, 1u);
+                    tc::mma_tf32(e, dh, dl, idesc, (c == 0 && kk == 0) ? 0u : 1u);
                 }
                 tc::mma_commit(&S.empty[s]);
                 if (c % G == G - 1 || c == nch - 1) {
