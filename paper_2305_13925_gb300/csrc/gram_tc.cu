@@ -21,9 +21,17 @@
 // instance in a third buffer (two, alternating between instances).
 //
 // Persistent, warp-specialised: the CTA walks its share of the instances.
-//   warps 0-7   producers: H (global -> registers, one stage ahead), TF32
-//               split, Y^T stage tiles (hi, lo) in the canonical no-swizzle
-//               K-major layout;
+//   warps 0-7   producers: H streamed with per-thread asynchronous copies
+//               (cp.async, 16 bytes, zero-filled past M and K) RAW - 1 stages
+//               ahead into a ring of raw stages, then TF32 split into Y^T
+//               stage tiles (hi, lo) in the canonical no-swizzle K-major
+//               layout.  Warp w owns the 8 columns k = 8 i + ((w + i) mod 8),
+//               i = 0..7, of every stage: each copy instruction reads whole
+//               column pieces (two of 256 bytes), which streams H near the
+//               HBM rate where scattered 64-byte pieces did not; the raw
+//               chunks are XOR-swizzled by i, so copies, raw reads and split
+//               stores are free of bank conflicts; a warp reads only what it
+//               copied, so a __syncwarp after its own cp.async wait suffices;
 //   warps 8-15  drain/epilogue: TMEM -> registers per group; at the end of an
 //               instance head sums + E + E^T go through shared memory into A
 //               (lower triangle mirrored, so A is exactly Hermitian) and
@@ -41,7 +49,9 @@ namespace {
 
 constexpr int ROWS = 128;                     // 2K rows of Y^T for K = 64
 constexpr int MCH = 32;                       // H rows (reduction values) per stage
-constexpr int STAGES = 4;
+constexpr int STAGES = 2;                     // split stages shared with the MMA warp
+constexpr int RAW = 6;                        // raw stages in flight per producer thread
+constexpr int RAWB = MCH * 64 * 8;            // bytes of one raw stage (16 KB)
 constexpr int G = 4;                          // stages per accumulation group
 constexpr int PART = ROWS * MCH * 4;          // bytes of one part (hi or lo) of a stage
 constexpr uint32_t LBO = 128;                 // K-adjacent core matrices
@@ -55,6 +65,7 @@ constexpr int TMEM_COLS = 4 * ROWS;           // two head-group buffers, two cor
 
 struct __align__(128) GramSmem {
     unsigned char stage[STAGES][2 * PART];
+    unsigned char raw[RAW][RAWB];               // [q][part][thread] 16-byte chunks
     float D[ROWS * DPITCH];
     uint64_t full[STAGES];
     uint64_t empty[STAGES];
@@ -65,6 +76,8 @@ struct __align__(128) GramSmem {
     uint32_t tmem;
     volatile int err;
 };
+
+static_assert(sizeof(GramSmem) <= 227 * 1024, "shared memory");
 
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, float a, float b, float c, float d) {
     asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(addr), "f"(a), "f"(b), "f"(c),
@@ -104,42 +117,74 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc64_kernel(const DevInst *_
 
     if (warp < NPW) {
         // ---------------- producers ----------------
-        const int tid = threadIdx.x;   // 0 .. 255
-        uint32_t chunk = 0;
-        for (int j = blockIdx.x; j < n_list && !S.err; j += gridDim.x) {
-            const DevInst &in = insts[list[j]];
-            const int M = in.M, K = in.K, ldh = in.ldh;
-            const float2 *__restrict__ H = in.H;
-            const bool bf16 = in.h_bf16 != 0;
-            const int nch = (M + MCH - 1) / MCH;
-            auto load = [&](int c, float4 (&buf)[2][2]) {
+        const uint32_t raw0 = tc::smem_u32(S.raw[0]);
+        // stream cursor: (instance ordinal, stage) in this CTA's walk
+        struct Cursor {
+            int j, c, nch, M, K, ldh;
+            const char *H;
+            bool bf16;
+        };
+        auto cursor_load = [&](Cursor &u) {
+            if (u.j < n_list) {
+                const DevInst &in = insts[list[u.j]];
+                u.M = in.M;
+                u.K = in.K;
+                u.ldh = in.ldh;
+                u.H = reinterpret_cast<const char *>(in.H);
+                u.bf16 = in.h_bf16 != 0;
+                u.nch = (u.M + MCH - 1) / MCH;
+            }
+        };
+        auto cursor_next = [&](Cursor &u) {
+            if (++u.c >= u.nch) {
+                u.c = 0;
+                u.j += gridDim.x;
+                cursor_load(u);
+            }
+        };
+        // warp w's chunks of stage u into raw stage rs.  complex64: column slot i
+        // holds 32 entries = 16 chunks pc of 2 entries at 16-byte slot pc ^ i;
+        // bfloat16: 8 chunks of 4 entries at slot pc ^ i.
+        auto issue = [&](const Cursor &u, int rs) {
+            if (u.j < n_list) {
+                const uint32_t wbase = raw0 + rs * RAWB + warp * 8 * 256;   // 8 column slots of 256 B
+                if (u.bf16) {
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int e = tid + 256 * q;
-                    const int k = (e & 7) + 8 * (e >> 6), mq = (e >> 3) & 7;
-                    const int m = c * MCH + 4 * mq;
-                    const size_t idx = (size_t)k * ldh + m;
-                    if (k < K && m + 3 < M && !bf16) {
-                        const float2 *p = H + idx;
-                        buf[q][0] = __ldg(reinterpret_cast<const float4 *>(p));
-                        buf[q][1] = __ldg(reinterpret_cast<const float4 *>(p) + 1);
-                    } else if (k < K && m + 3 < M) {   // bfloat16 pairs, 16 bytes = 4 entries
-                        const uint4 u = __ldg(reinterpret_cast<const uint4 *>(
-                            reinterpret_cast<const uint32_t *>(H) + idx));
-                        const float2 a = bf16x2_to_float2(u.x), b = bf16x2_to_float2(u.y);
-                        const float2 c2 = bf16x2_to_float2(u.z), d = bf16x2_to_float2(u.w);
-                        buf[q][0] = make_float4(a.x, a.y, b.x, b.y);
-                        buf[q][1] = make_float4(c2.x, c2.y, d.x, d.y);
-                    } else {
-                        float2 v[4];
+                    for (int q = 0; q < 2; ++q) {
+                        const int i = 4 * q + (lane >> 3), pc = lane & 7;
+                        const int k = 8 * i + ((warp + i) & 7);
+                        const int m = u.c * MCH + 4 * pc;
+                        const int left = k < u.K ? min(max(u.M - m, 0), 4) : 0;
+                        const char *src = u.H + ((size_t)k * u.ldh + m) * 4;
+                        tc::cp_async16(wbase + i * 128 + ((pc ^ i) & 7) * 16, left ? src : u.H, left * 4);
+                    }
+                } else {
 #pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            v[i] = (k < K && m + i < M) ? load_h(H, bf16, idx + i) : make_float2(0.f, 0.f);
-                        buf[q][0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-                        buf[q][1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+                    for (int q = 0; q < 4; ++q) {
+                        const int i = 2 * q + (lane >> 4), pc = lane & 15;
+                        const int k = 8 * i + ((warp + i) & 7);
+                        const int m = u.c * MCH + 2 * pc;
+                        const int left = k < u.K ? min(max(u.M - m, 0), 2) : 0;
+                        const char *src = u.H + ((size_t)k * u.ldh + m) * 8;
+                        tc::cp_async16(wbase + i * 256 + (pc ^ i) * 16, left ? src : u.H, left * 8);
                     }
                 }
-            };
+            }
+            tc::cp_async_commit();   // one group per stage, empty past the end
+        };
+        Cursor iu{(int)blockIdx.x, 0, 0, 0, 0, 0, nullptr, false};
+        cursor_load(iu);
+#pragma unroll 1
+        for (int p = 0; p < RAW - 1; ++p) {
+            issue(iu, p);
+            cursor_next(iu);
+        }
+        uint32_t chunk = 0, sc = 0;
+        for (int j = blockIdx.x; j < n_list && !S.err; j += gridDim.x) {
+            const DevInst &in = insts[list[j]];
+            const int M = in.M;
+            const bool bf16 = in.h_bf16 != 0;
+            const int nch = (M + MCH - 1) / MCH;
             auto put = [&](const float4 (&buf)[2][2]) -> bool {
                 const int s = chunk % STAGES;
                 if (chunk >= STAGES &&
@@ -150,8 +195,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc64_kernel(const DevInst *_
                 const uint32_t base = tc::smem_u32(S.stage[s]);
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
-                    const int e = tid + 256 * q;
-                    const int k = (e & 7) + 8 * (e >> 6), mq = (e >> 3) & 7;
+                    const int i = lane & 7, mq = (lane >> 3) + 4 * q;
+                    const int k = 8 * i + ((warp + i) & 7);
                     const float re[4] = {buf[q][0].x, buf[q][0].z, buf[q][1].x, buf[q][1].z};
                     const float im[4] = {buf[q][0].y, buf[q][0].w, buf[q][1].y, buf[q][1].w};
                     float rh[4], rl[4], ih[4], il[4];
@@ -173,19 +218,33 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc64_kernel(const DevInst *_
                 ++chunk;
                 return true;
             };
-            // loads run two stages ahead of the shared-memory stores
-            float4 bA[2][2], bB[2][2];
-            if (nch > 0) load(0, bA);
-            if (nch > 1) load(1, bB);
-            for (int c = 0; c < nch; c += 2) {
-                if (!put(bA)) break;
-                if (c + 2 < nch) load(c + 2, bA);
-                if (c + 1 < nch) {
-                    if (!put(bB)) break;
-                    if (c + 3 < nch) load(c + 3, bB);
+            bool ok = true;
+            for (int c = 0; c < nch && ok; ++c, ++sc) {
+                tc::cp_async_wait<RAW - 2>();   // this thread's chunks of stage sc have landed
+                __syncwarp();                   // ... and those of the rest of its warp
+                const int rs = sc % RAW;
+                float4 buf[2][2];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {   // entries 4 mq .. 4 mq + 3 of column slot i
+                    const int i = lane & 7, mq = (lane >> 3) + 4 * q;
+                    const unsigned char *wr = S.raw[rs] + warp * 8 * 256;
+                    if (bf16) {
+                        const uint4 u = *reinterpret_cast<const uint4 *>(wr + i * 128 + ((mq ^ i) & 7) * 16);
+                        const float2 a = bf16x2_to_float2(u.x), b = bf16x2_to_float2(u.y);
+                        const float2 c2 = bf16x2_to_float2(u.z), d = bf16x2_to_float2(u.w);
+                        buf[q][0] = make_float4(a.x, a.y, b.x, b.y);
+                        buf[q][1] = make_float4(c2.x, c2.y, d.x, d.y);
+                    } else {
+                        buf[q][0] = *reinterpret_cast<const float4 *>(wr + i * 256 + ((2 * mq) ^ i) * 16);
+                        buf[q][1] = *reinterpret_cast<const float4 *>(wr + i * 256 + ((2 * mq + 1) ^ i) * 16);
+                    }
                 }
+                issue(iu, (sc + RAW - 1) % RAW);   // refills the stage read one step ago
+                cursor_next(iu);
+                ok = put(buf);
             }
         }
+        tc::cp_async_wait_all();   // no copy may still be landing when the CTA exits
     } else if (warp < MMA_WARP) {
         // ---------------- drain / epilogue ----------------
         const int dw = warp - NPW;                 // 0 .. 7
