@@ -12,9 +12,19 @@
 // reduction is only 2K long, so one TMEM accumulation per tile suffices.
 //
 // Persistent, warp-specialised, one CTA per SM walking its instances:
-//   warps 0-7   producers: per instance B (from the iterate X), then per tile
-//               H stage tiles [Hr | Hi] (16 users per stage) transposed into
-//               the canonical K-major layout;
+//   warps 0-7   producers: a stream of raw stages fetched RAW - 1 stages
+//               ahead with per-thread asynchronous copies (cp.async, 16
+//               bytes, zero-filled past M and K): per instance two stages of
+//               the iterate X (each thread copies the chunks it converts),
+//               then the H stages, where warp w copies antennas
+//               16 w .. 16 w + 15 of the stage's 16 users -- whole 128-byte
+//               lines per column -- and converts exactly those rows, so a
+//               __syncwarp after its own cp.async wait suffices.  Every stage
+//               keeps warp w's bytes in its own 2 KB of the raw stage: the
+//               warps run unsynchronised, and a warp refilling a stage must
+//               not overwrite bytes another warp has yet to read.  Conversion:
+//               B = [Xr^T ; Xi^T] and per stage H tiles [Hr | Hi], TF32 head
+//               and tail, transposed into the canonical K-major layout;
 //   warps 8-15  drain: TMEM (two alternating 128-column accumulators) ->
 //               registers -> W (complex64, column-major, coalesced) and this
 //               tile's ||W||_F^2 partial in its own slot;
@@ -30,7 +40,9 @@ namespace {
 
 constexpr int TMR = 128;                      // W rows per tile
 constexpr int KCH = 16;                       // users (reduction values) per stage
-constexpr int STAGES = 4;
+constexpr int STAGES = 2;                     // split stages shared with the MMA warp
+constexpr int RAW = 6;                        // raw stages in flight per producer thread
+constexpr int RAWB = 16 * 1024;               // bytes of one raw stage
 constexpr int APART = TMR * KCH * 4;          // one of Yr_hi, Yr_lo, Yi_hi, Yi_lo: 8 KB
 constexpr int BPART = 128 * 64 * 4;           // one of B_hi, B_lo: 32 KB
 constexpr uint32_t LBO = 128;
@@ -45,6 +57,7 @@ constexpr int TMEM_COLS = 256;
 struct __align__(128) HxSmem {
     unsigned char B[2 * BPART];
     unsigned char stage[STAGES][4 * APART];
+    unsigned char raw[RAW][RAWB];
     float wsum[2][NDW];
     uint64_t full[STAGES];
     uint64_t empty[STAGES];
@@ -55,6 +68,8 @@ struct __align__(128) HxSmem {
     uint32_t tmem;
     volatile int err;
 };
+
+static_assert(sizeof(HxSmem) <= 227 * 1024, "shared memory");
 
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, float a, float b, float c, float d) {
     asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(addr), "f"(a), "f"(b), "f"(c),
@@ -96,80 +111,137 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_tc64_kernel(const DevInst *__r
     if (warp < NPW) {
         // ---------------- producers ----------------
         const int tid = threadIdx.x;   // 0 .. 255
-        uint32_t chunk = 0, ninst = 0;
         const uint32_t bbase = tc::smem_u32(S.B);
+        const uint32_t raw0 = tc::smem_u32(S.raw[0]);
+        // stream cursor: (instance ordinal, stage) of this CTA's walk; per instance
+        // stages 0 and 1 carry X (columns 32 t ..), then the H stages
+        struct Cursor {
+            int j, t, nst, nks, M, K, ldh;
+            const char *H;
+            const char *X;
+            bool bf16;
+        };
+        auto cursor_load = [&](Cursor &u) {
+            if (u.j < n_list) {
+                const DevInst &in = insts[list[u.j]];
+                u.M = in.M;
+                u.K = in.K;
+                u.ldh = in.ldh;
+                u.H = reinterpret_cast<const char *>(in.H);
+                u.X = reinterpret_cast<const char *>(in.X);
+                u.bf16 = in.h_bf16 != 0;
+                u.nks = (u.K + KCH - 1) / KCH;
+                u.nst = 2 + ((u.M + TMR - 1) / TMR) * u.nks;
+            }
+        };
+        auto cursor_next = [&](Cursor &u) {
+            if (++u.t >= u.nst) {
+                u.t = 0;
+                u.j += gridDim.x;
+                cursor_load(u);
+            }
+        };
+        auto issue = [&](const Cursor &u, int rs) {
+            if (u.j < n_list) {
+                const uint32_t rb = raw0 + rs * RAWB;
+                if (u.t < 2) {
+                    // X rows 4 rq .. 4 rq + 3 of column n, as two chunks of two rows
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int e = tid + 256 * (2 * u.t + h);
+                        const int n = (e & 7) + 8 * (e >> 7), rq = (e >> 3) & 15;
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) {
+                            const int r = 4 * rq + 2 * c;
+                            const int left = n < u.K ? min(max(u.K - r, 0), 2) : 0;
+                            const char *src = u.X + ((size_t)n * 64 + r) * 8;
+                            tc::cp_async16(rb + warp * 2048 + ((2 * h + c) * 32 + lane) * 16, left ? src : u.X,
+                                           left * 8);
+                        }
+                    }
+                } else {
+                    const int st = u.t - 2, mt = st / u.nks, ks = st % u.nks;
+                    const uint32_t wb = rb + warp * 2048;   // this warp's 16 columns x 128 bytes
+                    if (u.bf16) {
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {   // 16 columns x 4 chunks of 4 antennas
+                            const int kk = 8 * q + (lane >> 2), pc = lane & 3;
+                            const int k = ks * KCH + kk, m = mt * TMR + 16 * warp + 4 * pc;
+                            const int left = k < u.K ? min(max(u.M - m, 0), 4) : 0;
+                            const char *src = u.H + ((size_t)k * u.ldh + m) * 4;
+                            tc::cp_async16(wb + kk * 64 + pc * 16, left ? src : u.H, left * 4);
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {   // 16 columns x 8 chunks of 2 antennas
+                            const int kk = 4 * q + (lane >> 3), pc = lane & 7;
+                            const int k = ks * KCH + kk, m = mt * TMR + 16 * warp + 2 * pc;
+                            const int left = k < u.K ? min(max(u.M - m, 0), 2) : 0;
+                            const char *src = u.H + ((size_t)k * u.ldh + m) * 8;
+                            tc::cp_async16(wb + kk * 128 + pc * 16, left ? src : u.H, left * 8);
+                        }
+                    }
+                }
+            }
+            tc::cp_async_commit();   // one group per stage, empty past the end
+        };
+        Cursor iu{(int)blockIdx.x, 0, 0, 0, 0, 0, 0, nullptr, nullptr, false};
+        cursor_load(iu);
+#pragma unroll 1
+        for (int p = 0; p < RAW - 1; ++p) {
+            issue(iu, p);
+            cursor_next(iu);
+        }
+        uint32_t chunk = 0, ninst = 0, sc = 0;
         for (int j = blockIdx.x; j < n_list && !S.err; j += gridDim.x, ++ninst) {
             const DevInst &in = insts[list[j]];
-            const int M = in.M, K = in.K, ldh = in.ldh;
-            const float2 *__restrict__ H = in.H;
+            const int M = in.M, K = in.K;
             const bool bf16 = in.h_bf16 != 0;
-            const float2 *__restrict__ X = in.X;   // ld 64
             // B = [Xr^T ; Xi^T], rewritten once the previous instance's MMAs are done
             if (ninst > 0 && !tc::mbar_wait(&S.bempty, (ninst - 1) & 1, WAIT_LIMIT)) {
                 S.err = 1;
                 break;
             }
+            for (int xs = 0; xs < 2; ++xs, ++sc) {
+                tc::cp_async_wait<RAW - 2>();   // the chunks this thread copied have landed
+                const unsigned char *rbuf = S.raw[sc % RAW];
+                float2 v[2][4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int e = tid + 256 * q;
-                const int n = (e & 7) + 8 * (e >> 7), rq = (e >> 3) & 15;
-                float2 v[4];
+                for (int h = 0; h < 2; ++h)
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int r = 4 * rq + i;
-                    v[i] = (n < K && r < K) ? __ldg(X + r + (size_t)n * 64) : make_float2(0.f, 0.f);
+                    for (int c = 0; c < 2; ++c) {
+                        const float4 w4 =
+                            *reinterpret_cast<const float4 *>(rbuf + warp * 2048 + ((2 * h + c) * 32 + lane) * 16);
+                        v[h][2 * c] = make_float2(w4.x, w4.y);
+                        v[h][2 * c + 1] = make_float2(w4.z, w4.w);
+                    }
+                issue(iu, (sc + RAW - 1) % RAW);
+                cursor_next(iu);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int e = tid + 256 * (2 * xs + h);
+                    const int n = (e & 7) + 8 * (e >> 7), rq = (e >> 3) & 15;
+                    float rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        tc::split_tf32(v[h][i].x, rh[i], rl[i]);
+                        tc::split_tf32(v[h][i].y, ih[i], il[i]);
+                    }
+                    const uint32_t o_r = (uint32_t)(n >> 3) * SBO_B + rq * LBO + (n & 7) * 16;
+                    const uint32_t o_i = (uint32_t)((64 + n) >> 3) * SBO_B + rq * LBO + (n & 7) * 16;
+                    st_shared_v4(bbase + o_r, rh[0], rh[1], rh[2], rh[3]);
+                    st_shared_v4(bbase + o_i, ih[0], ih[1], ih[2], ih[3]);
+                    st_shared_v4(bbase + BPART + o_r, rl[0], rl[1], rl[2], rl[3]);
+                    st_shared_v4(bbase + BPART + o_i, il[0], il[1], il[2], il[3]);
                 }
-                float rh[4], rl[4], ih[4], il[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    tc::split_tf32(v[i].x, rh[i], rl[i]);
-                    tc::split_tf32(v[i].y, ih[i], il[i]);
-                }
-                const uint32_t o_r = (uint32_t)(n >> 3) * SBO_B + rq * LBO + (n & 7) * 16;
-                const uint32_t o_i = (uint32_t)((64 + n) >> 3) * SBO_B + rq * LBO + (n & 7) * 16;
-                st_shared_v4(bbase + o_r, rh[0], rh[1], rh[2], rh[3]);
-                st_shared_v4(bbase + o_i, ih[0], ih[1], ih[2], ih[3]);
-                st_shared_v4(bbase + BPART + o_r, rl[0], rl[1], rl[2], rl[3]);
-                st_shared_v4(bbase + BPART + o_i, il[0], il[1], il[2], il[3]);
             }
             tc::fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&S.bfull);
-            // H tiles: stage t = (tile t / nks, users 16 (t % nks) ...); loads run two stages ahead
+            // H tiles: stage t = (tile t / nks, users 16 (t % nks) ...)
             const int nmt = (M + TMR - 1) / TMR;
             const int nks = (K + KCH - 1) / KCH;
             const int T = nmt * nks;
-            auto load = [&](int t, float2 (&h)[2][4]) {
-                const int mt = t / nks, ks = t % nks;
-                if (bf16) {   // storage type decided once per stage, not per element
-                    const uint32_t *__restrict__ Hb = reinterpret_cast<const uint32_t *>(H);
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const int e = tid + 256 * q;
-                        const int m = e & 127, kq = e >> 7;
-                        const int gm = mt * TMR + m;
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const int k = ks * KCH + 4 * kq + i;
-                            h[q][i] = (gm < M && k < K) ? bf16x2_to_float2(__ldg(Hb + gm + (size_t)k * ldh))
-                                                        : make_float2(0.f, 0.f);
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const int e = tid + 256 * q;
-                        const int m = e & 127, kq = e >> 7;
-                        const int gm = mt * TMR + m;
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const int k = ks * KCH + 4 * kq + i;
-                            h[q][i] = (gm < M && k < K) ? __ldg(H + gm + (size_t)k * ldh)
-                                                        : make_float2(0.f, 0.f);
-                        }
-                    }
-                }
-            };
             auto put = [&](const float2 (&h)[2][4]) -> bool {
                 const int s = chunk % STAGES;
                 if (chunk >= STAGES &&
@@ -180,8 +252,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_tc64_kernel(const DevInst *__r
                 const uint32_t base = tc::smem_u32(S.stage[s]);
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
-                    const int e = tid + 256 * q;
-                    const int m = e & 127, kq = e >> 7;
+                    const int m = 16 * warp + (lane & 15), kq = (lane >> 4) + 2 * q;
                     float rh[4], rl[4], ih[4], il[4];
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
@@ -200,18 +271,28 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_tc64_kernel(const DevInst *__r
                 ++chunk;
                 return true;
             };
-            float2 hA[2][4], hB[2][4];
-            if (T > 0) load(0, hA);
-            if (T > 1) load(1, hB);
-            for (int t = 0; t < T; t += 2) {
-                if (!put(hA)) break;
-                if (t + 2 < T) load(t + 2, hA);
-                if (t + 1 < T) {
-                    if (!put(hB)) break;
-                    if (t + 3 < T) load(t + 3, hB);
+            bool ok = true;
+            for (int t = 0; t < T && ok; ++t, ++sc) {
+                tc::cp_async_wait<RAW - 2>();   // this thread's chunks of the stage have landed
+                __syncwarp();                   // ... and those of the rest of its warp
+                const unsigned char *wr = S.raw[sc % RAW] + warp * 2048;
+                float2 h[2][4];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {   // antenna m, users 4 kq .. 4 kq + 3
+                    const int ml = lane & 15, kq = (lane >> 4) + 2 * q;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int kk = 4 * kq + i;
+                        h[q][i] = bf16 ? bf16x2_to_float2(*reinterpret_cast<const uint32_t *>(wr + kk * 64 + ml * 4))
+                                       : *reinterpret_cast<const float2 *>(wr + kk * 128 + ml * 8);
+                    }
                 }
+                issue(iu, (sc + RAW - 1) % RAW);   // refills the stage read one step ago
+                cursor_next(iu);
+                ok = put(h);
             }
         }
+        tc::cp_async_wait_all();   // no copy may still be landing when the CTA exits
     } else if (warp < MMA_WARP) {
         // ---------------- drain ----------------
         const int dw = warp - NPW;

@@ -85,3 +85,26 @@ def test_tensor_plain_cg_variant(simt_iteration):
     for i in range(8):
         ref = O.precode(Hs[i], xi[i], "cg", max_iter=6)
         assert rel_fro(out["W"][i], ref["W"]) <= tol_for(Hs[i], xi[i], "cg", 6)
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_tensor_many_instances_per_cta(bf16):
+    """456 instances of the K = 64 class (three per persistent CTA), M not a
+    multiple of the 128-row tile and K < 64 mixed in: the copy streams, split
+    stages, B rewrites and TMEM buffers that cross instance boundaries inside
+    one CTA, every instance against the oracle."""
+    rng = np.random.default_rng(3)
+    Hs, xis = [], []
+    for n in range(456):
+        M = int(rng.choice([96, 257, 1000, 1024]))
+        K = int(rng.choice([33, 48, 64]))
+        spec = C.ChannelSpec(M=M, S=1, K=K, r=(0.5, 0.5), n_vis=(1, 1), snr_db=(10.0,))
+        inst = C.generate_instance(spec, 21, n)
+        Hs.append(C.round_complex_bf16(inst.H) if bf16 else C.round_complex64(inst.H))
+        xis.append(inst.xi)
+    out = run(Hs, xis, T=6, precision="tf32x3", bf16=bf16)
+    refs = O.precode_batch(Hs, xis, "standard", max_iter=6)[0]
+    assert (out["status"] == 0).all()
+    errs = [rel_fro(out["W"][i], refs[i]) for i in range(len(Hs))]
+    worst = int(np.argmax(errs))
+    assert errs[worst] <= TOL_W, (worst, Hs[worst].shape, errs[worst])
