@@ -174,8 +174,13 @@ __device__ __forceinline__ float tf32_rna(float x) {
     asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
     return __uint_as_float(r);
 }
+// x = hi + lo exactly, hi = x rounded to TF32 (nearest, ties away from zero):
+// adding half a TF32 unit (bit 12) to the magnitude bits and clearing the 13
+// low bits rounds the magnitude half-up, the same result as tf32_rna for
+// finite x in two full-rate integer operations (a carry into the exponent is
+// the correct rounding up to the next binade)
 __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo) {
-    hi = tf32_rna(x);
+    hi = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
     lo = x - hi;
 }
 
