@@ -87,22 +87,29 @@ static double norm2(int K, const cplx *a)
  * z = C^{-1} r, lambda = r^H z / d^H P d, and beta = r_new^H z_new / r^H z
  * (the ratio of Eq. 20 as printed is garbled; this is the standard PCG
  * ratio, the same form Algorithm 1 uses).  dinv = NULL gives C = I, plain CG.
- * w^0 = 0.  Step 2's test runs before each update: when tol > 0 the
+ * The initial point w^0 is x0, or 0 when x0 is NULL (Step 1 leaves w^0 open;
+ * the residual form starts from r^0 = s - P w^0, which for a warm start from
+ * a previous slot's solution is small).  Step 2's test runs before each
+ * update, always relative to ||s||: when tol > 0 the
  * column stops once ||r|| <= tol ||b||; tol <= 0 runs exactly max_iter
  * updates.  An exactly converged column (d^H P d == 0 with r == 0) keeps
  * its iterate.
  * Pinned by: exactness in <= K steps, the Krylov-subspace minimisation
- * property of (preconditioned) CG, one-step exactness for diagonal P, and
- * the recurrence residual agreeing with s - P w.                          */
+ * property of (preconditioned) CG, one-step exactness for diagonal P, the
+ * recurrence residual agreeing with s - P w, and for w^0 != 0: a start at
+ * the solution stays there, and every iterate equals w^0 plus the cold
+ * iterate for the right-hand side s - P w^0.                              */
 static int pcg_standard(int K, const cplx *A, const double *dinv, const cplx *b,
-                        int max_iter, double tol, cplx *x, int *iters, double *relres,
-                        cplx *r, cplx *z, cplx *d, cplx *q)
+                        const cplx *x0, int max_iter, double tol, cplx *x, int *iters,
+                        double *relres, cplx *r, cplx *z, cplx *d, cplx *q)
 {
     int status = ORC_OK;
     double bnorm = norm2(K, b);
+    for (int i = 0; i < K; ++i)
+        x[i] = x0 ? x0[i] : 0.0;
+    matvec(K, A, x, q);                           /* P w^0 */
     for (int i = 0; i < K; ++i) {
-        x[i] = 0.0;
-        r[i] = b[i];
+        r[i] = b[i] - q[i];
         z[i] = dinv ? dinv[i] * r[i] : r[i];
         d[i] = z[i];
     }
@@ -143,19 +150,22 @@ static int pcg_standard(int K, const cplx *A, const double *dinv, const cplx *b,
  *   loop  alpha = r^H r / (m^H C^{-1} P m); w += alpha m;
  *         r -= alpha C^{-1} P m; b = r_new^H r_new / r^H r; m = r_new + b m.
  * C = D, the diagonal of P (Eq. 21).  C^{-1} P is not Hermitian, so alpha
- * is complex in general.  The tolerance test (tol > 0) is applied before
+ * is complex in general.  With an initial point w^0 = x0 (NULL: 0) the
+ * scaled residual starts as r = C^{-1} (s - P w^0).  The tolerance test (tol > 0) is applied before
  * each update to the unscaled residual D r = s - P w: ||D r|| <= tol ||s||.
  * Pinned by: one-step exactness for diagonal P, equality with plain CG when
  * D = cI, convergence to P^{-1} s, and D r agreeing with s - P w.         */
 static int pcg_alg1(int K, const cplx *A, const double *dinv, const double *dvec,
-                    const cplx *s, int max_iter, double tol, cplx *w, int *iters,
-                    double *relres, cplx *r, cplx *m, cplx *u, cplx *tmp)
+                    const cplx *s, const cplx *x0, int max_iter, double tol, cplx *w,
+                    int *iters, double *relres, cplx *r, cplx *m, cplx *u, cplx *tmp)
 {
     int status = ORC_OK;
     double snorm = norm2(K, s);
+    for (int i = 0; i < K; ++i)
+        w[i] = x0 ? x0[i] : 0.0;
+    matvec(K, A, w, tmp);                         /* P w^0 */
     for (int i = 0; i < K; ++i) {
-        w[i] = 0.0;
-        r[i] = dinv[i] * s[i];
+        r[i] = dinv[i] * (s[i] - tmp[i]);
         m[i] = r[i];
     }
     double rr = creal(dotc(K, r, r));
@@ -199,10 +209,12 @@ static int pcg_alg1(int K, const cplx *A, const double *dinv, const double *dvec
 /* ------------------------------------------------------------------------ */
 /* Solve P X = B column by column with the chosen iteration (Eq. 16 for each
  * column of B; B = I gives X = P^{-1} as used by the RZF precoder, Eq. 7).
- * B may be NULL for the identity.  iters / relres receive per-column
+ * B may be NULL for the identity.  X0 (K x nrhs, ld ldx0) is the initial
+ * point of every column, NULL for zero.  iters / relres receive per-column
  * values (may be NULL).  Returns the worst column status.                 */
 int orc_pcg(int K, const cplx *A, const cplx *B, int ldb, int nrhs, int variant,
-            int max_iter, double tol, cplx *X, int ldx, int *iters, double *relres)
+            int max_iter, double tol, const cplx *X0, int ldx0, cplx *X, int ldx, int *iters,
+            double *relres)
 {
     double *dvec = malloc(sizeof(double) * K);
     double *dinv = malloc(sizeof(double) * K);
@@ -224,10 +236,11 @@ int orc_pcg(int K, const cplx *A, const cplx *B, int ldb, int nrhs, int variant,
         double rel = 0.0;
         int st;
         cplx *x = X + (size_t)j * ldx;
+        const cplx *x0 = X0 ? X0 + (size_t)j * ldx0 : NULL;
         if (variant == ORC_ALG1)
-            st = pcg_alg1(K, A, dinv, dvec, b, max_iter, tol, x, &it, &rel, r, z, d, q);
+            st = pcg_alg1(K, A, dinv, dvec, b, x0, max_iter, tol, x, &it, &rel, r, z, d, q);
         else
-            st = pcg_standard(K, A, variant == ORC_CG ? NULL : dinv, b, max_iter, tol, x,
+            st = pcg_standard(K, A, variant == ORC_CG ? NULL : dinv, b, x0, max_iter, tol, x,
                               &it, &rel, r, z, d, q);
         if (iters) iters[j] = it;
         if (relres) relres[j] = rel;
@@ -370,7 +383,7 @@ int orc_precode(int M, int K, const cplx *H, int ldh, double xi, int variant, in
         return ORC_NOMEM;
     }
     orc_gram(M, K, H, ldh, xi, A);
-    int st = orc_pcg(K, A, NULL, K, K, variant, max_iter, tol, X, K, it, rr);
+    int st = orc_pcg(K, A, NULL, K, K, variant, max_iter, tol, NULL, K, X, K, it, rr);
     orc_matmul(M, K, K, H, ldh, X, K, W, ldw);
     if (beta) *beta = orc_power_factor(M, K, W, ldw, power);
     int imax = 0;

@@ -54,7 +54,7 @@ def lib():
             P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
             L.orc_gram.argtypes = [I, I, P, I, D, P]
             L.orc_gram.restype = None
-            L.orc_pcg.argtypes = [I, P, P, I, I, I, I, D, P, I, P, P]
+            L.orc_pcg.argtypes = [I, P, P, I, I, I, I, D, P, I, P, I, P, P]
             L.orc_pcg.restype = I
             L.orc_matmul.argtypes = [I, I, I, P, I, P, I, P, I]
             L.orc_matmul.restype = None
@@ -94,8 +94,9 @@ def gram(H: np.ndarray, xi: float) -> np.ndarray:
 
 
 def pcg(A: np.ndarray, B: np.ndarray | None = None, variant="standard", max_iter: int = 8,
-        tol: float = 0.0):
-    """Solve A X = B (B = None for the identity) with the chosen iteration.
+        tol: float = 0.0, X0: np.ndarray | None = None):
+    """Solve A X = B (B = None for the identity) with the chosen iteration,
+    starting from X0 (None: zero) in every column.
 
     Returns (X, iters per column, recurrence relative residual per column, status).
     """
@@ -108,11 +109,12 @@ def pcg(A: np.ndarray, B: np.ndarray | None = None, variant="standard", max_iter
         Bf = _f(B.reshape(K, -1))
         nrhs, ldb = Bf.shape[1], K
         Bp = _p(Bf)
+    X0f = None if X0 is None else _f(np.asarray(X0).reshape(K, nrhs))
     X = np.zeros((K, nrhs), dtype=np.complex128, order="F")
     it = np.zeros(nrhs, dtype=np.int32)
     rr = np.zeros(nrhs, dtype=np.float64)
     st = lib().orc_pcg(K, _p(Af), Bp, ldb, nrhs, _variant(variant), int(max_iter), float(tol),
-                       _p(X), K, _p(it), _p(rr))
+                       None if X0f is None else _p(X0f), K, _p(X), K, _p(it), _p(rr))
     return np.ascontiguousarray(X), it, rr, st
 
 
@@ -183,6 +185,25 @@ def precode(H: np.ndarray, xi: float, variant="standard", max_iter: int = 8, tol
                            ctypes.byref(iters), ctypes.byref(relres))
     return dict(W=np.ascontiguousarray(W), A=np.ascontiguousarray(A), X=np.ascontiguousarray(X),
                 beta=beta.value, iters=iters.value, relres=relres.value, status=st)
+
+
+def precode_symbols(H: np.ndarray, xi: float, B: np.ndarray, variant="standard",
+                    max_iter: int = 8, tol: float = 0.0, power: float = 1.0,
+                    X0: np.ndarray | None = None):
+    """Per-symbol form (Eqs. 15-16): solve P W = B for the K x n block B of
+    symbol vectors (from X0, None: zero), then the unnormalised transmit
+    block H W.  beta normalises the block's average transmit power to P:
+    beta = sqrt(P n / ||H W||_F^2), which equals the beta of Eq. 7 in
+    expectation for unit-power symbols.  Dict with X (= W of Eq. 16), S (=
+    H W), A, beta, iters (max over columns), relres (max), status."""
+    Hf = _f(H)
+    M, K = Hf.shape
+    n = np.asarray(B).reshape(K, -1).shape[1]
+    A = gram(Hf, xi)
+    X, it, rr, st = pcg(A, np.asarray(B).reshape(K, n), variant, max_iter, tol, X0)
+    S = matmul(Hf, X)
+    beta = power_factor(S, power * n)
+    return dict(X=X, S=S, A=A, beta=beta, iters=int(it.max()), relres=float(rr.max()), status=st)
 
 
 def precode_batch(Hs, xis, variant="standard", max_iter: int = 8, tol: float = 0.0,

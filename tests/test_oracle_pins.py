@@ -343,3 +343,75 @@ def test_batch_equals_single_instances():
         one = O.precode(inst.H, inst.xi, "standard", max_iter=6)
         assert np.array_equal(Ws[i], one["W"]) and beta[i] == one["beta"]
         assert iters[i] == 6 and status[i] == O.OK
+
+
+# ---------------------------------------------------------------------------
+# Warm start (initial point w^0 of Sec. III-B Step 1) and the per-symbol
+# right-hand-side form (Eqs. 15-16)
+
+def _hpd_system(K, seed, n=None):
+    rng = np.random.default_rng(seed)
+    H = (rng.standard_normal((3 * K, K)) + 1j * rng.standard_normal((3 * K, K))) / np.sqrt(2)
+    A = O.gram(H, 0.3)
+    n = K if n is None else n
+    B = rng.standard_normal((K, n)) + 1j * rng.standard_normal((K, n))
+    return H, A, B
+
+
+@pytest.mark.parametrize("variant", ["standard", "cg", "alg1"])
+def test_warm_start_from_the_solution_stays_there(variant):
+    """Starting at X* = A^{-1} B: the tolerance test stops before the first
+    update (0 iterations, X = X0 exactly), and fixed-T runs stay at X*."""
+    _, A, B = _hpd_system(12, 41, 5)
+    Xs = np.linalg.solve(A, B)
+    X, it, rr, st = O.pcg(A, B, variant, max_iter=20, tol=1e-10, X0=Xs)
+    assert (it == 0).all() and np.array_equal(X, Xs)
+    X, it, rr, st = O.pcg(A, B, variant, max_iter=6, X0=Xs)
+    assert np.linalg.norm(X - Xs) <= 1e-10 * np.linalg.norm(Xs)
+
+
+@pytest.mark.parametrize("variant", ["standard", "cg", "alg1"])
+def test_warm_start_is_the_shifted_cold_solve(variant):
+    """PCG from w^0 on P w = s runs the same Krylov recurrences as PCG from 0
+    on P e = s - P w^0: every fixed-T iterate is w^0 + e_T.  A dropped or
+    mis-signed P w^0 term, or an output without w^0, fails this."""
+    _, A, B = _hpd_system(16, 42, 6)
+    rng = np.random.default_rng(43)
+    X0 = rng.standard_normal(B.shape) + 1j * rng.standard_normal(B.shape)
+    for T in (1, 3, 7):
+        Xw = O.pcg(A, B, variant, max_iter=T, X0=X0)[0]
+        E = O.pcg(A, B - A @ X0, variant, max_iter=T)[0]
+        assert np.linalg.norm(Xw - (X0 + E)) <= 1e-11 * np.linalg.norm(Xw), (variant, T)
+
+
+def test_warm_start_near_the_solution_converges_sooner():
+    """The slot-to-slot use: a start close to the solution reaches the
+    tolerance in fewer iterations, and at tolerance both reach A^{-1} B."""
+    _, A, B = _hpd_system(24, 44, 8)
+    Xs = np.linalg.solve(A, B)
+    rng = np.random.default_rng(45)
+    X0 = Xs * (1 + 1e-3 * rng.standard_normal(Xs.shape))
+    Xc, itc, _, _ = O.pcg(A, B, "standard", max_iter=200, tol=1e-9)
+    Xw, itw, _, _ = O.pcg(A, B, "standard", max_iter=200, tol=1e-9, X0=X0)
+    assert itw.max() < itc.max()
+    for X in (Xc, Xw):
+        assert np.linalg.norm(X - Xs) <= 1e-7 * np.linalg.norm(Xs)
+
+
+def test_per_symbol_form_eq15_16():
+    """Eqs. 15-16: for B = I the per-symbol form is the RZF precoder (S = W
+    of Eq. 7, and the block power factor is sqrt(K) times Eq. 7's beta for
+    the K unit symbol vectors); at tolerance S = H (H^H H + xi I)^{-1} B
+    (direct solve); the block power factor normalises the mean power of the
+    transmitted vectors to P."""
+    H, _, B = _hpd_system(10, 46, 4)
+    xi = 0.3
+    ref = O.precode(H, xi, "standard", max_iter=6, power=2.0)
+    s = O.precode_symbols(H, xi, np.eye(10), "standard", max_iter=6, power=2.0)
+    assert np.allclose(s["S"], ref["W"], rtol=0, atol=1e-13 * np.abs(ref["W"]).max())
+    assert math.isclose(s["beta"], math.sqrt(10) * ref["beta"], rel_tol=1e-12)
+    s = O.precode_symbols(H, xi, B, "standard", max_iter=100, tol=1e-12, power=2.0)
+    S_direct = H @ np.linalg.solve(H.conj().T @ H + xi * np.eye(10), B)
+    assert np.linalg.norm(s["S"] - S_direct) <= 1e-9 * np.linalg.norm(S_direct)
+    mean_power = np.linalg.norm(s["beta"] * s["S"]) ** 2 / B.shape[1]
+    assert math.isclose(mean_power, 2.0, rel_tol=1e-12)
