@@ -111,15 +111,30 @@ typedef struct {
     const void *H;           /* device, complex64 M x K column-major, 16-byte aligned */
     double xi;               /* regulariser, >= 0 (> 0 when K > M) */
     double power;            /* total transmit power P for beta; <= 0 means 1 */
-    void *W;                 /* device out, complex64 M x K column-major */
+    void *W;                 /* device out, complex64 M x n column-major (n = K, or n_rhs when B
+                                is given): W = H X, the precoder of Eq. 7 (B = I) or the
+                                transmit block of Eq. 15 (before the power factor) */
     int ldw;                 /* leading dimension of W, >= M, even */
-    void *X;                 /* optional device out, complex64 K x K (ld K): the iterate */
+    void *X;                 /* optional device out, complex64 K x n (ld K): the iterate */
     void *A;                 /* optional device out, complex64 K x K (ld K): H^H H + xi I */
     int max_iter;            /* T, 0 <= T <= 4096 */
     float tol;               /* > 0: stop a column once ||r|| <= tol ||b||; <= 0: exactly T steps */
     int h_dtype;             /* JACPCG_H_C64 (0) or JACPCG_H_BF16 */
-    float *resid_hist;       /* optional device out, refine_sweeps + 1 floats: ||I - A X||_F / sqrt(K)
+    float *resid_hist;       /* optional device out, refine_sweeps + 1 floats: ||B - A X||_F / sqrt(n)
                                 (FP64-evaluated) before each sweep and after the last */
+    /* Right-hand sides, Eq. 16 per symbol vector: P w = s for the n_rhs columns
+     * s of B (Sec. III, "Stationary Iterative Methods", Eqs. 15-16).  NULL: B = I_K,
+     * the RZF precoder of Eq. 7.  With B, beta normalises the block's mean
+     * transmit power: beta = sqrt(P n_rhs / ||W||_F^2), which is Eq. 7's beta in
+     * expectation over unit-power symbols. */
+    const void *B;           /* optional device in, complex64 K x n_rhs column-major, 16-byte aligned */
+    int ldb;                 /* leading dimension of B, >= K */
+    int n_rhs;               /* columns of B: 1 .. the K class (8, 16, .. 256: the next power of
+                                two >= max(K, 8)); ignored when B is NULL */
+    const void *X0;          /* optional device in, complex64 K x n (ld K), 16-byte aligned: the
+                                initial point of the iteration (Sec. III-B Step 1; e.g. the
+                                previous slot's X); NULL: 0.  The tolerance stays relative to
+                                ||b||; iters counts the updates after X0 */
 } jacpcg_instance;
 
 typedef struct jacpcg_ctx jacpcg_ctx;
@@ -131,7 +146,8 @@ typedef struct jacpcg_plan jacpcg_plan;
 jacpcg_status jacpcg_create(const jacpcg_config *cfg, jacpcg_ctx **out);
 
 /* Precode n_inst independent channels in one batched launch sequence on
- * `stream` (Eq. 7 for each instance, B = I_K).  inst[i] describes instance
+ * `stream` (Eq. 7 for each instance with B = I_K, or Eqs. 15-16 for a block
+ * of symbol vectors B, from X0 when given).  inst[i] describes instance
  * i (host array, read during the call).  Per-instance outputs are device
  * arrays of n_inst entries (any may be NULL): status (jacpcg_status per
  * instance), iters (largest per-column iteration count), resid (largest
@@ -254,7 +270,7 @@ jacpcg_status jacpcg_server_destroy(jacpcg_server *srv);
  * baseline the batched path is measured against.  No context: the caller
  * passes a device workspace of at least 5 K^2 * 8 + 16 K + 256 bytes for the
  * largest K of the batch (ENOMEM otherwise).  Per-instance outputs as in
- * jacpcg_precode.  Errors: EINVAL, ENOMEM, ECUDA. */
+ * jacpcg_precode.  B and X0 must be NULL.  Errors: EINVAL, ENOMEM, ECUDA. */
 jacpcg_status jacpcg_precode_plain(const jacpcg_instance *inst, int n_inst, int variant,
                                    void *workspace, size_t workspace_bytes, int32_t *status_dev,
                                    int32_t *iters_dev, float *resid_dev, float *beta_dev,
@@ -275,7 +291,8 @@ jacpcg_status jacpcg_precode_plain(const jacpcg_instance *inst, int n_inst, int 
  * them (one stream, one thread).  Returns ENOMEM, and enqueues nothing,
  * when the batch needs more scratch than the array holds (about 120
  * instances of M = 1024, K = 64, or 7 of K = 256); EINVAL for invalid
- * arguments as jacpcg_precode (K <= 256, no max_M limit). */
+ * arguments as jacpcg_precode (K <= 256, no max_M limit; B and X0 must be
+ * NULL, complex64 H only). */
 #define JACPCG_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
 jacpcg_status jacpcg_precode_noalloc(const jacpcg_instance *inst, int n_inst, int variant,
                                      int32_t *status_dev, int32_t *iters_dev, float *resid_dev,

@@ -49,7 +49,9 @@ class jacpcg_instance(ctypes.Structure):
                 ("H", ctypes.c_void_p), ("xi", ctypes.c_double), ("power", ctypes.c_double),
                 ("W", ctypes.c_void_p), ("ldw", ctypes.c_int), ("X", ctypes.c_void_p),
                 ("A", ctypes.c_void_p), ("max_iter", ctypes.c_int), ("tol", ctypes.c_float),
-                ("h_dtype", ctypes.c_int), ("resid_hist", ctypes.c_void_p)]
+                ("h_dtype", ctypes.c_int), ("resid_hist", ctypes.c_void_p),
+                ("B", ctypes.c_void_p), ("ldb", ctypes.c_int), ("n_rhs", ctypes.c_int),
+                ("X0", ctypes.c_void_p)]
 
 
 class jacpcg_server_config(ctypes.Structure):
@@ -332,11 +334,13 @@ def jacpcg_server_destroy(srv) -> None:
 # --- torch convenience ---------------------------------------------------------
 
 def instance(H, W, xi: float, max_iter: int, tol: float = 0.0, power: float = 1.0, X=None,
-             A=None, resid_hist=None) -> jacpcg_instance:
+             A=None, resid_hist=None, B=None, X0=None) -> jacpcg_instance:
     """Describe one channel held in torch tensors of device storage layout:
     H (complex64, or bfloat16 with a trailing (re, im) axis) and W
     (complex64) have shape (K, M) (column k of the matrix is row k of the
-    tensor, i.e. column-major storage of the M x K matrix)."""
+    tensor, i.e. column-major storage of the M x K matrix).  B: optional
+    (n_rhs, K) complex64 symbol vectors (Eq. 16; W then has shape (n_rhs, M)
+    and X (n_rhs, K)); X0: optional initial point, contiguous (n, K)."""
     import torch
     bf16 = H.dtype == torch.bfloat16
     if bf16:
@@ -344,12 +348,20 @@ def instance(H, W, xi: float, max_iter: int, tol: float = 0.0, power: float = 1.
         K, M, ldh = H.shape[-3], H.shape[-2], H.stride(-3) // 2
     else:
         K, M, ldh = H.shape[-2], H.shape[-1], H.stride(-2)
+    if B is not None:
+        assert B.dtype == torch.complex64 and B.shape[-1] == K and B.stride(-1) == 1
+    if X0 is not None:
+        assert X0.dtype == torch.complex64 and X0.shape[-1] == K and X0.is_contiguous()
     return jacpcg_instance(M=M, K=K, ldh=ldh, H=H.data_ptr(), xi=float(xi),
                            power=float(power), W=W.data_ptr(), ldw=W.stride(-2),
                            X=None if X is None else X.data_ptr(),
                            A=None if A is None else A.data_ptr(), max_iter=int(max_iter),
                            tol=float(tol), h_dtype=JACPCG_H_BF16 if bf16 else JACPCG_H_C64,
-                           resid_hist=None if resid_hist is None else resid_hist.data_ptr())
+                           resid_hist=None if resid_hist is None else resid_hist.data_ptr(),
+                           B=None if B is None else B.data_ptr(),
+                           ldb=0 if B is None else B.stride(-2),
+                           n_rhs=0 if B is None else B.shape[-2],
+                           X0=None if X0 is None else X0.data_ptr())
 
 
 class Precoder:

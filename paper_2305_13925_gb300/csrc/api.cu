@@ -112,7 +112,7 @@ struct Arena {
 
 // What one kernel launch of a plan covers.
 struct Launch {
-    enum Kind { GRAM, PCG, HX, GRAM_TC, HX_TC, PCG_TC } kind;
+    enum Kind { GRAM, PCG, HX, GRAM_TC, HX_TC, PCG_TC, RESID_INIT } kind;
     int phase;        // 0 Gram, 1 iteration, 2 W = H X
     int param;        // TB (Gram), KC (iteration), TN (W = H X)
     size_t list_off;  // byte offset of its work list inside the plan block
@@ -191,21 +191,27 @@ jacpcg_status validate(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n
         if (q.max_iter < 0 || q.max_iter > 4096) return JACPCG_EINVAL;
         if (q.h_dtype != JACPCG_H_C64 && q.h_dtype != JACPCG_H_BF16) return JACPCG_EINVAL;
         if (q.h_dtype == JACPCG_H_BF16 && (q.ldh & 3)) return JACPCG_EINVAL;   // 16-byte columns
+        if (q.B && (q.n_rhs < 1 || q.n_rhs > k_class(q.K) || q.ldb < q.K || !aligned16(q.B)))
+            return JACPCG_EINVAL;
+        if (q.X0 && !aligned16(q.X0)) return JACPCG_EINVAL;
     }
     return JACPCG_OK;
 }
 
+// right-hand sides of an instance: K for B = I, else n_rhs
+int n_cols(const jacpcg_instance &q) { return q.B ? q.n_rhs : q.K; }
+
 // Byte layout of one plan block.
 struct Layout {
-    size_t insts, gram, tcl, pcg, hx, hxl, res, accum, ws, total;
-    int n_gram, n_pcg, n_hx, n_res;
+    size_t insts, gram, tcl, pcg, hx, hxl, res, init, accum, ws, total;
+    int n_gram, n_pcg, n_hx, n_res, n_init;
     bool refine;
     std::vector<size_t> ws_off;   // per instance
 };
 
 int n_wtiles(const jacpcg_instance &q) {
     const int KC = k_class(q.K), TN = hx_tn(KC);
-    return ((q.M + HX_TM - 1) / HX_TM) * ((q.K + TN - 1) / TN);
+    return ((q.M + HX_TM - 1) / HX_TM) * ((n_cols(q) + TN - 1) / TN);
 }
 int n_gtiles(const jacpcg_instance &q) {
     const int KC = k_class(q.K), TB = gram_tb(KC);
@@ -216,13 +222,16 @@ int n_pblocks(const jacpcg_instance &q, const int *shape_idx) {
     const int KC = k_class(q.K);
     const PcgShape s = pcg_shape(KC, shape_idx[kc_index(KC)]);
     const int per = s.CW * s.NW;
-    return (q.K + per - 1) / per;
+    return (n_cols(q) + per - 1) / per;
 }
+// A, X, 1/diag, W partials; then R and its column norms (refinement or a
+// warm start), then ||b_j||^2 (warm start)
 size_t inst_ws_bytes(const jacpcg_instance &q, bool refine) {
     const size_t KC = k_class(q.K);
     size_t b = align_up(KC * KC * sizeof(float2)) * 2 + align_up(KC * sizeof(float)) +
                align_up(n_wtiles(q) * sizeof(float));
-    if (refine) b += align_up(KC * KC * sizeof(float2)) + align_up(KC * sizeof(float));
+    if (refine || q.X0) b += align_up(KC * KC * sizeof(float2)) + align_up(KC * sizeof(float));
+    if (q.X0) b += align_up(KC * sizeof(float));
     return b;
 }
 
@@ -237,10 +246,11 @@ bool pcg_on_tc(const jacpcg_config &cfg, int KC) {
 
 Layout make_layout(const jacpcg_instance *inst, int n, bool refine, const int *shape_idx) {
     Layout L{};
-    L.n_gram = L.n_pcg = L.n_hx = L.n_res = 0;
+    L.n_gram = L.n_pcg = L.n_hx = L.n_res = L.n_init = 0;
     L.refine = refine;
     for (int i = 0; i < n; ++i) {
-        if (refine) L.n_res += inst[i].K;
+        if (refine) L.n_res += n_cols(inst[i]);
+        if (inst[i].X0) L.n_init += n_cols(inst[i]);
         L.n_gram += n_gtiles(inst[i]);
         L.n_pcg += n_pblocks(inst[i], shape_idx);
         L.n_hx += n_wtiles(inst[i]);
@@ -253,6 +263,7 @@ Layout make_layout(const jacpcg_instance *inst, int n, bool refine, const int *s
     L.hx = o;     o += align_up(sizeof(int4) * L.n_hx);
     L.hxl = o;    o += align_up(sizeof(int) * n);
     L.res = o;    o += align_up(sizeof(int2) * L.n_res);
+    L.init = o;   o += align_up(sizeof(int2) * L.n_init);
     L.accum = o;  o += align_up(sizeof(int32_t) * n) * 3;
     L.ws = o;
     L.ws_off.resize(n);
@@ -291,12 +302,19 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
         d.power = q.power > 0.0 ? (float)q.power : 1.0f;
         d.tol = q.tol;
         d.h_bf16 = q.h_dtype == JACPCG_H_BF16;
-        if (L.refine) {
+        d.B = static_cast<const float2 *>(q.B);
+        d.ldb = q.B ? q.ldb : 0;
+        d.ncols = n_cols(q);
+        d.X0 = static_cast<const float2 *>(q.X0);
+        if (L.refine || q.X0) {
             const size_t base = 2 * align_up((size_t)KC * KC * sizeof(float2)) + align_up(KC * sizeof(float)) +
                                 align_up(n_wtiles(q) * sizeof(float));
             d.R = reinterpret_cast<float2 *>(w + base);
             d.rnorm = reinterpret_cast<float *>(w + base + align_up((size_t)KC * KC * sizeof(float2)));
-            d.resid_hist = q.resid_hist;
+            if (L.refine) d.resid_hist = q.resid_hist;
+            if (q.X0)
+                d.bn2 = reinterpret_cast<float *>(w + base + align_up((size_t)KC * KC * sizeof(float2)) +
+                                                  align_up(KC * sizeof(float)));
         }
         hi[i] = d;
     }
@@ -304,9 +322,17 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
         int2 *rb = reinterpret_cast<int2 *>(host + L.res);
         int r = 0;
         for (int i = 0; i < n; ++i)
-            for (int j = 0; j < inst[i].K; ++j) rb[r++] = make_int2(i, j);
+            for (int j = 0; j < n_cols(inst[i]); ++j) rb[r++] = make_int2(i, j);
     }
     launches.clear();
+    if (L.n_init) {   // warm starts: X = X0, R = B - A X0, ||b_j||^2 before the iteration
+        int2 *ib = reinterpret_cast<int2 *>(host + L.init);
+        int r = 0;
+        for (int i = 0; i < n; ++i)
+            if (inst[i].X0)
+                for (int j = 0; j < n_cols(inst[i]); ++j) ib[r++] = make_int2(i, j);
+        launches.push_back({Launch::RESID_INIT, 1, 0, L.init, L.n_init});
+    }
     // Gram on the tensor cores: one CTA per instance
     const int prec = ctx->cfg.precision;
     int *tl = reinterpret_cast<int *>(host + L.tcl);
@@ -339,7 +365,7 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
         const PcgShape s = pcg_shape(KC, sh);
         for (int i = 0; i < n; ++i) {
             if (k_class(inst[i].K) != KC || pcg_on_tc(ctx->cfg, KC)) continue;
-            for (int c0 = 0; c0 < inst[i].K; c0 += s.CW * s.NW) pb[p++] = make_int2(i, c0);
+            for (int c0 = 0; c0 < n_cols(inst[i]); c0 += s.CW * s.NW) pb[p++] = make_int2(i, c0);
         }
         if (p > start) launches.push_back({Launch::PCG, 1, KC, L.pcg + start * sizeof(int2), p - start, sh});
     }
@@ -357,7 +383,7 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
         for (int i = 0; i < n; ++i) {
             const int KC = k_class(inst[i].K);
             if (hx_tn(KC) != TN || gram_on_tc(prec, KC)) continue;
-            const int nm = (inst[i].M + HX_TM - 1) / HX_TM, nn = (inst[i].K + TN - 1) / TN;
+            const int nm = (inst[i].M + HX_TM - 1) / HX_TM, nn = (n_cols(inst[i]) + TN - 1) / TN;
             int slot = 0;
             for (int nt = 0; nt < nn; ++nt)
                 for (int mt = 0; mt < nm; ++mt) ht[h++] = make_int4(i, mt, nt, slot++);
@@ -408,6 +434,10 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
                 case Launch::PCG_TC:
                     e = launch_pcg_tc64(ctx->cfg.variant, pl->d_insts, static_cast<const int *>(list), l.count,
                                         pl->acc, s, 0);
+                    break;
+                case Launch::RESID_INIT:
+                    e = launch_residual_init(pl->d_insts, static_cast<const int2 *>(list), l.count, s,
+                                             ctx->cfg.refine_residual == JACPCG_RESID_FP64);
                     break;
             }
             if (e != cudaSuccess) return cuda_fail(ctx, e);
@@ -613,7 +643,9 @@ jacpcg_status jacpcg_create(const jacpcg_config *cfg, jacpcg_ctx **out) {
         q.K = cfg->max_K;
         std::vector<jacpcg_instance> v(cfg->max_instances, q);
         const int zero[6] = {0, 0, 0, 0, 0, 0};
-        bytes = 2 * make_layout(v.data(), cfg->max_instances, cfg->refine_sweeps > 0, zero).total;
+        // room for two calls at the limits, with the residual workspace that
+        // refinement or warm starts need
+        bytes = 2 * make_layout(v.data(), cfg->max_instances, true, zero).total;
     }
     bytes = align_up(bytes);
     if (cudaMalloc(reinterpret_cast<void **>(&ctx->arena.base), bytes) != cudaSuccess) {

@@ -18,8 +18,8 @@ enum : int32_t { FLAG_NOTHPD = 1, FLAG_NOTCONV = 2, FLAG_TIMEOUT = 4 };
 // from K to KC are zero.
 struct DevInst {
     const float2 *H;      // M x K, leading dimension ldh (caller)
-    float2 *W;            // M x K, leading dimension ldw (caller)
-    float2 *Xout;         // optional K x K, ld K (caller)
+    float2 *W;            // M x ncols, leading dimension ldw (caller)
+    float2 *Xout;         // optional K x ncols, ld K (caller)
     float2 *Aout;         // optional K x K, ld K (caller)
     float2 *A;            // workspace KC x KC: H^H H + xi I
     float *dinv;          // workspace KC: 1 / A_kk (0 beyond K)
@@ -35,6 +35,12 @@ struct DevInst {
     float2 *R;            // workspace KC x KC: refinement residual I - A X (null without refinement)
     float *rnorm;         // workspace KC: per-column ||R_j||^2 of the last residual
     float *resid_hist;    // caller's optional refinement history
+    // right-hand sides (Eq. 16 per symbol vector): B == null means B = I_K
+    const float2 *B;      // K x ncols, leading dimension ldb (caller)
+    const float2 *X0;     // optional initial point, K x ncols, ld K (caller)
+    float *bn2;           // workspace KC: ||b_j||^2 for the warm-started solve
+    int ldb;
+    int ncols;            // right-hand sides: K for B = I, else n_rhs (<= KC)
 };
 
 // One entry of H as complex FP32 (bfloat16 converts exactly).

@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(256) hx_simt_kernel(const DevInst *__restrict_
 
     const int4 t = tiles[blockIdx.x];        // (instance, m tile, n tile, slot)
     const DevInst &in = insts[t.x];
-    const int M = in.M, K = in.K, ldh = in.ldh, KC = in.KC;
+    const int M = in.M, K = in.K, ldh = in.ldh, KC = in.KC, NCOL = in.ncols;
     const float2 *__restrict__ H = in.H;
     const float2 *__restrict__ X = in.X;
     const bool bf16 = in.h_bf16 != 0;
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) hx_simt_kernel(const DevInst *__restrict_
             const int e = threadIdx.x + 256 * q;
             const int n = e / KCH, kk = e % KCH;
             const int k = k0 + kk, j = j0 + n;
-            rx[q] = (k < K && j < K) ? __ldg(X + k + (size_t)j * KC) : make_float2(0.f, 0.f);
+            rx[q] = (k < K && j < NCOL) ? __ldg(X + k + (size_t)j * KC) : make_float2(0.f, 0.f);
         }
     };
     fetch(0);
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(256) hx_simt_kernel(const DevInst *__restrict_
 #pragma unroll
         for (int u = 0; u < UM; ++u) {
             const int m = m0 + ty * UM + u;
-            if (m < M && j < K) {
+            if (m < M && j < NCOL) {
                 W[m + (size_t)j * ldw] = acc[u][v];
                 nrm = fmaf(acc[u][v].x, acc[u][v].x, nrm);
                 nrm = fmaf(acc[u][v].y, acc[u][v].y, nrm);
@@ -139,7 +139,9 @@ __global__ void finalize_kernel(const DevInst *__restrict__ insts, int n_inst, D
     else if (!isfinite(s)) st = 6;                   // JACPCG_ENONFINITE
     else if (f & FLAG_NOTHPD) st = 5;                // JACPCG_ENOTHPD
     else if (f & FLAG_NOTCONV) st = 4;               // JACPCG_ENOTCONV
-    const double P = in.power > 0.f ? (double)in.power : 1.0;
+    // Eq. 7: beta = sqrt(P / ||W||_F^2); for a block of n symbol vectors
+    // (Eq. 15) the block's mean transmit power is normalised to P
+    const double P = (in.power > 0.f ? (double)in.power : 1.0) * (in.B ? (double)in.ncols : 1.0);
     if (out.status) out.status[inst] = st;
     if (out.iters) out.iters[inst] = acc.iters[inst];
     if (out.resid) out.resid[inst] = __uint_as_float(acc.resid_bits[inst]);

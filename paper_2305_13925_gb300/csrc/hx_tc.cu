@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_tc64_kernel(const DevInst *__r
         // stream cursor: (instance ordinal, stage) of this CTA's walk; per instance
         // stages 0 and 1 carry X (columns 32 t ..), then the H stages
         struct Cursor {
-            int j, t, nst, nks, M, K, ldh;
+            int j, t, nst, nks, M, K, ldh, ncols;
             const char *H;
             const char *X;
             bool bf16;
@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_tc64_kernel(const DevInst *__r
                 const DevInst &in = insts[list[u.j]];
                 u.M = in.M;
                 u.K = in.K;
+                u.ncols = in.ncols;
                 u.ldh = in.ldh;
                 u.H = reinterpret_cast<const char *>(in.H);
                 u.X = reinterpret_cast<const char *>(in.X);
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_tc64_kernel(const DevInst *__r
 #pragma unroll
                         for (int c = 0; c < 2; ++c) {
                             const int r = 4 * rq + 2 * c;
-                            const int left = n < u.K ? min(max(u.K - r, 0), 2) : 0;
+                            const int left = n < u.ncols ? min(max(u.K - r, 0), 2) : 0;
                             const char *src = u.X + ((size_t)n * 64 + r) * 8;
                             tc::cp_async16(rb + warp * 2048 + ((2 * h + c) * 32 + lane) * 16, left ? src : u.X,
                                            left * 8);
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_tc64_kernel(const DevInst *__r
             }
             tc::cp_async_commit();   // one group per stage, empty past the end
         };
-        Cursor iu{(int)blockIdx.x, 0, 0, 0, 0, 0, 0, nullptr, nullptr, false};
+        Cursor iu{(int)blockIdx.x, 0, 0, 0, 0, 0, 0, 0, nullptr, nullptr, false};
         cursor_load(iu);
 #pragma unroll 1
         for (int p = 0; p < RAW - 1; ++p) {
@@ -302,7 +303,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_tc64_kernel(const DevInst *__r
         uint32_t tile = 0;
         for (int j = blockIdx.x; j < n_list; j += gridDim.x) {
             const DevInst &in = insts[list[j]];
-            const int M = in.M, K = in.K, ldw = in.ldw;
+            const int M = in.M, NCOL = in.ncols, ldw = in.ldw;
             float2 *__restrict__ W = in.W;
             const int nmt = (M + TMR - 1) / TMR;
             for (int mt = 0; mt < nmt; ++mt, ++tile) {
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_tc64_kernel(const DevInst *__r
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
                         const int jj = 32 * half + i;
-                        if (jj < K) {
+                        if (jj < NCOL) {
                             W[gm + (size_t)jj * ldw] = make_float2(wr[i], wi[i]);
                             nrm = fmaf(wr[i], wr[i], nrm);
                             nrm = fmaf(wi[i], wi[i], nrm);

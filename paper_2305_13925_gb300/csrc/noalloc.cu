@@ -89,6 +89,7 @@ extern "C" jacpcg_status jacpcg_precode_noalloc(const jacpcg_instance *inst, int
         if (!std::isfinite(q.power) || !std::isfinite(q.tol)) return JACPCG_EINVAL;
         if (q.max_iter < 0 || q.max_iter > 4096) return JACPCG_EINVAL;
         if (q.h_dtype != JACPCG_H_C64) return JACPCG_EINVAL;   // complex64 H only
+        if (q.B || q.X0) return JACPCG_EINVAL;                // B = I, zero start only
     }
     // sizes: tables, accumulators, workspace -- all must fit the static arrays
     size_t ng = 0, np = 0, nh = 0, ws = 0;
@@ -141,6 +142,7 @@ extern "C" jacpcg_status jacpcg_precode_noalloc(const jacpcg_instance *inst, int
         d.wpart = reinterpret_cast<float *>(b + 2 * up((size_t)KC * KC * sizeof(float2)) +
                                             up(KC * sizeof(float)));
         d.M = q.M; d.K = q.K; d.ldh = q.ldh; d.ldw = q.ldw; d.KC = KC;
+        d.ncols = q.K;   // B = I
         d.max_iter = q.max_iter;
         d.n_wpart = w_tiles(q.M, q.K);
         d.variant = variant;

@@ -23,10 +23,13 @@
 //   2 plain CG (variant 0 with D = I).
 // Stopping (tol > 0): a column stops before an update once
 // ||r||^2 <= tol^2 ||b||^2 (Alg. 1: ||D r||^2).
-// Right-hand side (mode): 0 solves A X = I_K and writes X; 1 solves
-// A dX = R for the refinement residual R of the instance's workspace and
-// adds dX to X (iterative refinement); only mode 0 reports iterations,
-// residuals and non-convergence.
+// Right-hand side (mode): 0 solves A X = B (B = I_K, or the instance's
+// symbol vectors, Eq. 16) and writes X -- from X0 when the instance has one,
+// as X0 plus the solve of A E = B - A X0 (the residual kernel has put R and
+// X = X0 in place), stopping relative to ||b||; 1 solves A dX = R for the
+// refinement residual R of the instance's workspace and adds dX to X
+// (iterative refinement); only mode 0 reports iterations, residuals and
+// non-convergence.
 #pragma once
 
 #include "common.cuh"
@@ -49,6 +52,7 @@ __global__ void __launch_bounds__(NW * 32) pcg_kernel(const DevInst *__restrict_
     const DevInst &in = insts[blk.x];
     const int K = in.K;
     const int T = in.max_iter;
+    const bool warm = mode == 0 && in.X0 != nullptr;   // R = B - A X0 and X = X0 are in place
     const float tol2 = in.tol > 0.f ? in.tol * in.tol : -1.f;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float2 *__restrict__ Ag = in.A;
@@ -76,7 +80,7 @@ __global__ void __launch_bounds__(NW * 32) pcg_kernel(const DevInst *__restrict_
 #pragma unroll
     for (int c = 0; c < CW; ++c) {
         col[c] = blk.y + warp * CW + c;
-        cvalid[c] = col[c] < K;
+        cvalid[c] = col[c] < in.ncols;
     }
 
     // state: x (iterate), r (residual), p (direction; m in Alg. 1)
@@ -84,6 +88,7 @@ __global__ void __launch_bounds__(NW * 32) pcg_kernel(const DevInst *__restrict_
     float rho[CW];      // r^H z (standard / CG) or r^H r (Alg. 1)
     float res2[CW];     // squared stopping residual
     float btol[CW];     // tol^2 ||b||^2
+    float bn2c[CW];     // ||b||^2 (the reported residual is relative to it)
     bool done[CW];
     int its[CW];
 #pragma unroll
@@ -92,10 +97,14 @@ __global__ void __launch_bounds__(NW * 32) pcg_kernel(const DevInst *__restrict_
 #pragma unroll
         for (int i = 0; i < RPL; ++i) {
             float2 b = make_float2(0.f, 0.f);
-            if (mode == 0) {
-                if (rvalid[i] && row[i] == col[c]) b.x = 1.f;               // B = I
+            if (mode == 0 && !warm) {
+                if (!in.B) {
+                    if (rvalid[i] && row[i] == col[c]) b.x = 1.f;           // B = I
+                } else if (rvalid[i] && cvalid[c]) {
+                    b = in.B[row[i] + (size_t)col[c] * in.ldb];               // symbol vectors
+                }
             } else if (rvalid[i] && cvalid[c]) {
-                b = in.R[row[i] + (size_t)col[c] * KC];                       // B = R
+                b = in.R[row[i] + (size_t)col[c] * KC];                       // B - A X (X0)
             }
             comp_fma(bb, b.x, b.x);
             comp_fma(bb, b.y, b.y);
@@ -120,7 +129,9 @@ __global__ void __launch_bounds__(NW * 32) pcg_kernel(const DevInst *__restrict_
         bb = comp_warp_allreduce(bb);
         rho[c] = rz.s + rz.c;
         res2[c] = rs.s + rs.c;
-        btol[c] = tol2 * (bb.s + bb.c);
+        // a warm start stops relative to ||b||, not to its residual
+        bn2c[c] = (warm && cvalid[c]) ? in.bn2[col[c]] : (bb.s + bb.c);
+        btol[c] = tol2 * bn2c[c];
         done[c] = !cvalid[c];
         its[c] = 0;
     }
@@ -320,7 +331,7 @@ __global__ void __launch_bounds__(NW * 32) pcg_kernel(const DevInst *__restrict_
         for (int i = 0; i < RPL; ++i) {
             if (row[i] >= KC) continue;
             float2 v = x[i][c];
-            if (mode == 1) {
+            if (mode == 1 || warm) {   // X += dX (X holds X0 for a warm start)
                 const float2 o = in.X[row[i] + (size_t)col[c] * KC];
                 v = make_float2(o.x + v.x, o.y + v.y);
             }
@@ -336,7 +347,8 @@ __global__ void __launch_bounds__(NW * 32) pcg_kernel(const DevInst *__restrict_
     for (int c = 0; c < CW; ++c) {
         if (!cvalid[c]) continue;
         itmax = max(itmax, its[c]);
-        resmax = fmaxf(resmax, sqrtf(fmaxf(res2[c], 0.f)));
+        const float rr = fmaxf(res2[c], 0.f);
+        resmax = fmaxf(resmax, sqrtf(bn2c[c] > 0.f ? rr / bn2c[c] : rr));
         if (tol2 > 0.f && !(res2[c] <= btol[c])) notconv = true;
     }
     if (lane == 0) {

@@ -147,7 +147,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
     for (int jj = blockIdx.x; jj < n_list; jj += gridDim.x) {
         const int id = list[jj];
         const DevInst &in = insts[id];
-        const int K = in.K, T = in.max_iter;
+        const int K = in.K, T = in.max_iter, NCOL = in.ncols;
+        const bool warm = mode == 0 && in.X0 != nullptr;   // R = B - A X0 and X = X0 in place
         const float tol2 = in.tol > 0.f ? in.tol * in.tol : -1.f;
 
         // ---- A in the real 2 x 2-block layout, TF32 head and tail ----
@@ -189,8 +190,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
         // ---- state init (Step 1; x = 0, r = b, p = D^{-1} r) ----
         float2 x[RPT], r[RPT], p[RPT];
         float dv[RPT];
-        float rho, res2, btol;
-        bool done = j >= K;                // column stopped (or beyond K)
+        float rho, res2, btol, bn2c;
+        bool done = j >= NCOL;             // column stopped (or beyond the right-hand sides)
         int itmax = 0;                     // iterations in which the column updated
         int notHPD = 0;
         {
@@ -200,10 +201,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
                 const int i = g + 4 * k;
                 dv[k] = (i < K) ? (VAR == 2 ? 1.f : in.dinv[i]) : 0.f;
                 float2 b = make_float2(0.f, 0.f);
-                if (mode == 0) {
-                    if (i < K && i == j) b.x = 1.f;
-                } else if (i < K && j < K) {
-                    b = in.R[i + (size_t)j * 64];
+                if (mode == 0 && !warm) {
+                    if (!in.B) {
+                        if (i < K && i == j) b.x = 1.f;                       // B = I
+                    } else if (i < K && j < NCOL) {
+                        b = in.B[i + (size_t)j * in.ldb];                     // symbol vectors
+                    }
+                } else if (i < K && j < NCOL) {
+                    b = in.R[i + (size_t)j * 64];                             // B - A X (X0)
                 }
                 x[k] = make_float2(0.f, 0.f);
                 r[k] = b;
@@ -213,7 +218,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
             }
             rho = col_total(sum16(t0));    // r^H z
             res2 = col_total(sum16(t1));   // ||r||^2 = ||b||^2
-            btol = tol2 * res2;
+            // a warm start stops relative to ||b||, not to its residual
+            bn2c = (warm && j < NCOL) ? in.bn2[j] : res2;
+            btol = tol2 * bn2c;
         }
         __syncthreads();   // A is in place for both teams
 
@@ -326,12 +333,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
         }
 
         // ---- outputs ----
-        if (j < K) {
+        if (j < NCOL) {
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
                 const int i = g + 4 * k;
                 float2 val = x[k];
-                if (mode == 1) {
+                if (mode == 1 || warm) {   // X += dX (X holds X0 for a warm start)
                     const float2 o = in.X[i + (size_t)j * 64];
                     val = make_float2(o.x + val.x, o.y + val.y);
                 }
@@ -341,9 +348,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
         }
         if (mode == 0 && g == 0) {   // one thread per column
             int f = err ? FLAG_TIMEOUT : 0;
-            if (j < K) {
+            if (j < NCOL) {
                 if (itmax > 0) atomicMax(acc_out.iters + id, itmax);
-                const float res = sqrtf(fmaxf(res2, 0.f));
+                const float rr = fmaxf(res2, 0.f);
+                const float res = sqrtf(bn2c > 0.f ? rr / bn2c : rr);   // relative to ||b||
                 if (res > 0.f) atomicMax(acc_out.resid_bits + id, __float_as_uint(res));
                 if (notHPD) f |= FLAG_NOTHPD;
                 if (tol2 > 0.f && !(res2 <= btol)) f |= FLAG_NOTCONV;

@@ -59,9 +59,10 @@ def test_struct_layout_matches_c(tmp_path):
 #include <stddef.h>
 #include "{HEADER}"
 int main(void) {{
-  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(jacpcg_config), offsetof(jacpcg_config, arena_bytes),
-         offsetof(jacpcg_config, flags), sizeof(jacpcg_instance), offsetof(jacpcg_instance, W),
-         offsetof(jacpcg_instance, tol));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(jacpcg_config),
+         offsetof(jacpcg_config, arena_bytes), offsetof(jacpcg_config, flags), sizeof(jacpcg_instance),
+         offsetof(jacpcg_instance, W), offsetof(jacpcg_instance, tol), offsetof(jacpcg_instance, B),
+         offsetof(jacpcg_instance, ldb), offsetof(jacpcg_instance, n_rhs), offsetof(jacpcg_instance, X0));
   return 0;
 }}
 """)
@@ -70,4 +71,4 @@ int main(void) {{
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     C, I = binding.jacpcg_config, binding.jacpcg_instance
     assert got == [ctypes.sizeof(C), C.arena_bytes.offset, C.flags.offset, ctypes.sizeof(I),
-                   I.W.offset, I.tol.offset]
+                   I.W.offset, I.tol.offset, I.B.offset, I.ldb.offset, I.n_rhs.offset, I.X0.offset]
