@@ -112,7 +112,7 @@ struct Arena {
 
 // What one kernel launch of a plan covers.
 struct Launch {
-    enum Kind { GRAM, PCG, HX, GRAM_TC, HX_TC, PCG_TC, RESID_INIT } kind;
+    enum Kind { GRAM, PCG, HX, GRAM_TC, HX_TC, PCG_TC } kind;
     int phase;        // 0 Gram, 1 iteration, 2 W = H X
     int param;        // TB (Gram), KC (iteration), TN (W = H X)
     size_t list_off;  // byte offset of its work list inside the plan block
@@ -203,8 +203,8 @@ int n_cols(const jacpcg_instance &q) { return q.B ? q.n_rhs : q.K; }
 
 // Byte layout of one plan block.
 struct Layout {
-    size_t insts, gram, tcl, pcg, hx, hxl, res, init, accum, ws, total;
-    int n_gram, n_pcg, n_hx, n_res, n_init;
+    size_t insts, gram, tcl, pcg, hx, hxl, res, accum, ws, total;
+    int n_gram, n_pcg, n_hx, n_res;
     bool refine;
     std::vector<size_t> ws_off;   // per instance
 };
@@ -224,14 +224,12 @@ int n_pblocks(const jacpcg_instance &q, const int *shape_idx) {
     const int per = s.CW * s.NW;
     return (n_cols(q) + per - 1) / per;
 }
-// A, X, 1/diag, W partials; then R and its column norms (refinement or a
-// warm start), then ||b_j||^2 (warm start)
+// A, X, 1/diag, W partials; then R and its column norms for refinement
 size_t inst_ws_bytes(const jacpcg_instance &q, bool refine) {
     const size_t KC = k_class(q.K);
     size_t b = align_up(KC * KC * sizeof(float2)) * 2 + align_up(KC * sizeof(float)) +
                align_up(n_wtiles(q) * sizeof(float));
-    if (refine || q.X0) b += align_up(KC * KC * sizeof(float2)) + align_up(KC * sizeof(float));
-    if (q.X0) b += align_up(KC * sizeof(float));
+    if (refine) b += align_up(KC * KC * sizeof(float2)) + align_up(KC * sizeof(float));
     return b;
 }
 
@@ -246,11 +244,10 @@ bool pcg_on_tc(const jacpcg_config &cfg, int KC) {
 
 Layout make_layout(const jacpcg_instance *inst, int n, bool refine, const int *shape_idx) {
     Layout L{};
-    L.n_gram = L.n_pcg = L.n_hx = L.n_res = L.n_init = 0;
+    L.n_gram = L.n_pcg = L.n_hx = L.n_res = 0;
     L.refine = refine;
     for (int i = 0; i < n; ++i) {
         if (refine) L.n_res += n_cols(inst[i]);
-        if (inst[i].X0) L.n_init += n_cols(inst[i]);
         L.n_gram += n_gtiles(inst[i]);
         L.n_pcg += n_pblocks(inst[i], shape_idx);
         L.n_hx += n_wtiles(inst[i]);
@@ -263,7 +260,6 @@ Layout make_layout(const jacpcg_instance *inst, int n, bool refine, const int *s
     L.hx = o;     o += align_up(sizeof(int4) * L.n_hx);
     L.hxl = o;    o += align_up(sizeof(int) * n);
     L.res = o;    o += align_up(sizeof(int2) * L.n_res);
-    L.init = o;   o += align_up(sizeof(int2) * L.n_init);
     L.accum = o;  o += align_up(sizeof(int32_t) * n) * 3;
     L.ws = o;
     L.ws_off.resize(n);
@@ -306,15 +302,12 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
         d.ldb = q.B ? q.ldb : 0;
         d.ncols = n_cols(q);
         d.X0 = static_cast<const float2 *>(q.X0);
-        if (L.refine || q.X0) {
+        if (L.refine) {
             const size_t base = 2 * align_up((size_t)KC * KC * sizeof(float2)) + align_up(KC * sizeof(float)) +
                                 align_up(n_wtiles(q) * sizeof(float));
             d.R = reinterpret_cast<float2 *>(w + base);
             d.rnorm = reinterpret_cast<float *>(w + base + align_up((size_t)KC * KC * sizeof(float2)));
-            if (L.refine) d.resid_hist = q.resid_hist;
-            if (q.X0)
-                d.bn2 = reinterpret_cast<float *>(w + base + align_up((size_t)KC * KC * sizeof(float2)) +
-                                                  align_up(KC * sizeof(float)));
+            d.resid_hist = q.resid_hist;
         }
         hi[i] = d;
     }
@@ -325,14 +318,6 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
             for (int j = 0; j < n_cols(inst[i]); ++j) rb[r++] = make_int2(i, j);
     }
     launches.clear();
-    if (L.n_init) {   // warm starts: X = X0, R = B - A X0, ||b_j||^2 before the iteration
-        int2 *ib = reinterpret_cast<int2 *>(host + L.init);
-        int r = 0;
-        for (int i = 0; i < n; ++i)
-            if (inst[i].X0)
-                for (int j = 0; j < n_cols(inst[i]); ++j) ib[r++] = make_int2(i, j);
-        launches.push_back({Launch::RESID_INIT, 1, 0, L.init, L.n_init});
-    }
     // Gram on the tensor cores: one CTA per instance
     const int prec = ctx->cfg.precision;
     int *tl = reinterpret_cast<int *>(host + L.tcl);
@@ -434,10 +419,6 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
                 case Launch::PCG_TC:
                     e = launch_pcg_tc64(ctx->cfg.variant, pl->d_insts, static_cast<const int *>(list), l.count,
                                         pl->acc, s, 0);
-                    break;
-                case Launch::RESID_INIT:
-                    e = launch_residual_init(pl->d_insts, static_cast<const int2 *>(list), l.count, s,
-                                             ctx->cfg.refine_residual == JACPCG_RESID_FP64);
                     break;
             }
             if (e != cudaSuccess) return cuda_fail(ctx, e);
@@ -643,9 +624,7 @@ jacpcg_status jacpcg_create(const jacpcg_config *cfg, jacpcg_ctx **out) {
         q.K = cfg->max_K;
         std::vector<jacpcg_instance> v(cfg->max_instances, q);
         const int zero[6] = {0, 0, 0, 0, 0, 0};
-        // room for two calls at the limits, with the residual workspace that
-        // refinement or warm starts need
-        bytes = 2 * make_layout(v.data(), cfg->max_instances, true, zero).total;
+        bytes = 2 * make_layout(v.data(), cfg->max_instances, cfg->refine_sweeps > 0, zero).total;
     }
     bytes = align_up(bytes);
     if (cudaMalloc(reinterpret_cast<void **>(&ctx->arena.base), bytes) != cudaSuccess) {

@@ -38,7 +38,6 @@ struct DevInst {
     // right-hand sides (Eq. 16 per symbol vector): B == null means B = I_K
     const float2 *B;      // K x ncols, leading dimension ldb (caller)
     const float2 *X0;     // optional initial point, K x ncols, ld K (caller)
-    float *bn2;           // workspace KC: ||b_j||^2 for the warm-started solve
     int ldb;
     int ncols;            // right-hand sides: K for B = I, else n_rhs (<= KC)
 };

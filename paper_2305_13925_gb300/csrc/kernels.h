@@ -68,10 +68,6 @@ JACPCG_DECLARE_PCG_CLASS(256)
 // then hist[sweep] = ||R||_F / sqrt(K) per instance
 cudaError_t launch_residual(const DevInst *insts, const int2 *blocks, int n_blocks, cudaStream_t s,
                             bool fp64);
-// warm start, before the iteration: X = X0, R = B - A X0 and ||b_j||^2 per
-// (instance, column) block
-cudaError_t launch_residual_init(const DevInst *insts, const int2 *blocks, int n_blocks, cudaStream_t s,
-                                 bool fp64);
 cudaError_t launch_resid_hist(const DevInst *insts, int n_inst, int sweep, cudaStream_t s);
 // tiles: (instance, m tile, n tile, partial slot)
 cudaError_t launch_hx_simt(int TN, const DevInst *insts, const int4 *tiles, int n_tiles,

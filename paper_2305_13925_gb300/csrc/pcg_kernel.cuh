@@ -24,9 +24,10 @@
 // Stopping (tol > 0): a column stops before an update once
 // ||r||^2 <= tol^2 ||b||^2 (Alg. 1: ||D r||^2).
 // Right-hand side (mode): 0 solves A X = B (B = I_K, or the instance's
-// symbol vectors, Eq. 16) and writes X -- from X0 when the instance has one,
-// as X0 plus the solve of A E = B - A X0 (the residual kernel has put R and
-// X = X0 in place), stopping relative to ||b||; 1 solves A dX = R for the
+// symbol vectors, Eq. 16) and writes X -- from the initial point X0 when the
+// instance has one (Sec. III-B Step 1: a pass before the first update forms
+// A X0 with the iteration's own product, r = b - A X0, Alg. 1 scaling it by
+// D^{-1}; the stopping test stays relative to ||b||); 1 solves A dX = R for the
 // refinement residual R of the instance's workspace and adds dX to X
 // (iterative refinement); only mode 0 reports iterations, residuals and
 // non-convergence.
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(NW * 32) pcg_kernel(const DevInst *__restrict_
     const DevInst &in = insts[blk.x];
     const int K = in.K;
     const int T = in.max_iter;
-    const bool warm = mode == 0 && in.X0 != nullptr;   // R = B - A X0 and X = X0 are in place
+    const bool warm = mode == 0 && in.X0 != nullptr;   // start from X0 (one extra product A X0)
     const float tol2 = in.tol > 0.f ? in.tol * in.tol : -1.f;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float2 *__restrict__ Ag = in.A;
@@ -97,19 +98,21 @@ __global__ void __launch_bounds__(NW * 32) pcg_kernel(const DevInst *__restrict_
 #pragma unroll
         for (int i = 0; i < RPL; ++i) {
             float2 b = make_float2(0.f, 0.f);
-            if (mode == 0 && !warm) {
+            if (mode == 0) {
                 if (!in.B) {
                     if (rvalid[i] && row[i] == col[c]) b.x = 1.f;           // B = I
                 } else if (rvalid[i] && cvalid[c]) {
                     b = in.B[row[i] + (size_t)col[c] * in.ldb];               // symbol vectors
                 }
             } else if (rvalid[i] && cvalid[c]) {
-                b = in.R[row[i] + (size_t)col[c] * KC];                       // B - A X (X0)
+                b = in.R[row[i] + (size_t)col[c] * KC];                       // refinement residual
             }
             comp_fma(bb, b.x, b.x);
             comp_fma(bb, b.y, b.y);
-            x[i][c] = make_float2(0.f, 0.f);
-            r[i][c] = VAR == 1 ? make_float2(dv[i] * b.x, dv[i] * b.y) : b;
+            x[i][c] = (warm && rvalid[i] && cvalid[c]) ? in.X0[row[i] + (size_t)col[c] * K]
+                                                       : make_float2(0.f, 0.f);
+            // a warm start keeps b in r until the first pass has formed A X0
+            r[i][c] = (VAR == 1 && !warm) ? make_float2(dv[i] * b.x, dv[i] * b.y) : b;
             p[i][c] = make_float2(dv[i] * b.x, dv[i] * b.y);   // z = D^{-1} r (standard, CG); m = r (Alg. 1)
             const float2 z = make_float2(dv[i] * r[i][c].x, dv[i] * r[i][c].y);
             if (VAR == 1) {
@@ -129,8 +132,7 @@ __global__ void __launch_bounds__(NW * 32) pcg_kernel(const DevInst *__restrict_
         bb = comp_warp_allreduce(bb);
         rho[c] = rz.s + rz.c;
         res2[c] = rs.s + rs.c;
-        // a warm start stops relative to ||b||, not to its residual
-        bn2c[c] = (warm && cvalid[c]) ? in.bn2[col[c]] : (bb.s + bb.c);
+        bn2c[c] = bb.s + bb.c;
         btol[c] = tol2 * bn2c[c];
         done[c] = !cvalid[c];
         its[c] = 0;
@@ -140,12 +142,13 @@ __global__ void __launch_bounds__(NW * 32) pcg_kernel(const DevInst *__restrict_
     float2 *Pw = P_s + (size_t)warp * KC * CW;   // this warp's p columns, [k][c]
     if (RESIDENT) __syncthreads();
 
-    for (int t = 0; t < T; ++t) {
+    for (int t = warm ? -1 : 0; t < T; ++t) {
+        const bool init = t < 0;   // the warm start's pass: q = A X0, no update
         // Step 2: stopping test before the update
-        bool any = false;
+        bool any = init;
 #pragma unroll
         for (int c = 0; c < CW; ++c) {
-            if (!done[c] && tol2 > 0.f && res2[c] <= btol[c]) done[c] = true;
+            if (!init && !done[c] && tol2 > 0.f && res2[c] <= btol[c]) done[c] = true;
             any |= !done[c];
         }
         if (RESIDENT) {
@@ -159,7 +162,7 @@ __global__ void __launch_bounds__(NW * 32) pcg_kernel(const DevInst *__restrict_
         for (int i = 0; i < RPL; ++i)
 #pragma unroll
             for (int c = 0; c < CW; ++c)
-                if (row[i] < KC) Pw[row[i] * CW + c] = p[i][c];
+                if (row[i] < KC) Pw[row[i] * CW + c] = init ? x[i][c] : p[i][c];
         __syncwarp();
 
         // q = A p
@@ -223,6 +226,41 @@ __global__ void __launch_bounds__(NW * 32) pcg_kernel(const DevInst *__restrict_
             }
         }
         __syncwarp();
+
+        if (init) {
+            // r = b - A X0 (Alg. 1: D^{-1} (b - A X0)), then Step 1 from there
+#pragma unroll
+            for (int c = 0; c < CW; ++c) {
+                Comp rz = {0.f, 0.f}, rs = {0.f, 0.f};
+#pragma unroll
+                for (int i = 0; i < RPL; ++i) {
+                    float2 rw = make_float2(r[i][c].x - q[i][c].x, r[i][c].y - q[i][c].y);
+                    if (VAR == 1) {
+                        rw = make_float2(dv[i] * rw.x, dv[i] * rw.y);
+                        r[i][c] = rw;
+                        p[i][c] = rw;
+                        comp_fma(rz, rw.x, rw.x);
+                        comp_fma(rz, rw.y, rw.y);
+                        comp_fma(rs, dd[i] * rw.x, dd[i] * rw.x);
+                        comp_fma(rs, dd[i] * rw.y, dd[i] * rw.y);
+                    } else {
+                        r[i][c] = rw;
+                        const float2 z = make_float2(dv[i] * rw.x, dv[i] * rw.y);
+                        p[i][c] = z;
+                        comp_fma(rz, rw.x, z.x);
+                        comp_fma(rz, rw.y, z.y);
+                        comp_fma(rs, rw.x, rw.x);
+                        comp_fma(rs, rw.y, rw.y);
+                    }
+                }
+                rz = comp_warp_allreduce(rz);
+                rs = comp_warp_allreduce(rs);
+                rho[c] = rz.s + rz.c;
+                res2[c] = rs.s + rs.c;
+            }
+            __syncwarp();   // p columns in shared memory are rewritten next pass
+            continue;
+        }
 
         // scalars and vector updates, column by column
 #pragma unroll
@@ -331,7 +369,7 @@ __global__ void __launch_bounds__(NW * 32) pcg_kernel(const DevInst *__restrict_
         for (int i = 0; i < RPL; ++i) {
             if (row[i] >= KC) continue;
             float2 v = x[i][c];
-            if (mode == 1 || warm) {   // X += dX (X holds X0 for a warm start)
+            if (mode == 1) {   // X += dX
                 const float2 o = in.X[row[i] + (size_t)col[c] * KC];
                 v = make_float2(o.x + v.x, o.y + v.y);
             }

@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
         const int id = list[jj];
         const DevInst &in = insts[id];
         const int K = in.K, T = in.max_iter, NCOL = in.ncols;
-        const bool warm = mode == 0 && in.X0 != nullptr;   // R = B - A X0 and X = X0 in place
+        const bool warm = mode == 0 && in.X0 != nullptr;   // start from X0: one extra product A X0
         const float tol2 = in.tol > 0.f ? in.tol * in.tol : -1.f;
 
         // ---- A in the real 2 x 2-block layout, TF32 head and tail ----
@@ -201,16 +201,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
                 const int i = g + 4 * k;
                 dv[k] = (i < K) ? (VAR == 2 ? 1.f : in.dinv[i]) : 0.f;
                 float2 b = make_float2(0.f, 0.f);
-                if (mode == 0 && !warm) {
+                if (mode == 0) {
                     if (!in.B) {
                         if (i < K && i == j) b.x = 1.f;                       // B = I
                     } else if (i < K && j < NCOL) {
                         b = in.B[i + (size_t)j * in.ldb];                     // symbol vectors
                     }
                 } else if (i < K && j < NCOL) {
-                    b = in.R[i + (size_t)j * 64];                             // B - A X (X0)
+                    b = in.R[i + (size_t)j * 64];                             // refinement residual
                 }
-                x[k] = make_float2(0.f, 0.f);
+                x[k] = (warm && i < K && j < NCOL) ? in.X0[i + (size_t)j * K] : make_float2(0.f, 0.f);
                 r[k] = b;
                 p[k] = make_float2(dv[k] * b.x, dv[k] * b.y);
                 t1[k] = fmaf(b.x, b.x, b.y * b.y);
@@ -218,21 +218,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
             }
             rho = col_total(sum16(t0));    // r^H z
             res2 = col_total(sum16(t1));   // ||r||^2 = ||b||^2
-            // a warm start stops relative to ||b||, not to its residual
-            bn2c = (warm && j < NCOL) ? in.bn2[j] : res2;
+            bn2c = res2;                   // stopping and reporting stay relative to ||b||
             btol = tol2 * bn2c;
         }
         __syncthreads();   // A is in place for both teams
 
-        for (int t = 0;; ++t) {
+        for (int t = warm ? -1 : 0;; ++t) {
+            const bool init = t < 0;   // the warm start's pass: Q = A X0, no update
             // Step 2: stopping test, then publish P = [Re p; Im p] (head, tail)
-            if (tol2 > 0.f && res2 <= btol) done = true;
-            const int any = (!done && t < T) ? 1 : 0;
+            if (!init && tol2 > 0.f && res2 <= btol) done = true;
+            const int any = (init || (!done && t < T)) ? 1 : 0;
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
+                const float2 v = init ? x[k] : p[k];
                 float ph, pl, qh, ql;
-                tc::split_tf32(p[k].x, ph, pl);
-                tc::split_tf32(p[k].y, qh, ql);
+                tc::split_tf32(v.x, ph, pl);
+                tc::split_tf32(v.y, qh, ql);
                 const uint32_t o = p_off + (uint32_t)(2 * k) * LBO;
                 st_shared_v2(b_hi + o, ph, qh);
                 st_shared_v2(b_lo + o, pl, ql);
@@ -295,6 +296,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
                 const int i = g + 4 * k;
                 q[k] = make_float2(S.Q[(2 * i) * QLD + j], S.Q[(2 * i + 1) * QLD + j]);
             }
+            if (init) {   // r = b - A X0, then Step 1 from there
+                float t0[RPT], t1[RPT];
+#pragma unroll
+                for (int k = 0; k < RPT; ++k) {
+                    r[k] = make_float2(r[k].x - q[k].x, r[k].y - q[k].y);
+                    p[k] = make_float2(dv[k] * r[k].x, dv[k] * r[k].y);
+                    t1[k] = fmaf(r[k].x, r[k].x, r[k].y * r[k].y);
+                    t0[k] = dv[k] * t1[k];
+                }
+                rho = col_total(sum16(t0));
+                res2 = col_total(sum16(t1));
+                continue;
+            }
             // lambda = r^H z / p^H A p
             float pAp;
             {
@@ -338,7 +352,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
             for (int k = 0; k < RPT; ++k) {
                 const int i = g + 4 * k;
                 float2 val = x[k];
-                if (mode == 1 || warm) {   // X += dX (X holds X0 for a warm start)
+                if (mode == 1) {   // X += dX
                     const float2 o = in.X[i + (size_t)j * 64];
                     val = make_float2(o.x + val.x, o.y + val.y);
                 }

@@ -1,7 +1,7 @@
-// refine.cu -- the true residual R = B - A X (B = I for the RZF precoder,
-// else the caller's right-hand sides), for iterative refinement and for a
-// warm start from X0, and the per-instance norm history.  Two evaluations,
-// both far more accurate than the FP32 iteration they correct:
+// refine.cu -- the true residual of iterative refinement, R = B - A X (B = I
+// for the RZF precoder, else the caller's right-hand sides), and its
+// per-instance norm history.  Two evaluations, both far more accurate than
+// the FP32 iteration they correct:
 //   FP64: every product and sum in FP64 (A and X are FP32, so each product
 //         is exact in FP64);
 //   DOT2: FP32 error-free transformations (TwoProduct by FMA, TwoSum), the
@@ -11,10 +11,7 @@
 //         the FP32 pipes, which on this GPU are far faster than FP64.
 // No passage of the paper: the paper solves Eq. 16 by the iteration alone;
 // refinement is the system layer that wins back accuracy lost to FP32 and
-// to bfloat16 inputs.  The warm start (initial point w^0 of Sec. III-B
-// Step 1) uses the same residual: PCG from X0 on A X = B is X0 plus PCG from
-// zero on A E = B - A X0, stopped relative to ||b|| -- so this kernel also
-// copies X0 into the iterate and records ||b_j||^2.
+// to bfloat16 inputs.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -36,8 +33,7 @@ __device__ __forceinline__ double block_sum256(double v, double *red) {
 }
 
 // One block per (instance, column j), one thread per row i (K <= 256).
-// INIT: the iterate is X0 (caller, ld K), copied into the workspace X.
-template <bool FP64, bool INIT>
+template <bool FP64>
 __global__ void __launch_bounds__(256) residual_kernel(const DevInst *__restrict__ insts,
                                                        const int2 *__restrict__ blocks) {
     __shared__ double red[256];
@@ -45,8 +41,8 @@ __global__ void __launch_bounds__(256) residual_kernel(const DevInst *__restrict
     const DevInst &in = insts[blk.x];
     const int K = in.K, KC = in.KC, j = blk.y, i = threadIdx.x;
     const float2 *__restrict__ A = in.A;
-    const float2 *__restrict__ X = INIT ? in.X0 : in.X;
-    const int ldx = INIT ? K : KC;
+    const float2 *__restrict__ X = in.X;
+    const int ldx = KC;
     float2 b = make_float2(0.f, 0.f);
     if (i < K) {
         if (in.B) b = in.B[i + (size_t)j * in.ldb];
@@ -80,17 +76,9 @@ __global__ void __launch_bounds__(256) residual_kernel(const DevInst *__restrict
             im = (double)ci.s + (double)ci.c;
         }
     }
-    if (i < KC) {
-        in.R[i + (size_t)j * KC] = make_float2((float)re, (float)im);
-        if (INIT) in.X[i + (size_t)j * KC] = i < K ? X[i + (size_t)j * ldx] : make_float2(0.f, 0.f);
-    }
+    if (i < KC) in.R[i + (size_t)j * KC] = make_float2((float)re, (float)im);
     const double rn = block_sum256(re * re + im * im, red);
-    if (INIT) {
-        const double bn = block_sum256((double)b.x * b.x + (double)b.y * b.y, red);
-        if (i == 0) in.bn2[j] = (float)bn;
-    } else if (i == 0) {
-        in.rnorm[j] = (float)rn;
-    }
+    if (i == 0) in.rnorm[j] = (float)rn;
 }
 
 // One warp per instance: fixed-order sum of the column norms.
@@ -113,19 +101,9 @@ cudaError_t launch_residual(const DevInst *insts, const int2 *blocks, int n_bloc
                             bool fp64) {
     if (n_blocks <= 0) return cudaSuccess;
     if (fp64)
-        residual_kernel<true, false><<<n_blocks, 256, 0, s>>>(insts, blocks);
+        residual_kernel<true><<<n_blocks, 256, 0, s>>>(insts, blocks);
     else
-        residual_kernel<false, false><<<n_blocks, 256, 0, s>>>(insts, blocks);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_residual_init(const DevInst *insts, const int2 *blocks, int n_blocks, cudaStream_t s,
-                                 bool fp64) {
-    if (n_blocks <= 0) return cudaSuccess;
-    if (fp64)
-        residual_kernel<true, true><<<n_blocks, 256, 0, s>>>(insts, blocks);
-    else
-        residual_kernel<false, true><<<n_blocks, 256, 0, s>>>(insts, blocks);
+        residual_kernel<false><<<n_blocks, 256, 0, s>>>(insts, blocks);
     return cudaGetLastError();
 }
 
