@@ -298,6 +298,32 @@ jacpcg_status jacpcg_precode_noalloc(const jacpcg_instance *inst, int n_inst, in
                                      int32_t *status_dev, int32_t *iters_dev, float *resid_dev,
                                      float *beta_dev, void *stream);
 
+/* Per-subarray (block) RZF, Eq. 7 and the block structure of Eq. 6: the
+ * array's antennas are split into row ranges, each serving its own set of
+ * users, and each block G_i = beta_i H_i (H_i^H H_i + xi I)^{-1} is an
+ * independent RZF precoder with its own power factor (beta_i over the
+ * block's own F_i).  A block is a row range [row0, row0 + rows) of antennas
+ * and a column range [col0, col0 + cols) of users of the full channel. */
+typedef struct {
+    int row0, rows;          /* antennas of the block */
+    int col0, cols;          /* users of the block */
+} jacpcg_block;
+
+/* Host-only helper: describe the n_blocks blocks of `full` as independent
+ * instances (out[i], host array of n_blocks), to be precoded together by
+ * jacpcg_precode (a ragged batch) or any entry point that takes instances.
+ * out[i] copies full's scalars (xi, power, max_iter, tol, h_dtype) and
+ * points H_i and W_i into full->H and full->W: W_i is the (row0, col0)
+ * block of W, so one call fills the blocks of the block precoder G and
+ * leaves the rest of W untouched (the caller zeroes it once).  X, A,
+ * resid_hist, B and X0 of the blocks are NULL.  Errors, checked before
+ * anything is written: EINVAL for a block outside full's M x K, an empty
+ * block, more users than antennas in a block when xi = 0, or a block whose
+ * H or W would not start on a 16-byte boundary (row0 must be even for
+ * complex64 H, a multiple of 4 for bfloat16 H; W is complex64). */
+jacpcg_status jacpcg_blocks(const jacpcg_instance *full, const jacpcg_block *blocks, int n_blocks,
+                            jacpcg_instance *out);
+
 /* Destroy a context (and any plans still alive).  Waits for the device. */
 jacpcg_status jacpcg_destroy(jacpcg_ctx *ctx);
 

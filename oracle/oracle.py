@@ -206,6 +206,23 @@ def precode_symbols(H: np.ndarray, xi: float, B: np.ndarray, variant="standard",
     return dict(X=X, S=S, A=A, beta=beta, iters=int(it.max()), relres=float(rr.max()), status=st)
 
 
+def precode_blocks(H: np.ndarray, xi: float, blocks, variant="standard", max_iter: int = 8,
+                   tol: float = 0.0, power: float = 1.0):
+    """Per-subarray block precoder (Eq. 7 with the block structure of Eq. 6):
+    each block (row0, rows, col0, cols) is the RZF of its sub-channel
+    H[row0:row0+rows, col0:col0+cols] with its own beta_i.  Returns (G, betas)
+    where G is M x K holding the unnormalised blocks W_i = H_i P_i^{-1} and
+    zeros elsewhere (as the paper's G before the beta_i are applied)."""
+    Hm = np.asarray(H)
+    G = np.zeros(Hm.shape, dtype=np.complex128)
+    betas = []
+    for (r0, nr, c0, nc) in blocks:
+        ref = precode(Hm[r0:r0 + nr, c0:c0 + nc], xi, variant, max_iter, tol, power)
+        G[r0:r0 + nr, c0:c0 + nc] = ref["W"]
+        betas.append(ref["beta"])
+    return G, betas
+
+
 def precode_batch(Hs, xis, variant="standard", max_iter: int = 8, tol: float = 0.0,
                   power: float = 1.0, nthreads: int | None = None):
     """Many precoders on host threads.  ``Hs``: sequence of (M_i, K_i) arrays

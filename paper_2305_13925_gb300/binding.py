@@ -34,7 +34,7 @@ EXPORTS = ("jacpcg_create", "jacpcg_precode", "jacpcg_plan_create", "jacpcg_plan
            "jacpcg_version", "jacpcg_precode_noalloc", "jacpcg_precode_plain",
            "jacpcg_server_create", "jacpcg_submit", "jacpcg_poll", "jacpcg_server_replay",
            "jacpcg_server_stats", "jacpcg_server_destroy", "jacpcg_autotune", "jacpcg_set_shape",
-           "jacpcg_get_shape", "jacpcg_last_cuda_error")
+           "jacpcg_get_shape", "jacpcg_last_cuda_error", "jacpcg_blocks")
 
 
 class jacpcg_config(ctypes.Structure):
@@ -52,6 +52,11 @@ class jacpcg_instance(ctypes.Structure):
                 ("h_dtype", ctypes.c_int), ("resid_hist", ctypes.c_void_p),
                 ("B", ctypes.c_void_p), ("ldb", ctypes.c_int), ("n_rhs", ctypes.c_int),
                 ("X0", ctypes.c_void_p)]
+
+
+class jacpcg_block(ctypes.Structure):
+    _fields_ = [("row0", ctypes.c_int), ("rows", ctypes.c_int), ("col0", ctypes.c_int),
+                ("cols", ctypes.c_int)]
 
 
 class jacpcg_server_config(ctypes.Structure):
@@ -108,6 +113,8 @@ def load(path: pathlib.Path | str | None = None):
         L.jacpcg_last_cuda_error.restype = ctypes.c_char_p
         L.jacpcg_get_shape.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                                        ctypes.POINTER(I)]
+        L.jacpcg_blocks.argtypes = [ctypes.POINTER(jacpcg_instance), ctypes.POINTER(jacpcg_block), I,
+                                    ctypes.POINTER(jacpcg_instance)]
         L.jacpcg_strerror.argtypes = [I]
         L.jacpcg_strerror.restype = ctypes.c_char_p
         L.jacpcg_version.restype = ctypes.c_char_p
@@ -116,7 +123,7 @@ def load(path: pathlib.Path | str | None = None):
                   "jacpcg_profile_read", "jacpcg_destroy", "jacpcg_precode_noalloc",
                   "jacpcg_precode_plain", "jacpcg_server_create", "jacpcg_submit", "jacpcg_poll",
                   "jacpcg_server_replay", "jacpcg_server_stats", "jacpcg_server_destroy",
-                  "jacpcg_autotune", "jacpcg_set_shape", "jacpcg_get_shape"):
+                  "jacpcg_autotune", "jacpcg_set_shape", "jacpcg_get_shape", "jacpcg_blocks"):
             getattr(L, n).restype = I
         _lib = L
         return L
@@ -142,6 +149,15 @@ def _ptr(t):
 
 def jacpcg_version() -> str:
     return load().jacpcg_version().decode()
+
+
+def jacpcg_blocks(full: jacpcg_instance, blocks) -> list:
+    """Sub-instances of the per-subarray block precoder (Eq. 7): ``blocks``
+    is a sequence of (row0, rows, col0, cols); host only."""
+    bl = (jacpcg_block * len(blocks))(*[jacpcg_block(*b) for b in blocks])
+    out = (jacpcg_instance * len(blocks))()
+    _check(load().jacpcg_blocks(ctypes.byref(full), bl, len(blocks), out), "jacpcg_blocks")
+    return list(out)
 
 
 def jacpcg_strerror(status: int) -> str:

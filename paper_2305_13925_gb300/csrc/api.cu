@@ -585,6 +585,43 @@ extern "C" {
 
 const char *jacpcg_version(void) { return "0.1.0"; }
 
+// Eq. 7: each block of the block precoder is an RZF of its own sub-channel;
+// the sub-instances point into the full channel and the full W.
+jacpcg_status jacpcg_blocks(const jacpcg_instance *full, const jacpcg_block *blocks, int n_blocks,
+                            jacpcg_instance *out) {
+    if (!full || !blocks || !out || n_blocks < 1 || !full->H || !full->W) return JACPCG_EINVAL;
+    const size_t hes = full->h_dtype == JACPCG_H_BF16 ? 4 : 8;
+    for (int b = 0; b < n_blocks; ++b) {
+        const jacpcg_block &k = blocks[b];
+        if (k.rows < 1 || k.cols < 1 || k.row0 < 0 || k.col0 < 0 || k.row0 + k.rows > full->M ||
+            k.col0 + k.cols > full->K)
+            return JACPCG_EINVAL;
+        if (k.cols > k.rows && !(full->xi > 0.0)) return JACPCG_EINVAL;
+        const size_t ho = ((size_t)k.col0 * full->ldh + k.row0) * hes;
+        const size_t wo = ((size_t)k.col0 * full->ldw + k.row0) * 8;
+        if (!aligned16(static_cast<const char *>(full->H) + ho) ||
+            !aligned16(static_cast<const char *>(full->W) + wo))
+            return JACPCG_EINVAL;
+    }
+    for (int b = 0; b < n_blocks; ++b) {
+        const jacpcg_block &k = blocks[b];
+        jacpcg_instance q = *full;
+        q.M = k.rows;
+        q.K = k.cols;
+        q.H = static_cast<const char *>(full->H) + ((size_t)k.col0 * full->ldh + k.row0) * hes;
+        q.W = static_cast<char *>(full->W) + ((size_t)k.col0 * full->ldw + k.row0) * 8;
+        q.X = nullptr;
+        q.A = nullptr;
+        q.resid_hist = nullptr;
+        q.B = nullptr;
+        q.ldb = 0;
+        q.n_rhs = 0;
+        q.X0 = nullptr;
+        out[b] = q;
+    }
+    return JACPCG_OK;
+}
+
 const char *jacpcg_strerror(jacpcg_status s) {
     switch (s) {
         case JACPCG_OK: return "ok";

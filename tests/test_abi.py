@@ -72,3 +72,31 @@ int main(void) {{
     C, I = binding.jacpcg_config, binding.jacpcg_instance
     assert got == [ctypes.sizeof(C), C.arena_bytes.offset, C.flags.offset, ctypes.sizeof(I),
                    I.W.offset, I.tol.offset, I.B.offset, I.ldb.offset, I.n_rhs.offset, I.X0.offset]
+
+
+def test_blocks_helper_points_into_the_full_channel():
+    """jacpcg_blocks is host-only arithmetic: sub-instance pointers, shapes and
+    scalars, and its EINVAL rules (no GPU, fake device addresses)."""
+    I = binding.jacpcg_instance
+    full = I(M=1024, K=64, ldh=1030, H=0x100000, xi=0.5, power=2.0, W=0x900000, ldw=1026,
+             max_iter=6, tol=1e-5, h_dtype=binding.JACPCG_H_C64)
+    blocks = [(0, 384, 0, 32), (384, 256, 0, 64), (640, 384, 32, 32)]
+    out = binding.jacpcg_blocks(full, blocks)
+    for q, (r0, nr, c0, nc) in zip(out, blocks):
+        assert (q.M, q.K, q.ldh, q.ldw) == (nr, nc, 1030, 1026)
+        assert q.H == 0x100000 + (c0 * 1030 + r0) * 8
+        assert q.W == 0x900000 + (c0 * 1026 + r0) * 8
+        assert (q.xi, q.power, q.max_iter) == (0.5, 2.0, 6) and abs(q.tol - 1e-5) < 1e-12
+        assert not q.X and not q.A and not q.B and not q.X0
+    bf = I(M=64, K=8, ldh=64, H=0x100000, xi=0.5, W=0x900000, ldw=64, h_dtype=binding.JACPCG_H_BF16)
+    assert binding.jacpcg_blocks(bf, [(4, 8, 1, 2)])[0].H == 0x100000 + (64 + 4) * 4
+    bad = [(0, 1025, 0, 8), (2, 8, 60, 8), (1, 8, 0, 2), (0, 0, 0, 2), (-2, 8, 0, 2)]
+    for b in bad:
+        with pytest.raises(binding.JacpcgError) as e:
+            binding.jacpcg_blocks(full, [b])
+        assert e.value.status == binding.JACPCG_EINVAL, b
+    with pytest.raises(binding.JacpcgError):                 # bfloat16 rows need row0 % 4 == 0
+        binding.jacpcg_blocks(bf, [(2, 8, 0, 2)])
+    nreg = I(M=64, K=8, ldh=64, H=0x100000, xi=0.0, W=0x900000, ldw=64)
+    with pytest.raises(binding.JacpcgError):                 # more users than antennas, xi = 0
+        binding.jacpcg_blocks(nreg, [(0, 4, 0, 6)])
