@@ -62,7 +62,7 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--plain-sample", type=int, default=64)
     ap.add_argument("--workload", default="batched",
-                    choices=["batched", "serving", "single", "xl", "ragged", "symbols"])
+                    choices=["batched", "serving", "single", "xl", "ragged", "symbols", "blocks"])
     ap.add_argument("--rates", default="5000,20000,50000,100000,200000")
     ap.add_argument("--trace-seconds", type=float, default=0.5)
     ap.add_argument("--pool", type=int, default=512)
@@ -568,6 +568,63 @@ def run_symbols(args):
     return _line(cfg, blocks["instances_per_s"], {"symbol_blocks": blocks, "warm_start": warm})
 
 
+def run_blocks(args):
+    """Per-subarray block precoder (Eq. 7, block structure of Eq. 6) on the
+    batched channels: 8 x 128 antennas, users split into two groups of 32;
+    group 1 on subarrays 0-2, both groups on subarrays 3-4, group 2 on 5-7:
+    three independent RZF blocks per channel (384 x 32, 256 x 64, 384 x 32),
+    each with its own beta, precoded as one ragged batch."""
+    import numpy as np
+    import torch
+    from oracle import oracle as O
+    from paper_2305_13925_gb300 import binding, build, channels as C
+    build.build()
+    n = args.n_inst
+    blocks = [(0, 384, 0, 32), (384, 256, 0, 64), (640, 384, 32, 32)]
+    Hst, xi = C.generate_batch_device_layout("batched_1024x64", n, 1)
+    K, M = Hst.shape[1], Hst.shape[2]
+    Hd = torch.from_numpy(Hst).cuda()
+    Wd = torch.zeros_like(Hd)
+    insts = []
+    for i in range(n):
+        insts += binding.jacpcg_blocks(binding.instance(Hd[i], Wd[i], float(xi[i]), args.iters), blocks)
+    nb = len(insts)
+    arr = (binding.jacpcg_instance * nb)(*insts)
+    st = torch.empty(nb, dtype=torch.int32, device="cuda")
+    prec = binding.Precoder(max_instances=nb, max_M=M, max_K=K, precision=args.precision, profile=True)
+    s = torch.cuda.current_stream()
+    for _ in range(3):
+        binding.jacpcg_precode(prec.ctx, arr, st, None, None, None, s.cuda_stream)
+    torch.cuda.synchronize()
+    binding.jacpcg_profile_read(prec.ctx)
+    reps = max(3, min(args.steps, 20))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        binding.jacpcg_precode(prec.ctx, arr, st, None, None, None, s.cuda_stream)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    ph, nex, _ = binding.jacpcg_profile_read(prec.ctx)
+    prec.close()
+    sample = list(range(5, n, max(1, n // 6)))[:6]
+    errs = []
+    for i in sample:
+        G, _ = O.precode_blocks(Hst[i].T.astype(np.complex128), xi[i], blocks, args.variant,
+                                max_iter=args.iters)
+        Wg = Wd[i].T.cpu().numpy().astype(np.complex128)
+        errs.append(float(np.linalg.norm(Wg - G) / np.linalg.norm(G)))
+    cfg = {"workload": f"blocks: {n} channels, M=1024 (8x128), K=64 in two groups of 32; blocks "
+                       "(antennas 0-383, users 0-31), (384-639, all), (640-1023, 32-63); "
+                       f"T={args.iters} fixed", "precision": args.precision}
+    return _line(cfg, n / (ms / 1e3), {
+        "unit_note": "channels per second, each three block precoders", "ms_per_step": ms,
+        "block_precoders_per_s": nb / (ms / 1e3), "phase_ms": [round(v / max(nex, 1), 4) for v in ph],
+        "status_ok": int((st == 0).sum().item()),
+        "accuracy": {"sample": sample, "max_rel_err_G_vs_oracle": max(errs), "bar": 1e-5,
+                     "pass": max(errs) <= 1e-5}})
+
+
 def run_ragged(args):
     """1024 channels with K uniform over {8..256} and M over {256..4096},
     tolerance 1e-5: the whole ragged batch as one plan replayed as one CUDA
@@ -662,6 +719,8 @@ def main():
         return run_xl(args)
     if args.workload == "symbols":
         return run_symbols(args)
+    if args.workload == "blocks":
+        return run_blocks(args)
     if args.workload == "ragged":
         return run_ragged(args)
 
