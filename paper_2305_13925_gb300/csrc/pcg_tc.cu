@@ -10,7 +10,11 @@
 // in row 2i + 1.  3xTF32 as in gram_tc.cu; the head*head product is
 // accumulated in two TMEM buffers (one per half of the reduction) and the
 // correction products in a third, so no truncating accumulation chain is
-// longer than 16 MMAs.
+// longer than 16 MMAs.  The expanded A (head and tail) lives in tensor
+// memory and is the MMAs' A operand there: per iteration the MMAs read only
+// the 1 KB P tiles from shared memory instead of re-reading a 4 KB A tile for
+// every MMA.  The next instance's A is prefetched (cp.async) into a shared
+// staging tile while the current one iterates.
 //
 // The columns of P are independent systems that share A, so the 64 columns
 // form two groups of 32, each a 4-warp team with its own MMAs (N = 32), TMEM
@@ -43,18 +47,19 @@ constexpr int NG = 2;                       // column groups (teams)
 constexpr int GC = NC / NG;                 // columns per group (MMA N)
 constexpr uint32_t LBO = 128;               // K-adjacent core matrices
 constexpr uint32_t SBO = (RR / 4) * LBO;    // 8-row groups
-constexpr int APART = (RR / 8) * SBO;       // one of A_hi, A_lo
 constexpr int BPART = (NC / 8) * SBO;       // one of P_hi, P_lo
 constexpr int QLD = NC + 4;                 // floats per row of the Q tile
 constexpr int NW = 8;                       // warps: two teams of four
 constexpr int NTHREADS = NW * 32;
 constexpr int TEAM = NTHREADS / NG;
 constexpr int RPT = KCP / 4;                // complex rows per thread
-constexpr int TMEM_COLS = 256;              // team t: [128 t, 128 t + 96): head k<64, head k>=64, corrections
+constexpr int TMEM_COLS = 512;              // team t: [128 t, 128 t + 96): head k<64, head k>=64, corrections;
+                                            // [256, 384): A head, [384, 512): A tail (128 lanes x 128 K)
+constexpr uint32_t TA_HI = 256, TA_LO = 384;
 constexpr uint32_t WAIT_LIMIT = 1u << 21;
 
 struct __align__(128) PcgSmem {
-    unsigned char A[2 * APART];
+    float2 Ast[KCP * KCP];                  // the next instance's A (complex, ld 64), prefetched
     unsigned char B[2 * BPART];
     float Q[RR * QLD];
     uint64_t qfull[NG];
@@ -130,8 +135,21 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = S.tmem;
-    const uint32_t a_hi = tc::smem_u32(S.A), a_lo = a_hi + APART;
     const uint32_t b_hi = tc::smem_u32(S.B), b_lo = b_hi + BPART;
+    const uint32_t ast = tc::smem_u32(S.Ast);
+    // A of the instance at list position jj -> staging tile (8 chunks of 16 B per thread)
+    auto prefetch_a = [&](int jj) {
+        if (jj < n_list) {
+            const char *src = reinterpret_cast<const char *>(insts[list[jj]].A);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = threadIdx.x + NTHREADS * u;
+                tc::cp_async16(ast + e * 16, src + (size_t)e * 16, 16);
+            }
+        }
+        tc::cp_async_commit();
+    };
+    prefetch_a(blockIdx.x);
     const uint32_t q_base = tc::smem_u32(S.Q);
     const bool issuer = (threadIdx.x == team * TEAM);
     const uint32_t tq = tmem + team * 128;                  // this team's TMEM columns
@@ -151,41 +169,34 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
         const bool warm = mode == 0 && in.X0 != nullptr;   // start from X0: one extra product A X0
         const float tol2 = in.tol > 0.f ? in.tol * in.tol : -1.f;
 
-        // ---- A in the real 2 x 2-block layout, TF32 head and tail ----
+        // ---- A in the real 2 x 2-block layout, TF32 head and tail, into TMEM ----
+        tc::cp_async_wait_all();
+        __syncthreads();   // staging tile complete; both teams are done with the previous instance
         {
-            const float2 *__restrict__ Ag = in.A;   // ld 64, zero beyond K
-            float2 av[8][2];
+            // warp w writes TMEM lanes 32 (w mod 4) .. (real rows), K columns 64 (w / 4) ..
+            const int rho = 32 * quad + lane, ii = rho >> 1, sp = rho & 1;
+            const int half = warp >> 2;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int e = threadIdx.x + NTHREADS * u;
-                const int ii = e & 63, kp = e >> 6;   // row, pair of columns (2 kp, 2 kp + 1)
-                av[u][0] = Ag[ii + (size_t)(2 * kp) * 64];
-                av[u][1] = Ag[ii + (size_t)(2 * kp + 1) * 64];
-            }
-            __syncthreads();   // both teams are done with the previous instance's A
+            for (int c = 0; c < 4; ++c) {
+                float hv[16], lv[16];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int e = threadIdx.x + NTHREADS * u;
-                const int ii = e & 63, kp = e >> 6;
-                const float2 a0 = av[u][0], a1 = av[u][1];
-                const float re[4] = {a0.x, -a0.y, a1.x, -a1.y};   // real row 2 ii
-                const float im[4] = {a0.y, a0.x, a1.y, a1.x};     // real row 2 ii + 1
-                float rh[4], rl[4], ih[4], il[4];
-#pragma unroll
-                for (int w = 0; w < 4; ++w) {
-                    tc::split_tf32(re[w], rh[w], rl[w]);
-                    tc::split_tf32(im[w], ih[w], il[w]);
+                for (int kk = 0; kk < 8; ++kk) {
+                    const float2 a = S.Ast[ii + (size_t)(32 * half + 8 * c + kk) * 64];
+                    const float v0 = sp ? a.y : a.x;      // column 2k of real row 2i + sp
+                    const float v1 = sp ? a.x : -a.y;     // column 2k + 1
+                    tc::split_tf32(v0, hv[2 * kk], lv[2 * kk]);
+                    tc::split_tf32(v1, hv[2 * kk + 1], lv[2 * kk + 1]);
                 }
-                const int a = 2 * ii;
-                const uint32_t o0 = (uint32_t)(a >> 3) * SBO + kp * LBO + (a & 7) * 16;
-                const uint32_t o1 = o0 + 16;                   // real row a + 1
-                st_shared_v4(a_hi + o0, rh[0], rh[1], rh[2], rh[3]);
-                st_shared_v4(a_lo + o0, rl[0], rl[1], rl[2], rl[3]);
-                st_shared_v4(a_hi + o1, ih[0], ih[1], ih[2], ih[3]);
-                st_shared_v4(a_lo + o1, il[0], il[1], il[2], il[3]);
+                const uint32_t ta = tmem + ((uint32_t)(32 * quad) << 16) + 64 * half + 16 * c;
+                tc::tmem_st16(ta + TA_HI, hv);
+                tc::tmem_st16(ta + TA_LO, lv);
             }
-            tc::fence_proxy_async_smem();
+            tc::tmem_st_wait();
         }
+        tc::tc_fence_before();
+        __syncthreads();   // A is in TMEM for both teams; the staging tile is free
+        tc::tc_fence_after();
+        prefetch_a(jj + gridDim.x);
 
         // ---- state init (Step 1; x = 0, r = b, p = D^{-1} r) ----
         float2 x[RPT], r[RPT], p[RPT];
@@ -221,7 +232,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
             bn2c = res2;                   // stopping and reporting stay relative to ||b||
             btol = tol2 * bn2c;
         }
-        __syncthreads();   // A is in place for both teams
 
         for (int t = warm ? -1 : 0;; ++t) {
             const bool init = t < 0;   // the warm start's pass: Q = A X0, no update
@@ -251,14 +261,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
 #pragma unroll 4
                 for (int kk = 0; kk < RR / 8; ++kk) {
                     const uint32_t off = (uint32_t)(2 * kk) * LBO;
-                    const uint64_t ah = tc::smem_desc(a_hi + off, LBO, SBO);
-                    const uint64_t al = tc::smem_desc(a_lo + off, LBO, SBO);
+                    const uint32_t ah = tmem + TA_HI + 8 * kk, al = tmem + TA_LO + 8 * kk;
                     const uint64_t bh = tc::smem_desc(bh0 + off, LBO, SBO);
                     const uint64_t bl = tc::smem_desc(bl0 + off, LBO, SBO);
                     const uint32_t d1 = tq + (kk < RR / 16 ? 0u : 32u);
-                    tc::mma_tf32(d1, ah, bh, idesc, (kk % (RR / 16)) ? 1u : 0u);
-                    tc::mma_tf32(tq + 64u, ah, bl, idesc, kk ? 1u : 0u);
-                    tc::mma_tf32(tq + 64u, al, bh, idesc, 1u);
+                    tc::mma_tf32_tmem_a(d1, ah, bh, idesc, (kk % (RR / 16)) ? 1u : 0u);
+                    tc::mma_tf32_tmem_a(tq + 64u, ah, bl, idesc, kk ? 1u : 0u);
+                    tc::mma_tf32_tmem_a(tq + 64u, al, bh, idesc, 1u);
                 }
                 tc::mma_commit(&S.qfull[team]);
             }
@@ -374,6 +383,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
         }
     }
 
+    tc::cp_async_wait_all();   // the last (empty or unused) prefetch group
     if (issuer) {
         tc::mma_commit(&S.fin[team]);
         tc::mbar_wait(&S.fin[team], 0, WAIT_LIMIT);
