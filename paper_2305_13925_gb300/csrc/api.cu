@@ -112,7 +112,7 @@ struct Arena {
 
 // What one kernel launch of a plan covers.
 struct Launch {
-    enum Kind { GRAM, PCG, HX, GRAM_TC, HX_TC, PCG_TC } kind;
+    enum Kind { GRAM, PCG, HX, GRAM_TC, GRAM_TCX, HX_TC, PCG_TC } kind;
     int phase;        // 0 Gram, 1 iteration, 2 W = H X
     int param;        // TB (Gram), KC (iteration), TN (W = H X)
     size_t list_off;  // byte offset of its work list inside the plan block
@@ -159,6 +159,7 @@ struct jacpcg_plan {
     int refine_sweeps = 0;
     size_t res_off = 0;
     int n_res = 0;
+    size_t acc_reset_bytes = 0;   // > 0: clear the accumulators before the Gram (multi-job instances)
 };
 
 namespace {
@@ -203,8 +204,8 @@ int n_cols(const jacpcg_instance &q) { return q.B ? q.n_rhs : q.K; }
 
 // Byte layout of one plan block.
 struct Layout {
-    size_t insts, gram, tcl, pcg, hx, hxl, res, accum, ws, total;
-    int n_gram, n_pcg, n_hx, n_res;
+    size_t insts, gram, tcl, gdl, gxl, pcg, hx, hxl, res, accum, ws, total;
+    int n_gram, n_pcg, n_hx, n_res, n_gd, n_gx;
     bool refine;
     std::vector<size_t> ws_off;   // per instance
 };
@@ -233,21 +234,28 @@ size_t inst_ws_bytes(const jacpcg_instance &q, bool refine) {
     return b;
 }
 
-// K classes whose Gram and W = H X run on the tensor cores at this precision
-bool gram_on_tc(int precision, int KC) { return precision == JACPCG_TF32X3 && KC == 64; }
+// K classes whose Gram runs on the tensor cores at this precision (64 x 64
+// user-group blocks: one diagonal job for the 64 class, 2 + 1 for 128, 4 + 6
+// for 256) ...
+bool gram_on_tc(int precision, int KC) { return precision == JACPCG_TF32X3 && KC >= 64; }
+// ... whose W = H X does ...
+bool hx_on_tc(int precision, int KC) { return precision == JACPCG_TF32X3 && KC == 64; }
 // ... and whose iteration does, unless the SIMT kernel is asked for (Algorithm 1
 // always keeps the SIMT kernel)
 bool pcg_on_tc(const jacpcg_config &cfg, int KC) {
-    return !(cfg.flags & JACPCG_FLAG_SIMT_ITERATION) && gram_on_tc(cfg.precision, KC) &&
+    return !(cfg.flags & JACPCG_FLAG_SIMT_ITERATION) && cfg.precision == JACPCG_TF32X3 && KC == 64 &&
            cfg.variant != JACPCG_ALG1;
 }
 
 Layout make_layout(const jacpcg_instance *inst, int n, bool refine, const int *shape_idx) {
     Layout L{};
-    L.n_gram = L.n_pcg = L.n_hx = L.n_res = 0;
+    L.n_gram = L.n_pcg = L.n_hx = L.n_res = L.n_gd = L.n_gx = 0;
     L.refine = refine;
     for (int i = 0; i < n; ++i) {
         if (refine) L.n_res += n_cols(inst[i]);
+        const int ng = k_class(inst[i].K) / 64;   // user groups of a tensor-core Gram
+        L.n_gd += ng;
+        L.n_gx += ng * (ng - 1) / 2;
         L.n_gram += n_gtiles(inst[i]);
         L.n_pcg += n_pblocks(inst[i], shape_idx);
         L.n_hx += n_wtiles(inst[i]);
@@ -256,6 +264,8 @@ Layout make_layout(const jacpcg_instance *inst, int n, bool refine, const int *s
     L.insts = o;  o += align_up(sizeof(DevInst) * n);
     L.gram = o;   o += align_up(sizeof(int4) * L.n_gram);
     L.tcl = o;    o += align_up(sizeof(int) * n);
+    L.gdl = o;    o += align_up(sizeof(int2) * L.n_gd);
+    L.gxl = o;    o += align_up(sizeof(int4) * L.n_gx);
     L.pcg = o;    o += align_up(sizeof(int2) * L.n_pcg);
     L.hx = o;     o += align_up(sizeof(int4) * L.n_hx);
     L.hxl = o;    o += align_up(sizeof(int) * n);
@@ -292,7 +302,7 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
                                             align_up(KC * sizeof(float)));
         d.M = q.M; d.K = q.K; d.ldh = q.ldh; d.ldw = q.ldw; d.KC = KC;
         d.max_iter = q.max_iter;
-        d.n_wpart = gram_on_tc(ctx->cfg.precision, KC) ? (q.M + 127) / 128 : n_wtiles(q);
+        d.n_wpart = hx_on_tc(ctx->cfg.precision, KC) ? (q.M + 127) / 128 : n_wtiles(q);
         d.variant = ctx->cfg.variant;
         d.xi = (float)q.xi;
         d.power = q.power > 0.0 ? (float)q.power : 1.0f;
@@ -318,13 +328,27 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
             for (int j = 0; j < n_cols(inst[i]); ++j) rb[r++] = make_int2(i, j);
     }
     launches.clear();
-    // Gram on the tensor cores: one CTA per instance
+    // Gram on the tensor cores: diagonal (instance, group) jobs, then the
+    // off-diagonal (instance, a, b) jobs of the 128 and 256 classes
     const int prec = ctx->cfg.precision;
+    int2 *gd = reinterpret_cast<int2 *>(host + L.gdl);
+    int4 *gx = reinterpret_cast<int4 *>(host + L.gxl);
+    int nd = 0, nx = 0;
+    for (int i = 0; i < n; ++i) {
+        const int KC = k_class(inst[i].K);
+        if (!gram_on_tc(prec, KC)) continue;
+        for (int a = 0; a < KC / 64; ++a) {
+            gd[nd++] = make_int2(i, a);
+            for (int b = a + 1; b < KC / 64; ++b) gx[nx++] = make_int4(i, a, b, 0);
+        }
+    }
+    if (nd) launches.push_back({Launch::GRAM_TC, 0, 0, L.gdl, nd});
+    if (nx) launches.push_back({Launch::GRAM_TCX, 0, 0, L.gxl, nx});
+    // the K = 64 class's tensor-core iteration: instance list
     int *tl = reinterpret_cast<int *>(host + L.tcl);
     int nt = 0;
     for (int i = 0; i < n; ++i)
-        if (gram_on_tc(prec, k_class(inst[i].K))) tl[nt++] = i;
-    if (nt) launches.push_back({Launch::GRAM_TC, 0, 0, L.tcl, nt});
+        if (pcg_on_tc(ctx->cfg, k_class(inst[i].K))) tl[nt++] = i;
     // Gram tiles (SIMT) grouped by tile edge
     int4 *gt = reinterpret_cast<int4 *>(host + L.gram);
     int g = 0;
@@ -342,8 +366,7 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
     // iteration blocks grouped by K class
     int2 *pb = reinterpret_cast<int2 *>(host + L.pcg);
     int p = 0;
-    if (nt && pcg_on_tc(ctx->cfg, 64))
-        launches.push_back({Launch::PCG_TC, 1, 64, L.tcl, nt});
+    if (nt) launches.push_back({Launch::PCG_TC, 1, 64, L.tcl, nt});
     for (int KC : {8, 16, 32, 64, 128, 256}) {
         const int start = p;
         const int sh = ctx->pcg_shape_idx[kc_index(KC)];
@@ -358,7 +381,7 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
     int *hl = reinterpret_cast<int *>(host + L.hxl);
     int nh = 0;
     for (int i = 0; i < n; ++i)
-        if (gram_on_tc(prec, k_class(inst[i].K))) hl[nh++] = i;
+        if (hx_on_tc(prec, k_class(inst[i].K))) hl[nh++] = i;
     if (nh) launches.push_back({Launch::HX_TC, 2, 0, L.hxl, nh});
     // W = H X tiles (SIMT) grouped by tile width; slot = index of the tile in its instance
     int4 *ht = reinterpret_cast<int4 *>(host + L.hx);
@@ -367,7 +390,7 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
         const int start = h;
         for (int i = 0; i < n; ++i) {
             const int KC = k_class(inst[i].K);
-            if (hx_tn(KC) != TN || gram_on_tc(prec, KC)) continue;
+            if (hx_tn(KC) != TN || hx_on_tc(prec, KC)) continue;
             const int nm = (inst[i].M + HX_TM - 1) / HX_TM, nn = (n_cols(inst[i]) + TN - 1) / TN;
             int slot = 0;
             for (int nt = 0; nt < nn; ++nt)
@@ -392,6 +415,9 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
         ev = ctx->prof_pool[ctx->prof_used++].data();
     }
     if (ev) CK(cudaEventRecord(ev[0], s));
+    if (pl->acc_reset_bytes) {   // several Gram jobs per instance report into shared accumulators
+        CK(cudaMemsetAsync(pl->acc.flags, 0, pl->acc_reset_bytes, s));
+    }
     for (int phase = 0; phase < 3; ++phase) {
         for (const Launch &l : pl->launches) {
             if (l.phase != phase) continue;
@@ -411,7 +437,10 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
                                        s);
                     break;
                 case Launch::GRAM_TC:
-                    e = launch_gram_tc64(pl->d_insts, static_cast<const int *>(list), l.count, pl->acc, s);
+                    e = launch_gram_tc64(pl->d_insts, static_cast<const int2 *>(list), l.count, pl->acc, s);
+                    break;
+                case Launch::GRAM_TCX:
+                    e = launch_gram_tc_cross(pl->d_insts, static_cast<const int4 *>(list), l.count, pl->acc, s);
                     break;
                 case Launch::HX_TC:
                     e = launch_hx_tc64(pl->d_insts, static_cast<const int *>(list), l.count, pl->acc, s);
@@ -494,6 +523,7 @@ jacpcg_status make_plan(jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, int
     pl->refine_sweeps = ctx->cfg.refine_sweeps;
     pl->res_off = L.res;
     pl->n_res = L.n_res;
+    if (L.n_gx) pl->acc_reset_bytes = 3 * align_up(sizeof(int32_t) * n);
     const size_t tbytes = L.accum;   // tables occupy [0, accum)
     auto fail = [&](jacpcg_status s) {
         ctx->arena.release(pl->off, pl->bytes, nullptr);

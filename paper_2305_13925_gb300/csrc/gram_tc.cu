@@ -1,5 +1,9 @@
-// gram_tc.cu -- A = H^H H + xi I on the tcgen05 tensor cores for the K = 64
-// class (Sec. II, definition of P_i after Eq. 7; diag for Eq. 21).
+// gram_tc.cu -- A = H^H H + xi I on the tcgen05 tensor cores (Sec. II,
+// definition of P_i after Eq. 7; diag for Eq. 21): the diagonal 64 x 64
+// blocks.  A job is (instance, user group a): the Gram of the 64 users
+// 64 a .. 64 a + 63 written into block (a, a) of A (leading dimension KC) with
+// its 1/diag entries; for the K = 64 class that is all of A, for the 128 and
+// 256 classes gram_tc_cross.cu computes the off-diagonal blocks.
 //
 // Complex arithmetic as one real GEMM: with Y = [Re H | Im H] (M x 2K real),
 // D = Y^T Y (2K x 2K) gives Re A = D11 + D22 and Im A = D12 - D21.  For
@@ -86,7 +90,7 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, float a, float b, fl
 }
 
 __global__ void __launch_bounds__(NTHREADS, 1) gram_tc64_kernel(const DevInst *__restrict__ insts,
-                                                                const int *__restrict__ list, int n_list,
+                                                                const int2 *__restrict__ list, int n_list,
                                                                 DevAccum acc_out) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     GramSmem &S = *reinterpret_cast<GramSmem *>(smem_raw);
@@ -120,18 +124,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc64_kernel(const DevInst *_
         const uint32_t raw0 = tc::smem_u32(S.raw[0]);
         // stream cursor: (instance ordinal, stage) in this CTA's walk
         struct Cursor {
-            int j, c, nch, M, K, ldh;
-            const char *H;
+            int j, c, nch, M, K, ldh;   // K: users of the job's group that exist (K - 64 a)
+            const char *H;              // column 64 a of H
             bool bf16;
         };
         auto cursor_load = [&](Cursor &u) {
             if (u.j < n_list) {
-                const DevInst &in = insts[list[u.j]];
+                const int2 job = list[u.j];
+                const DevInst &in = insts[job.x];
                 u.M = in.M;
-                u.K = in.K;
+                u.K = in.K - 64 * job.y;
                 u.ldh = in.ldh;
-                u.H = reinterpret_cast<const char *>(in.H);
                 u.bf16 = in.h_bf16 != 0;
+                u.H = reinterpret_cast<const char *>(in.H) + (size_t)64 * job.y * in.ldh * (u.bf16 ? 4 : 8);
                 u.nch = (u.M + MCH - 1) / MCH;
             }
         };
@@ -181,7 +186,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc64_kernel(const DevInst *_
         }
         uint32_t chunk = 0, sc = 0;
         for (int j = blockIdx.x; j < n_list && !S.err; j += gridDim.x) {
-            const DevInst &in = insts[list[j]];
+            const DevInst &in = insts[list[j].x];
             const int M = in.M;
             const bool bf16 = in.h_bf16 != 0;
             const int nch = (M + MCH - 1) / MCH;
@@ -254,7 +259,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc64_kernel(const DevInst *_
         const int dtid = threadIdx.x - NPW * 32;   // 0 .. 255
         uint32_t grp = 0, ninst = 0;
         for (int j = blockIdx.x; j < n_list; j += gridDim.x, ++ninst) {
-            const int id = list[j];
+            const int id = list[j].x;
+            const int c0 = 64 * list[j].y;             // the job's users: c0 .. c0 + 63
             const DevInst &in = insts[id];
             const int nch = (in.M + MCH - 1) / MCH;
             const int ngrp = (nch + G - 1) / G;
@@ -306,7 +312,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc64_kernel(const DevInst *_
             if (lane == 0) tc::mbar_arrive(&S.core[ninst & 1]);
             asm volatile("bar.sync 1, 256;\n" ::: "memory");
             const bool bad = S.err != 0;
-            const int K = in.K;
+            const int K = in.K, KC = in.KC;
             const float xi = in.xi;
             float2 *__restrict__ A = in.A;
             float2 *__restrict__ Aout = in.Aout;
@@ -316,22 +322,27 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc64_kernel(const DevInst *_
                 float re = S.D[k * DPITCH + jj] + S.D[(64 + k) * DPITCH + 64 + jj];
                 float im = S.D[k * DPITCH + 64 + jj] - S.D[(64 + k) * DPITCH + jj];
                 if (r < c) im = -im;
+                const int gr = c0 + r, gc = c0 + c;        // position in A
                 if (r == c) {
                     im = 0.f;
-                    if (r < K) {
+                    if (gr < K) {
                         re += xi;
-                        in.dinv[r] = 1.0f / re;
+                        in.dinv[gr] = 1.0f / re;
                     } else {
-                        in.dinv[r] = 0.f;
+                        in.dinv[gr] = 0.f;
                     }
                 }
-                A[r + (size_t)c * 64] = make_float2(re, im);
-                if (Aout && r < K && c < K) Aout[r + (size_t)c * K] = make_float2(re, im);
+                A[gr + (size_t)gc * KC] = make_float2(re, im);
+                if (Aout && gr < K && gc < K) Aout[gr + (size_t)gc * K] = make_float2(re, im);
             }
             if (dtid == 0) {
-                acc_out.flags[id] = bad ? FLAG_TIMEOUT : 0;
-                acc_out.iters[id] = 0;
-                acc_out.resid_bits[id] = 0u;
+                if (KC == 64) {   // the instance's only job resets its accumulators
+                    acc_out.flags[id] = bad ? FLAG_TIMEOUT : 0;
+                    acc_out.iters[id] = 0;
+                    acc_out.resid_bits[id] = 0u;
+                } else if (bad) {   // several jobs: reset before the launch, report only
+                    atomicOr(acc_out.flags + id, FLAG_TIMEOUT);
+                }
             }
             asm volatile("bar.sync 1, 256;\n" ::: "memory");   // D is rewritten by the next instance
         }
@@ -340,7 +351,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc64_kernel(const DevInst *_
         constexpr uint32_t idesc = tc::idesc_tf32(ROWS, ROWS);
         uint32_t chunk = 0, grp = 0, ninst = 0;
         for (int j = blockIdx.x; j < n_list && !S.err; j += gridDim.x, ++ninst) {
-            const DevInst &in = insts[list[j]];
+            const DevInst &in = insts[list[j].x];
             const int nch = (in.M + MCH - 1) / MCH;
             const uint32_t e = tmem + (2 + (ninst & 1)) * ROWS;
             if (ninst >= 2) {   // the correction buffer of two instances ago has been read
@@ -389,7 +400,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc64_kernel(const DevInst *_
     tc::tc_fence_before();
     __syncthreads();
     if (S.err && threadIdx.x == 0) {
-        for (int j = blockIdx.x; j < n_list; j += gridDim.x) atomicOr(acc_out.flags + list[j], FLAG_TIMEOUT);
+        for (int j = blockIdx.x; j < n_list; j += gridDim.x) atomicOr(acc_out.flags + list[j].x, FLAG_TIMEOUT);
     }
     if (warp == MMA_WARP) {
         tc::tc_fence_after();
@@ -399,7 +410,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc64_kernel(const DevInst *_
 
 }  // namespace
 
-cudaError_t launch_gram_tc64(const DevInst *insts, const int *list, int n, DevAccum acc,
+cudaError_t launch_gram_tc64(const DevInst *insts, const int2 *list, int n, DevAccum acc,
                              cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const size_t smem = sizeof(GramSmem);

@@ -40,9 +40,13 @@ constexpr int HX_TM = 64;
 // tiles: (instance, bi, bj, 0) with bi >= bj
 cudaError_t launch_gram_simt(int TB, const DevInst *insts, const int4 *tiles, int n_tiles,
                              DevAccum acc, cudaStream_t s);
-// tensor-core Gram for the K = 64 class (3xTF32); list: instance ids, one CTA each
-cudaError_t launch_gram_tc64(const DevInst *insts, const int *list, int n, DevAccum acc,
+// tensor-core Gram (3xTF32), diagonal 64 x 64 blocks; list: (instance, user group) jobs
+cudaError_t launch_gram_tc64(const DevInst *insts, const int2 *list, int n, DevAccum acc,
                              cudaStream_t s);
+// tensor-core Gram, off-diagonal blocks (a, b), a < b, and their mirrors (K = 128 and
+// 256 classes); list: (instance, a, b, 0) jobs
+cudaError_t launch_gram_tc_cross(const DevInst *insts, const int4 *list, int n, DevAccum acc,
+                                 cudaStream_t s);
 // tensor-core W = H X for the K = 64 class (3xTF32); list: instance ids
 cudaError_t launch_hx_tc64(const DevInst *insts, const int *list, int n, DevAccum acc,
                            cudaStream_t s);

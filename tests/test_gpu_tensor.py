@@ -108,3 +108,38 @@ def test_tensor_many_instances_per_cta(bf16):
     errs = [rel_fro(out["W"][i], refs[i]) for i in range(len(Hs))]
     worst = int(np.argmax(errs))
     assert errs[worst] <= TOL_W, (worst, Hs[worst].shape, errs[worst])
+
+
+@pytest.mark.parametrize("K,M", [(65, 300), (100, 512), (128, 1024), (129, 700), (200, 1024),
+                                 (256, 2048), (256, 300)])
+def test_tensor_gram_multiblock_classes(K, M):
+    """K = 128 and 256 classes: the Gram as 64 x 64 user-group blocks on the
+    tensor cores (diagonal jobs + off-diagonal jobs with their conjugate
+    mirrors), K not a multiple of 64 included; A exactly Hermitian and within
+    the tensor accumulation bar, W through the SIMT iteration within 1e-5."""
+    spec = C.ChannelSpec(M=M, S=1, K=K, r=(0.5, 0.5), n_vis=(1, 1), snr_db=(10.0,))
+    inst = C.generate_instance(spec, 13, K * 3 + M)
+    check([inst.H], [inst.xi], T=5)
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_tensor_gram_multiblock_many_instances(bf16):
+    """Many K = 128 / 256 instances in one call (the off-diagonal jobs of one
+    instance run on different SMs and report into shared accumulators)."""
+    rng = np.random.default_rng(14)
+    Hs, xis = [], []
+    for n in range(40):
+        K = int(rng.choice([100, 128, 200, 256]))
+        M = int(rng.choice([300, 600]))
+        spec = C.ChannelSpec(M=M, S=1, K=K, r=(0.5, 0.5), n_vis=(1, 1), snr_db=(10.0,))
+        inst = C.generate_instance(spec, 15, n)
+        Hs.append(C.round_complex_bf16(inst.H) if bf16 else C.round_complex64(inst.H))
+        xis.append(inst.xi)
+    out = run(Hs, xis, T=4, precision="tf32x3", bf16=bf16, want_A=True)
+    refs = O.precode_batch(Hs, xis, "standard", max_iter=4)[0]
+    assert (out["status"] == 0).all()
+    for i, H in enumerate(Hs):
+        A = O.gram(H, xis[i])
+        assert np.array_equal(out["A"][i], out["A"][i].conj().T)
+        assert rel_fro(out["A"][i], A) <= TOL_A, i
+        assert rel_fro(out["W"][i], refs[i]) <= TOL_W, (i, H.shape)
