@@ -112,7 +112,7 @@ struct Arena {
 
 // What one kernel launch of a plan covers.
 struct Launch {
-    enum Kind { GRAM, PCG, HX, GRAM_TC, GRAM_TCX, HX_TC, PCG_TC } kind;
+    enum Kind { GRAM, PCG, HX, GRAM_TC, GRAM_TCX, HX_TC, HX_TCW, PCG_TC } kind;
     int phase;        // 0 Gram, 1 iteration, 2 W = H X
     int param;        // TB (Gram), KC (iteration), TN (W = H X)
     size_t list_off;  // byte offset of its work list inside the plan block
@@ -204,8 +204,8 @@ int n_cols(const jacpcg_instance &q) { return q.B ? q.n_rhs : q.K; }
 
 // Byte layout of one plan block.
 struct Layout {
-    size_t insts, gram, tcl, gdl, gxl, pcg, hx, hxl, res, accum, ws, total;
-    int n_gram, n_pcg, n_hx, n_res, n_gd, n_gx;
+    size_t insts, gram, tcl, gdl, gxl, pcg, hx, hxl, hwl, res, accum, ws, total;
+    int n_gram, n_pcg, n_hx, n_res, n_gd, n_gx, n_hw;
     bool refine;
     std::vector<size_t> ws_off;   // per instance
 };
@@ -238,8 +238,10 @@ size_t inst_ws_bytes(const jacpcg_instance &q, bool refine) {
 // user-group blocks: one diagonal job for the 64 class, 2 + 1 for 128, 4 + 6
 // for 256) ...
 bool gram_on_tc(int precision, int KC) { return precision == JACPCG_TF32X3 && KC >= 64; }
-// ... whose W = H X does ...
-bool hx_on_tc(int precision, int KC) { return precision == JACPCG_TF32X3 && KC == 64; }
+// ... whose W = H X does (the 64 class with X resident, 128 and 256 with X
+// streamed per stage, one job per 64 output columns) ...
+bool hx_on_tc(int precision, int KC) { return precision == JACPCG_TF32X3 && KC >= 64; }
+int hx_tc_groups(const jacpcg_instance &q) { return (n_cols(q) + 63) / 64; }
 // ... and whose iteration does, unless the SIMT kernel is asked for (Algorithm 1
 // always keeps the SIMT kernel)
 bool pcg_on_tc(const jacpcg_config &cfg, int KC) {
@@ -249,13 +251,14 @@ bool pcg_on_tc(const jacpcg_config &cfg, int KC) {
 
 Layout make_layout(const jacpcg_instance *inst, int n, bool refine, const int *shape_idx) {
     Layout L{};
-    L.n_gram = L.n_pcg = L.n_hx = L.n_res = L.n_gd = L.n_gx = 0;
+    L.n_gram = L.n_pcg = L.n_hx = L.n_res = L.n_gd = L.n_gx = L.n_hw = 0;
     L.refine = refine;
     for (int i = 0; i < n; ++i) {
         if (refine) L.n_res += n_cols(inst[i]);
         const int ng = k_class(inst[i].K) / 64;   // user groups of a tensor-core Gram
         L.n_gd += ng;
         L.n_gx += ng * (ng - 1) / 2;
+        L.n_hw += hx_tc_groups(inst[i]);
         L.n_gram += n_gtiles(inst[i]);
         L.n_pcg += n_pblocks(inst[i], shape_idx);
         L.n_hx += n_wtiles(inst[i]);
@@ -269,6 +272,7 @@ Layout make_layout(const jacpcg_instance *inst, int n, bool refine, const int *s
     L.pcg = o;    o += align_up(sizeof(int2) * L.n_pcg);
     L.hx = o;     o += align_up(sizeof(int4) * L.n_hx);
     L.hxl = o;    o += align_up(sizeof(int) * n);
+    L.hwl = o;    o += align_up(sizeof(int2) * L.n_hw);
     L.res = o;    o += align_up(sizeof(int2) * L.n_res);
     L.accum = o;  o += align_up(sizeof(int32_t) * n) * 3;
     L.ws = o;
@@ -302,7 +306,9 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
                                             align_up(KC * sizeof(float)));
         d.M = q.M; d.K = q.K; d.ldh = q.ldh; d.ldw = q.ldw; d.KC = KC;
         d.max_iter = q.max_iter;
-        d.n_wpart = hx_on_tc(ctx->cfg.precision, KC) ? (q.M + 127) / 128 : n_wtiles(q);
+        d.n_wpart = !hx_on_tc(ctx->cfg.precision, KC) ? n_wtiles(q)
+                    : KC == 64                         ? (q.M + 127) / 128
+                                                       : ((q.M + 127) / 128) * hx_tc_groups(q);
         d.variant = ctx->cfg.variant;
         d.xi = (float)q.xi;
         d.power = q.power > 0.0 ? (float)q.power : 1.0f;
@@ -381,8 +387,14 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
     int *hl = reinterpret_cast<int *>(host + L.hxl);
     int nh = 0;
     for (int i = 0; i < n; ++i)
-        if (hx_on_tc(prec, k_class(inst[i].K))) hl[nh++] = i;
+        if (hx_on_tc(prec, k_class(inst[i].K)) && k_class(inst[i].K) == 64) hl[nh++] = i;
     if (nh) launches.push_back({Launch::HX_TC, 2, 0, L.hxl, nh});
+    int2 *hw = reinterpret_cast<int2 *>(host + L.hwl);
+    int nw = 0;
+    for (int i = 0; i < n; ++i)
+        if (hx_on_tc(prec, k_class(inst[i].K)) && k_class(inst[i].K) > 64)
+            for (int b = 0; b < hx_tc_groups(inst[i]); ++b) hw[nw++] = make_int2(i, b);
+    if (nw) launches.push_back({Launch::HX_TCW, 2, 0, L.hwl, nw});
     // W = H X tiles (SIMT) grouped by tile width; slot = index of the tile in its instance
     int4 *ht = reinterpret_cast<int4 *>(host + L.hx);
     int h = 0;
@@ -444,6 +456,9 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
                     break;
                 case Launch::HX_TC:
                     e = launch_hx_tc64(pl->d_insts, static_cast<const int *>(list), l.count, pl->acc, s);
+                    break;
+                case Launch::HX_TCW:
+                    e = launch_hx_tc_wide(pl->d_insts, static_cast<const int2 *>(list), l.count, pl->acc, s);
                     break;
                 case Launch::PCG_TC:
                     e = launch_pcg_tc64(ctx->cfg.variant, pl->d_insts, static_cast<const int *>(list), l.count,

@@ -50,6 +50,10 @@ cudaError_t launch_gram_tc_cross(const DevInst *insts, const int4 *list, int n, 
 // tensor-core W = H X for the K = 64 class (3xTF32); list: instance ids
 cudaError_t launch_hx_tc64(const DevInst *insts, const int *list, int n, DevAccum acc,
                            cudaStream_t s);
+// tensor-core W = H X for the K = 128 and 256 classes (X streamed per stage);
+// list: (instance, 64-column output group) jobs
+cudaError_t launch_hx_tc_wide(const DevInst *insts, const int2 *list, int n, DevAccum acc,
+                              cudaStream_t s);
 // tensor-core iteration for the K = 64 class (standard or plain CG); list: instance ids
 cudaError_t launch_pcg_tc64(int variant, const DevInst *insts, const int *list, int n, DevAccum acc,
                             cudaStream_t s, int mode);
