@@ -17,9 +17,12 @@
 // staging tile while the current one iterates.
 //
 // The columns of P are independent systems that share A, so the 64 columns
-// form two groups of 32, each a 4-warp team with its own MMAs (N = 32), TMEM
-// buffers, mbarrier and named barrier: while the tensor core multiplies one
-// team's P, the other team updates its vectors.  Per iteration a team
+// may form NG groups, each a team of warps with its own MMAs (N = 64 / NG),
+// TMEM buffers, mbarrier and named barrier; with two teams the tensor core
+// multiplies one team's P while the other updates its vectors, but every
+// team issues the full 48 MMAs per iteration.  With A in tensor memory one
+// team of 8 warps (N = 64) measures faster on GB300 (0.31 vs 0.34 ms per
+// 2048-channel batch), so NG = 1.  Per iteration a team
 //   1. writes P (TF32 head and tail) into the MMA's K-major layout and votes
 //      on continuing (barrier reduction); its first thread issues 48 MMAs;
 //   2. copies Q from TMEM (warp w reads TMEM lanes 32 (w mod 4) ..) into a
@@ -43,7 +46,7 @@ namespace {
 constexpr int KCP = 64;                     // K class
 constexpr int RR = 2 * KCP;                 // real rows = real reduction length
 constexpr int NC = KCP;                     // right-hand sides
-constexpr int NG = 2;                       // column groups (teams)
+constexpr int NG = 1;                       // column groups (teams): 1 or 2
 constexpr int GC = NC / NG;                 // columns per group (MMA N)
 constexpr uint32_t LBO = 128;               // K-adjacent core matrices
 constexpr uint32_t SBO = (RR / 4) * LBO;    // 8-row groups
@@ -52,6 +55,8 @@ constexpr int QLD = NC + 4;                 // floats per row of the Q tile
 constexpr int NW = 8;                       // warps: two teams of four
 constexpr int NTHREADS = NW * 32;
 constexpr int TEAM = NTHREADS / NG;
+constexpr int PARTS = (NW / NG) / 4;        // warps of a team per TMEM lane quarter
+constexpr int TEAM_COLS = NG == 1 ? 256 : 128;   // TMEM columns per team: head k<64, head k>=64, corrections
 constexpr int RPT = KCP / 4;                // complex rows per thread
 constexpr int TMEM_COLS = 512;              // team t: [128 t, 128 t + 96): head k<64, head k>=64, corrections;
                                             // [256, 384): A head, [384, 512): A tail (128 lanes x 128 K)
@@ -116,7 +121,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
     extern __shared__ __align__(128) unsigned char smem_raw[];
     PcgSmem &S = *reinterpret_cast<PcgSmem *>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int team = warp >> 2, quad = warp & 3;
+    const int team = warp / (NW / NG), quad = warp & 3;
+    const int col_off = 32 * ((warp >> 2) % PARTS);   // this warp's 32 of its team's columns
     const int bar_id = 1 + team;
 
     if (threadIdx.x == 0) {
@@ -152,7 +158,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
     prefetch_a(blockIdx.x);
     const uint32_t q_base = tc::smem_u32(S.Q);
     const bool issuer = (threadIdx.x == team * TEAM);
-    const uint32_t tq = tmem + team * 128;                  // this team's TMEM columns
+    const uint32_t tq = tmem + team * TEAM_COLS;            // this team's TMEM columns
 
     // column-wise geometry: column j, complex rows g + 4 k
     const int jl = lane & 7, g = lane >> 3;
@@ -264,10 +270,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
                     const uint32_t ah = tmem + TA_HI + 8 * kk, al = tmem + TA_LO + 8 * kk;
                     const uint64_t bh = tc::smem_desc(bh0 + off, LBO, SBO);
                     const uint64_t bl = tc::smem_desc(bl0 + off, LBO, SBO);
-                    const uint32_t d1 = tq + (kk < RR / 16 ? 0u : 32u);
+                    const uint32_t d1 = tq + (kk < RR / 16 ? 0u : (uint32_t)GC);
                     tc::mma_tf32_tmem_a(d1, ah, bh, idesc, (kk % (RR / 16)) ? 1u : 0u);
-                    tc::mma_tf32_tmem_a(tq + 64u, ah, bl, idesc, kk ? 1u : 0u);
-                    tc::mma_tf32_tmem_a(tq + 64u, al, bh, idesc, 1u);
+                    tc::mma_tf32_tmem_a(tq + 2u * GC, ah, bl, idesc, kk ? 1u : 0u);
+                    tc::mma_tf32_tmem_a(tq + 2u * GC, al, bh, idesc, 1u);
                 }
                 tc::mma_commit(&S.qfull[team]);
             }
@@ -280,14 +286,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
             ++phase;
             tc::tc_fence_after();
             {
-                const uint32_t ta = tq + ((uint32_t)(32 * quad) << 16);
-                const uint32_t qrow = q_base + (uint32_t)((32 * quad + lane) * QLD + GC * team) * 4;
+                const uint32_t ta = tq + ((uint32_t)(32 * quad) << 16) + col_off;
+                const uint32_t qrow = q_base + (uint32_t)((32 * quad + lane) * QLD + GC * team + col_off) * 4;
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     float u0[16], u1[16], u2[16];
                     tc::tmem_ld16(ta + 16 * h, u0);
-                    tc::tmem_ld16(ta + 32 + 16 * h, u1);
-                    tc::tmem_ld16(ta + 64 + 16 * h, u2);
+                    tc::tmem_ld16(ta + GC + 16 * h, u1);
+                    tc::tmem_ld16(ta + 2 * GC + 16 * h, u2);
                     tc::tmem_ld_wait();
 #pragma unroll
                     for (int m = 0; m < 4; ++m) {
