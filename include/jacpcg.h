@@ -103,6 +103,17 @@ typedef struct {
                                 FP32 iteration (the instance's max_iter and tol, relative to
                                 ||R||), X += dX */
     int refine_residual;     /* JACPCG_RESID_DOT2 (default) or JACPCG_RESID_FP64 */
+    float refine_tol;        /* 0 (default): every sweep runs for every instance.  > 0: an
+                                instance stops refining (its remaining correction solves and
+                                residual evaluations are skipped) once its largest per-column
+                                relative true residual ||B_j - A X_j|| / ||B_j|| is at most
+                                refine_tol, or has not fallen below half its value before the
+                                last sweep (the FP32 iteration's floor); finite, >= 0 */
+    float refine_solve_tol;  /* 0 (default): each correction solve A dX = R stops a column at the
+                                instance's tol relative to ||R_j||.  > 0: at this tolerance
+                                instead (a sweep needs only to cut the error by a fixed factor;
+                                the residual is recomputed accurately before the next one).  The
+                                solve still stops at the instance's max_iter; finite, >= 0 */
 } jacpcg_config;
 
 typedef struct {

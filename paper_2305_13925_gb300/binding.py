@@ -41,7 +41,8 @@ class jacpcg_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("max_instances", ctypes.c_int), ("max_M", ctypes.c_int),
                 ("max_K", ctypes.c_int), ("arena_bytes", ctypes.c_size_t),
                 ("precision", ctypes.c_int), ("variant", ctypes.c_int), ("flags", ctypes.c_int),
-                ("refine_sweeps", ctypes.c_int), ("refine_residual", ctypes.c_int)]
+                ("refine_sweeps", ctypes.c_int), ("refine_residual", ctypes.c_int),
+                ("refine_tol", ctypes.c_float), ("refine_solve_tol", ctypes.c_float)]
 
 
 class jacpcg_instance(ctypes.Structure):
@@ -385,7 +386,8 @@ class Precoder:
 
     def __init__(self, max_instances: int, max_M: int, max_K: int, variant="standard",
                  precision="fp32", device: int = 0, arena_bytes: int = 0, profile: bool = False,
-                 refine_sweeps: int = 0, refine_fp64: bool = False, simt_iteration: bool = False):
+                 refine_sweeps: int = 0, refine_fp64: bool = False, simt_iteration: bool = False,
+                 refine_tol: float = 0.0, refine_solve_tol: float = 0.0):
         self.cfg = jacpcg_config(device=device, max_instances=max_instances, max_M=max_M,
                                  max_K=max_K, arena_bytes=arena_bytes,
                                  precision=PRECISIONS[precision] if isinstance(precision, str) else precision,
@@ -393,7 +395,8 @@ class Precoder:
                                  flags=(JACPCG_FLAG_PROFILE if profile else 0)
                                  | (JACPCG_FLAG_SIMT_ITERATION if simt_iteration else 0),
                                  refine_sweeps=int(refine_sweeps),
-                                 refine_residual=JACPCG_RESID_FP64 if refine_fp64 else JACPCG_RESID_DOT2)
+                                 refine_residual=JACPCG_RESID_FP64 if refine_fp64 else JACPCG_RESID_DOT2,
+                                 refine_tol=float(refine_tol), refine_solve_tol=float(refine_solve_tol))
         self.ctx = jacpcg_create(self.cfg)
 
     def close(self):

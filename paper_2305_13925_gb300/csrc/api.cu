@@ -230,7 +230,7 @@ size_t inst_ws_bytes(const jacpcg_instance &q, bool refine) {
     const size_t KC = k_class(q.K);
     size_t b = align_up(KC * KC * sizeof(float2)) * 2 + align_up(KC * sizeof(float)) +
                align_up(n_wtiles(q) * sizeof(float));
-    if (refine) b += align_up(KC * KC * sizeof(float2)) + align_up(KC * sizeof(float));
+    if (refine) b += align_up(KC * KC * sizeof(float2)) + align_up((2 * KC + 2) * sizeof(float));
     return b;
 }
 
@@ -254,7 +254,7 @@ Layout make_layout(const jacpcg_instance *inst, int n, bool refine, const int *s
     L.n_gram = L.n_pcg = L.n_hx = L.n_res = L.n_gd = L.n_gx = L.n_hw = 0;
     L.refine = refine;
     for (int i = 0; i < n; ++i) {
-        if (refine) L.n_res += n_cols(inst[i]);
+        if (refine) L.n_res += (n_cols(inst[i]) + RES_CB - 1) / RES_CB;
         const int ng = k_class(inst[i].K) / 64;   // user groups of a tensor-core Gram
         L.n_gd += ng;
         L.n_gx += ng * (ng - 1) / 2;
@@ -323,6 +323,9 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
                                 align_up(n_wtiles(q) * sizeof(float));
             d.R = reinterpret_cast<float2 *>(w + base);
             d.rnorm = reinterpret_cast<float *>(w + base + align_up((size_t)KC * KC * sizeof(float2)));
+            d.rctl = d.rnorm + 2 * KC;
+            d.rtol2 = ctx->cfg.refine_tol * ctx->cfg.refine_tol;
+            d.rsolve_tol = ctx->cfg.refine_solve_tol;
             d.resid_hist = q.resid_hist;
         }
         hi[i] = d;
@@ -331,7 +334,7 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
         int2 *rb = reinterpret_cast<int2 *>(host + L.res);
         int r = 0;
         for (int i = 0; i < n; ++i)
-            for (int j = 0; j < n_cols(inst[i]); ++j) rb[r++] = make_int2(i, j);
+            for (int j = 0; j < n_cols(inst[i]); j += RES_CB) rb[r++] = make_int2(i, j);
     }
     launches.clear();
     // Gram on the tensor cores: diagonal (instance, group) jobs, then the
@@ -472,7 +475,7 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
             // iterative refinement: R = I - A X (FP64), A dX = R (FP32 iteration), X += dX
             const int2 *rb = reinterpret_cast<const int2 *>(pl->dev + pl->res_off);
             for (int sw = 0; sw <= pl->refine_sweeps; ++sw) {
-                if (launch_residual(pl->d_insts, rb, pl->n_res, s,
+                if (launch_residual(pl->d_insts, rb, pl->n_res, sw, s,
                                     ctx->cfg.refine_residual == JACPCG_RESID_FP64) != cudaSuccess ||
                     launch_resid_hist(pl->d_insts, pl->n_inst, sw, s) != cudaSuccess)
                     return cuda_fail(ctx);
@@ -691,6 +694,8 @@ jacpcg_status jacpcg_create(const jacpcg_config *cfg, jacpcg_ctx **out) {
     if (cfg->refine_sweeps < 0 || cfg->refine_sweeps > 3) return JACPCG_EINVAL;
     if (cfg->refine_residual != JACPCG_RESID_DOT2 && cfg->refine_residual != JACPCG_RESID_FP64)
         return JACPCG_EINVAL;
+    if (!(cfg->refine_tol >= 0.f) || cfg->refine_tol > 1e30f) return JACPCG_EINVAL;   // also NaN
+    if (!(cfg->refine_solve_tol >= 0.f) || cfg->refine_solve_tol > 1e30f) return JACPCG_EINVAL;
     jacpcg_ctx *ctx = new (std::nothrow) jacpcg_ctx();
     if (!ctx) return JACPCG_ENOMEM;
     ctx->cfg = *cfg;

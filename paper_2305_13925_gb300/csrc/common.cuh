@@ -33,7 +33,11 @@ struct DevInst {
     float xi, power, tol;
     int h_bf16;           // H holds bfloat16 (re, im) pairs instead of complex64
     float2 *R;            // workspace KC x KC: refinement residual I - A X (null without refinement)
-    float *rnorm;         // workspace KC: per-column ||R_j||^2 of the last residual
+    float *rnorm;         // workspace 2 KC: per-column ||R_j||^2 of the last residual, then ||B_j||^2
+    float *rctl;          // workspace 2: largest column ||R_j||^2 / ||B_j||^2 at the last
+                          // evaluation, and 1 once the instance has stopped refining
+    float rtol2;          // refine_tol^2 (0: every sweep runs)
+    float rsolve_tol;     // tolerance of the correction solves (0: tol)
     float *resid_hist;    // caller's optional refinement history
     // right-hand sides (Eq. 16 per symbol vector): B == null means B = I_K
     const float2 *B;      // K x ncols, leading dimension ldb (caller)

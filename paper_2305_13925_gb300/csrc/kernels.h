@@ -72,10 +72,13 @@ JACPCG_DECLARE_PCG_CLASS(64)
 JACPCG_DECLARE_PCG_CLASS(128)
 JACPCG_DECLARE_PCG_CLASS(256)
 #undef JACPCG_DECLARE_PCG_CLASS
-// refinement: R = I - A X in FP64 and per-column ||R_j||^2 (blocks: (instance, column)),
-// then hist[sweep] = ||R||_F / sqrt(K) per instance
-cudaError_t launch_residual(const DevInst *insts, const int2 *blocks, int n_blocks, cudaStream_t s,
-                            bool fp64);
+// refinement: R = B - A X (FP64 or Dot2) and per-column ||R_j||^2, ||B_j||^2 (blocks:
+// (instance, first column), RES_CB columns each; from the second evaluation on,
+// instances that stopped refining are skipped), then hist[sweep] = ||R||_F / sqrt(n)
+// and the stop decision per instance
+constexpr int RES_CB = 8;
+cudaError_t launch_residual(const DevInst *insts, const int2 *blocks, int n_blocks, int sweep,
+                            cudaStream_t s, bool fp64);
 cudaError_t launch_resid_hist(const DevInst *insts, int n_inst, int sweep, cudaStream_t s);
 // tiles: (instance, m tile, n tile, partial slot)
 cudaError_t launch_hx_simt(int TN, const DevInst *insts, const int4 *tiles, int n_tiles,

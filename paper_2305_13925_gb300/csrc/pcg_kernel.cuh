@@ -51,10 +51,12 @@ __global__ void __launch_bounds__(NW * 32) pcg_kernel(const DevInst *__restrict_
 
     const int2 blk = blocks[blockIdx.x];
     const DevInst &in = insts[blk.x];
+    if (mode == 1 && in.rctl[1] != 0.f) return;   // the instance stopped refining
     const int K = in.K;
     const int T = in.max_iter;
     const bool warm = mode == 0 && in.X0 != nullptr;   // start from X0 (one extra product A X0)
-    const float tol2 = in.tol > 0.f ? in.tol * in.tol : -1.f;
+    const float tl = (mode == 1 && in.rsolve_tol > 0.f) ? in.rsolve_tol : in.tol;   // correction solves
+    const float tol2 = tl > 0.f ? tl * tl : -1.f;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float2 *__restrict__ Ag = in.A;
 

@@ -173,11 +173,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
         const DevInst &in = insts[id];
         const int K = in.K, T = in.max_iter, NCOL = in.ncols;
         const bool warm = mode == 0 && in.X0 != nullptr;   // start from X0: one extra product A X0
-        const float tol2 = in.tol > 0.f ? in.tol * in.tol : -1.f;
+        const float tl = (mode == 1 && in.rsolve_tol > 0.f) ? in.rsolve_tol : in.tol;   // correction solves
+        const float tol2 = tl > 0.f ? tl * tl : -1.f;
 
         // ---- A in the real 2 x 2-block layout, TF32 head and tail, into TMEM ----
         tc::cp_async_wait_all();
         __syncthreads();   // staging tile complete; both teams are done with the previous instance
+        if (mode == 1 && in.rctl[1] != 0.f) {   // the instance stopped refining (uniform)
+            prefetch_a(jj + gridDim.x);
+            continue;
+        }
         {
             // warp w writes TMEM lanes 32 (w mod 4) .. (real rows), K columns 64 (w / 4) ..
             const int rho = 32 * quad + lane, ii = rho >> 1, sp = rho & 1;

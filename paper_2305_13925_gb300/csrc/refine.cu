@@ -9,6 +9,10 @@
 //         dot product", SIAM J. Sci. Comput. 26(6), 2005), whose result is as
 //         accurate as if computed in twice the working precision; it runs on
 //         the FP32 pipes, which on this GPU are far faster than FP64.
+// Each evaluation also decides, per instance, whether refinement goes on:
+// it stops once the largest relative column residual is at most refine_tol
+// or no longer halves (the FP32 floor), and stopped instances skip the
+// remaining correction solves and evaluations.
 // No passage of the paper: the paper solves Eq. 16 by the iteration alone;
 // refinement is the system layer that wins back accuracy lost to FP32 and
 // to bfloat16 inputs.
@@ -19,91 +23,162 @@ namespace jacpcg {
 
 namespace {
 
-__device__ __forceinline__ double block_sum256(double v, double *red) {
-    const int i = threadIdx.x;
-    red[i] = v;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (i < o) red[i] += red[i + o];
-        __syncthreads();
-    }
-    const double s = red[0];
-    __syncthreads();
-    return s;
-}
+// One block per (instance, block of RES_CB columns j0 ..), one thread per row
+// i (K <= 256).  Each thread carries the RES_CB residual entries of its row;
+// rows k of X are staged in shared memory RES_KCH at a time and read as
+// broadcasts, so A is read once per column block instead of once per column.
+// Column norms: per-warp xor-butterfly sums, then the eight warp totals in a
+// fixed order.
+constexpr int RES_KCH = 32;
 
-// One block per (instance, column j), one thread per row i (K <= 256).
 template <bool FP64>
 __global__ void __launch_bounds__(256) residual_kernel(const DevInst *__restrict__ insts,
-                                                       const int2 *__restrict__ blocks) {
-    __shared__ double red[256];
+                                                       const int2 *__restrict__ blocks, int sweep) {
+    constexpr int CB = RES_CB;
+    __shared__ float2 Xs[RES_KCH][CB];
+    __shared__ double red[2][8][CB];
     const int2 blk = blocks[blockIdx.x];
     const DevInst &in = insts[blk.x];
-    const int K = in.K, KC = in.KC, j = blk.y, i = threadIdx.x;
+    if (sweep > 0 && in.rctl[1] != 0.f) return;   // stopped refining: R and its norms stand
+    const int K = in.K, KC = in.KC, j0 = blk.y, i = threadIdx.x;
+    const int nj = min(CB, in.ncols - j0);
     const float2 *__restrict__ A = in.A;
     const float2 *__restrict__ X = in.X;
     const int ldx = KC;
-    float2 b = make_float2(0.f, 0.f);
-    if (i < K) {
-        if (in.B) b = in.B[i + (size_t)j * in.ldb];
-        else if (i == j) b.x = 1.f;
-    }
-    double re = 0.0, im = 0.0;
-    if (i < K) {
-        if (FP64) {
-            for (int k = 0; k < K; ++k) {
-                const float2 a = A[i + (size_t)k * KC];
-                const float2 x = X[k + (size_t)j * ldx];
-                re = fma((double)a.x, (double)x.x, re);
-                re = fma(-(double)a.y, (double)x.y, re);
-                im = fma((double)a.x, (double)x.y, im);
-                im = fma((double)a.y, (double)x.x, im);
-            }
-            re = (double)b.x - re;
-            im = (double)b.y - im;
-        } else {
-            // (s, c) pairs: s the rounded sum, c the accumulated error terms
-            Comp cr = {b.x, 0.f}, ci = {b.y, 0.f};
-            for (int k = 0; k < K; ++k) {
-                const float2 a = A[i + (size_t)k * KC];
-                const float2 x = X[k + (size_t)j * ldx];
-                comp_fma(cr, -a.x, x.x);
-                comp_fma(cr, a.y, x.y);
-                comp_fma(ci, -a.x, x.y);
-                comp_fma(ci, -a.y, x.x);
-            }
-            re = (double)cr.s + (double)cr.c;
-            im = (double)ci.s + (double)ci.c;
+    float2 b[CB];
+#pragma unroll
+    for (int c = 0; c < CB; ++c) {
+        b[c] = make_float2(0.f, 0.f);
+        if (i < K && c < nj) {
+            if (in.B) b[c] = in.B[i + (size_t)(j0 + c) * in.ldb];
+            else if (i == j0 + c) b[c].x = 1.f;
         }
     }
-    if (i < KC) in.R[i + (size_t)j * KC] = make_float2((float)re, (float)im);
-    const double rn = block_sum256(re * re + im * im, red);
-    if (i == 0) in.rnorm[j] = (float)rn;
+    // FP64: plain FP64 sums; DOT2: (s, c) pairs, s the rounded sum, c the accumulated errors
+    double dre[FP64 ? CB : 1], dim[FP64 ? CB : 1];
+    Comp cre[FP64 ? 1 : CB], cim[FP64 ? 1 : CB];
+#pragma unroll
+    for (int c = 0; c < CB; ++c) {
+        if (FP64) {
+            dre[c] = 0.0;
+            dim[c] = 0.0;
+        } else {
+            cre[c] = Comp{b[c].x, 0.f};
+            cim[c] = Comp{b[c].y, 0.f};
+        }
+    }
+    for (int k0 = 0; k0 < K; k0 += RES_KCH) {
+        const int nk = min(RES_KCH, K - k0);
+        __syncthreads();   // the previous chunk has been read
+        for (int e = threadIdx.x; e < RES_KCH * CB; e += blockDim.x) {
+            const int kk = e / CB, c = e % CB;
+            Xs[kk][c] = (kk < nk && c < nj) ? X[(k0 + kk) + (size_t)(j0 + c) * ldx] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        if (i < K) {
+#pragma unroll 4
+            for (int kk = 0; kk < nk; ++kk) {
+                const float2 a = A[i + (size_t)(k0 + kk) * KC];
+#pragma unroll
+                for (int c = 0; c < CB; ++c) {
+                    const float2 x = Xs[kk][c];
+                    if (FP64) {
+                        dre[c] = fma((double)a.x, (double)x.x, dre[c]);
+                        dre[c] = fma(-(double)a.y, (double)x.y, dre[c]);
+                        dim[c] = fma((double)a.x, (double)x.y, dim[c]);
+                        dim[c] = fma((double)a.y, (double)x.x, dim[c]);
+                    } else {
+                        comp_fma(cre[c], -a.x, x.x);
+                        comp_fma(cre[c], a.y, x.y);
+                        comp_fma(cim[c], -a.x, x.y);
+                        comp_fma(cim[c], -a.y, x.x);
+                    }
+                }
+            }
+        }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < CB; ++c) {
+        double re = 0.0, im = 0.0;
+        if (i < K) {
+            if (FP64) {
+                re = (double)b[c].x - dre[c];
+                im = (double)b[c].y - dim[c];
+            } else {
+                re = (double)cre[c].s + (double)cre[c].c;
+                im = (double)cim[c].s + (double)cim[c].c;
+            }
+        }
+        if (i < KC && c < nj) in.R[i + (size_t)(j0 + c) * KC] = make_float2((float)re, (float)im);
+        double rn = re * re + im * im;
+        double bn = (double)b[c].x * b[c].x + (double)b[c].y * b[c].y;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            rn += __shfl_xor_sync(0xffffffffu, rn, o);
+            bn += __shfl_xor_sync(0xffffffffu, bn, o);
+        }
+        if (lane == 0) {
+            red[0][warp][c] = rn;
+            red[1][warp][c] = bn;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < nj) {
+        const int c = threadIdx.x, nw = blockDim.x >> 5;
+        double rn = 0.0, bn = 0.0;
+        for (int w = 0; w < nw; ++w) {
+            rn += red[0][w][c];
+            bn += red[1][w][c];
+        }
+        in.rnorm[j0 + c] = (float)rn;
+        in.rnorm[KC + j0 + c] = (float)bn;
+    }
 }
 
-// One warp per instance: fixed-order sum of the column norms.
+// One warp per instance: fixed-order sum of the column norms for the history,
+// and the stop decision.  An instance stops refining once its largest relative
+// column residual (squared) is at most rtol2, or is above a quarter of its value
+// at the previous evaluation (the residual norm did not halve: the FP32
+// iteration's floor is reached, further sweeps only repeat the work).
 __global__ void resid_hist_kernel(const DevInst *__restrict__ insts, int n_inst, int sweep) {
     const int inst = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (inst >= n_inst) return;
     const DevInst &in = insts[inst];
-    if (!in.resid_hist) return;
     double s = 0.0;
-    for (int j = lane; j < in.ncols; j += 32) s += (double)in.rnorm[j];
+    float rel = 0.f;
+    for (int j = lane; j < in.ncols; j += 32) {
+        const float rn = in.rnorm[j], bn = in.rnorm[in.KC + j];
+        s += (double)rn;
+        rel = fmaxf(rel, bn > 0.f ? rn / bn : rn);
+    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) in.resid_hist[sweep] = (float)sqrt(s / in.ncols);
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        rel = fmaxf(rel, __shfl_xor_sync(0xffffffffu, rel, o));
+    }
+    if (lane != 0) return;
+    if (in.resid_hist) in.resid_hist[sweep] = (float)sqrt(s / in.ncols);
+    float *c = in.rctl;
+    if (sweep == 0) {
+        c[1] = (in.rtol2 > 0.f && rel <= in.rtol2) ? 1.f : 0.f;
+        c[0] = rel;
+    } else if (c[1] == 0.f) {
+        if (in.rtol2 > 0.f && (rel <= in.rtol2 || rel > 0.25f * c[0])) c[1] = 1.f;
+        c[0] = rel;
+    }
 }
 
 }  // namespace
 
-cudaError_t launch_residual(const DevInst *insts, const int2 *blocks, int n_blocks, cudaStream_t s,
-                            bool fp64) {
+cudaError_t launch_residual(const DevInst *insts, const int2 *blocks, int n_blocks, int sweep,
+                            cudaStream_t s, bool fp64) {
     if (n_blocks <= 0) return cudaSuccess;
     if (fp64)
-        residual_kernel<true><<<n_blocks, 256, 0, s>>>(insts, blocks);
+        residual_kernel<true><<<n_blocks, 256, 0, s>>>(insts, blocks, sweep);
     else
-        residual_kernel<false><<<n_blocks, 256, 0, s>>>(insts, blocks);
+        residual_kernel<false><<<n_blocks, 256, 0, s>>>(insts, blocks, sweep);
     return cudaGetLastError();
 }
 

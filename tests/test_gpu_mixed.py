@@ -58,3 +58,68 @@ def test_refinement_reaches_direct_rzf(shape, fp64):
         # the first sweep removes most of the residual; later ones reach the FP32 floor of X
         assert hist[1] < hist[0] / 10 and hist[-1] <= hist[1] * 1.5, hist
         assert after["status"][k] == 0
+
+
+def _mixed_batch():
+    """Two K = 256 channels (SIMT iteration) and two K = 64 channels (tensor
+    iteration) in one batch, bfloat16 storage."""
+    H1, x1 = C.generate_batch("xl_4096x256", 2, 5, dtype="bf16")
+    H2, x2 = C.generate_batch("batched_1024x64", 2, 5, dtype="bf16")
+    return list(H1) + list(H2), list(x1) + list(x2)
+
+
+def test_refinement_tol_stops_at_once():
+    """refine_tol = 1 stops every instance at the first residual evaluation:
+    no correction runs, the history repeats its first value and W equals the
+    unrefined W."""
+    Hs, xis = _mixed_batch()
+    plain = run(Hs, xis, T=60, tol=1e-3, bf16=True, precision="tf32x3")
+    out = run(Hs, xis, T=60, tol=1e-3, bf16=True, precision="tf32x3", refine_sweeps=3,
+              want_hist=True, refine_tol=1.0)
+    for k in range(len(Hs)):
+        h = out["hist"][k]
+        assert h[0] > 0 and np.all(h == h[0]), h
+        assert rel_fro(out["W"][k], plain["W"][k]) == 0.0
+        assert out["status"][k] == 0
+
+
+@pytest.mark.parametrize("solve_tol", [0.0, 1e-2])
+def test_refinement_tol_stops_early_and_reaches_direct_rzf(solve_tol):
+    """refine_tol = 1e-7 with a loose first solve: each instance refines until
+    its relative residual is below the target or stops falling; the history
+    is constant from the stop on and W ends within 1e-5 of the direct RZF,
+    also when each correction solve stops at 1e-2 of its residual."""
+    Hs, xis = _mixed_batch()
+    out = run(Hs, xis, T=60, tol=1e-3, bf16=True, precision="tf32x3", refine_sweeps=3,
+              want_hist=True, refine_tol=1e-7, refine_solve_tol=solve_tol)
+    for k in range(len(Hs)):
+        h = out["hist"][k]
+        Wd, _, _ = O.rzf_direct(Hs[k], xis[k])
+        assert rel_fro(out["W"][k], Wd) <= 1e-5, (k, h)
+        assert h[1] < h[0] / 10, h
+        rep = [s for s in range(1, len(h)) if h[s] == h[s - 1]]
+        if rep:   # stopped: nothing changes afterwards
+            assert np.all(h[rep[0]:] == h[rep[0]]), h
+        assert out["status"][k] == 0
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_refinement_residual_matches_fp64(fp64):
+    """The true residual the refinement evaluates (Dot2 or FP64), checked
+    through its history entry ||I - A X||_F / sqrt(K) against the same
+    quantity recomputed in FP64 from the GPU's own A and X; K = 17, 100 and
+    256 leave ragged 16-column blocks and rows beyond K in the K classes."""
+    Hs, xis = [], []
+    for K, M, seed in ((17, 256, 1), (100, 512, 2), (256, 1024, 3)):
+        spec = C.ChannelSpec(M=M, S=4, K=K, r=(0.5, 0.5), n_vis=(2, 3), snr_db=(10.0,))
+        inst = C.generate_instance(spec, seed, K)
+        Hs.append(inst.H)
+        xis.append(inst.xi)
+    out = run(Hs, xis, T=60, tol=1e-3, precision="tf32x3", refine_sweeps=1, want_hist=True,
+              refine_tol=1.0, want_X=True, want_A=True, refine_fp64=fp64)
+    for k, H in enumerate(Hs):
+        K = H.shape[1]
+        R = np.eye(K) - out["A"][k] @ out["X"][k]
+        ref = np.linalg.norm(R) / np.sqrt(K)
+        h = out["hist"][k]
+        assert ref > 0 and abs(h[0] - ref) <= 1e-4 * ref, (K, h[0], ref)
