@@ -45,7 +45,7 @@ SM_MAX_MHZ = 2070.0
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n-inst", type=int, default=2048)
@@ -169,6 +169,16 @@ class ClockSampler:
                 stdout=self.file, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # the timed region starts only once the sampler is producing rows
+        t0 = time.time()
+        while time.time() - t0 < 10.0 and self.proc.poll() is None:
+            try:
+                if os.path.getsize(self.file.name) > 0:
+                    break
+            except OSError:
+                pass
+            time.sleep(0.05)
 
     def stop(self):
         out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}

@@ -114,10 +114,15 @@ __device__ __forceinline__ float col_total(float v) {
     return v;
 }
 
-template <int VAR>
+// MODE 0 solves A X = B from X0 (or 0); MODE 1 is a refinement correction
+// solve (right-hand side R, X += dX, instances that stopped refining skipped).
+// The form is a template parameter so the main solve carries none of the
+// refinement code.
+template <int VAR, int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__restrict__ insts,
                                                                const int *__restrict__ list, int n_list,
-                                                               DevAccum acc_out, int mode) {
+                                                               DevAccum acc_out) {
+    constexpr int mode = MODE;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     PcgSmem &S = *reinterpret_cast<PcgSmem *>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -179,9 +184,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
         // ---- A in the real 2 x 2-block layout, TF32 head and tail, into TMEM ----
         tc::cp_async_wait_all();
         __syncthreads();   // staging tile complete; both teams are done with the previous instance
-        if (mode == 1 && in.rctl[1] != 0.f) {   // the instance stopped refining (uniform)
-            prefetch_a(jj + gridDim.x);
-            continue;
+        if constexpr (MODE == 1) {
+            if (in.rctl[1] != 0.f) {   // the instance stopped refining (uniform)
+                prefetch_a(jj + gridDim.x);
+                continue;
+            }
         }
         {
             // warp w writes TMEM lanes 32 (w mod 4) .. (real rows), K columns 64 (w / 4) ..
@@ -421,11 +428,11 @@ cudaError_t launch_pcg_tc64(int variant, const DevInst *insts, const int *list, 
     auto go = [&](auto kern) -> cudaError_t {
         cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (r != cudaSuccess) return r;
-        kern<<<grid, NTHREADS, smem, s>>>(insts, list, n, acc, mode);
+        kern<<<grid, NTHREADS, smem, s>>>(insts, list, n, acc);
         return cudaGetLastError();
     };
-    if (variant == 2) return go(pcg_tc64_kernel<2>);   // plain CG
-    return go(pcg_tc64_kernel<0>);
+    if (variant == 2) return mode ? go(pcg_tc64_kernel<2, 1>) : go(pcg_tc64_kernel<2, 0>);   // plain CG
+    return mode ? go(pcg_tc64_kernel<0, 1>) : go(pcg_tc64_kernel<0, 0>);
 }
 
 }  // namespace jacpcg
