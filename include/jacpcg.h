@@ -233,10 +233,11 @@ int64_t jacpcg_launch_count(const jacpcg_ctx *ctx);
  * server lives) and a scheduler thread.  Each request is one instance whose
  * H and W are device buffers that stay valid until the request completes.
  * While fewer than max_inflight batches are on the GPU, the scheduler takes
- * every waiting request (at most max_batch), admits them if the context
- * arena has room for their plan (else it waits for a running batch to
- * retire, or launches fewer), and runs them as one ragged batch on its own
- * stream: requests that arrive while others run join the next batch and
+ * the waiting requests (at most max_batch; by default only those of the
+ * oldest waiting request's cost class, see batch_policy), admits them if the
+ * context arena has room for their plan (else it waits for a running batch
+ * to retire, or launches fewer), and runs them as one ragged batch on its
+ * own stream: requests that arrive while others run join the next batch and
  * their work overlaps on the device.  Results are bitwise the same as the
  * request's result alone.  Latency = host time from submit to the end of
  * its batch on the GPU (a host callback on the batch's stream). */
@@ -248,7 +249,19 @@ typedef struct {
     int plain;              /* 1: run each batch with the plain per-instance comparator
                                (jacpcg_precode_plain) instead of the batched path */
     int plain_variant;      /* iteration form for plain = 1 */
+    int batch_policy;       /* JACPCG_BATCH_COST_CLASS (0, default) or JACPCG_BATCH_FIFO */
 } jacpcg_server_config;
+
+/* Batch formation (jacpcg_server_config.batch_policy).  A batch ends when its
+ * slowest request does, so one expensive request delays every request
+ * launched with it.  COST_CLASS: a batch takes, in arrival order, only the
+ * waiting requests of the oldest waiting request's cost class -- the K class
+ * (8 .. 64, 128, 256), with K = 256 split further into channels with
+ * M >= 4 K and the rest (near-square channels, often ill-conditioned and
+ * slow to converge) -- so cheap requests never wait inside an expensive
+ * batch, and the classes overlap on the device in separate batches.  FIFO:
+ * every waiting request in arrival order. */
+enum { JACPCG_BATCH_COST_CLASS = 0, JACPCG_BATCH_FIFO = 1 };
 
 jacpcg_status jacpcg_server_create(jacpcg_ctx *ctx, const jacpcg_server_config *cfg,
                                    jacpcg_server **out);

@@ -62,7 +62,8 @@ class jacpcg_block(ctypes.Structure):
 
 class jacpcg_server_config(ctypes.Structure):
     _fields_ = [("max_batch", ctypes.c_int), ("max_inflight", ctypes.c_int),
-                ("max_queue", ctypes.c_int), ("plain", ctypes.c_int), ("plain_variant", ctypes.c_int)]
+                ("max_queue", ctypes.c_int), ("plain", ctypes.c_int), ("plain_variant", ctypes.c_int),
+                ("batch_policy", ctypes.c_int)]
 
 
 class JacpcgError(RuntimeError):
@@ -297,10 +298,14 @@ def load_tuning(ctx, path) -> None:
             jacpcg_set_shape(ctx, int(k), int(v["shape"] if isinstance(v, dict) else v))
 
 
+JACPCG_BATCH_COST_CLASS, JACPCG_BATCH_FIFO = 0, 1
+
+
 def jacpcg_server_create(ctx, max_batch=256, max_inflight=4, max_queue=0, plain=False,
-                         plain_variant=JACPCG_STANDARD):
+                         plain_variant=JACPCG_STANDARD, batch_policy=JACPCG_BATCH_COST_CLASS):
     cfg = jacpcg_server_config(max_batch=max_batch, max_inflight=max_inflight, max_queue=max_queue,
-                               plain=int(plain), plain_variant=int(plain_variant))
+                               plain=int(plain), plain_variant=int(plain_variant),
+                               batch_policy=int(batch_policy))
     srv = ctypes.c_void_p()
     _check(load().jacpcg_server_create(ctx, ctypes.byref(cfg), ctypes.byref(srv)), "jacpcg_server_create")
     return srv

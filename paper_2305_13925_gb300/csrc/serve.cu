@@ -2,8 +2,10 @@
 //
 // Requests (one channel each, already on the device) are submitted from any
 // host thread and get a ticket.  A scheduler thread owns the context: while
-// fewer than max_inflight batches are on the GPU it takes every waiting
-// request (up to max_batch), checks the arena for room (admission by free
+// fewer than max_inflight batches are on the GPU it takes the waiting
+// requests of the oldest one's cost class (K class; K = 256 split by
+// M >= 4 K), so that a cheap request never waits inside a batch held up by
+// a slow one (up to max_batch), checks the arena for room (admission by free
 // device memory; otherwise it waits for a batch to retire), builds a ragged
 // plan and launches it on its own stream, so requests that arrive while
 // other batches run are admitted as soon as a slot and memory free up and
@@ -74,7 +76,8 @@ struct jacpcg_server {
     std::vector<bool> slot_busy;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
-    std::deque<Request> pending;
+    std::deque<Request> queue[4];         // waiting requests per cost class (FIFO: class 0 only)
+    size_t n_pending = 0;
     std::unordered_map<uint64_t, Result> results;
     std::vector<Batch *> inflight;
     uint64_t next_ticket = 1;
@@ -131,29 +134,44 @@ void fail_all(jacpcg_server *s, std::vector<Request> &reqs) {
     s->cv_done.notify_all();
 }
 
+// Cost class of a request (JACPCG_BATCH_COST_CLASS): the K class, with the
+// 256 class split by M >= 4 K.
+int cost_class(const jacpcg_instance &q) {
+    const int K = q.K;
+    if (K <= 64) return 0;
+    if (K <= 128) return 1;
+    return q.M >= 4 * K ? 2 : 3;
+}
+
 void scheduler(jacpcg_server *s) {
     std::unique_lock<std::mutex> lk(s->mu);
     while (true) {
         reap(s);
-        if (s->stop && s->pending.empty() && s->inflight.empty()) break;
+        if (s->stop && s->n_pending == 0 && s->inflight.empty()) break;
         int slot = -1;
         for (size_t k = 0; k < s->slot_busy.size(); ++k)
             if (!s->slot_busy[k]) {
                 slot = (int)k;
                 break;
             }
-        if (s->pending.empty() || slot < 0 || s->failed) {
+        if (s->n_pending == 0 || slot < 0 || s->failed) {
             // nothing to launch now: sleep briefly (callbacks do not notify the lock)
             s->cv_work.wait_for(lk, std::chrono::microseconds(20));
             continue;
         }
-        // take up to max_batch waiting requests, shrinking until the arena admits them
-        size_t take = std::min<size_t>(s->pending.size(), (size_t)s->cfg.max_batch);
+        // the class of the oldest waiting request (tickets grow with arrival)
+        int cls = -1;
+        for (int c = 0; c < 4; ++c)
+            if (!s->queue[c].empty() && (cls < 0 || s->queue[c].front().ticket < s->queue[cls].front().ticket))
+                cls = c;
+        std::deque<Request> &q = s->queue[cls];
+        // take up to max_batch of its requests, shrinking until the arena admits them
+        size_t take = std::min<size_t>(q.size(), (size_t)s->cfg.max_batch);
         std::vector<jacpcg_instance> insts;
         size_t need = 0, have = 0;
         while (take > 0) {
             insts.clear();
-            for (size_t k = 0; k < take; ++k) insts.push_back(s->pending[k].inst);
+            for (size_t k = 0; k < take; ++k) insts.push_back(q[k].inst);
             if (jacpcg_plan_bytes(s->ctx, insts.data(), (int)take, &need) != JACPCG_OK) {
                 need = SIZE_MAX;
                 break;
@@ -168,8 +186,9 @@ void scheduler(jacpcg_server *s) {
         }
         if (take == 0) {
             if (need == SIZE_MAX || s->inflight.empty()) {   // cannot ever fit: reject the head
-                std::vector<Request> bad{s->pending.front()};
-                s->pending.pop_front();
+                std::vector<Request> bad{q.front()};
+                q.pop_front();
+                --s->n_pending;
                 auto it = s->results.find(bad[0].ticket);
                 if (it != s->results.end()) {
                     it->second.state = 1;
@@ -181,8 +200,9 @@ void scheduler(jacpcg_server *s) {
             }
             continue;
         }
-        std::vector<Request> reqs(s->pending.begin(), s->pending.begin() + take);
-        s->pending.erase(s->pending.begin(), s->pending.begin() + take);
+        std::vector<Request> reqs(q.begin(), q.begin() + take);
+        q.erase(q.begin(), q.begin() + take);
+        s->n_pending -= take;
         Batch *b = new (std::nothrow) Batch();
         if (!b) {
             fail_all(s, reqs);
@@ -230,7 +250,8 @@ extern "C" {
 
 jacpcg_status jacpcg_server_create(jacpcg_ctx *ctx, const jacpcg_server_config *cfg,
                                    jacpcg_server **out) {
-    if (!ctx || !cfg || !out || cfg->max_batch < 1 || cfg->max_inflight < 1 || cfg->max_inflight > 64)
+    if (!ctx || !cfg || !out || cfg->max_batch < 1 || cfg->max_inflight < 1 || cfg->max_inflight > 64 ||
+        (cfg->batch_policy != JACPCG_BATCH_COST_CLASS && cfg->batch_policy != JACPCG_BATCH_FIFO))
         return JACPCG_EINVAL;
     jacpcg_server *s = new (std::nothrow) jacpcg_server();
     if (!s) return JACPCG_ENOMEM;
@@ -269,12 +290,13 @@ jacpcg_status jacpcg_submit(jacpcg_server *s, const jacpcg_instance *inst, uint6
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->failed) return JACPCG_ECUDA;
     if (s->stop) return JACPCG_EBUSY;
-    if (s->cfg.max_queue > 0 && (int)s->pending.size() >= s->cfg.max_queue) return JACPCG_EBUSY;
+    if (s->cfg.max_queue > 0 && s->n_pending >= (size_t)s->cfg.max_queue) return JACPCG_EBUSY;
     Request r{s->next_ticket++, *inst, now_us()};
     Result res;
     res.t_submit = r.t_submit;
     s->results.emplace(r.ticket, res);
-    s->pending.push_back(r);
+    s->queue[s->cfg.batch_policy == JACPCG_BATCH_COST_CLASS ? cost_class(r.inst) : 0].push_back(r);
+    ++s->n_pending;
     *ticket = r.ticket;
     s->cv_work.notify_one();
     return JACPCG_OK;

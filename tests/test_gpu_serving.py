@@ -54,6 +54,41 @@ def test_server_results_equal_alone(torch_gpu, precision):
         assert np.array_equal(W, alone[k]), k
 
 
+@pytest.mark.parametrize("policy", ["cost_class", "fifo"])
+def test_server_cost_classes(torch_gpu, policy):
+    """Requests of the 64 class, of the 256 class with M >= 4 K and of the
+    near-square 256 class: under the cost-class policy no batch mixes
+    classes (so at least three batches run); under FIFO any mix may share a
+    batch.  Either way each result equals the request's result alone."""
+    torch = torch_gpu
+    from paper_2305_13925_gb300 import binding
+    insts = (C.generate_ragged(4, 81, k_set=(64,), m_set=(256,))
+             + C.generate_ragged(2, 82, k_set=(256,), m_set=(1024,))
+             + C.generate_ragged(2, 83, k_set=(256,), m_set=(512,)))
+    order = [0, 4, 6, 1, 5, 2, 7, 3]                       # classes interleaved in arrival order
+    insts = [insts[k] for k in order]
+    runs = [run([i.H], [i.xi], T=12, tol=1e-5, precision="tf32x3") for i in insts]
+    alone = [r["W"][0] for r in runs]
+    alone_status = [int(r["status"][0]) for r in runs]   # near-square channels may stop unconverged
+    Hd, Wd, descs = _pool(torch, insts, T=12, tol=1e-5)
+    prec = binding.Precoder(max_instances=16, max_M=1024, max_K=256, precision="tf32x3")
+    pol = binding.JACPCG_BATCH_COST_CLASS if policy == "cost_class" else binding.JACPCG_BATCH_FIFO
+    srv = binding.jacpcg_server_create(prec.ctx, max_batch=16, max_inflight=2, batch_policy=pol)
+    try:
+        tickets = [binding.jacpcg_submit(srv, d) for d in descs]
+        res = [binding.jacpcg_poll(srv, t) for t in tickets]
+        n_done, n_batches, _ = binding.jacpcg_server_stats(srv)
+    finally:
+        binding.jacpcg_server_destroy(srv)
+        prec.close()
+    assert [r[0] for r in res] == alone_status and n_done == len(insts)
+    if policy == "cost_class":
+        assert n_batches >= 3
+    torch.cuda.synchronize()
+    for k in range(len(insts)):
+        assert np.array_equal(Wd[k].T.cpu().numpy().astype(np.complex128), alone[k]), k
+
+
 def test_server_replay_poisson_trace(torch_gpu):
     torch = torch_gpu
     from paper_2305_13925_gb300 import binding
