@@ -88,6 +88,7 @@ enum {
                                         kernel (by default its A P product runs on the tensor
                                         cores for the standard and CG forms) */
 };
+/* Other flag bits are rejected (EINVAL). */
 
 typedef struct {
     int device;              /* CUDA device ordinal */
@@ -162,7 +163,10 @@ jacpcg_status jacpcg_create(const jacpcg_config *cfg, jacpcg_ctx **out);
  * i (host array, read during the call).  Per-instance outputs are device
  * arrays of n_inst entries (any may be NULL): status (jacpcg_status per
  * instance), iters (largest per-column iteration count), resid (largest
- * per-column recurrence residual ||r|| / ||b||), beta (power factor).
+ * per-column recurrence residual ||r|| / ||b||), beta (power factor; 0 when
+ * W = 0, e.g. max_iter = 0 or an all-zero channel, where it is undefined).
+ * n_inst = 0 is an empty batch: nothing is enqueued and JACPCG_OK returned
+ * (inst may then be NULL).
  * The call waits, on the host, until the previous precode call of this
  * context has finished reading its staging memory; it does not wait for
  * the GPU work it enqueues.  Calls on one context must use one stream (or

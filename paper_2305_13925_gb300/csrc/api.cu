@@ -691,6 +691,7 @@ jacpcg_status jacpcg_create(const jacpcg_config *cfg, jacpcg_ctx **out) {
         return JACPCG_EINVAL;
     if (cfg->precision != JACPCG_FP32 && cfg->precision != JACPCG_TF32X3) return JACPCG_EINVAL;
     if (cfg->variant < JACPCG_STANDARD || cfg->variant > JACPCG_CG) return JACPCG_EINVAL;
+    if (cfg->flags & ~(JACPCG_FLAG_PROFILE | JACPCG_FLAG_SIMT_ITERATION)) return JACPCG_EINVAL;
     if (cfg->refine_sweeps < 0 || cfg->refine_sweeps > 3) return JACPCG_EINVAL;
     if (cfg->refine_residual != JACPCG_RESID_DOT2 && cfg->refine_residual != JACPCG_RESID_FP64)
         return JACPCG_EINVAL;
@@ -771,6 +772,7 @@ jacpcg_status jacpcg_plan_destroy(jacpcg_plan *plan) {
 jacpcg_status jacpcg_precode(jacpcg_ctx *ctx, const jacpcg_instance *inst, int n_inst,
                              int32_t *status_dev, int32_t *iters_dev, float *resid_dev,
                              float *beta_dev, void *stream) {
+    if (ctx && !ctx->broken && n_inst == 0) return JACPCG_OK;   // an empty batch
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     jacpcg_plan *pl = nullptr;
     jacpcg_status st =

@@ -324,3 +324,35 @@ def test_every_launch_shape_bit_identical_and_autotune():
     prec.close()
     for k in range(len(Hs)):
         assert np.array_equal(tuned["W"][k], base["W"][k])
+
+
+def test_empty_batch_is_a_no_op():
+    """n_inst = 0: JACPCG_OK, nothing enqueued (the output arrays keep their
+    contents); the context stays usable."""
+    import torch
+    from paper_2305_13925_gb300 import binding
+    prec = binding.Precoder(max_instances=4, max_M=64, max_K=8)
+    try:
+        st = torch.full((4,), 77, dtype=torch.int32, device="cuda")
+        prec.precode([], st)
+        torch.cuda.synchronize()
+        assert (st == 77).all()
+    finally:
+        prec.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tf32x3"])
+def test_zero_iterations(precision):
+    """T = 0 (the degenerate schedule): X stays 0, so W = H X is exactly zero,
+    iters 0, status OK, and beta (undefined for W = 0) is reported as 0;
+    K = 64 (tensor classes) and K = 17 (SIMT) in one batch."""
+    H1, x1 = C.generate_batch("batched_1024x64", 1, 3)
+    spec = C.ChannelSpec(M=256, S=4, K=17, r=(0.5, 0.5), n_vis=(2, 3), snr_db=(10.0,))
+    i2 = C.generate_instance(spec, 3, 17)
+    out = run([H1[0], i2.H], [x1[0], i2.xi], T=0, precision=precision)
+    for k in range(2):
+        assert not np.any(out["W"][k]), k
+        assert out["status"][k] == 0 and out["iters"][k] == 0 and out["beta"][k] == 0.0
+        ref = O.precode(C.round_complex64([H1[0], i2.H][k]), [x1[0], i2.xi][k], "standard", max_iter=0)
+        assert not np.any(ref["W"])
+
