@@ -52,7 +52,7 @@ def parse_args():
     ap.add_argument("--iters", type=int, default=6)
     ap.add_argument("--variant", default="standard", choices=["standard", "alg1", "cg"])
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3"])
-    ap.add_argument("--mode", default="precode", choices=["precode", "plan", "graph"])
+    ap.add_argument("--mode", default="graph", choices=["precode", "plan", "graph"])
     ap.add_argument("--simt-iteration", action="store_true")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=10)
@@ -77,6 +77,9 @@ def workload_config(args, n):
                      f"K={spec.K}, complex64, T={args.iters} fixed, {args.variant} Jac-PCG, B=I_K"),
         "instances_per_gpu": n, "M": spec.M, "K": spec.K, "T": args.iters,
         "variant": args.variant, "precision": args.precision, "mode": args.mode,
+        "mode_is": {"graph": "jacpcg_plan_execute of a prepared plan replayed as one CUDA graph per step",
+                    "plan": "jacpcg_plan_execute of a prepared plan (tables resident) per step",
+                    "precode": "one jacpcg_precode call per step (table upload included)"}[args.mode],
         "iteration": ("simt" if getattr(args, "simt_iteration", False) or args.precision != "tf32x3"
                       else "tensor (K=64 class)"),
         "l2": "inputs larger than L2 (H is 1.07 GB per step), no flush needed",
@@ -831,13 +834,31 @@ def main():
         ev[k + 1].record(stream)
     torch.cuda.synchronize()
     barrier()
-    clocks = sampler.stop()
     total_ms = ev[0].elapsed_time(ev[-1])
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     launches = binding.jacpcg_launch_count(prec.ctx) - l0
     phase_ms, n_exec, per_exec = (None, 0, 0)
+    kernel_timing = "the timed steps themselves (per-phase CUDA events on the launching stream)"
     if plan is None or args.mode == "plan":
         phase_ms, n_exec, per_exec = binding.jacpcg_profile_read(prec.ctx)
+    else:
+        # graph replays carry no per-phase events: time the same four kernels
+        # through a profiled plan of the same batch, right after, in this run
+        kplan = prec.plan(arr, status, iters, resid, beta, use_graph=False)
+        nk = min(args.steps, 200)
+        for _ in range(3):
+            binding.jacpcg_plan_execute(kplan, s_handle)
+        torch.cuda.synchronize()
+        binding.jacpcg_profile_read(prec.ctx)
+        for _ in range(nk):
+            binding.jacpcg_plan_execute(kplan, s_handle)
+        torch.cuda.synchronize()
+        phase_ms, n_exec, per_exec = binding.jacpcg_profile_read(prec.ctx)
+        binding.jacpcg_plan_destroy(kplan)
+        kernel_timing = (f"{nk} executes of a profiled (non-graph) plan of the same batch right after the "
+                         "timed graph replays, per-phase CUDA events on the launching stream; the graph "
+                         "replays the same four kernels")
+    clocks = sampler.stop()
     t_max = reduce_max(total_ms, dist, "cuda")
     value = job_throughput(n, world, args.steps, t_max)
     st = status.cpu().numpy()
@@ -880,6 +901,7 @@ def main():
                                       "peak_source": "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs, burst)",
                                       "tensor": tensor})
         roofline = dict(per_phase[dom])
+        roofline["kernel_timing"] = kernel_timing
         roofline["all_phases"] = per_phase
 
     # end to end through the C ABI with host buffers, chunked and overlapped
