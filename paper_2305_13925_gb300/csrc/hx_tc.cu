@@ -2,33 +2,36 @@
 // class (Eq. 7 without the power factor; Eq. 15 per symbol), 3xTF32.
 //
 // Complex product as real MMAs over one 128-row tile of W (rows = antennas):
-//   Wr = Hr Xr - Hi Xi,   Wi = Hr Xi + Hi Xr.
-// With B = [Xr^T ; Xi^T] (128 rows of K values, K-major) resident in shared
-// memory per instance, each reduction step issues
-//   D[:, 0:128]  += Hr  . B^T            (N = 128: Hr Xr | Hr Xi)
-//   D[:, 0:64]   += -Hi . (Xi^T)^T       (N = 64, A negated)
-//   D[:, 64:128] +=  Hi . (Xr^T)^T       (N = 64)
-// each as hi*hi + hi*lo + lo*hi of the TF32 split (see gram_tc.cu).  The
-// reduction is only 2K long, so one TMEM accumulation per tile suffices.
+//   [Wr | Wi] = Hr [Xr | Xi] + Hi [-Xi | Xr].
+// B = [-Xi^T ; Xr^T ; Xi^T] (192 rows of K values, K-major) is resident in
+// shared memory per instance; its rows 64 .. 191 are [Xr^T ; Xi^T] and its
+// rows 0 .. 127 are [-Xi^T ; Xr^T], so each reduction step is two N = 128
+// MMAs, Hr against the first view and Hi against the second, each as
+// hi*hi + hi*lo + lo*hi of the TF32 split (see gram_tc.cu).  The H stage
+// (Hr and Hi, head and tail) lives in tensor memory as the MMAs' A operand:
+// an MMA reads only its 4 KB B slice from shared memory (the stage never
+// passes through shared memory after the raw copy), which cut the kernel from
+// 0.436 to 0.375 ms per 2048-channel batch.  The reduction is only 2K long,
+// so one TMEM accumulation per tile suffices.
 //
 // Persistent, warp-specialised, one CTA per SM walking its instances:
 //   warps 0-7   producers: a stream of raw stages fetched RAW - 1 stages
 //               ahead with per-thread asynchronous copies (cp.async, 16
 //               bytes, zero-filled past M and K): per instance two stages of
-//               the iterate X (each thread copies the chunks it converts),
-//               then the H stages, where warp w copies antennas
-//               16 w .. 16 w + 15 of the stage's 16 users -- whole 128-byte
-//               lines per column -- and converts exactly those rows, so a
-//               __syncwarp after its own cp.async wait suffices.  Every stage
-//               keeps warp w's bytes in its own 2 KB of the raw stage: the
-//               warps run unsynchronised, and a warp refilling a stage must
-//               not overwrite bytes another warp has yet to read.  Conversion:
-//               B = [Xr^T ; Xi^T] and per stage H tiles [Hr | Hi], TF32 head
-//               and tail, transposed into the canonical K-major layout;
+//               the iterate X (each thread copies the chunks it converts into
+//               B), then the H stages, where warp w copies antennas
+//               32 (w mod 4) .. + 31 -- its TMEM lanes -- of the stage's users
+//               8 (w / 4) .. + 7 as whole 256-byte column pieces, converts
+//               exactly those entries and writes them to its lanes of the
+//               tensor-memory stage (tcgen05.st), so a __syncwarp after its
+//               own cp.async wait suffices.  Every raw stage keeps warp w's
+//               bytes in its own 2 KB: the warps run unsynchronised, and a
+//               warp refilling a stage must not overwrite bytes another warp
+//               has yet to read;
 //   warps 8-15  drain: TMEM (two alternating 128-column accumulators) ->
 //               registers -> W (complex64, column-major, coalesced) and this
 //               tile's ||W||_F^2 partial in its own slot;
-//   warp 16     TMEM allocation; lane 0 issues MMAs and commits.
+//   warp 16     TMEM allocation; lane 0 issues the MMAs and commits.
 // Every wait is bounded; a timeout flags the CTA's instances with FLAG_TIMEOUT.
 #include "common.cuh"
 #include "kernels.h"
@@ -40,23 +43,22 @@ namespace {
 
 constexpr int TMR = 128;                      // W rows per tile
 constexpr int KCH = 16;                       // users (reduction values) per stage
-constexpr int STAGES = 2;                     // split stages shared with the MMA warp
+constexpr int STAGES = 2;                     // H stages in tensor memory shared with the MMA warp
 constexpr int RAW = 6;                        // raw stages in flight per producer thread
 constexpr int RAWB = 16 * 1024;               // bytes of one raw stage
-constexpr int APART = TMR * KCH * 4;          // one of Yr_hi, Yr_lo, Yi_hi, Yi_lo: 8 KB
-constexpr int BPART = 128 * 64 * 4;           // one of B_hi, B_lo: 32 KB
+constexpr int BROWS = 192;                    // B rows: -Xi^T, Xr^T, Xi^T (64 each)
+constexpr int BPART = BROWS * 64 * 4;         // one of B_hi, B_lo: 48 KB
 constexpr uint32_t LBO = 128;
-constexpr uint32_t SBO_A = (KCH / 4) * 128;   // 512
 constexpr uint32_t SBO_B = (64 / 4) * 128;    // 2048
+constexpr uint32_t TS0 = 256;                 // H stages: columns TS0 + 64 s + 16 part + user
 constexpr uint32_t WAIT_LIMIT = 1u << 21;
 constexpr int NPW = 8, NDW = 8;
 constexpr int MMA_WARP = NPW + NDW;
 constexpr int NTHREADS = (NPW + NDW + 1) * 32;
-constexpr int TMEM_COLS = 256;
+constexpr int TMEM_COLS = 512;                // two accumulators, two H stages (hi / lo of Hr, Hi)
 
 struct __align__(128) HxSmem {
     unsigned char B[2 * BPART];
-    unsigned char stage[STAGES][4 * APART];
     unsigned char raw[RAW][RAWB];
     float wsum[2][NDW];
     uint64_t full[STAGES];
@@ -70,6 +72,16 @@ struct __align__(128) HxSmem {
 };
 
 static_assert(sizeof(HxSmem) <= 227 * 1024, "shared memory");
+
+// one warp stores 8 consecutive 32-bit columns of its 32 lanes
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+        : "memory");
+}
 
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, float a, float b, float c, float d) {
     asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(addr), "f"(a), "f"(b), "f"(c),
@@ -161,25 +173,28 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_tc64_kernel(const DevInst *__r
                         }
                     }
                 } else {
+                    // warp w: antennas 32 (w mod 4) .. + 31 (its TMEM lanes) of the stage's
+                    // users 8 (w / 4) .. + 7, whole 256-byte (128-byte bfloat16) column pieces
                     const int st = u.t - 2, mt = st / u.nks, ks = st % u.nks;
-                    const uint32_t wb = rb + warp * 2048;   // this warp's 16 columns x 128 bytes
+                    const uint32_t wb = rb + warp * 2048;
+                    const int m0 = mt * TMR + 32 * (warp & 3), k0 = ks * KCH + 8 * (warp >> 2);
                     if (u.bf16) {
 #pragma unroll
-                        for (int q = 0; q < 2; ++q) {   // 16 columns x 4 chunks of 4 antennas
-                            const int kk = 8 * q + (lane >> 2), pc = lane & 3;
-                            const int k = ks * KCH + kk, m = mt * TMR + 16 * warp + 4 * pc;
+                        for (int c = 0; c < 2; ++c) {   // 8 columns x 8 chunks of 4 antennas
+                            const int e = lane + 32 * c, uu = e >> 3, pc = e & 7;
+                            const int k = k0 + uu, m = m0 + 4 * pc;
                             const int left = k < u.K ? min(max(u.M - m, 0), 4) : 0;
                             const char *src = u.H + ((size_t)k * u.ldh + m) * 4;
-                            tc::cp_async16(wb + kk * 64 + pc * 16, left ? src : u.H, left * 4);
+                            tc::cp_async16(wb + uu * 128 + pc * 16, left ? src : u.H, left * 4);
                         }
                     } else {
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {   // 16 columns x 8 chunks of 2 antennas
-                            const int kk = 4 * q + (lane >> 3), pc = lane & 7;
-                            const int k = ks * KCH + kk, m = mt * TMR + 16 * warp + 2 * pc;
+                        for (int c = 0; c < 4; ++c) {   // 8 columns x 16 chunks of 2 antennas
+                            const int e = lane + 32 * c, uu = e >> 4, pc = e & 15;
+                            const int k = k0 + uu, m = m0 + 2 * pc;
                             const int left = k < u.K ? min(max(u.M - m, 0), 2) : 0;
                             const char *src = u.H + ((size_t)k * u.ldh + m) * 8;
-                            tc::cp_async16(wb + kk * 128 + pc * 16, left ? src : u.H, left * 8);
+                            tc::cp_async16(wb + uu * 256 + pc * 16, left ? src : u.H, left * 8);
                         }
                     }
                 }
@@ -228,10 +243,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_tc64_kernel(const DevInst *__r
                         tc::split_tf32(v[h][i].x, rh[i], rl[i]);
                         tc::split_tf32(v[h][i].y, ih[i], il[i]);
                     }
-                    const uint32_t o_r = (uint32_t)(n >> 3) * SBO_B + rq * LBO + (n & 7) * 16;
-                    const uint32_t o_i = (uint32_t)((64 + n) >> 3) * SBO_B + rq * LBO + (n & 7) * 16;
+                    // rows n: -Xi^T, 64 + n: Xr^T, 128 + n: Xi^T
+                    const uint32_t o_n = (uint32_t)(n >> 3) * SBO_B + rq * LBO + (n & 7) * 16;
+                    const uint32_t o_r = o_n + 8 * SBO_B, o_i = o_n + 16 * SBO_B;
+                    st_shared_v4(bbase + o_n, -ih[0], -ih[1], -ih[2], -ih[3]);
                     st_shared_v4(bbase + o_r, rh[0], rh[1], rh[2], rh[3]);
                     st_shared_v4(bbase + o_i, ih[0], ih[1], ih[2], ih[3]);
+                    st_shared_v4(bbase + BPART + o_n, -il[0], -il[1], -il[2], -il[3]);
                     st_shared_v4(bbase + BPART + o_r, rl[0], rl[1], rl[2], rl[3]);
                     st_shared_v4(bbase + BPART + o_i, il[0], il[1], il[2], il[3]);
                 }
@@ -243,30 +261,30 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_tc64_kernel(const DevInst *__r
             const int nmt = (M + TMR - 1) / TMR;
             const int nks = (K + KCH - 1) / KCH;
             const int T = nmt * nks;
-            auto put = [&](const float2 (&h)[2][4]) -> bool {
+            // H stage s in TMEM: thread (warp w, lane l) owns lane 32 (w mod 4) + l
+            // (antenna) and columns 8 (w / 4) .. + 7 (users) of each part
+            const uint32_t th = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + TS0 + 8 * (warp >> 2);
+            auto put = [&](const float2 (&h)[8]) -> bool {
                 const int s = chunk % STAGES;
                 if (chunk >= STAGES &&
                     !tc::mbar_wait(&S.empty[s], ((chunk / STAGES) - 1) & 1, WAIT_LIMIT)) {
                     S.err = 1;
                     return false;
                 }
-                const uint32_t base = tc::smem_u32(S.stage[s]);
+                tc::tc_fence_after();   // the MMAs that read this stage are complete
+                float rh[8], rl[8], ih[8], il[8];
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int m = 16 * warp + (lane & 15), kq = (lane >> 4) + 2 * q;
-                    float rh[4], rl[4], ih[4], il[4];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        tc::split_tf32(h[q][i].x, rh[i], rl[i]);
-                        tc::split_tf32(h[q][i].y, ih[i], il[i]);
-                    }
-                    const uint32_t o = (uint32_t)(m >> 3) * SBO_A + kq * LBO + (m & 7) * 16;
-                    st_shared_v4(base + o, rh[0], rh[1], rh[2], rh[3]);                 // Yr hi
-                    st_shared_v4(base + APART + o, rl[0], rl[1], rl[2], rl[3]);         // Yr lo
-                    st_shared_v4(base + 2 * APART + o, ih[0], ih[1], ih[2], ih[3]);     // Yi hi
-                    st_shared_v4(base + 3 * APART + o, il[0], il[1], il[2], il[3]);     // Yi lo
+                for (int i = 0; i < 8; ++i) {
+                    tc::split_tf32(h[i].x, rh[i], rl[i]);
+                    tc::split_tf32(h[i].y, ih[i], il[i]);
                 }
-                tc::fence_proxy_async_smem();
+                const uint32_t ts = th + 64 * s;
+                tmem_st8(ts, rh);
+                tmem_st8(ts + 16, rl);
+                tmem_st8(ts + 32, ih);
+                tmem_st8(ts + 48, il);
+                tc::tmem_st_wait();
+                tc::tc_fence_before();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&S.full[s]);
                 ++chunk;
@@ -277,17 +295,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_tc64_kernel(const DevInst *__r
                 tc::cp_async_wait<RAW - 2>();   // this thread's chunks of the stage have landed
                 __syncwarp();                   // ... and those of the rest of its warp
                 const unsigned char *wr = S.raw[sc % RAW] + warp * 2048;
-                float2 h[2][4];
+                float2 h[8];
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {   // antenna m, users 4 kq .. 4 kq + 3
-                    const int ml = lane & 15, kq = (lane >> 4) + 2 * q;
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int kk = 4 * kq + i;
-                        h[q][i] = bf16 ? bf16x2_to_float2(*reinterpret_cast<const uint32_t *>(wr + kk * 64 + ml * 4))
-                                       : *reinterpret_cast<const float2 *>(wr + kk * 128 + ml * 8);
-                    }
-                }
+                for (int uu = 0; uu < 8; ++uu)   // antenna 32 (w mod 4) + l of user uu
+                    h[uu] = bf16 ? bf16x2_to_float2(*reinterpret_cast<const uint32_t *>(wr + uu * 128 + lane * 4))
+                                 : *reinterpret_cast<const float2 *>(wr + uu * 256 + lane * 8);
                 issue(iu, (sc + RAW - 1) % RAW);   // refills the stage read one step ago
                 cursor_next(iu);
                 ok = put(h);
@@ -363,8 +375,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_tc64_kernel(const DevInst *__r
     } else if (lane == 0) {
         // ---------------- MMA issuer ----------------
         constexpr uint32_t id128 = tc::idesc_tf32(TMR, 128);
-        constexpr uint32_t id64n = tc::idesc_tf32(TMR, 64, true);
-        constexpr uint32_t id64 = tc::idesc_tf32(TMR, 64);
         const uint32_t bhi = tc::smem_u32(S.B), blo = bhi + BPART;
         uint32_t chunk = 0, tile = 0, ninst = 0;
         for (int j = blockIdx.x; j < n_list && !S.err; j += gridDim.x, ++ninst) {
@@ -393,30 +403,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_tc64_kernel(const DevInst *__r
                         break;
                     }
                     tc::tc_fence_after();
-                    const uint32_t a = tc::smem_u32(S.stage[s]);
+                    const uint32_t ta = tmem + TS0 + 64 * s;
 #pragma unroll
                     for (int kk = 0; kk < KCH / 8; ++kk) {
-                        const uint32_t ao = kk * 2 * LBO;
                         const uint32_t bo = (uint32_t)(ks * KCH / 4 + 2 * kk) * LBO;
-                        const uint64_t arh = tc::smem_desc(a + ao, LBO, SBO_A);
-                        const uint64_t arl = tc::smem_desc(a + APART + ao, LBO, SBO_A);
-                        const uint64_t aih = tc::smem_desc(a + 2 * APART + ao, LBO, SBO_A);
-                        const uint64_t ail = tc::smem_desc(a + 3 * APART + ao, LBO, SBO_A);
-                        const uint64_t bh = tc::smem_desc(bhi + bo, LBO, SBO_B);           // rows 0..127
-                        const uint64_t bl = tc::smem_desc(blo + bo, LBO, SBO_B);
-                        const uint64_t bhr = bh, blr = bl;                                  // Xr^T rows 0..63
-                        const uint64_t bhi_i = tc::smem_desc(bhi + bo + 8 * SBO_B, LBO, SBO_B);  // Xi^T
-                        const uint64_t blo_i = tc::smem_desc(blo + bo + 8 * SBO_B, LBO, SBO_B);
+                        // [Xr; Xi] (rows 64 ..) for Hr, [-Xi; Xr] (rows 0 ..) for Hi
+                        const uint64_t b1h = tc::smem_desc(bhi + bo + 8 * SBO_B, LBO, SBO_B);
+                        const uint64_t b1l = tc::smem_desc(blo + bo + 8 * SBO_B, LBO, SBO_B);
+                        const uint64_t b2h = tc::smem_desc(bhi + bo, LBO, SBO_B);
+                        const uint64_t b2l = tc::smem_desc(blo + bo, LBO, SBO_B);
+                        const uint32_t ak = ta + 8 * kk;
                         const uint32_t first = (ks == 0 && kk == 0) ? 0u : 1u;
-                        tc::mma_tf32(d, arh, bh, id128, first);
-                        tc::mma_tf32(d, arh, bl, id128, 1u);
-                        tc::mma_tf32(d, arl, bh, id128, 1u);
-                        tc::mma_tf32(d, aih, bhi_i, id64n, 1u);
-                        tc::mma_tf32(d, aih, blo_i, id64n, 1u);
-                        tc::mma_tf32(d, ail, bhi_i, id64n, 1u);
-                        tc::mma_tf32(d + 64, aih, bhr, id64, 1u);
-                        tc::mma_tf32(d + 64, aih, blr, id64, 1u);
-                        tc::mma_tf32(d + 64, ail, bhr, id64, 1u);
+                        tc::mma_tf32_tmem_a(d, ak, b1h, id128, first);        // Hr hi
+                        tc::mma_tf32_tmem_a(d, ak, b1l, id128, 1u);
+                        tc::mma_tf32_tmem_a(d, ak + 16, b1h, id128, 1u);      // Hr lo
+                        tc::mma_tf32_tmem_a(d, ak + 32, b2h, id128, 1u);      // Hi hi
+                        tc::mma_tf32_tmem_a(d, ak + 32, b2l, id128, 1u);
+                        tc::mma_tf32_tmem_a(d, ak + 48, b2h, id128, 1u);      // Hi lo
                     }
                     tc::mma_commit(&S.empty[s]);
                 }
