@@ -7,10 +7,13 @@
 // 128 x 128 real matrix whose 2 x 2 blocks are [[Ar, -Ai], [Ai, Ar]] (real
 // row 2i + s is part s of complex row i), P into the 128 x 64 real matrix
 // with rows 2k + t, so Q_real = A_real P_real has Re q_i in row 2i and Im q_i
-// in row 2i + 1.  3xTF32 as in gram_tc.cu; the head*head product is
-// accumulated in two TMEM buffers (one per half of the reduction) and the
-// correction products in a third, so no truncating accumulation chain is
-// longer than 16 MMAs.  The expanded A (head and tail) lives in tensor
+// in row 2i + 1.  3xTF32 as in gram_tc.cu: per k-step the A head multiplies
+// [P head | P tail] in one N = 128 MMA (the tail tile follows the head tile in
+// shared memory, so the two form one 128-row B operand; TMEM columns 0-63
+// take head*head, 64-127 head*tail), and the A tail multiplies the P head in
+// an N = 64 MMA into columns 128-191 -- 32 MMAs per iteration instead of 48
+// (0.277 vs 0.315 ms per 2048-channel batch), no truncating accumulation
+// chain longer than 16 MMAs.  The expanded A (head and tail) lives in tensor
 // memory and is the MMAs' A operand there: per iteration the MMAs read only
 // the 1 KB P tiles from shared memory instead of re-reading a 4 KB A tile for
 // every MMA.  The next instance's A is prefetched (cp.async) into a shared
@@ -20,11 +23,12 @@
 // may form NG groups, each a team of warps with its own MMAs (N = 64 / NG),
 // TMEM buffers, mbarrier and named barrier; with two teams the tensor core
 // multiplies one team's P while the other updates its vectors, but every
-// team issues the full 48 MMAs per iteration.  With A in tensor memory one
-// team of 8 warps (N = 64) measures faster on GB300 (0.31 vs 0.34 ms per
-// 2048-channel batch), so NG = 1.  Per iteration a team
+// team issues its own full set of MMAs per iteration.  With A in tensor
+// memory one team of 8 warps (N = 64) measures faster on GB300 (0.31 vs 0.34
+// ms per 2048-channel batch), and only one team lets the head products fuse
+// into one N = 128 MMA, so NG = 1.  Per iteration the team
 //   1. writes P (TF32 head and tail) into the MMA's K-major layout and votes
-//      on continuing (barrier reduction); its first thread issues 48 MMAs;
+//      on continuing (barrier reduction); its first thread issues 32 MMAs;
 //   2. copies Q from TMEM (warp w reads TMEM lanes 32 (w mod 4) ..) into a
 //      padded shared-memory tile, then a team barrier;
 //   3. works column-wise: thread (warp w, lane l) owns column 8 w + (l mod 8)
@@ -56,9 +60,9 @@ constexpr int NW = 8;                       // warps: two teams of four
 constexpr int NTHREADS = NW * 32;
 constexpr int TEAM = NTHREADS / NG;
 constexpr int PARTS = (NW / NG) / 4;        // warps of a team per TMEM lane quarter
-constexpr int TEAM_COLS = NG == 1 ? 256 : 128;   // TMEM columns per team: head k<64, head k>=64, corrections
+constexpr int TEAM_COLS = NG == 1 ? 256 : 128;   // TMEM columns per team: head*head, head*tail, tail*head
 constexpr int RPT = KCP / 4;                // complex rows per thread
-constexpr int TMEM_COLS = 512;              // team t: [128 t, 128 t + 96): head k<64, head k>=64, corrections;
+constexpr int TMEM_COLS = 512;              // [0, 192): head*head, head*tail, tail*head;
                                             // [256, 384): A head, [384, 512): A tail (128 lanes x 128 K)
 constexpr uint32_t TA_HI = 256, TA_LO = 384;
 constexpr uint32_t WAIT_LIMIT = 1u << 21;
@@ -274,18 +278,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
             if (issuer) {
                 tc::tc_fence_after();
                 constexpr uint32_t idesc = tc::idesc_tf32(RR, GC);
+                constexpr uint32_t idesc2 = tc::idesc_tf32(RR, 2 * GC);
+                static_assert(NG == 1 && BPART == (GC / 8) * (int)SBO, "P tail tile directly after the head tile");
                 const uint32_t bh0 = b_hi + (uint32_t)team * (GC / 8) * SBO;
-                const uint32_t bl0 = b_lo + (uint32_t)team * (GC / 8) * SBO;
 #pragma unroll 4
                 for (int kk = 0; kk < RR / 8; ++kk) {
                     const uint32_t off = (uint32_t)(2 * kk) * LBO;
                     const uint32_t ah = tmem + TA_HI + 8 * kk, al = tmem + TA_LO + 8 * kk;
                     const uint64_t bh = tc::smem_desc(bh0 + off, LBO, SBO);
-                    const uint64_t bl = tc::smem_desc(bl0 + off, LBO, SBO);
-                    const uint32_t d1 = tq + (kk < RR / 16 ? 0u : (uint32_t)GC);
-                    tc::mma_tf32_tmem_a(d1, ah, bh, idesc, (kk % (RR / 16)) ? 1u : 0u);
-                    tc::mma_tf32_tmem_a(tq + 2u * GC, ah, bl, idesc, kk ? 1u : 0u);
-                    tc::mma_tf32_tmem_a(tq + 2u * GC, al, bh, idesc, 1u);
+                    // head x [P head | P tail] as one N = 128 MMA (the tail tile follows the head)
+                    tc::mma_tf32_tmem_a(tq, ah, bh, idesc2, kk ? 1u : 0u);
+                    tc::mma_tf32_tmem_a(tq + 2u * GC, al, bh, idesc, kk ? 1u : 0u);
                 }
                 tc::mma_commit(&S.qfull[team]);
             }
