@@ -5,13 +5,16 @@
 // resident in shared memory as in hx_tc.cu, so every stage brings the 16
 // users' slice of X's group-b columns along with the 128 x 16 tile of H.
 //
-// Complex product as real MMAs over one 128-row tile of W, per stage with
-// B = [Xr^T ; Xi^T] of the stage's 16 users (128 rows, K-major):
-//   D[:, 0:128]  += Hr  . B^T            (N = 128: Hr Xr | Hr Xi)
-//   D[:, 0:64]   += -Hi . (Xi^T)^T       (N = 64, A negated)
-//   D[:, 64:128] +=  Hi . (Xr^T)^T       (N = 64)
-// each as hi*hi + hi*lo + lo*hi of the TF32 split (Ootomo and Yokota,
-// IJHPCA 2022).  The tensor core's FP32 accumulation truncates, and a tile
+// Complex product as real MMAs over one 128-row tile of W, as in hx_tc.cu:
+//   [Wr | Wi] = Hr [Xr | Xi] + Hi [-Xi | Xr],
+// per stage with B = [-Xi^T ; Xr^T ; Xi^T] of the stage's 16 users (192 rows,
+// K-major) in shared memory -- rows 64 .. 191 are [Xr^T ; Xi^T], rows 0 .. 127
+// [-Xi^T ; Xr^T] -- and the H stage (Hr, Hi, TF32 head and tail) in tensor
+// memory as the MMAs' A operand: two N = 128 MMAs per k-step and split
+// product (hi*hi + hi*lo + lo*hi; Ootomo and Yokota, IJHPCA 2022), each
+// reading only its B slice from shared memory (2.67 vs 3.16 ms for the
+// 256-channel M = 4096, K = 256 batch with the H tile split into shared
+// memory).  The tensor core's FP32 accumulation truncates, and a tile
 // reduces over up to 32 stages, so the chain is cut as in gram_tc.cu: every G
 // stages the MMAs switch between two TMEM buffers and the drain warps add
 // the finished group into FP32 registers (no chain longer than the K = 64
@@ -21,11 +24,12 @@
 //   warps 0-7   producers: raw stages fetched RAW - 1 ahead with per-thread
 //               asynchronous copies (cp.async, 16 bytes, zero-filled past M,
 //               K and the instance's columns); warp w copies antennas
-//               16 w .. 16 w + 15 of the stage's 16 users (whole 128-byte
-//               column lines) and columns 8 w .. 8 w + 7 of the X slice (whole
-//               128-byte column pieces, chunks XOR-swizzled), converts exactly
-//               what it copied (a __syncwarp after its own cp.async wait) into
-//               the TF32 head and tail of [Hr | Hi] and of B;
+//               32 (w mod 4) .. + 31 (its TMEM lanes) of the stage's users
+//               8 (w / 4) .. + 7 (whole 256-byte column pieces) and columns
+//               8 w .. 8 w + 7 of the X slice (whole 128-byte column pieces,
+//               chunks XOR-swizzled), converts exactly what it copied (a
+//               __syncwarp after its own cp.async wait): H into its TMEM
+//               lanes (tcgen05.st), X into B;
 //   warps 8-15  drain: TMEM (two alternating 128-column accumulators, one
 //               per group) -> FP32 registers summed over the tile's groups ->
 //               W (complex64, column-major, coalesced) and the tile's
@@ -42,20 +46,20 @@ namespace {
 
 constexpr int TMR = 128;                      // W rows per tile
 constexpr int KCH = 16;                       // users (reduction values) per stage
-constexpr int STAGES = 2;                     // split stages shared with the MMA warp
-constexpr int RAW = 5;                        // raw stages in flight per producer thread
+constexpr int STAGES = 2;                     // stages shared with the MMA warp
+constexpr int RAW = 7;                        // raw stages in flight per producer thread
 constexpr int RAWH = 16 * 1024;               // H part of a raw stage (warp w: 2 KB)
 constexpr int RAWB = RAWH + 8 * 1024;         // + X slice (warp w: 1 KB)
-constexpr int APART = TMR * KCH * 4;          // one of Yr_hi, Yr_lo, Yi_hi, Yi_lo: 8 KB
-constexpr int XPART = 128 * KCH * 4;          // one of B_hi, B_lo: 8 KB
-constexpr int SPLIT = 4 * APART + 2 * XPART;  // one split stage: 48 KB
+constexpr int XPART = 192 * KCH * 4;          // one of B_hi, B_lo: rows -Xi^T, Xr^T, Xi^T, 12 KB
+constexpr int SPLIT = 2 * XPART;              // one B stage: 24 KB
 constexpr uint32_t LBO = 128;
-constexpr uint32_t SBO = (KCH / 4) * 128;     // 512, both operands
+constexpr uint32_t SBO = (KCH / 4) * 128;     // 512
+constexpr uint32_t TS0 = 256;                 // H stages in TMEM: columns TS0 + 64 s + 16 part + user
 constexpr uint32_t WAIT_LIMIT = 1u << 21;
 constexpr int NPW = 8, NDW = 8;
 constexpr int MMA_WARP = NPW + NDW;
 constexpr int NTHREADS = (NPW + NDW + 1) * 32;
-constexpr int TMEM_COLS = 256;
+constexpr int TMEM_COLS = 512;                // two accumulators, two H stages
 constexpr int G = 4;                          // stages per accumulation group
 
 struct __align__(128) HxwSmem {
@@ -71,6 +75,16 @@ struct __align__(128) HxwSmem {
     volatile int err;
 };
 static_assert(sizeof(HxwSmem) <= 227 * 1024, "shared memory");
+
+// one warp stores 8 consecutive 32-bit columns of its 32 lanes
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+        : "memory");
+}
 
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, float a, float b, float c, float d) {
     asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(addr), "f"(a), "f"(b), "f"(c),
@@ -145,24 +159,27 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_tc_wide_kernel(const DevInst *
             if (u.j < n_list) {
                 const uint32_t rb = raw0 + rs * RAWB;
                 const int mt = u.t / u.nks, ks = u.t % u.nks;
-                const uint32_t wb = rb + warp * 2048;   // this warp's 16 users x 16 antennas of H
+                // warp w: antennas 32 (w mod 4) .. + 31 (its TMEM lanes) of the stage's
+                // users 8 (w / 4) .. + 7, whole 256-byte (128-byte bfloat16) column pieces
+                const uint32_t wb = rb + warp * 2048;
+                const int m0 = mt * TMR + 32 * (warp & 3), k0 = ks * KCH + 8 * (warp >> 2);
                 if (u.bf16) {
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) {   // 16 columns x 4 chunks of 4 antennas
-                        const int kk = 8 * q + (lane >> 2), pc = lane & 3;
-                        const int k = ks * KCH + kk, m = mt * TMR + 16 * warp + 4 * pc;
+                    for (int c = 0; c < 2; ++c) {   // 8 columns x 8 chunks of 4 antennas
+                        const int e = lane + 32 * c, uu = e >> 3, pc = e & 7;
+                        const int k = k0 + uu, m = m0 + 4 * pc;
                         const int left = k < u.K ? min(max(u.M - m, 0), 4) : 0;
                         const char *src = u.H + ((size_t)k * u.ldh + m) * 4;
-                        tc::cp_async16(wb + kk * 64 + pc * 16, left ? src : u.H, left * 4);
+                        tc::cp_async16(wb + uu * 128 + pc * 16, left ? src : u.H, left * 4);
                     }
                 } else {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {   // 16 columns x 8 chunks of 2 antennas
-                        const int kk = 4 * q + (lane >> 3), pc = lane & 7;
-                        const int k = ks * KCH + kk, m = mt * TMR + 16 * warp + 2 * pc;
+                    for (int c = 0; c < 4; ++c) {   // 8 columns x 16 chunks of 2 antennas
+                        const int e = lane + 32 * c, uu = e >> 4, pc = e & 15;
+                        const int k = k0 + uu, m = m0 + 2 * pc;
                         const int left = k < u.K ? min(max(u.M - m, 0), 2) : 0;
                         const char *src = u.H + ((size_t)k * u.ldh + m) * 8;
-                        tc::cp_async16(wb + kk * 128 + pc * 16, left ? src : u.H, left * 8);
+                        tc::cp_async16(wb + uu * 256 + pc * 16, left ? src : u.H, left * 8);
                     }
                 }
                 // X slice: users ks*16 .. +15 of columns col0 + 8 w + cj, 8 chunks of 2 users
@@ -196,17 +213,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_tc_wide_kernel(const DevInst *
                 __syncwarp();                   // ... and those of the rest of its warp
                 const unsigned char *wr = S.raw[sc % RAW] + warp * 2048;
                 const unsigned char *xr = S.raw[sc % RAW] + RAWH + warp * 1024;
-                float2 h[2][4];
+                float2 h[8];   // antenna 32 (w mod 4) + lane of users 8 (w / 4) + uu
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {   // antenna m, users 4 kq .. 4 kq + 3
-                    const int ml = lane & 15, kq = (lane >> 4) + 2 * q;
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int kk = 4 * kq + i;
-                        h[q][i] = bf16 ? bf16x2_to_float2(*reinterpret_cast<const uint32_t *>(wr + kk * 64 + ml * 4))
-                                       : *reinterpret_cast<const float2 *>(wr + kk * 128 + ml * 8);
-                    }
-                }
+                for (int uu = 0; uu < 8; ++uu)
+                    h[uu] = bf16 ? bf16x2_to_float2(*reinterpret_cast<const uint32_t *>(wr + uu * 128 + lane * 4))
+                                 : *reinterpret_cast<const float2 *>(wr + uu * 256 + lane * 8);
                 float4 xv[2];   // column 8 w + cj, users 4 kq .. 4 kq + 3
                 {
                     const int cj = lane & 7, kq = lane >> 3;
@@ -215,7 +226,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_tc_wide_kernel(const DevInst *
                 }
                 issue(iu, (sc + RAW - 1) % RAW);   // refills the stage read one step ago
                 cursor_next(iu);
-                // put: the TF32 head and tail of both operands into the split stage
+                // put: H (head and tail) into this warp's TMEM lanes, B into the shared stage
                 const int s = chunk % STAGES;
                 if (chunk >= STAGES &&
                     !tc::mbar_wait(&S.empty[s], ((chunk / STAGES) - 1) & 1, WAIT_LIMIT)) {
@@ -223,23 +234,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_tc_wide_kernel(const DevInst *
                     ok = false;
                     break;
                 }
-                const uint32_t base = tc::smem_u32(S.stage[s]);
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int m = 16 * warp + (lane & 15), kq = (lane >> 4) + 2 * q;
-                    float rh[4], rl[4], ih[4], il[4];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        tc::split_tf32(h[q][i].x, rh[i], rl[i]);
-                        tc::split_tf32(h[q][i].y, ih[i], il[i]);
-                    }
-                    const uint32_t o = (uint32_t)(m >> 3) * SBO + kq * LBO + (m & 7) * 16;
-                    st_shared_v4(base + o, rh[0], rh[1], rh[2], rh[3]);                 // Yr hi
-                    st_shared_v4(base + APART + o, rl[0], rl[1], rl[2], rl[3]);         // Yr lo
-                    st_shared_v4(base + 2 * APART + o, ih[0], ih[1], ih[2], ih[3]);     // Yi hi
-                    st_shared_v4(base + 3 * APART + o, il[0], il[1], il[2], il[3]);     // Yi lo
-                }
+                tc::tc_fence_after();   // the MMAs that read this stage are complete
                 {
+                    float rh[8], rl[8], ih[8], il[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        tc::split_tf32(h[i].x, rh[i], rl[i]);
+                        tc::split_tf32(h[i].y, ih[i], il[i]);
+                    }
+                    const uint32_t ts = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + TS0 + 64 * s + 8 * (warp >> 2);
+                    tmem_st8(ts, rh);
+                    tmem_st8(ts + 16, rl);
+                    tmem_st8(ts + 32, ih);
+                    tmem_st8(ts + 48, il);
+                }
+                const uint32_t base = tc::smem_u32(S.stage[s]);
+                {
+                    // B rows n: -Xi^T, 64 + n: Xr^T, 128 + n: Xi^T
                     const int n = 8 * warp + (lane & 7), kq = lane >> 3;
                     const float re[4] = {xv[0].x, xv[0].z, xv[1].x, xv[1].z};
                     const float im[4] = {xv[0].y, xv[0].w, xv[1].y, xv[1].w};
@@ -249,15 +260,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_tc_wide_kernel(const DevInst *
                         tc::split_tf32(re[i], rh[i], rl[i]);
                         tc::split_tf32(im[i], ih[i], il[i]);
                     }
-                    const uint32_t xbase = base + 4 * APART;
-                    const uint32_t o_r = (uint32_t)(n >> 3) * SBO + kq * LBO + (n & 7) * 16;
-                    const uint32_t o_i = (uint32_t)((64 + n) >> 3) * SBO + kq * LBO + (n & 7) * 16;
-                    st_shared_v4(xbase + o_r, rh[0], rh[1], rh[2], rh[3]);             // Xr^T hi
-                    st_shared_v4(xbase + o_i, ih[0], ih[1], ih[2], ih[3]);             // Xi^T hi
-                    st_shared_v4(xbase + XPART + o_r, rl[0], rl[1], rl[2], rl[3]);     // Xr^T lo
-                    st_shared_v4(xbase + XPART + o_i, il[0], il[1], il[2], il[3]);     // Xi^T lo
+                    const uint32_t o_n = (uint32_t)(n >> 3) * SBO + kq * LBO + (n & 7) * 16;
+                    const uint32_t o_r = o_n + 8 * SBO, o_i = o_n + 16 * SBO;
+                    st_shared_v4(base + o_n, -ih[0], -ih[1], -ih[2], -ih[3]);
+                    st_shared_v4(base + o_r, rh[0], rh[1], rh[2], rh[3]);
+                    st_shared_v4(base + o_i, ih[0], ih[1], ih[2], ih[3]);
+                    st_shared_v4(base + XPART + o_n, -il[0], -il[1], -il[2], -il[3]);
+                    st_shared_v4(base + XPART + o_r, rl[0], rl[1], rl[2], rl[3]);
+                    st_shared_v4(base + XPART + o_i, il[0], il[1], il[2], il[3]);
                 }
+                tc::tmem_st_wait();
                 tc::fence_proxy_async_smem();
+                tc::tc_fence_before();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&S.full[s]);
                 ++chunk;
@@ -342,8 +356,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_tc_wide_kernel(const DevInst *
     } else if (lane == 0) {
         // ---------------- MMA issuer ----------------
         constexpr uint32_t id128 = tc::idesc_tf32(TMR, 128);
-        constexpr uint32_t id64n = tc::idesc_tf32(TMR, 64, true);
-        constexpr uint32_t id64 = tc::idesc_tf32(TMR, 64);
         uint32_t chunk = 0, grp = 0;
         for (int j = blockIdx.x; j < n_list && !S.err; j += gridDim.x) {
             const DevInst &in = insts[list[j].x];
@@ -366,30 +378,24 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_tc_wide_kernel(const DevInst *
                         break;
                     }
                     tc::tc_fence_after();
-                    const uint32_t a = tc::smem_u32(S.stage[s]);
-                    const uint32_t xh = a + 4 * APART, xl = xh + XPART;
+                    const uint32_t xh = tc::smem_u32(S.stage[s]), xl = xh + XPART;
+                    const uint32_t ta = tmem + TS0 + 64 * s;
 #pragma unroll
                     for (int kk = 0; kk < KCH / 8; ++kk) {
                         const uint32_t off = kk * 2 * LBO;
-                        const uint64_t arh = tc::smem_desc(a + off, LBO, SBO);
-                        const uint64_t arl = tc::smem_desc(a + APART + off, LBO, SBO);
-                        const uint64_t aih = tc::smem_desc(a + 2 * APART + off, LBO, SBO);
-                        const uint64_t ail = tc::smem_desc(a + 3 * APART + off, LBO, SBO);
-                        const uint64_t bh = tc::smem_desc(xh + off, LBO, SBO);                // rows 0..127
-                        const uint64_t bl = tc::smem_desc(xl + off, LBO, SBO);
-                        const uint64_t bhr = bh, blr = bl;                                     // Xr^T rows 0..63
-                        const uint64_t bhi_i = tc::smem_desc(xh + off + 8 * SBO, LBO, SBO);   // Xi^T
-                        const uint64_t blo_i = tc::smem_desc(xl + off + 8 * SBO, LBO, SBO);
+                        // [Xr; Xi] (rows 64 ..) for Hr, [-Xi; Xr] (rows 0 ..) for Hi
+                        const uint64_t b1h = tc::smem_desc(xh + off + 8 * SBO, LBO, SBO);
+                        const uint64_t b1l = tc::smem_desc(xl + off + 8 * SBO, LBO, SBO);
+                        const uint64_t b2h = tc::smem_desc(xh + off, LBO, SBO);
+                        const uint64_t b2l = tc::smem_desc(xl + off, LBO, SBO);
+                        const uint32_t ak = ta + 8 * kk;
                         const uint32_t first = (ks % G == 0 && kk == 0) ? 0u : 1u;
-                        tc::mma_tf32(d, arh, bh, id128, first);
-                        tc::mma_tf32(d, arh, bl, id128, 1u);
-                        tc::mma_tf32(d, arl, bh, id128, 1u);
-                        tc::mma_tf32(d, aih, bhi_i, id64n, 1u);
-                        tc::mma_tf32(d, aih, blo_i, id64n, 1u);
-                        tc::mma_tf32(d, ail, bhi_i, id64n, 1u);
-                        tc::mma_tf32(d + 64, aih, bhr, id64, 1u);
-                        tc::mma_tf32(d + 64, aih, blr, id64, 1u);
-                        tc::mma_tf32(d + 64, ail, bhr, id64, 1u);
+                        tc::mma_tf32_tmem_a(d, ak, b1h, id128, first);        // Hr hi
+                        tc::mma_tf32_tmem_a(d, ak, b1l, id128, 1u);
+                        tc::mma_tf32_tmem_a(d, ak + 16, b1h, id128, 1u);      // Hr lo
+                        tc::mma_tf32_tmem_a(d, ak + 32, b2h, id128, 1u);      // Hi hi
+                        tc::mma_tf32_tmem_a(d, ak + 32, b2l, id128, 1u);
+                        tc::mma_tf32_tmem_a(d, ak + 48, b2h, id128, 1u);      // Hi lo
                     }
                     tc::mma_commit(&S.empty[s]);
                     if (ks % G == G - 1 || ks == nks - 1) {
