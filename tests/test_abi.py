@@ -53,25 +53,32 @@ def test_null_arguments_rejected_without_gpu(lib):
 
 
 def test_struct_layout_matches_c(tmp_path):
+    """Every field offset and every size of the structs the binding mirrors
+    (config, instance, server config, block) equals the C header's."""
+    structs = [("jacpcg_config", binding.jacpcg_config), ("jacpcg_instance", binding.jacpcg_instance),
+               ("jacpcg_server_config", binding.jacpcg_server_config), ("jacpcg_block", binding.jacpcg_block)]
+    lines, want = [], []
+    for cname, py in structs:
+        lines.append(f'  printf("%zu\\n", sizeof({cname}));')
+        want.append(ctypes.sizeof(py))
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({cname}, {fname}));')
+            want.append(getattr(py, fname).offset)
     src = tmp_path / "layout.c"
+    body = "\n".join(lines)
     src.write_text(f"""
 #include <stdio.h>
 #include <stddef.h>
 #include "{HEADER}"
 int main(void) {{
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(jacpcg_config),
-         offsetof(jacpcg_config, arena_bytes), offsetof(jacpcg_config, flags), sizeof(jacpcg_instance),
-         offsetof(jacpcg_instance, W), offsetof(jacpcg_instance, tol), offsetof(jacpcg_instance, B),
-         offsetof(jacpcg_instance, ldb), offsetof(jacpcg_instance, n_rhs), offsetof(jacpcg_instance, X0));
+{body}
   return 0;
 }}
 """)
     exe = tmp_path / "layout"
     subprocess.check_call(["gcc", "-std=c99", "-o", str(exe), str(src)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
-    C, I = binding.jacpcg_config, binding.jacpcg_instance
-    assert got == [ctypes.sizeof(C), C.arena_bytes.offset, C.flags.offset, ctypes.sizeof(I),
-                   I.W.offset, I.tol.offset, I.B.offset, I.ldb.offset, I.n_rhs.offset, I.X0.offset]
+    assert got == want
 
 
 def test_blocks_helper_points_into_the_full_channel():
