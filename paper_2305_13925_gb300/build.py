@@ -62,7 +62,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> pathlib.Path:
     if force or not LIB.exists() or any(o.stat().st_mtime > LIB.stat().st_mtime for o in objs):
         tmp = LIB.with_suffix(f".{os.getpid()}.tmp")
         subprocess.check_call([nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", str(tmp),
-                               *map(str, objs)])
+                               *map(str, objs), "-ldl"])   # -ldl: NVTX loads its tool library
         os.replace(tmp, LIB)
     return LIB
 

@@ -3,6 +3,7 @@
 // CUDA-graph capture and the launch sequence Gram -> iteration -> W = H X
 // -> finalise for every K class of a (possibly ragged) batch.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -417,6 +418,16 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
 
 constexpr size_t MAX_PROFILED = 4096;
 
+// NVTX range around the host-side enqueue of one phase: Nsight tools show the
+// phases by name and attribute their kernels; without a tool attached each
+// push / pop is a no-op.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_launched) {
     jacpcg_ctx *ctx = pl->ctx;
     int nl = 0;
@@ -433,7 +444,9 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
     if (pl->acc_reset_bytes) {   // several Gram jobs per instance report into shared accumulators
         CK(cudaMemsetAsync(pl->acc.flags, 0, pl->acc_reset_bytes, s));
     }
+    static const char *const kPhase[3] = {"jacpcg: Gram", "jacpcg: iteration", "jacpcg: W = H X"};
     for (int phase = 0; phase < 3; ++phase) {
+        const NvtxRange range(kPhase[phase]);
         for (const Launch &l : pl->launches) {
             if (l.phase != phase) continue;
             cudaError_t e = cudaSuccess;
@@ -473,6 +486,7 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
         }
         if (phase == 1 && pl->refine_sweeps > 0) {
             // iterative refinement: R = I - A X (FP64), A dX = R (FP32 iteration), X += dX
+            const NvtxRange refine_range("jacpcg: refinement");
             const int2 *rb = reinterpret_cast<const int2 *>(pl->dev + pl->res_off);
             for (int sw = 0; sw <= pl->refine_sweeps; ++sw) {
                 if (launch_residual(pl->d_insts, rb, pl->n_res, sw, s,
@@ -501,6 +515,7 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
         if (ev) CK(cudaEventRecord(ev[phase + 1], s));
     }
     {
+        const NvtxRange range("jacpcg: finalize");
         const cudaError_t e = launch_finalize(pl->d_insts, pl->n_inst, pl->acc, pl->out, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e);
     }

@@ -356,3 +356,67 @@ def test_zero_iterations(precision):
         ref = O.precode(C.round_complex64([H1[0], i2.H][k]), [x1[0], i2.xi][k], "standard", max_iter=0)
         assert not np.any(ref["W"])
 
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tf32x3"])
+def test_output_guards_untouched(precision):
+    """Canary padding: W (ldw > M), X and A sit inside buffers filled with a
+    sentinel; after the call every byte outside the outputs' M x K (K x K)
+    regions -- guards before and after, rows M .. ldw - 1 of each W column --
+    still holds the sentinel, and the outputs match the oracle.  K = 17
+    (SIMT), 64 and 100 (tensor classes), M = 300 (not a tile multiple)."""
+    import torch
+    from paper_2305_13925_gb300 import binding
+    from gpu_util import to_dev
+    sent = complex(1234.5, -6789.25)
+    G = 64                                          # guard entries (512 bytes) on each side
+    M = 300
+    cases = []
+    for K, seed in ((17, 31), (64, 32), (100, 33)):
+        spec = C.ChannelSpec(M=M, S=4, K=K, r=(0.5, 0.5), n_vis=(2, 3), snr_db=(10.0,))
+        inst = C.generate_instance(spec, seed, K)
+        ldw = M + 6
+        Wb = torch.full((2 * G + K * ldw,), sent, dtype=torch.complex64, device="cuda")
+        Xb = torch.full((2 * G + K * K,), sent, dtype=torch.complex64, device="cuda")
+        Ab = torch.full((2 * G + K * K,), sent, dtype=torch.complex64, device="cuda")
+        W = Wb[G:G + K * ldw].view(K, ldw)[:, :M]
+        X = Xb[G:G + K * K].view(K, K)
+        A = Ab[G:G + K * K].view(K, K)
+        cases.append((inst, to_dev(inst.H, torch), W, X, A, Wb, Xb, Ab, ldw))
+    prec = binding.Precoder(max_instances=3, max_M=M, max_K=100, precision=precision)
+    try:
+        descs = [binding.instance(c[1], c[2], c[0].xi, 6, X=c[3], A=c[4]) for c in cases]
+        st = torch.full((3,), -1, dtype=torch.int32, device="cuda")
+        prec.precode(descs, st)
+        torch.cuda.synchronize()
+    finally:
+        prec.close()
+    assert (st == 0).all()
+    for inst, _, W, X, A, Wb, Xb, Ab, ldw in cases:
+        K = inst.H.shape[1]
+        wb = Wb.cpu().numpy()
+        assert np.all(wb[:G] == sent) and np.all(wb[G + K * ldw:] == sent)
+        assert np.all(wb[G:G + K * ldw].reshape(K, ldw)[:, M:] == sent)
+        for b, n in ((Xb.cpu().numpy(), K * K), (Ab.cpu().numpy(), K * K)):
+            assert np.all(b[:G] == sent) and np.all(b[G + n:] == sent)
+        ref = O.precode(C.round_complex64(inst.H), inst.xi, "standard", max_iter=6)
+        assert rel_fro(W.T.cpu().numpy().astype(np.complex128), ref["W"]) <= 1e-5, K
+
+
+@pytest.mark.parametrize("K", [17, 64])
+def test_extreme_column_norms(K):
+    """User channels scaled by amplitudes from 1e-3 to 1e3 (a dynamic range of
+    1e12 on the diagonal of A): the Jacobi scaling keeps the iteration
+    well-posed and W matches the oracle at fixed T within 1e-5 on both
+    precisions."""
+    spec = C.ChannelSpec(M=512, S=4, K=K, r=(0.5, 0.5), n_vis=(2, 3), snr_db=(10.0,))
+    inst = C.generate_instance(spec, 41, K)
+    scale = 10.0 ** np.linspace(-3.0, 3.0, K)
+    H = (inst.H * scale[None, :]).astype(np.complex64).astype(np.complex128)
+    xi = inst.xi * 1e-6
+    ref = O.precode(H, xi, "standard", max_iter=6)
+    for precision in ("fp32", "tf32x3"):
+        out = run([H], [xi], T=6, precision=precision)
+        assert out["status"][0] == 0
+        e = rel_fro(out["W"][0], ref["W"])
+        assert e <= 1e-5, (precision, e)
