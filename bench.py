@@ -248,6 +248,16 @@ def cpu_baseline_leg(Hst, xi, T, variant, seconds, Wd=None):
     out = {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
            "sample": f"first {n} of the {len(H)} channels of this step, FP64 plain C, {cores} threads, "
                      f"{dt:.1f} s"}
+    # the same oracle on one host thread, over a quarter of the time
+    t0 = time.perf_counter()
+    O.precode_batch(list(H[:1]), xi[:1], variant, max_iter=T, nthreads=1)
+    rate1 = 1.0 / max(time.perf_counter() - t0, 1e-6)
+    n1 = int(min(len(H), max(1, rate1 * seconds / 4)))
+    t0 = time.perf_counter()
+    O.precode_batch(list(H[:n1]), xi[:n1], variant, max_iter=T, nthreads=1)
+    dt1 = time.perf_counter() - t0
+    out["one_core"] = {"value": n1 / dt1, "unit": UNIT, "cores": 1,
+                       "sample": f"first {n1} channels of this step, 1 thread, {dt1:.1f} s"}
     acc = None
     if Wd is not None:
         W_gpu = Wd[:n].cpu().numpy()
