@@ -141,6 +141,7 @@ struct jacpcg_ctx {
     int last_launches = 0;
     std::vector<jacpcg_plan *> plans;
     int pcg_shape_idx[6] = {0, 0, 0, 0, 0, 0};   // chosen iteration shape per K class
+    CUtensorMap amap{};   // the arena as rows of 64 floats, for the tiled copies of A
 };
 
 struct jacpcg_plan {
@@ -478,7 +479,7 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
                     break;
                 case Launch::PCG_TC:
                     e = launch_pcg_tc64(ctx->cfg.variant, pl->d_insts, static_cast<const int *>(list), l.count,
-                                        pl->acc, s, 0);
+                                        pl->acc, &ctx->amap, ctx->arena.base, s, 0);
                     break;
             }
             if (e != cudaSuccess) return cuda_fail(ctx, e);
@@ -504,7 +505,7 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
                     else if (l.kind == Launch::PCG_TC)
                         e = launch_pcg_tc64(ctx->cfg.variant, pl->d_insts,
                                             reinterpret_cast<const int *>(pl->dev + l.list_off), l.count,
-                                            pl->acc, s, 1);
+                                            pl->acc, &ctx->amap, ctx->arena.base, s, 1);
                     else
                         continue;
                     if (e != cudaSuccess) return cuda_fail(ctx, e);
@@ -641,6 +642,33 @@ jacpcg_status execute(jacpcg_plan *pl, cudaStream_t s) {
     return JACPCG_OK;
 }
 
+// The arena as a 2-D FP32 tensor: one row of 64 floats per 256-byte allocation
+// unit, so every workspace block (A of a K = 64 instance: 128 rows) starts at a
+// row.  The tensor-core iteration stages A with one tiled TMA copy of a 64 x 128
+// box.  The encoder is the driver's, reached through the runtime.
+bool encode_arena_map(jacpcg_ctx *ctx) {
+    static_assert(ALIGN == 256, "arena rows are 256 bytes");
+    using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    const cuuint64_t dims[2] = {64, ctx->arena.size / ALIGN};
+    const cuuint64_t strides[1] = {ALIGN};
+    const cuuint32_t box[2] = {64, 128};
+    const cuuint32_t elem[2] = {1, 1};
+    return reinterpret_cast<Encode>(fn)(&ctx->amap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ctx->arena.base, dims,
+                                        strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -738,7 +766,8 @@ jacpcg_status jacpcg_create(const jacpcg_config *cfg, jacpcg_ctx **out) {
     ctx->arena.size = bytes;
     ctx->arena.free_.emplace(0, bytes);
     bool ok = cudaEventCreateWithFlags(&ctx->staging_ev, cudaEventDisableTiming) == cudaSuccess &&
-              cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) == cudaSuccess;
+              cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) == cudaSuccess &&
+              encode_arena_map(ctx);
     if (!ok) {
         (void)cudaGetLastError();
         jacpcg_destroy(ctx);

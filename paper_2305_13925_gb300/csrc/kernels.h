@@ -1,6 +1,7 @@
 // kernels.h -- host-side launch wrappers for the device kernels (internal).
 #pragma once
 
+#include <cuda.h>   // CUtensorMap
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -54,9 +55,11 @@ cudaError_t launch_hx_tc64(const DevInst *insts, const int *list, int n, DevAccu
 // list: (instance, 64-column output group) jobs
 cudaError_t launch_hx_tc_wide(const DevInst *insts, const int2 *list, int n, DevAccum acc,
                               cudaStream_t s);
-// tensor-core iteration for the K = 64 class (standard or plain CG); list: instance ids
+// tensor-core iteration for the K = 64 class (standard or plain CG); list: instance ids;
+// amap: 2-D FP32 tensor map over the arena holding every instance's A (rows of 64
+// floats, box 64 x 128), arena: its base address
 cudaError_t launch_pcg_tc64(int variant, const DevInst *insts, const int *list, int n, DevAccum acc,
-                            cudaStream_t s, int mode);
+                            const CUtensorMap *amap, const char *arena, cudaStream_t s, int mode);
 // blocks: (instance, first column); mode 0: A X = I, mode 1: A dX = R, X += dX
 cudaError_t launch_pcg(int KC, int variant, const DevInst *insts, const int2 *blocks,
                        int n_blocks, DevAccum acc, cudaStream_t s, int mode = 0);

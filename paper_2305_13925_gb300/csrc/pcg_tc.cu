@@ -16,8 +16,11 @@
 // chain longer than 16 MMAs.  The expanded A (head and tail) lives in tensor
 // memory and is the MMAs' A operand there: per iteration the MMAs read only
 // the 1 KB P tiles from shared memory instead of re-reading a 4 KB A tile for
-// every MMA.  The next instance's A is prefetched (cp.async) into a shared
-// staging tile while the current one iterates.
+// every MMA.  The next instance's A is prefetched into a shared staging tile
+// while the current one iterates: one tiled TMA copy (cp.async.bulk.tensor)
+// through a tensor map over the library's workspace arena, whose rows of 256
+// bytes hold A (64 x 64 complex, ld 64) at a row boundary, completion counted
+// in bytes on an mbarrier.
 //
 // The columns of P are independent systems that share A, so the 64 columns
 // may form NG groups, each a team of warps with its own MMAs (N = 64 / NG),
@@ -73,8 +76,10 @@ struct __align__(128) PcgSmem {
     float Q[RR * QLD];
     uint64_t qfull[NG];
     uint64_t fin[NG];
+    uint64_t abar;                          // the staging tile's copy has landed
     uint32_t tmem;
     volatile int err;                       // a bounded wait ran out (sticky)
+    volatile int aerr;                      // ... the wait for a staging copy (no further copies)
 };
 static_assert(sizeof(PcgSmem) <= 227 * 1024, "shared memory");
 
@@ -125,7 +130,9 @@ __device__ __forceinline__ float col_total(float v) {
 template <int VAR, int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__restrict__ insts,
                                                                const int *__restrict__ list, int n_list,
-                                                               DevAccum acc_out) {
+                                                               DevAccum acc_out,
+                                                               const __grid_constant__ CUtensorMap amap,
+                                                               const char *arena) {
     constexpr int mode = MODE;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     PcgSmem &S = *reinterpret_cast<PcgSmem *>(smem_raw);
@@ -139,7 +146,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
             tc::mbar_init(&S.qfull[t], 1);
             tc::mbar_init(&S.fin[t], 1);
         }
+        tc::mbar_init(&S.abar, 1);
         S.err = 0;
+        S.aerr = 0;
         tc::mbar_init_fence();
     }
     if (warp == 0) {
@@ -152,17 +161,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
     const uint32_t tmem = S.tmem;
     const uint32_t b_hi = tc::smem_u32(S.B), b_lo = b_hi + BPART;
     const uint32_t ast = tc::smem_u32(S.Ast);
-    // A of the instance at list position jj -> staging tile (8 chunks of 16 B per thread)
+    // A of the instance at list position jj -> staging tile: the 128 arena rows
+    // from A's row on, one tiled copy issued by thread 0 (A lies 256-byte aligned
+    // in the arena, so its row index is exact and the copy starts at x = 0)
     auto prefetch_a = [&](int jj) {
-        if (jj < n_list) {
+        if (threadIdx.x == 0 && jj < n_list && !S.aerr) {
             const char *src = reinterpret_cast<const char *>(insts[list[jj]].A);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int e = threadIdx.x + NTHREADS * u;
-                tc::cp_async16(ast + e * 16, src + (size_t)e * 16, 16);
-            }
+            tc::fence_proxy_async_smem();   // the staging tile's earlier reads come first
+            tc::mbar_arrive_expect_tx(&S.abar, (uint32_t)sizeof(S.Ast));
+            tc::tma_load_2d(ast, &amap, 0, (int)((src - arena) / 256), &S.abar);
         }
-        tc::cp_async_commit();
     };
     prefetch_a(blockIdx.x);
     const uint32_t q_base = tc::smem_u32(S.Q);
@@ -174,7 +182,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
     const int j = 8 * warp + jl;
     // byte offset of (column j, row g) in P_hi / P_lo; row g + 4 k adds 2 k core matrices
     const uint32_t p_off = (uint32_t)warp * SBO + (uint32_t)(g >> 1) * LBO + jl * 16 + (g & 1) * 8;
-    uint32_t phase = 0;
+    uint32_t phase = 0, aphase = 0;
+    uint32_t a_lost = ~0u;   // parity of a staging copy whose wait ran out
     int err = 0;
 
     for (int jj = blockIdx.x; jj < n_list; jj += gridDim.x) {
@@ -186,8 +195,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
         const float tol2 = tl > 0.f ? tl * tl : -1.f;
 
         // ---- A in the real 2 x 2-block layout, TF32 head and tail, into TMEM ----
-        tc::cp_async_wait_all();
-        __syncthreads();   // staging tile complete; both teams are done with the previous instance
+        // staging tile complete (every thread observes the copy; the vote makes a
+        // timeout uniform); both teams are done with the previous instance
+        const bool a_skip = S.aerr;   // set before an earlier barrier: uniform
+        const bool a_ok = !a_skip && tc::mbar_wait(&S.abar, aphase & 1, WAIT_LIMIT);
+        if (__syncthreads_or(!a_ok)) {
+            if (!a_skip) a_lost = aphase;   // this copy may still land
+            err = 1;
+            S.err = 1;
+            S.aerr = 1;
+        }
+        ++aphase;
         if constexpr (MODE == 1) {
             if (in.rctl[1] != 0.f) {   // the instance stopped refining (uniform)
                 prefetch_a(jj + gridDim.x);
@@ -404,7 +422,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
         }
     }
 
-    tc::cp_async_wait_all();   // the last (empty or unused) prefetch group
+    // every copy issued was waited for, except one whose wait ran out
+    if (threadIdx.x == 0 && a_lost != ~0u) tc::mbar_wait(&S.abar, a_lost & 1, WAIT_LIMIT);
     if (issuer) {
         tc::mma_commit(&S.fin[team]);
         tc::mbar_wait(&S.fin[team], 0, WAIT_LIMIT);
@@ -420,7 +439,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
 }  // namespace
 
 cudaError_t launch_pcg_tc64(int variant, const DevInst *insts, const int *list, int n, DevAccum acc,
-                            cudaStream_t s, int mode) {
+                            const CUtensorMap *amap, const char *arena, cudaStream_t s, int mode) {
     if (n <= 0) return cudaSuccess;
     const size_t smem = sizeof(PcgSmem);
     int dev = 0, sms = 0;
@@ -431,7 +450,7 @@ cudaError_t launch_pcg_tc64(int variant, const DevInst *insts, const int *list, 
     auto go = [&](auto kern) -> cudaError_t {
         cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (r != cudaSuccess) return r;
-        kern<<<grid, NTHREADS, smem, s>>>(insts, list, n, acc);
+        kern<<<grid, NTHREADS, smem, s>>>(insts, list, n, acc, *amap, arena);
         return cudaGetLastError();
     };
     if (variant == 2) return mode ? go(pcg_tc64_kernel<2, 1>) : go(pcg_tc64_kernel<2, 0>);   // plain CG

@@ -56,14 +56,17 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                  : "memory");
 }
 
-// ---- bulk asynchronous copies (the TMA unit) ---------------------------------
-// global -> shared, `bytes` a multiple of 16, both addresses 16-byte aligned;
-// completion is signalled as transaction bytes on the mbarrier
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+// ---- tiled tensor copies (the TMA unit) --------------------------------------
+// the box at element coordinates (x, y) of a 2-D tensor map -> shared memory at
+// dst (16-byte aligned); x times the element size must be a multiple of 16
+// bytes.  Completion is signalled as transaction bytes on the mbarrier.  tmap
+// is the generic address of a tensor map in kernel parameter (__grid_constant__)
+// or global memory.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *tmap, int x, int y, uint64_t *bar) {
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(dst),
+        "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
 }
 
