@@ -153,8 +153,10 @@ typedef struct jacpcg_ctx jacpcg_ctx;
 typedef struct jacpcg_plan jacpcg_plan;
 
 /* Create a context on cfg->device: validates the limits, reserves the
- * device workspace arena and pinned staging memory.  *out receives the
- * context.  Errors: EINVAL (bad limits), ENOMEM, ECUDA. */
+ * device workspace arena and pinned staging memory, and encodes the arena's
+ * tensor map (rows of 256 bytes, for the iteration's tiled copies).  *out
+ * receives the context.  Errors: EINVAL (bad limits), ENOMEM (arena), ECUDA
+ * (events, streams, or the driver's tensor-map encoder unavailable). */
 jacpcg_status jacpcg_create(const jacpcg_config *cfg, jacpcg_ctx **out);
 
 /* Precode n_inst independent channels in one batched launch sequence on
