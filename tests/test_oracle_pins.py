@@ -250,6 +250,60 @@ def test_alg1_converges_when_preconditioned_operator_is_mild():
     assert np.linalg.norm(X - Xs) / np.linalg.norm(Xs) < 1e-9
 
 
+def _gfrac(pair):
+    from fractions import Fraction
+    return complex(float(Fraction(pair[0])), float(Fraction(pair[1])))
+
+
+def test_alg1_hand_worked_complex_step_k2():
+    """Algorithm 1 on a 2 x 2 system with unequal diagonal, where C^{-1} P is
+    not Hermitian and alpha is complex: the first two iterates equal the values
+    derived by hand from the printed steps (tests/golden/alg1_k2_worked.json).
+    Catches a conjugated or transposed step denominator, a step taken on
+    r instead of m, a missing D^{-1} in the residual update, a wrong b."""
+    g = json.loads((GOLDEN / "alg1_k2_worked.json").read_text())
+    P = np.array([[_gfrac(e) for e in row] for row in g["P"]])
+    s = np.array([_gfrac(e) for e in g["s"]]).reshape(2, 1)
+    for T, key in ((1, "w1"), (2, "w2")):
+        w, it, rr, st = O.pcg(P, s, "alg1", max_iter=T)
+        want = np.array([_gfrac(e) for e in g[key]])
+        assert st == O.OK and it[0] == T
+        assert np.abs(w[:, 0] - want).max() <= 1e-15, (key, w[:, 0], want)
+        # the recurrence residual D r equals s - P w (last printed r)
+        r_want = np.array([_gfrac(e) for e in g["r" + key[1]]])
+        d = np.real(np.diag(P))
+        assert abs(rr[0] - np.linalg.norm(d * r_want) / np.linalg.norm(s)) <= 1e-15
+    exact = np.array([_gfrac(e) for e in g["exact_solution"]])
+    assert np.abs(w[:, 0] - exact).max() > 1e-2       # not exact in K steps
+
+
+@pytest.mark.parametrize("seed", [81, 82])
+def test_alg1_direction_orthogonal_to_next_residual(seed):
+    """Algorithm 1's alpha = r^H r / (m^H C^{-1} P m) makes every new scaled
+    residual orthogonal to the direction just taken: m_t^H r_{t+1} = 0 (from
+    m_t^H r_t = r_t^H r_t, which the b-update keeps).  With m_t proportional
+    to w_{t+1} - w_t and D r_{t+1} = s - P w_{t+1}, this reads
+    (w_{t+1} - w_t)^H D^{-1} (s - P w_{t+1}) = 0.  On a random channel with a
+    spread diagonal alpha is complex, so a conjugated denominator fails."""
+    H, A = small_system(K=12, M=40, seed=seed, spread=(0.3, 3.0), xi=0.4)
+    rng = np.random.default_rng(seed)
+    s = (rng.standard_normal(12) + 1j * rng.standard_normal(12)).reshape(12, 1)
+    dinv = 1.0 / np.real(np.diag(A))
+    prev = np.zeros(12, dtype=complex)
+    imag_steps = 0
+    for T in range(1, 6):
+        w = O.pcg(A, s, "alg1", max_iter=T)[0][:, 0]
+        step = w - prev
+        r = dinv * (s[:, 0] - A @ w)
+        assert abs(np.vdot(step, r)) <= 1e-11 * np.linalg.norm(step) * np.linalg.norm(r)
+        # alpha = r^H r / den is complex iff den = m^H D^{-1} P m is, and den has
+        # the phase of step^H D^{-1} P step (step = alpha m)
+        z = np.vdot(step, dinv * (A @ step))
+        imag_steps += abs(z.imag) > 1e-3 * abs(z)
+        prev = w
+    assert imag_steps >= 3
+
+
 def test_column_independence():
     """Each column of X depends only on its own column of B (Eq. 16 per column)."""
     H, A = small_system(K=6, M=20, seed=71)
