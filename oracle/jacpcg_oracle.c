@@ -251,6 +251,98 @@ int orc_pcg(int K, const cplx *A, const cplx *B, int ldb, int nrhs, int variant,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Sec. III-A, the two stationary iterations the paper compares, for P w = s
+ * in the fixed-point form of Eq. 11, w^{t+1} = A_i w^t + b_i (the printed
+ * "w^t = A_i w^t + b_i" read as one step from t to t + 1), with D, L, U the
+ * diagonal, strictly lower and strictly upper parts of P:
+ *   GS:  A_i = -(D + L)^{-1} U, b_i = (D + L)^{-1} s: each sweep forms
+ *        v = s - U w^t and solves (D + L) w^{t+1} = v by forward substitution;
+ *   JOR: A_i = I - omega D^{-1} P, b_i = omega D^{-1} s: each sweep forms
+ *        w^{t+1} = w^t - omega D^{-1} (P w^t) + omega D^{-1} s.
+ * The paper does not give omega; it is an input.  The start is w^0 = x0
+ * (NULL: 0).  Stopping (tol > 0): before each sweep, stop once
+ * ||s - P w|| <= tol ||s|| (these methods carry no recurrence residual, so
+ * the true residual is formed every sweep).  iters = sweeps done; relres =
+ * ||s - P w|| / ||s|| of the returned w.
+ * Pinned by: a hand-worked K = 2 example of both, exactness after one sweep
+ * for diagonal P (omega = 1), one GS sweep against a library triangular
+ * solve, the monotone decrease of GS's P-norm error (P HPD), JOR's
+ * contraction by (kappa - 1) / (kappa + 1) per sweep in the D^{1/2}-weighted
+ * norm at omega = 2 / (lambda_min + lambda_max) of D^{-1} P, and
+ * convergence to P^{-1} s.                                                */
+enum { ORC_JOR = 3, ORC_GS = 4 };
+
+static void stationary_column(int K, const cplx *A, const double *dvec, int method,
+                              double omega, const cplx *s, const cplx *x0, int max_iter,
+                              double tol, cplx *w, int *iters, double *relres, cplx *y,
+                              cplx *v)
+{
+    double snorm = norm2(K, s);
+    for (int i = 0; i < K; ++i)
+        w[i] = x0 ? x0[i] : 0.0;
+    int t = 0;
+    double rn;
+    for (;;) {
+        matvec(K, A, w, y);                           /* P w^t */
+        double acc = 0.0;
+        for (int i = 0; i < K; ++i) {
+            cplx e = s[i] - y[i];
+            acc += creal(e) * creal(e) + cimag(e) * cimag(e);
+        }
+        rn = sqrt(acc);
+        if (t >= max_iter || (tol > 0.0 && rn <= tol * snorm))
+            break;
+        if (method == ORC_JOR) {
+            for (int i = 0; i < K; ++i)
+                w[i] = w[i] - (omega / dvec[i]) * y[i] + (omega / dvec[i]) * s[i];
+        } else {
+            for (int i = 0; i < K; ++i) {             /* v = s - U w^t */
+                cplx acc_u = s[i];
+                for (int j = i + 1; j < K; ++j)
+                    acc_u -= A[i + (size_t)j * K] * w[j];
+                v[i] = acc_u;
+            }
+            for (int i = 0; i < K; ++i) {             /* (D + L) w^{t+1} = v */
+                cplx acc_l = v[i];
+                for (int j = 0; j < i; ++j)
+                    acc_l -= A[i + (size_t)j * K] * w[j];
+                w[i] = acc_l / dvec[i];
+            }
+        }
+        ++t;
+    }
+    *iters = t;
+    *relres = (snorm > 0.0) ? rn / snorm : 0.0;
+}
+
+int orc_stationary(int K, const cplx *A, const cplx *B, int ldb, int nrhs, int method,
+                   double omega, int max_iter, double tol, const cplx *X0, int ldx0, cplx *X,
+                   int ldx, int *iters, double *relres)
+{
+    double *dvec = malloc(sizeof(double) * K);
+    cplx *work = malloc(sizeof(cplx) * (size_t)K * 3);
+    if (!dvec || !work) {
+        free(dvec); free(work);
+        return ORC_NOMEM;
+    }
+    for (int i = 0; i < K; ++i)
+        dvec[i] = creal(A[i + (size_t)i * K]);
+    cplx *b = work, *y = work + K, *v = work + 2 * K;
+    for (int j = 0; j < nrhs; ++j) {
+        for (int i = 0; i < K; ++i)
+            b[i] = B ? B[i + (size_t)j * ldb] : (i == j ? 1.0 : 0.0);
+        int it = 0;
+        double rel = 0.0;
+        stationary_column(K, A, dvec, method, omega, b, X0 ? X0 + (size_t)j * ldx0 : NULL,
+                          max_iter, tol, X + (size_t)j * ldx, &it, &rel, y, v);
+        if (iters) iters[j] = it;
+        if (relres) relres[j] = rel;
+    }
+    free(dvec); free(work);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Eq. 15: the precoded signal is beta H w; for the full precoder W = H X
  * (Eq. 7 without the power factor).  H is M x K (ldh), X is K x N (ldx).  */
 void orc_matmul(int M, int K, int N, const cplx *H, int ldh, const cplx *X, int ldx,

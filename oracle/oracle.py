@@ -26,8 +26,9 @@ HERE = pathlib.Path(__file__).resolve().parent
 SRC = HERE / "jacpcg_oracle.c"
 LIB = HERE / "_build" / "libjacpcg_oracle.so"
 
-STANDARD, ALG1, CG = 0, 1, 2
-VARIANTS = {"standard": STANDARD, "alg1": ALG1, "cg": CG}
+STANDARD, ALG1, CG, JOR, GS = 0, 1, 2, 3, 4
+VARIANTS = {"standard": STANDARD, "alg1": ALG1, "cg": CG, "jor": JOR, "gs": GS}
+STATIONARY = (JOR, GS)
 OK, BREAKDOWN, NOMEM, NOTHPD = 0, 1, 2, 3
 
 _lock = threading.Lock()
@@ -56,6 +57,8 @@ def lib():
             L.orc_gram.restype = None
             L.orc_pcg.argtypes = [I, P, P, I, I, I, I, D, P, I, P, I, P, P]
             L.orc_pcg.restype = I
+            L.orc_stationary.argtypes = [I, P, P, I, I, I, D, I, D, P, I, P, I, P, P]
+            L.orc_stationary.restype = I
             L.orc_matmul.argtypes = [I, I, I, P, I, P, I, P, I]
             L.orc_matmul.restype = None
             L.orc_power_factor.argtypes = [I, I, P, I, D]
@@ -94,11 +97,14 @@ def gram(H: np.ndarray, xi: float) -> np.ndarray:
 
 
 def pcg(A: np.ndarray, B: np.ndarray | None = None, variant="standard", max_iter: int = 8,
-        tol: float = 0.0, X0: np.ndarray | None = None):
+        tol: float = 0.0, X0: np.ndarray | None = None, omega: float = 1.0):
     """Solve A X = B (B = None for the identity) with the chosen iteration,
-    starting from X0 (None: zero) in every column.
+    starting from X0 (None: zero) in every column.  The Krylov forms
+    ("standard", "alg1", "cg") are Sec. III-B's; "jor" and "gs" are the
+    stationary iterations of Sec. III-A (omega: JOR's relaxation factor).
 
-    Returns (X, iters per column, recurrence relative residual per column, status).
+    Returns (X, iters per column, relative residual per column, status): the
+    recurrence residual for the Krylov forms, the true residual for JOR / GS.
     """
     Af = _f(A)
     K = Af.shape[0]
@@ -113,8 +119,14 @@ def pcg(A: np.ndarray, B: np.ndarray | None = None, variant="standard", max_iter
     X = np.zeros((K, nrhs), dtype=np.complex128, order="F")
     it = np.zeros(nrhs, dtype=np.int32)
     rr = np.zeros(nrhs, dtype=np.float64)
-    st = lib().orc_pcg(K, _p(Af), Bp, ldb, nrhs, _variant(variant), int(max_iter), float(tol),
-                       None if X0f is None else _p(X0f), K, _p(X), K, _p(it), _p(rr))
+    v = _variant(variant)
+    x0p = None if X0f is None else _p(X0f)
+    if v in STATIONARY:
+        st = lib().orc_stationary(K, _p(Af), Bp, ldb, nrhs, v, float(omega), int(max_iter),
+                                  float(tol), x0p, K, _p(X), K, _p(it), _p(rr))
+    else:
+        st = lib().orc_pcg(K, _p(Af), Bp, ldb, nrhs, v, int(max_iter), float(tol), x0p, K, _p(X),
+                           K, _p(it), _p(rr))
     return np.ascontiguousarray(X), it, rr, st
 
 
@@ -170,8 +182,15 @@ def sum_se(H: np.ndarray, G: np.ndarray, sigma2: float = 1.0) -> float:
 
 
 def precode(H: np.ndarray, xi: float, variant="standard", max_iter: int = 8, tol: float = 0.0,
-            power: float = 1.0):
-    """Full precoder for one channel: dict with W, X, A, beta, iters, relres, status."""
+            power: float = 1.0, omega: float = 1.0):
+    """Full precoder for one channel: dict with W, X, A, beta, iters, relres, status.
+    JOR and GS (Sec. III-A) take the same steps: Gram, the iteration, W = H X, beta."""
+    if _variant(variant) in STATIONARY:
+        A = gram(H, xi)
+        X, it, rr, st = pcg(A, None, variant, max_iter, tol, omega=omega)
+        W = matmul(H, X)
+        return dict(W=W, A=A, X=X, beta=power_factor(W, power), iters=int(it.max()),
+                    relres=float(rr.max()), status=st)
     Hf = _f(H)
     M, K = Hf.shape
     W = np.zeros((M, K), dtype=np.complex128, order="F")

@@ -507,3 +507,142 @@ def test_block_precoder_paper_structure_blocks_are_independent_rzf():
         Hi = H[r0:r0 + nr, c0:c0 + nc]
         Wd = Hi @ np.linalg.inv(Hi.conj().T @ Hi + 0.2 * np.eye(nc))
         assert np.linalg.norm(G[r0:r0 + nr, c0:c0 + nc] - Wd) <= 1e-9 * np.linalg.norm(Wd)
+
+
+# --------------------------------------------------------------------------
+# Stationary iterations of Sec. III-A: Gauss-Seidel and JOR
+
+def _omega_opt(A):
+    """2 / (lambda_min + lambda_max) of D^{-1} P (its eigenvalues are those of
+    the Hermitian D^{-1/2} P D^{-1/2}); returns (omega, kappa)."""
+    d = np.real(np.diag(A))
+    lam = np.linalg.eigvalsh(A / np.sqrt(np.outer(d, d)))
+    return 2.0 / (lam[0] + lam[-1]), lam[-1] / lam[0]
+
+
+def test_stationary_hand_worked_k2():
+    """GS and JOR (omega = 1 and 1/2) on the 2 x 2 system with unequal
+    diagonal: the first two sweeps equal the values derived by hand from the
+    printed splittings (tests/golden/stationary_k2_worked.json).  Catches GS
+    using old values for the lower part (that is Jacobi), a transposed
+    splitting (U for L), a missing omega or D^{-1}."""
+    g = json.loads((GOLDEN / "stationary_k2_worked.json").read_text())
+    P = np.array([[_gfrac(e) for e in row] for row in g["P"]])
+    s = np.array([_gfrac(e) for e in g["s"]]).reshape(2, 1)
+    from fractions import Fraction
+    cases = [("gs", 1.0, g["gs"])] + [("jor", float(Fraction(c["omega"])), c) for c in g["jor"]]
+    for method, omega, c in cases:
+        for T, key in ((1, "w1"), (2, "w2")):
+            w, it, rr, st = O.pcg(P, s, method, max_iter=T, omega=omega)
+            want = np.array([_gfrac(e) for e in c[key]])
+            assert st == O.OK and it[0] == T
+            assert np.abs(w[:, 0] - want).max() <= 1e-15, (method, omega, key, w[:, 0], want)
+            assert abs(rr[0] - np.linalg.norm(s[:, 0] - P @ want) / np.linalg.norm(s)) <= 1e-14
+
+
+def test_stationary_exact_for_diagonal_P_and_K1():
+    """Diagonal P (orthogonal channels): L = U = 0, so one GS sweep and one JOR
+    sweep with omega = 1 give D^{-1} s, and further sweeps keep it.  K = 1:
+    one sweep gives s / p (GS; JOR with omega = 1), omega s / p for JOR."""
+    H = dft_columns(32, 8) * np.geomspace(0.5, 5.0, 8)[None, :]
+    A = np.diag(np.diag(O.gram(H, 0.2)))
+    exact = np.diag(1.0 / np.diag(A))
+    for m in ("gs", "jor"):
+        X1 = O.pcg(A, None, m, max_iter=1)[0]
+        assert np.abs(X1 - exact).max() <= 1e-15 * np.abs(exact).max()
+        assert np.abs(O.pcg(A, None, m, max_iter=4)[0] - exact).max() <= 1e-15 * np.abs(exact).max()
+    p = np.array([[3.0 + 0j]])
+    s = np.array([[1.5 - 2j]])
+    assert O.pcg(p, s, "gs", max_iter=1)[0][0, 0] == s[0, 0] / 3.0
+    assert abs(O.pcg(p, s, "jor", max_iter=1, omega=0.25)[0][0, 0] - 0.25 * s[0, 0] / 3.0) < 1e-16
+
+
+def test_gs_sweep_is_a_lower_triangular_solve():
+    """One GS sweep from any w^t is the solution of (D + L) w^{t+1} = s - U w^t
+    (scipy's triangular solver as the independent routine)."""
+    sl = pytest.importorskip("scipy.linalg")
+    H, A = small_system(K=9, M=30, seed=91)
+    rng = np.random.default_rng(91)
+    s = rng.standard_normal(9) + 1j * rng.standard_normal(9)
+    w0 = rng.standard_normal(9) + 1j * rng.standard_normal(9)
+    w1 = O.pcg(A, s.reshape(9, 1), "gs", max_iter=1, X0=w0.reshape(9, 1))[0][:, 0]
+    want = sl.solve_triangular(np.tril(A), s - np.triu(A, 1) @ w0, lower=True)
+    assert np.linalg.norm(w1 - want) <= 1e-13 * np.linalg.norm(want)
+
+
+def test_gs_energy_error_decreases_monotonically():
+    """GS updates one coordinate at a time to the minimiser of the quadratic
+    w^H P w - 2 Re(w^H s) along it, so for Hermitian positive definite P the
+    energy-norm error ||w^t - P^{-1} s||_P never grows, and GS converges
+    (theorem for HPD matrices).  A sweep that used the old values of the
+    lower part (Jacobi) breaks the monotone decrease on this system."""
+    H, A = small_system(K=12, M=20, seed=93, spread=(0.3, 3.0), xi=0.2)
+    rng = np.random.default_rng(93)
+    s = rng.standard_normal(12) + 1j * rng.standard_normal(12)
+    ws = np.linalg.solve(A, s)
+    errs = []
+    for T in range(0, 12):
+        e = O.pcg(A, s.reshape(12, 1), "gs", max_iter=T)[0][:, 0] - ws
+        errs.append(np.sqrt(np.real(np.vdot(e, A @ e))))
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+    w = O.pcg(A, s.reshape(12, 1), "gs", max_iter=5000, tol=1e-14)[0][:, 0]
+    assert np.linalg.norm(w - ws) <= 1e-10 * np.linalg.norm(ws)
+
+
+def test_jor_contracts_at_the_spectral_rate():
+    """JOR at omega = 2 / (lambda_min + lambda_max) of D^{-1} P: in the
+    D^{1/2}-weighted norm the error map I - omega D^{-1/2} P D^{-1/2} is
+    Hermitian with spectral radius (kappa - 1) / (kappa + 1), so every sweep
+    shrinks that norm by at least this factor, and JOR converges to P^{-1} s.
+    A missing D^{-1} or omega, or a wrong sign, breaks the bound."""
+    H, A = small_system(K=10, M=40, seed=95, spread=(0.4, 2.5), xi=0.3)
+    omega, kappa = _omega_opt(A)
+    rho = (kappa - 1.0) / (kappa + 1.0)
+    dh = np.sqrt(np.real(np.diag(A)))
+    rng = np.random.default_rng(95)
+    s = rng.standard_normal(10) + 1j * rng.standard_normal(10)
+    ws = np.linalg.solve(A, s)
+    prev = np.linalg.norm(dh * ws)            # w^0 = 0
+    for T in range(1, 9):
+        e = O.pcg(A, s.reshape(10, 1), "jor", max_iter=T, omega=omega)[0][:, 0] - ws
+        cur = np.linalg.norm(dh * e)
+        assert cur <= rho * prev * (1 + 1e-9)
+        prev = cur
+    w = O.pcg(A, s.reshape(10, 1), "jor", max_iter=5000, tol=1e-14, omega=omega)[0][:, 0]
+    assert np.linalg.norm(w - ws) <= 1e-10 * np.linalg.norm(ws)
+
+
+def test_stationary_tolerance_semantics():
+    """tol > 0 stops before the first sweep whose true residual is at most
+    tol ||s||; the reported residual is that true residual."""
+    H, A = small_system(K=8, M=30, seed=97, spread=(0.8, 1.5), xi=0.3)
+    omega, _ = _omega_opt(A)
+    s = np.ones((8, 1), dtype=complex)
+    for m in ("gs", "jor"):
+        w, it, rr, st = O.pcg(A, s, m, max_iter=500, tol=1e-6, omega=omega)
+        true = np.linalg.norm(s[:, 0] - A @ w[:, 0]) / np.linalg.norm(s)
+        assert rr[0] <= 1e-6 and abs(rr[0] - true) <= 1e-12
+        wp = O.pcg(A, s, m, max_iter=int(it[0]) - 1, omega=omega)[0]
+        assert np.linalg.norm(s[:, 0] - A @ wp[:, 0]) / np.linalg.norm(s) > 1e-6
+
+
+def test_paper_convergence_ordering_on_table1_geometry():
+    """Sec. IV on Fig. 3 and the summary table: Jac-PCG converges faster than
+    CG, and GS faster than JOR.  The least-square error of W against the
+    direct-inversion RZF, averaged over ten channels of the Table I geometry
+    (M = 100, K = 32), keeps that order at every T from 2 to 8 (JOR at its
+    convergent omega = 2 / (lambda_min + lambda_max) of D^{-1} P)."""
+    insts = [C.paper_table1(0, i) for i in range(10)]
+    lse = {m: np.zeros(9) for m in ("standard", "cg", "gs", "jor")}
+    for inst in insts:
+        H = C.round_complex64(inst.H)
+        A = O.gram(H, inst.xi)
+        omega, _ = _omega_opt(A)
+        Wd = O.rzf_direct(H, inst.xi)[0]
+        for m in lse:
+            for T in range(2, 9):
+                W = O.precode(H, inst.xi, m, max_iter=T, omega=omega)["W"]
+                lse[m][T] += np.linalg.norm(W - Wd) ** 2 / np.linalg.norm(Wd) ** 2 / len(insts)
+    for T in range(2, 9):
+        assert lse["standard"][T] < lse["cg"][T], T
+        assert lse["gs"][T] < lse["jor"][T], T
