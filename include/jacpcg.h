@@ -57,15 +57,25 @@ typedef enum {
  * (the printed ratio of Eq. 20 is garbled).  ALG1: Algorithm 1 as printed
  * (conjugate gradients with Euclidean inner products on the left-scaled
  * system D^{-1} A X = D^{-1} B; its step alpha is complex).  CG: plain
- * conjugate gradients (C = I). */
-enum { JACPCG_STANDARD = 0, JACPCG_ALG1 = 1, JACPCG_CG = 2 };
+ * conjugate gradients (C = I).  JOR: the stationary Jacobi over-relaxation
+ * of Sec. III-A, w^{t+1} = (I - omega D^{-1} A) w^t + omega D^{-1} b, run in
+ * residual form (x += omega D^{-1} r, r -= A omega D^{-1} r) with the
+ * instance's omega; it converges for 0 < omega < 2 / lambda_max(D^{-1} A)
+ * (the paper gives no omega).  Algorithm 1 and JOR run on the SIMT kernels.
+ * DIRECT: the direct RZF the paper compares against (Appendix): P = L L^H
+ * by Cholesky, then X = P^{-1} B by forward and back substitution, in FP32;
+ * max_iter, tol and X0 are ignored, iters and resid report 0, a pivot <= 0
+ * gives NOTHPD (X = 0); refinement is not offered with it (EINVAL). */
+enum { JACPCG_STANDARD = 0, JACPCG_ALG1 = 1, JACPCG_CG = 2, JACPCG_JOR = 3, JACPCG_DIRECT = 4 };
 
 /* Arithmetic of the Gram and W = H X contractions.
  * FP32:   FP32 FMA on the SIMT pipes.
  * TF32X3: tensor cores (tcgen05, kind::tf32) with each FP32 operand split
  *         into a TF32 head and a TF32 tail, three products accumulated in
  *         FP32 (about FP32 accuracy).
- * The iteration always runs in FP32 with compensated dot products. */
+ * The iteration's vectors and scalars are FP32 in both cases and every
+ * per-column dot product is compensated (Dot2); with TF32X3 its product
+ * A P runs on the tensor cores in 3xTF32 for the K = 64 class. */
 enum { JACPCG_FP32 = 0, JACPCG_TF32X3 = 1 };
 
 /* Storage type of H (jacpcg_instance.h_dtype).  BF16: each complex entry is
@@ -97,7 +107,8 @@ typedef struct {
     int max_K;               /* largest K accepted, 1 <= max_K <= 256 */
     size_t arena_bytes;      /* device workspace arena; 0 = sized for one call at the limits */
     int precision;           /* JACPCG_FP32 or JACPCG_TF32X3 */
-    int variant;             /* JACPCG_STANDARD, JACPCG_ALG1 or JACPCG_CG */
+    int variant;             /* JACPCG_STANDARD, JACPCG_ALG1, JACPCG_CG, JACPCG_JOR or
+                                JACPCG_DIRECT */
     int flags;               /* JACPCG_FLAG_* */
     int refine_sweeps;       /* 0..3 iterative-refinement sweeps after the solve: R = I - A X
                                 evaluated as refine_residual says, A dX = R solved by the same
@@ -133,7 +144,8 @@ typedef struct {
     float tol;               /* > 0: stop a column once ||r|| <= tol ||b||; <= 0: exactly T steps */
     int h_dtype;             /* JACPCG_H_C64 (0) or JACPCG_H_BF16 */
     float *resid_hist;       /* optional device out, refine_sweeps + 1 floats: ||B - A X||_F / sqrt(n)
-                                (FP64-evaluated) before each sweep and after the last */
+                                before each sweep and after the last, evaluated as the
+                                refinement residual (Dot2 by default, FP64 on request) */
     /* Right-hand sides, Eq. 16 per symbol vector: P w = s for the n_rhs columns
      * s of B (Sec. III, "Stationary Iterative Methods", Eqs. 15-16).  NULL: B = I_K,
      * the RZF precoder of Eq. 7.  With B, beta normalises the block's mean
@@ -147,6 +159,17 @@ typedef struct {
                                 initial point of the iteration (Sec. III-B Step 1; e.g. the
                                 previous slot's X); NULL: 0.  The tolerance stays relative to
                                 ||b||; iters counts the updates after X0 */
+    float omega;             /* JOR relaxation factor (variant JACPCG_JOR only), 0 <= omega < 2;
+                                0 means 1 (the Jacobi iteration); e.g. 2 / (lambda_min +
+                                lambda_max) of D^{-1} A, which always converges */
+    float *sinr;             /* optional device out, K floats: the per-user SINR of Eq. 9
+                                (centralised form, single-antenna users, G = beta W):
+                                gamma_k = beta^2 |h_k^H w_k|^2 / (beta^2 sum_{j!=k}
+                                |h_k^H w_j|^2 + noise), computed on the GPU from this call's W
+                                and beta after the precoder; the sum SE of Eq. 10 is
+                                sum_k log2(1 + gamma_k).  Only with B = NULL (EINVAL otherwise);
+                                4-byte aligned */
+    float noise;             /* noise power sigma^2 of sinr; 0 means 1; finite, >= 0 */
 } jacpcg_instance;
 
 typedef struct jacpcg_ctx jacpcg_ctx;
@@ -300,7 +323,7 @@ jacpcg_status jacpcg_server_destroy(jacpcg_server *srv);
  * baseline the batched path is measured against.  No context: the caller
  * passes a device workspace of at least 5 K^2 * 8 + 16 K + 256 bytes for the
  * largest K of the batch (ENOMEM otherwise).  Per-instance outputs as in
- * jacpcg_precode.  B and X0 must be NULL.  Errors: EINVAL, ENOMEM, ECUDA. */
+ * jacpcg_precode.  B, X0 and sinr must be NULL.  Errors: EINVAL, ENOMEM, ECUDA. */
 jacpcg_status jacpcg_precode_plain(const jacpcg_instance *inst, int n_inst, int variant,
                                    void *workspace, size_t workspace_bytes, int32_t *status_dev,
                                    int32_t *iters_dev, float *resid_dev, float *beta_dev,
@@ -308,21 +331,24 @@ jacpcg_status jacpcg_precode_plain(const jacpcg_instance *inst, int n_inst, int 
 
 /* Precode without allocating anything (no counterpart in the paper: this
  * is an integration aid).  For callers that cannot call cudaMalloc or any
- * allocating routine -- code running while someone else captures a CUDA
- * graph, real-time slot loops that forbid allocator latency, integrations
- * whose memory was fixed at start-up.  Same work, kernels and results as
- * jacpcg_precode with a context of the given variant and FP32 precision,
- * but no context: the tables, accumulators and Gram / iterate workspace
- * live in one static device array of JACPCG_NOALLOC_SCRATCH_BYTES that
- * every GPU loading the library holds until the process exits.  Runs on
- * the current device.  The first call on a device looks up the array's
- * device address (make that first call before any stream capture).  All
- * calls share the array: calls whose GPU work overlaps race, so serialise
- * them (one stream, one thread).  Returns ENOMEM, and enqueues nothing,
+ * allocating routine -- real-time slot loops that forbid allocator latency,
+ * integrations whose memory was fixed at start-up.  The same work and SIMT
+ * kernels as jacpcg_precode with a context of the given variant (STANDARD,
+ * ALG1 or CG) and FP32 precision, each K class on its default launch shape (a context's
+ * autotuner may pick another, so W agrees with jacpcg_precode within the
+ * 1e-5 relative W tolerance, not bit for bit), but no context: the tables,
+ * accumulators and Gram / iterate workspace live in one static device
+ * array of JACPCG_NOALLOC_SCRATCH_BYTES that every GPU loading the library
+ * holds until the process exits; the tables reach it as kernel parameters.
+ * Runs on the current device.  The first call on a device looks up the
+ * array's device address (make that first call before any stream capture);
+ * the lookup is repeated if the device's context is replaced
+ * (cudaDeviceReset).  All calls share the array: calls whose GPU work
+ * overlaps race, so serialise them (one stream, one thread).  Returns ENOMEM, and enqueues nothing,
  * when the batch needs more scratch than the array holds (about 120
  * instances of M = 1024, K = 64, or 7 of K = 256); EINVAL for invalid
- * arguments as jacpcg_precode (K <= 256, no max_M limit; B and X0 must be
- * NULL, complex64 H only). */
+ * arguments as jacpcg_precode (K <= 256, no max_M limit; B, X0 and sinr
+ * must be NULL, complex64 H only). */
 #define JACPCG_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
 jacpcg_status jacpcg_precode_noalloc(const jacpcg_instance *inst, int n_inst, int variant,
                                      int32_t *status_dev, int32_t *iters_dev, float *resid_dev,
@@ -342,7 +368,7 @@ typedef struct {
 /* Host-only helper: describe the n_blocks blocks of `full` as independent
  * instances (out[i], host array of n_blocks), to be precoded together by
  * jacpcg_precode (a ragged batch) or any entry point that takes instances.
- * out[i] copies full's scalars (xi, power, max_iter, tol, h_dtype) and
+ * out[i] copies full's scalars (xi, power, max_iter, tol, h_dtype, omega) and
  * points H_i and W_i into full->H and full->W: W_i is the (row0, col0)
  * block of W, so one call fills the blocks of the block precoder G and
  * leaves the rest of W untouched (the caller zeroes it once).  X, A,
@@ -353,6 +379,16 @@ typedef struct {
  * complex64 H, a multiple of 4 for bfloat16 H; W is complex64). */
 jacpcg_status jacpcg_blocks(const jacpcg_instance *full, const jacpcg_block *blocks, int n_blocks,
                             jacpcg_instance *out);
+
+/* Measurement aid (no counterpart in the paper): enqueue on `stream` one
+ * launch of `blocks` CTAs of 256 threads, each thread running 8 independent
+ * FP32 FMA chains of 16 * iters steps, so that the caller can time the FP32
+ * FMA roof of the device with CUDA events (the roof the SIMT kernels are
+ * reported against).  *flops (may be NULL) receives the flops of the launch,
+ * blocks * 256 * iters * 16 * 8 * 2.  scratch_dev: device array of `blocks`
+ * floats (never written in practice).  Errors: EINVAL, ECUDA. */
+jacpcg_status jacpcg_probe_fp32_fma(int blocks, int iters, float *scratch_dev, void *stream,
+                                    double *flops);
 
 /* Destroy a context (and any plans still alive).  Waits for the device. */
 jacpcg_status jacpcg_destroy(jacpcg_ctx *ctx);

@@ -19,13 +19,14 @@ LIB_PATH = PKG / "_build" / "libjacpcg.so"
 
 JACPCG_OK, JACPCG_EINVAL, JACPCG_ENOMEM, JACPCG_ECUDA = 0, 1, 2, 3
 JACPCG_ENOTCONV, JACPCG_ENOTHPD, JACPCG_ENONFINITE, JACPCG_ETIMEOUT, JACPCG_EBUSY = 4, 5, 6, 7, 8
-JACPCG_STANDARD, JACPCG_ALG1, JACPCG_CG = 0, 1, 2
+JACPCG_STANDARD, JACPCG_ALG1, JACPCG_CG, JACPCG_JOR, JACPCG_DIRECT = 0, 1, 2, 3, 4
 JACPCG_FP32, JACPCG_TF32X3 = 0, 1
 JACPCG_FLAG_PROFILE = 1
 JACPCG_FLAG_SIMT_ITERATION = 2
 JACPCG_H_C64, JACPCG_H_BF16 = 0, 1
 JACPCG_RESID_DOT2, JACPCG_RESID_FP64 = 0, 1
-VARIANTS = {"standard": JACPCG_STANDARD, "alg1": JACPCG_ALG1, "cg": JACPCG_CG}
+VARIANTS = {"standard": JACPCG_STANDARD, "alg1": JACPCG_ALG1, "cg": JACPCG_CG, "jor": JACPCG_JOR,
+            "direct": JACPCG_DIRECT}
 PRECISIONS = {"fp32": JACPCG_FP32, "tf32x3": JACPCG_TF32X3}
 
 EXPORTS = ("jacpcg_create", "jacpcg_precode", "jacpcg_plan_create", "jacpcg_plan_execute",
@@ -34,7 +35,7 @@ EXPORTS = ("jacpcg_create", "jacpcg_precode", "jacpcg_plan_create", "jacpcg_plan
            "jacpcg_version", "jacpcg_precode_noalloc", "jacpcg_precode_plain",
            "jacpcg_server_create", "jacpcg_submit", "jacpcg_poll", "jacpcg_server_replay",
            "jacpcg_server_stats", "jacpcg_server_destroy", "jacpcg_autotune", "jacpcg_set_shape",
-           "jacpcg_get_shape", "jacpcg_last_cuda_error", "jacpcg_blocks")
+           "jacpcg_get_shape", "jacpcg_last_cuda_error", "jacpcg_blocks", "jacpcg_probe_fp32_fma")
 
 
 class jacpcg_config(ctypes.Structure):
@@ -52,7 +53,8 @@ class jacpcg_instance(ctypes.Structure):
                 ("A", ctypes.c_void_p), ("max_iter", ctypes.c_int), ("tol", ctypes.c_float),
                 ("h_dtype", ctypes.c_int), ("resid_hist", ctypes.c_void_p),
                 ("B", ctypes.c_void_p), ("ldb", ctypes.c_int), ("n_rhs", ctypes.c_int),
-                ("X0", ctypes.c_void_p)]
+                ("X0", ctypes.c_void_p), ("omega", ctypes.c_float), ("sinr", ctypes.c_void_p),
+                ("noise", ctypes.c_float)]
 
 
 class jacpcg_block(ctypes.Structure):
@@ -118,6 +120,7 @@ def load(path: pathlib.Path | str | None = None):
         L.jacpcg_blocks.argtypes = [ctypes.POINTER(jacpcg_instance), ctypes.POINTER(jacpcg_block), I,
                                     ctypes.POINTER(jacpcg_instance)]
         L.jacpcg_strerror.argtypes = [I]
+        L.jacpcg_probe_fp32_fma.argtypes = [I, I, P, P, ctypes.POINTER(ctypes.c_double)]
         L.jacpcg_strerror.restype = ctypes.c_char_p
         L.jacpcg_version.restype = ctypes.c_char_p
         for n in ("jacpcg_create", "jacpcg_precode", "jacpcg_plan_create", "jacpcg_plan_execute",
@@ -254,6 +257,14 @@ def jacpcg_profile_read(ctx):
     return list(ms), n.value, per.value
 
 
+def jacpcg_probe_fp32_fma(blocks: int, iters: int, scratch, stream) -> float:
+    """Enqueue the FP32 FMA measurement kernel; returns the launch's flops."""
+    f = ctypes.c_double()
+    _check(load().jacpcg_probe_fp32_fma(int(blocks), int(iters), scratch.data_ptr(), stream,
+                                        ctypes.byref(f)), "jacpcg_probe_fp32_fma")
+    return f.value
+
+
 def jacpcg_last_cuda_error(ctx) -> str:
     return load().jacpcg_last_cuda_error(ctx).decode()
 
@@ -356,13 +367,16 @@ def jacpcg_server_destroy(srv) -> None:
 # --- torch convenience ---------------------------------------------------------
 
 def instance(H, W, xi: float, max_iter: int, tol: float = 0.0, power: float = 1.0, X=None,
-             A=None, resid_hist=None, B=None, X0=None) -> jacpcg_instance:
+             A=None, resid_hist=None, B=None, X0=None, omega: float = 0.0, sinr=None,
+             noise: float = 0.0) -> jacpcg_instance:
     """Describe one channel held in torch tensors of device storage layout:
     H (complex64, or bfloat16 with a trailing (re, im) axis) and W
     (complex64) have shape (K, M) (column k of the matrix is row k of the
     tensor, i.e. column-major storage of the M x K matrix).  B: optional
     (n_rhs, K) complex64 symbol vectors (Eq. 16; W then has shape (n_rhs, M)
-    and X (n_rhs, K)); X0: optional initial point, contiguous (n, K)."""
+    and X (n_rhs, K)); X0: optional initial point, contiguous (n, K); omega:
+    the JOR relaxation factor (variant "jor"; 0 means 1); sinr: optional float32
+    (K,) device tensor for the per-user SINR of Eq. 9 (noise: sigma^2, 0 means 1)."""
     import torch
     bf16 = H.dtype == torch.bfloat16
     if bf16:
@@ -383,7 +397,8 @@ def instance(H, W, xi: float, max_iter: int, tol: float = 0.0, power: float = 1.
                            B=None if B is None else B.data_ptr(),
                            ldb=0 if B is None else B.stride(-2),
                            n_rhs=0 if B is None else B.shape[-2],
-                           X0=None if X0 is None else X0.data_ptr())
+                           X0=None if X0 is None else X0.data_ptr(), omega=float(omega),
+                           sinr=None if sinr is None else sinr.data_ptr(), noise=float(noise))
 
 
 class Precoder:

@@ -113,8 +113,8 @@ struct Arena {
 
 // What one kernel launch of a plan covers.
 struct Launch {
-    enum Kind { GRAM, PCG, HX, GRAM_TC, GRAM_TCX, HX_TC, HX_TCW, PCG_TC } kind;
-    int phase;        // 0 Gram, 1 iteration, 2 W = H X
+    enum Kind { GRAM, PCG, HX, GRAM_TC, GRAM_TCX, HX_TC, HX_TCW, PCG_TC, CHOL, SINR } kind;
+    int phase;        // 0 Gram, 1 iteration, 2 W = H X, 3 SINR (after the power factor)
     int param;        // TB (Gram), KC (iteration), TN (W = H X)
     size_t list_off;  // byte offset of its work list inside the plan block
     int count;        // CTAs
@@ -197,6 +197,9 @@ jacpcg_status validate(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n
         if (q.B && (q.n_rhs < 1 || q.n_rhs > k_class(q.K) || q.ldb < q.K || !aligned16(q.B)))
             return JACPCG_EINVAL;
         if (q.X0 && !aligned16(q.X0)) return JACPCG_EINVAL;
+        if (!(q.omega >= 0.f) || !(q.omega < 2.f)) return JACPCG_EINVAL;   // also NaN
+        if (q.sinr && (q.B || (reinterpret_cast<uintptr_t>(q.sinr) & 3))) return JACPCG_EINVAL;
+        if (!(q.noise >= 0.f) || !std::isfinite(q.noise)) return JACPCG_EINVAL;
     }
     return JACPCG_OK;
 }
@@ -206,8 +209,8 @@ int n_cols(const jacpcg_instance &q) { return q.B ? q.n_rhs : q.K; }
 
 // Byte layout of one plan block.
 struct Layout {
-    size_t insts, gram, tcl, gdl, gxl, pcg, hx, hxl, hwl, res, accum, ws, total;
-    int n_gram, n_pcg, n_hx, n_res, n_gd, n_gx, n_hw;
+    size_t insts, gram, tcl, gdl, gxl, pcg, hx, hxl, hwl, res, sinr, accum, ws, total;
+    int n_gram, n_pcg, n_hx, n_res, n_gd, n_gx, n_hw, n_sinr;
     bool refine;
     std::vector<size_t> ws_off;   // per instance
 };
@@ -245,15 +248,15 @@ bool gram_on_tc(int precision, int KC) { return precision == JACPCG_TF32X3 && KC
 bool hx_on_tc(int precision, int KC) { return precision == JACPCG_TF32X3 && KC >= 64; }
 int hx_tc_groups(const jacpcg_instance &q) { return (n_cols(q) + 63) / 64; }
 // ... and whose iteration does, unless the SIMT kernel is asked for (Algorithm 1
-// always keeps the SIMT kernel)
+// and JOR always keep the SIMT kernel)
 bool pcg_on_tc(const jacpcg_config &cfg, int KC) {
     return !(cfg.flags & JACPCG_FLAG_SIMT_ITERATION) && cfg.precision == JACPCG_TF32X3 && KC == 64 &&
-           cfg.variant != JACPCG_ALG1;
+           (cfg.variant == JACPCG_STANDARD || cfg.variant == JACPCG_CG);
 }
 
 Layout make_layout(const jacpcg_instance *inst, int n, bool refine, const int *shape_idx) {
     Layout L{};
-    L.n_gram = L.n_pcg = L.n_hx = L.n_res = L.n_gd = L.n_gx = L.n_hw = 0;
+    L.n_gram = L.n_pcg = L.n_hx = L.n_res = L.n_gd = L.n_gx = L.n_hw = L.n_sinr = 0;
     L.refine = refine;
     for (int i = 0; i < n; ++i) {
         if (refine) L.n_res += (n_cols(inst[i]) + RES_CB - 1) / RES_CB;
@@ -264,6 +267,7 @@ Layout make_layout(const jacpcg_instance *inst, int n, bool refine, const int *s
         L.n_gram += n_gtiles(inst[i]);
         L.n_pcg += n_pblocks(inst[i], shape_idx);
         L.n_hx += n_wtiles(inst[i]);
+        if (inst[i].sinr) L.n_sinr += (inst[i].K + 7) / 8;
     }
     size_t o = 0;
     L.insts = o;  o += align_up(sizeof(DevInst) * n);
@@ -276,6 +280,7 @@ Layout make_layout(const jacpcg_instance *inst, int n, bool refine, const int *s
     L.hxl = o;    o += align_up(sizeof(int) * n);
     L.hwl = o;    o += align_up(sizeof(int2) * L.n_hw);
     L.res = o;    o += align_up(sizeof(int2) * L.n_res);
+    L.sinr = o;   o += align_up(sizeof(int2) * L.n_sinr);
     L.accum = o;  o += align_up(sizeof(int32_t) * n) * 3;
     L.ws = o;
     L.ws_off.resize(n);
@@ -312,6 +317,9 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
                     : KC == 64                         ? (q.M + 127) / 128
                                                        : ((q.M + 127) / 128) * hx_tc_groups(q);
         d.variant = ctx->cfg.variant;
+        d.omega = q.omega > 0.f ? q.omega : 1.f;
+        d.sinr = q.sinr;
+        d.noise = q.noise;
         d.xi = (float)q.xi;
         d.power = q.power > 0.0 ? (float)q.power : 1.0f;
         d.tol = q.tol;
@@ -378,7 +386,17 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
     int2 *pb = reinterpret_cast<int2 *>(host + L.pcg);
     int p = 0;
     if (nt) launches.push_back({Launch::PCG_TC, 1, 64, L.tcl, nt});
+    if (ctx->cfg.variant == JACPCG_DIRECT) {   // direct solve: instance lists per K class
+        int c = 0;
+        for (int KC : {8, 16, 32, 64, 128, 256}) {
+            const int start = c;
+            for (int i = 0; i < n; ++i)
+                if (k_class(inst[i].K) == KC) tl[c++] = i;
+            if (c > start) launches.push_back({Launch::CHOL, 1, KC, L.tcl + start * sizeof(int), c - start});
+        }
+    }
     for (int KC : {8, 16, 32, 64, 128, 256}) {
+        if (ctx->cfg.variant == JACPCG_DIRECT) break;
         const int start = p;
         const int sh = ctx->pcg_shape_idx[kc_index(KC)];
         const PcgShape s = pcg_shape(KC, sh);
@@ -414,6 +432,16 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
                 for (int mt = 0; mt < nm; ++mt) ht[h++] = make_int4(i, mt, nt, slot++);
         }
         if (h > start) launches.push_back({Launch::HX, 2, TN, L.hx + start * sizeof(int4), h - start});
+    }
+    // per-user SINR (Eq. 9) after the power factor: (instance, block of 8 users) jobs per K class
+    int2 *sj = reinterpret_cast<int2 *>(host + L.sinr);
+    int ns = 0;
+    for (int KC : {8, 16, 32, 64, 128, 256}) {
+        const int start = ns;
+        for (int i = 0; i < n; ++i)
+            if (inst[i].sinr && k_class(inst[i].K) == KC)
+                for (int b = 0; b < (inst[i].K + 7) / 8; ++b) sj[ns++] = make_int2(i, b);
+        if (ns > start) launches.push_back({Launch::SINR, 3, KC, L.sinr + start * sizeof(int2), ns - start});
     }
 }
 
@@ -481,6 +509,9 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
                     e = launch_pcg_tc64(ctx->cfg.variant, pl->d_insts, static_cast<const int *>(list), l.count,
                                         pl->acc, &ctx->amap, ctx->arena.base, s, 0);
                     break;
+                case Launch::CHOL:
+                    e = launch_chol(l.param, pl->d_insts, static_cast<const int *>(list), l.count, pl->acc, s);
+                    break;
             }
             if (e != cudaSuccess) return cuda_fail(ctx, e);
             ++nl;
@@ -521,6 +552,14 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
         if (e != cudaSuccess) return cuda_fail(ctx, e);
     }
     ++nl;
+    for (const Launch &l : pl->launches) {
+        if (l.phase != 3) continue;
+        const NvtxRange range("jacpcg: SINR");
+        const cudaError_t e = launch_sinr(l.param, pl->d_insts, reinterpret_cast<const int2 *>(pl->dev + l.list_off),
+                                          l.count, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e);
+        ++nl;
+    }
     if (ev) CK(cudaEventRecord(ev[4], s));
     *n_launched = nl;
     return JACPCG_OK;
@@ -733,7 +772,8 @@ jacpcg_status jacpcg_create(const jacpcg_config *cfg, jacpcg_ctx **out) {
     if (cfg->max_K < 1 || cfg->max_K > 256 || cfg->max_M < 1 || cfg->max_instances < 1)
         return JACPCG_EINVAL;
     if (cfg->precision != JACPCG_FP32 && cfg->precision != JACPCG_TF32X3) return JACPCG_EINVAL;
-    if (cfg->variant < JACPCG_STANDARD || cfg->variant > JACPCG_CG) return JACPCG_EINVAL;
+    if (cfg->variant < JACPCG_STANDARD || cfg->variant > JACPCG_DIRECT) return JACPCG_EINVAL;
+    if (cfg->variant == JACPCG_DIRECT && cfg->refine_sweeps > 0) return JACPCG_EINVAL;
     if (cfg->flags & ~(JACPCG_FLAG_PROFILE | JACPCG_FLAG_SIMT_ITERATION)) return JACPCG_EINVAL;
     if (cfg->refine_sweeps < 0 || cfg->refine_sweeps > 3) return JACPCG_EINVAL;
     if (cfg->refine_residual != JACPCG_RESID_DOT2 && cfg->refine_residual != JACPCG_RESID_FP64)

@@ -29,7 +29,8 @@ struct DevInst {
     int KC;               // K class
     int max_iter;
     int n_wpart;          // number of W = H X tiles of this instance
-    int variant;          // JACPCG_STANDARD / ALG1 / CG
+    int variant;          // JACPCG_STANDARD / ALG1 / CG / JOR
+    float omega;          // JOR relaxation factor
     float xi, power, tol;
     int h_bf16;           // H holds bfloat16 (re, im) pairs instead of complex64
     float2 *R;            // workspace KC x KC: refinement residual I - A X (null without refinement)
@@ -44,6 +45,8 @@ struct DevInst {
     const float2 *X0;     // optional initial point, K x ncols, ld K (caller)
     int ldb;
     int ncols;            // right-hand sides: K for B = I, else n_rhs (<= KC)
+    float *sinr;          // optional per-user SINR out, K floats (caller); B = I only
+    float noise;          // noise power sigma^2 of the SINR (0: 1)
 };
 
 // One entry of H as complex FP32 (bfloat16 converts exactly).
@@ -111,20 +114,19 @@ __device__ __forceinline__ void comp_fma(Comp &v, float a, float b) {
     v.s = s;
     v.c += pe + e;
 }
-__device__ __forceinline__ void comp_add(Comp &v, Comp w) {
-    float s, e;
-    two_sum(v.s, w.s, s, e);
-    v.s = s;
-    v.c += w.c + e;
-}
-// warp-wide all-reduce of a compensated value (fixed xor butterfly order)
+// warp-wide all-reduce of a compensated value (fixed xor butterfly order).
+// Partners combine as (s_a + s_b, (c_a + c_b) + e): each operation is
+// commutative or exact, so every lane ends with bit-identical totals and
+// decisions taken on them (stopping tests) are warp-uniform.
 __device__ __forceinline__ Comp comp_warp_allreduce(Comp v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        Comp w;
-        w.s = __shfl_xor_sync(0xffffffffu, v.s, o);
-        w.c = __shfl_xor_sync(0xffffffffu, v.c, o);
-        comp_add(v, w);
+        const float ws = __shfl_xor_sync(0xffffffffu, v.s, o);
+        const float wc = __shfl_xor_sync(0xffffffffu, v.c, o);
+        float s, e;
+        two_sum(v.s, ws, s, e);
+        v.s = s;
+        v.c = (v.c + wc) + e;
     }
     return v;
 }

@@ -60,6 +60,11 @@ cudaError_t launch_hx_tc_wide(const DevInst *insts, const int2 *list, int n, Dev
 // floats, box 64 x 128), arena: its base address
 cudaError_t launch_pcg_tc64(int variant, const DevInst *insts, const int *list, int n, DevAccum acc,
                             const CUtensorMap *amap, const char *arena, cudaStream_t s, int mode);
+// direct solve (Cholesky, forward and back substitution) of the K = KC class;
+// list: instance ids.  Replaces the iteration for the JACPCG_DIRECT variant.
+cudaError_t launch_chol(int KC, const DevInst *insts, const int *list, int n, DevAccum acc, cudaStream_t s);
+// per-user SINR (Eq. 9) from H, W and the power factor; jobs: (instance, block of 8 users)
+cudaError_t launch_sinr(int KC, const DevInst *insts, const int2 *jobs, int n, cudaStream_t s);
 // blocks: (instance, first column); mode 0: A X = I, mode 1: A dX = R, X += dX
 cudaError_t launch_pcg(int KC, int variant, const DevInst *insts, const int2 *blocks,
                        int n_blocks, DevAccum acc, cudaStream_t s, int mode = 0);

@@ -1,30 +1,35 @@
 // noalloc.cu -- jacpcg_precode_noalloc: the batched precoder for callers
 // that cannot allocate memory.
 //
-// Some callers cannot call cudaMalloc or any allocating routine: code that
-// runs while a CUDA graph is being captured by someone else, real-time
-// slot loops that forbid allocator latency and fragmentation, and
-// embedded integrations whose memory was fixed at start-up.  This entry
-// point allocates nothing, on the device or on the host: the instance table,
-// tile lists, per-instance accumulators and the Gram / iterate workspace
-// all live in one file-scope __device__ array of JACPCG_NOALLOC_SCRATCH_BYTES
-// (every GPU that loads the library holds it until the process exits), and
-// the host image of the tables is a file-scope static array.  It runs the
-// same kernels as jacpcg_precode.
+// Some callers cannot call cudaMalloc or any allocating routine: real-time
+// slot loops that forbid allocator latency and fragmentation, and embedded
+// integrations whose memory was fixed at start-up.  This entry point
+// allocates nothing, on the device or on the host: the instance table, tile
+// lists, per-instance accumulators and the Gram / iterate workspace all live
+// in one file-scope __device__ array of JACPCG_NOALLOC_SCRATCH_BYTES (every
+// GPU that loads the library holds it until the process exits).  The tables
+// are built in a file-scope static host array and reach the device as the
+// by-value parameters of small upload kernels (no host-to-device copy, so
+// the host never waits on the stream).  It runs the same kernels as
+// jacpcg_precode, with each K class's default launch shape.
 //
 // The array's name in host code is a host-side stand-in, not a device
-// address, so its device address is looked up once per device with
-// cudaGetSymbolAddress (the first call on a device does this set-up; make
-// that first call before any stream capture) and passed to the kernels.
+// address, so its device address is looked up with cudaGetSymbolAddress
+// once per device, with that device current (the first call on a device
+// does this set-up; make that first call before any stream capture), and
+// passed to the kernels.  The lookup is repeated when the device's context
+// is replaced (cudaDeviceReset reloads the module at a new address).
 // Every call shares the array and the array keeps the last call's contents;
 // the per-instance accumulators are reset by the first kernel of each call.
 // Calls whose GPU work overlaps (two streams, or two threads) race on the
 // array: serialise them.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 #include <mutex>
 
 #include "../../include/jacpcg.h"
@@ -44,7 +49,43 @@ __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 alignas(256) unsigned char g_host_tables[kTableBytes];
 void *g_scratch_addr[kMaxDevices];
+unsigned long long g_scratch_ctx[kMaxDevices];   // id of the context the address belongs to
 std::mutex g_mutex;
+
+// Tables travel as kernel parameters: each launch carries kChunk bytes by
+// value and copies them into the scratch array.
+constexpr int kChunk = 16 * 1024;
+struct TableChunk {
+    alignas(16) unsigned char bytes[kChunk];
+};
+static_assert(sizeof(TableChunk) + 32 <= 32764, "kernel parameter limit");
+__global__ void __launch_bounds__(256) upload_tables(const __grid_constant__ TableChunk c, char *dst, int n) {
+    const int4 *src = reinterpret_cast<const int4 *>(c.bytes);
+    int4 *out = reinterpret_cast<int4 *>(dst);
+    for (int i = threadIdx.x; i < n / 16; i += blockDim.x) out[i] = src[i];
+}
+
+// The unique id of the current context (cuCtxGetCurrent + cuCtxGetId through
+// the runtime's driver entry points; no link against the driver library).
+bool current_context_id(unsigned long long &id) {
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1{}, q2{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) !=
+                cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return false;
+        get_current = reinterpret_cast<GetCurrent>(f1);
+        get_id = reinterpret_cast<GetId>(f2);
+    }
+    CUcontext ctx = nullptr;
+    return get_current(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, &id) == CUDA_SUCCESS;
+}
 
 size_t up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 int kclass(int K) {
@@ -90,6 +131,7 @@ extern "C" jacpcg_status jacpcg_precode_noalloc(const jacpcg_instance *inst, int
         if (q.max_iter < 0 || q.max_iter > 4096) return JACPCG_EINVAL;
         if (q.h_dtype != JACPCG_H_C64) return JACPCG_EINVAL;   // complex64 H only
         if (q.B || q.X0) return JACPCG_EINVAL;                // B = I, zero start only
+        if (q.sinr) return JACPCG_EINVAL;                     // no SINR output here
     }
     // sizes: tables, accumulators, workspace -- all must fit the static arrays
     size_t ng = 0, np = 0, nh = 0, ws = 0;
@@ -113,13 +155,19 @@ extern "C" jacpcg_status jacpcg_precode_noalloc(const jacpcg_instance *inst, int
         (void)cudaGetLastError();
         return JACPCG_ECUDA;
     }
-    if (!g_scratch_addr[dev]) {   // once per device, with that device current
+    // once per device (and again if its context was replaced), with that
+    // device current; the runtime call itself makes the primary context current
+    unsigned long long ctx_id = 0;
+    const bool have_ctx = current_context_id(ctx_id);
+    if (!g_scratch_addr[dev] || !have_ctx || g_scratch_ctx[dev] != ctx_id) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
             (void)cudaGetLastError();
             return JACPCG_ECUDA;
         }
+        if (!current_context_id(ctx_id)) return JACPCG_ECUDA;
         g_scratch_addr[dev] = p;
+        g_scratch_ctx[dev] = ctx_id;
     }
     char *base = static_cast<char *>(g_scratch_addr[dev]);
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -193,11 +241,15 @@ extern "C" jacpcg_status jacpcg_precode_noalloc(const jacpcg_instance *inst, int
         }
         if (h > start) groups[ngroups++] = {2, TN, start, h - start};
     }
-    // pageable source: the copy has left g_host_tables when this returns
-    if (cudaMemcpyAsync(base, g_host_tables, o_acc, cudaMemcpyHostToDevice, s) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return JACPCG_ECUDA;
+    // the tables as kernel parameters, kChunk bytes per launch (o_acc is a
+    // multiple of 256, so every chunk is a whole number of 16-byte words)
+    for (size_t off = 0; off < o_acc; off += kChunk) {
+        const int n = (int)std::min<size_t>(kChunk, o_acc - off);
+        TableChunk c;
+        std::memcpy(c.bytes, g_host_tables + off, n);
+        upload_tables<<<1, 256, 0, s>>>(c, base + off, n);
     }
+    if (cudaGetLastError() != cudaSuccess) return JACPCG_ECUDA;
     const DevInst *d_insts = reinterpret_cast<const DevInst *>(base + o_insts);
     DevAccum acc;
     acc.flags = reinterpret_cast<int32_t *>(base + o_acc);

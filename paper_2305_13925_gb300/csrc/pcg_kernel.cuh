@@ -20,7 +20,10 @@
 //   1 Algorithm 1 as printed: r = D^{-1} b, m = r, alpha = r^H r / m^H D^{-1} A m
 //     (complex), w += alpha m, r -= alpha D^{-1} A m, b = r'^H r' / r^H r,
 //     m = r' + b m;
-//   2 plain CG (variant 0 with D = I).
+//   2 plain CG (variant 0 with D = I);
+//   3 JOR (Sec. III-A), w^{t+1} = (I - omega D^{-1} A) w^t + omega D^{-1} b in
+//     residual form: p = omega D^{-1} r, x += p, r -= A p (no step or direction
+//     ratios; only ||r|| is reduced, for the stopping test).
 // Stopping (tol > 0): a column stops before an update once
 // ||r||^2 <= tol^2 ||b||^2 (Alg. 1: ||D r||^2).
 // Right-hand side (mode): 0 solves A X = B (B = I_K, or the instance's
@@ -59,6 +62,7 @@ __global__ void __launch_bounds__(NW * 32) pcg_kernel(const DevInst *__restrict_
     const float tol2 = tl > 0.f ? tl * tl : -1.f;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float2 *__restrict__ Ag = in.A;
+    const float om = VAR == 3 ? in.omega : 1.f;   // JOR relaxation factor
 
     if (RESIDENT) {  // whole A into shared memory, 16 bytes per access
         const float4 *src = reinterpret_cast<const float4 *>(Ag);
@@ -116,6 +120,7 @@ __global__ void __launch_bounds__(NW * 32) pcg_kernel(const DevInst *__restrict_
             // a warm start keeps b in r until the first pass has formed A X0
             r[i][c] = (VAR == 1 && !warm) ? make_float2(dv[i] * b.x, dv[i] * b.y) : b;
             p[i][c] = make_float2(dv[i] * b.x, dv[i] * b.y);   // z = D^{-1} r (standard, CG); m = r (Alg. 1)
+            if (VAR == 3) p[i][c] = make_float2(om * p[i][c].x, om * p[i][c].y);   // omega D^{-1} r
             const float2 z = make_float2(dv[i] * r[i][c].x, dv[i] * r[i][c].y);
             if (VAR == 1) {
                 comp_fma(rz, r[i][c].x, r[i][c].x);
@@ -248,7 +253,7 @@ __global__ void __launch_bounds__(NW * 32) pcg_kernel(const DevInst *__restrict_
                     } else {
                         r[i][c] = rw;
                         const float2 z = make_float2(dv[i] * rw.x, dv[i] * rw.y);
-                        p[i][c] = z;
+                        p[i][c] = VAR == 3 ? make_float2(om * z.x, om * z.y) : z;
                         comp_fma(rz, rw.x, z.x);
                         comp_fma(rz, rw.y, z.y);
                         comp_fma(rs, rw.x, rw.x);
@@ -267,7 +272,28 @@ __global__ void __launch_bounds__(NW * 32) pcg_kernel(const DevInst *__restrict_
         // scalars and vector updates, column by column
 #pragma unroll
         for (int c = 0; c < CW; ++c) {
-            if (VAR == 1) {
+            if (VAR == 3) {
+                // JOR: x += p, r -= A p, p = omega D^{-1} r
+                const bool upd = !done[c];
+                Comp rs = {0.f, 0.f};
+#pragma unroll
+                for (int i = 0; i < RPL; ++i) {
+                    if (upd) {
+                        x[i][c].x += p[i][c].x;
+                        x[i][c].y += p[i][c].y;
+                        r[i][c].x -= q[i][c].x;
+                        r[i][c].y -= q[i][c].y;
+                        p[i][c] = make_float2(om * (dv[i] * r[i][c].x), om * (dv[i] * r[i][c].y));
+                    }
+                    comp_fma(rs, r[i][c].x, r[i][c].x);
+                    comp_fma(rs, r[i][c].y, r[i][c].y);
+                }
+                rs = comp_warp_allreduce(rs);
+                if (upd) {
+                    res2[c] = rs.s + rs.c;
+                    ++its[c];
+                }
+            } else if (VAR == 1) {
                 // u = D^{-1} A m, den = m^H u (complex)
                 Comp dr = {0.f, 0.f}, di = {0.f, 0.f};
 #pragma unroll
@@ -417,6 +443,7 @@ cudaError_t launch_cfg(int variant, const DevInst *insts, const int2 *blocks, in
         case 0: go(pcg_kernel<KC, CW, NW, RES, 0>); break;
         case 1: go(pcg_kernel<KC, CW, NW, RES, 1>); break;
         case 2: go(pcg_kernel<KC, CW, NW, RES, 2>); break;
+        case 3: go(pcg_kernel<KC, CW, NW, RES, 3>); break;
         default: return cudaErrorInvalidValue;
     }
     return e;

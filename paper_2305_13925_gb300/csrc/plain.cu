@@ -200,7 +200,7 @@ extern "C" jacpcg_status jacpcg_precode_plain(const jacpcg_instance *inst, int n
         if (!std::isfinite(q.xi) || q.xi < 0.0 || (q.K > q.M && !(q.xi > 0.0))) return JACPCG_EINVAL;
         if (q.max_iter < 0 || q.max_iter > 4096 || !std::isfinite(q.tol)) return JACPCG_EINVAL;
         if (q.h_dtype != JACPCG_H_C64) return JACPCG_EINVAL;   // complex64 H only
-        if (q.B || q.X0) return JACPCG_EINVAL;                // B = I, zero start only
+        if (q.B || q.X0 || q.sinr) return JACPCG_EINVAL;      // B = I, zero start only, no SINR
         if (q.K > maxK) maxK = q.K;
     }
     // workspace: A, X, R, P, Q (K x K complex), dinv, rho, res2 (K floats), its (K ints), flags

@@ -34,7 +34,7 @@ def to_dev_bf16(H: np.ndarray, torch):
 def run(Hs, xis, variant="standard", T=6, tol=0.0, want_X=False, want_A=False, power=1.0,
         plan=False, graph=False, repeats=1, precision="fp32", prec=None, bf16=False,
         refine_sweeps=0, want_hist=False, refine_fp64=False, simt_iteration=False, refine_tol=0.0,
-        refine_solve_tol=0.0):
+        refine_solve_tol=0.0, omegas=None):
     """Precode each (M_i, K_i) channel of ``Hs`` in one batch on the GPU."""
     import torch
     n = len(Hs)
@@ -45,7 +45,8 @@ def run(Hs, xis, variant="standard", T=6, tol=0.0, want_X=False, want_A=False, p
     hist = [torch.full((refine_sweeps + 1,), -1.0, device="cuda") for _ in Hs] if want_hist else None
     insts = [binding.instance(Hd[i], Wd[i], xis[i], T, tol, power,
                               X=Xd[i] if want_X else None, A=Ad[i] if want_A else None,
-                              resid_hist=hist[i] if want_hist else None)
+                              resid_hist=hist[i] if want_hist else None,
+                              omega=0.0 if omegas is None else float(omegas[i]))
              for i in range(n)]
     status = torch.full((n,), -1, dtype=torch.int32, device="cuda")
     iters = torch.full((n,), -1, dtype=torch.int32, device="cuda")

@@ -17,7 +17,7 @@ HEADER = ROOT / "include" / "jacpcg.h"
 def declared_functions():
     text = HEADER.read_text()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(jacpcg_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(jacpcg_[a-z0-9_]+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")

@@ -98,7 +98,8 @@ def check_batch(Hs, xis, variant="standard", T=6, tol_w=None, **kw):
         assert e <= bar, (i, H.shape, e, bar)
         assert rel_fro(out["A"][i], ref["A"]) <= 1e-6
         assert rel_fro(out["X"][i], ref["X"]) <= bar
-        assert abs(out["beta"][i] - ref["beta"]) <= 1e-5 * ref["beta"]
+        # beta = sqrt(P) / ||W||_F: its relative error is at most W's
+        assert abs(out["beta"][i] - ref["beta"]) <= max(1e-5, bar) * ref["beta"]
         assert out["iters"][i] == ref["iters"]
         assert out["status"][i] == 0
     return out, errs
@@ -154,6 +155,27 @@ def test_alg1_variant_parity():
     H, xi = C.generate_batch("single_256x16", 6, 5)
     Hn = [h / np.maximum(np.linalg.norm(h, axis=0), 1e-30)[None, :] for h in H]
     check_batch(Hn, list(xi), variant="alg1", T=8)
+
+
+@pytest.mark.parametrize("preset,n,seed,Ts,precision", [
+    ("single_256x16", 6, 5, (2, 3), "fp32"),
+    ("batched_1024x64", 4, 1, (2, 4), "tf32x3"),
+])
+def test_alg1_variant_parity_complex_step(preset, n, seed, Ts, precision):
+    """Algorithm 1 on the channels as generated: shadowing spreads the diagonal
+    of P over one to three decades, so C^{-1} P is not Hermitian and every step
+    alpha is complex.  Element by element against the oracle at T = 2..4, before
+    the printed iteration drifts; the bar (at most 2e-3 here) is far below the
+    distance (>= 1.7e-2 on these channels) of an evaluation whose step
+    denominator is conjugated."""
+    H, xi = C.generate_batch(preset, n, seed)
+    for h, x in zip(H, xi):
+        d = np.real(np.diag(O.gram(C.round_complex64(h), x)))
+        assert d.max() > 20 * d.min()
+    for T in Ts:
+        bars = [tol_for(C.round_complex64(h), x, "alg1", T) for h, x in zip(H, xi)]
+        assert max(bars) <= 2e-3, bars
+        check_batch(list(H), list(xi), variant="alg1", T=T, precision=precision)
 
 
 @pytest.mark.parametrize("K,M", [(1, 64), (2, 9), (3, 130), (8, 256), (17, 1000), (33, 96),

@@ -1,8 +1,8 @@
 """jacpcg_precode_noalloc, the entry point for callers that cannot allocate
-(code running under someone else's stream capture, real-time slot loops,
-integrations with memory fixed at start-up).  It must give the same
-precoders as jacpcg_precode, call after call, while using only its static
-device scratch array.  This file is collected last on purpose."""
+(real-time slot loops that forbid allocator latency, integrations whose
+memory was fixed at start-up).  It must give the same precoders as
+jacpcg_precode within the W tolerance, call after call, while using only its
+static device scratch array.  This file is collected last on purpose."""
 import numpy as np
 import pytest
 
@@ -57,19 +57,26 @@ def test_noalloc_matches_precode_on_two_calls(torch_gpu):
         assert (status.cpu().numpy() == 0).all()
     stream = torch.cuda.current_stream().cuda_stream
     free = []
+    outs = [(torch.full((n,), -1, dtype=torch.int32, device="cuda"),
+             torch.zeros(n, dtype=torch.float32, device="cuda")) for _ in range(2)]
+    torch.cuda.synchronize()
+    torch_mem = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved())
     for call in range(2):
         for w in Wd:
             w.fill_(complex(np.nan, np.nan))
-        status = torch.full((n,), -1, dtype=torch.int32, device="cuda")
-        beta = torch.zeros(n, dtype=torch.float32, device="cuda")
-        binding.jacpcg_precode_noalloc(insts, "standard", status, None, None, beta, stream)
+        st_call, beta_call = outs[call]
+        binding.jacpcg_precode_noalloc(insts, "standard", st_call, None, None, beta_call, stream)
         torch.cuda.synchronize()
         free.append(torch.cuda.mem_get_info()[0])
-        assert (status.cpu().numpy() == 0).all(), call
-        assert (beta.cpu().numpy() > 0).all()
+        assert (st_call.cpu().numpy() == 0).all(), call
+        assert (beta_call.cpu().numpy() > 0).all()
         for i, w in enumerate(Wd):
             assert _rel(w.cpu().numpy(), ref[i]) <= TOL_W, (call, i)
-    assert free[0] == free[1]          # the second call took no device memory
+    # neither call took memory from torch's allocator; and, as supporting
+    # evidence only (other processes share the device's free-memory figure),
+    # the device's free memory did not move between the two calls
+    assert (torch.cuda.memory_allocated(), torch.cuda.memory_reserved()) == torch_mem
+    assert free[0] == free[1]
 
 
 def test_noalloc_rejects_batches_beyond_its_scratch(torch_gpu):
