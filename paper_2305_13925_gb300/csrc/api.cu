@@ -113,7 +113,7 @@ struct Arena {
 
 // What one kernel launch of a plan covers.
 struct Launch {
-    enum Kind { GRAM, PCG, HX, GRAM_TC, GRAM_TCX, HX_TC, HX_TCW, PCG_TC, CHOL, SINR } kind;
+    enum Kind { GRAM, PCG, HX, GRAM_TC, GRAM_TCX, HX_TC, HX_TCW, PCG_TC, CHOL, SINR, TCW_PREP, PCG_TCW } kind;
     int phase;        // 0 Gram, 1 iteration, 2 W = H X, 3 SINR (after the power factor)
     int param;        // TB (Gram), KC (iteration), TN (W = H X)
     size_t list_off;  // byte offset of its work list inside the plan block
@@ -209,8 +209,8 @@ int n_cols(const jacpcg_instance &q) { return q.B ? q.n_rhs : q.K; }
 
 // Byte layout of one plan block.
 struct Layout {
-    size_t insts, gram, tcl, gdl, gxl, pcg, hx, hxl, hwl, res, sinr, accum, ws, total;
-    int n_gram, n_pcg, n_hx, n_res, n_gd, n_gx, n_hw, n_sinr;
+    size_t insts, gram, tcl, gdl, gxl, pcg, hx, hxl, hwl, res, sinr, twl, twj, accum, ws, total;
+    int n_gram, n_pcg, n_hx, n_res, n_gd, n_gx, n_hw, n_sinr, n_twj;
     bool refine;
     std::vector<size_t> ws_off;   // per instance
 };
@@ -230,14 +230,18 @@ int n_pblocks(const jacpcg_instance &q, const int *shape_idx) {
     const int per = s.CW * s.NW;
     return (n_cols(q) + per - 1) / per;
 }
-// A, X, 1/diag, W partials; then R and its column norms for refinement
-size_t inst_ws_bytes(const jacpcg_instance &q, bool refine) {
+// A, X, 1/diag, W partials; then R and its column norms for refinement; then,
+// for the 128 and 256 classes' tensor-core iteration, A split into its
+// streamed TF32 stages (4 KC^2 floats)
+size_t inst_ws_bytes(const jacpcg_instance &q, bool refine, bool tcw) {
     const size_t KC = k_class(q.K);
     size_t b = align_up(KC * KC * sizeof(float2)) * 2 + align_up(KC * sizeof(float)) +
                align_up(n_wtiles(q) * sizeof(float));
     if (refine) b += align_up(KC * KC * sizeof(float2)) + align_up((2 * KC + 2) * sizeof(float));
+    if (tcw) b += align_up(4 * KC * KC * sizeof(float));
     return b;
 }
+constexpr int TCW_NB = 32;   // columns per CTA of the 128 / 256-class tensor-core iteration
 
 // K classes whose Gram runs on the tensor cores at this precision (64 x 64
 // user-group blocks: one diagonal job for the 64 class, 2 + 1 for 128, 4 + 6
@@ -253,10 +257,16 @@ bool pcg_on_tc(const jacpcg_config &cfg, int KC) {
     return !(cfg.flags & JACPCG_FLAG_SIMT_ITERATION) && cfg.precision == JACPCG_TF32X3 && KC == 64 &&
            (cfg.variant == JACPCG_STANDARD || cfg.variant == JACPCG_CG);
 }
+// ... and, for the 128 and 256 classes, the streamed-A tensor-core iteration
+bool pcg_on_tcw(const jacpcg_config &cfg, int KC) {
+    return !(cfg.flags & JACPCG_FLAG_SIMT_ITERATION) && cfg.precision == JACPCG_TF32X3 && KC >= 128 &&
+           (cfg.variant == JACPCG_STANDARD || cfg.variant == JACPCG_CG);
+}
 
-Layout make_layout(const jacpcg_instance *inst, int n, bool refine, const int *shape_idx) {
+Layout make_layout(const jacpcg_config &cfg, const jacpcg_instance *inst, int n, bool refine,
+                   const int *shape_idx) {
     Layout L{};
-    L.n_gram = L.n_pcg = L.n_hx = L.n_res = L.n_gd = L.n_gx = L.n_hw = L.n_sinr = 0;
+    L.n_gram = L.n_pcg = L.n_hx = L.n_res = L.n_gd = L.n_gx = L.n_hw = L.n_sinr = L.n_twj = 0;
     L.refine = refine;
     for (int i = 0; i < n; ++i) {
         if (refine) L.n_res += (n_cols(inst[i]) + RES_CB - 1) / RES_CB;
@@ -268,6 +278,7 @@ Layout make_layout(const jacpcg_instance *inst, int n, bool refine, const int *s
         L.n_pcg += n_pblocks(inst[i], shape_idx);
         L.n_hx += n_wtiles(inst[i]);
         if (inst[i].sinr) L.n_sinr += (inst[i].K + 7) / 8;
+        if (pcg_on_tcw(cfg, k_class(inst[i].K))) L.n_twj += (n_cols(inst[i]) + TCW_NB - 1) / TCW_NB;
     }
     size_t o = 0;
     L.insts = o;  o += align_up(sizeof(DevInst) * n);
@@ -281,12 +292,14 @@ Layout make_layout(const jacpcg_instance *inst, int n, bool refine, const int *s
     L.hwl = o;    o += align_up(sizeof(int2) * L.n_hw);
     L.res = o;    o += align_up(sizeof(int2) * L.n_res);
     L.sinr = o;   o += align_up(sizeof(int2) * L.n_sinr);
+    L.twl = o;    o += align_up(sizeof(int) * n);
+    L.twj = o;    o += align_up(sizeof(int2) * L.n_twj);
     L.accum = o;  o += align_up(sizeof(int32_t) * n) * 3;
     L.ws = o;
     L.ws_off.resize(n);
     for (int i = 0; i < n; ++i) {
         L.ws_off[i] = o;
-        o += inst_ws_bytes(inst[i], refine);
+        o += inst_ws_bytes(inst[i], refine, pcg_on_tcw(cfg, k_class(inst[i].K)));
     }
     L.total = o;
     return L;
@@ -328,6 +341,9 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
         d.ldb = q.B ? q.ldb : 0;
         d.ncols = n_cols(q);
         d.X0 = static_cast<const float2 *>(q.X0);
+        if (pcg_on_tcw(ctx->cfg, KC)) {   // the split stages follow everything else
+            d.As = reinterpret_cast<float *>(w + inst_ws_bytes(q, L.refine, false));
+        }
         if (L.refine) {
             const size_t base = 2 * align_up((size_t)KC * KC * sizeof(float2)) + align_up(KC * sizeof(float)) +
                                 align_up(n_wtiles(q) * sizeof(float));
@@ -386,6 +402,27 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
     int2 *pb = reinterpret_cast<int2 *>(host + L.pcg);
     int p = 0;
     if (nt) launches.push_back({Launch::PCG_TC, 1, 64, L.tcl, nt});
+    // the 128 and 256 classes on the tensor cores: split A once, then the jobs
+    // (instance, 32 columns), instance-major so that the CTAs of an instance
+    // stream its A from L2 at about the same time
+    {
+        int *twl = reinterpret_cast<int *>(host + L.twl);
+        int2 *twj = reinterpret_cast<int2 *>(host + L.twj);
+        int ni = 0, nj = 0;
+        for (int KC : {128, 256}) {
+            if (!pcg_on_tcw(ctx->cfg, KC)) continue;
+            const int i0 = ni, j0 = nj;
+            for (int i = 0; i < n; ++i) {
+                if (k_class(inst[i].K) != KC) continue;
+                twl[ni++] = i;
+                for (int c0 = 0; c0 < n_cols(inst[i]); c0 += TCW_NB) twj[nj++] = make_int2(i, c0);
+            }
+            if (ni > i0) {
+                launches.push_back({Launch::TCW_PREP, 1, KC, L.twl + i0 * sizeof(int), ni - i0});
+                launches.push_back({Launch::PCG_TCW, 1, KC, L.twj + j0 * sizeof(int2), nj - j0});
+            }
+        }
+    }
     if (ctx->cfg.variant == JACPCG_DIRECT) {   // direct solve: instance lists per K class
         int c = 0;
         for (int KC : {8, 16, 32, 64, 128, 256}) {
@@ -401,7 +438,7 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
         const int sh = ctx->pcg_shape_idx[kc_index(KC)];
         const PcgShape s = pcg_shape(KC, sh);
         for (int i = 0; i < n; ++i) {
-            if (k_class(inst[i].K) != KC || pcg_on_tc(ctx->cfg, KC)) continue;
+            if (k_class(inst[i].K) != KC || pcg_on_tc(ctx->cfg, KC) || pcg_on_tcw(ctx->cfg, KC)) continue;
             for (int c0 = 0; c0 < n_cols(inst[i]); c0 += s.CW * s.NW) pb[p++] = make_int2(i, c0);
         }
         if (p > start) launches.push_back({Launch::PCG, 1, KC, L.pcg + start * sizeof(int2), p - start, sh});
@@ -512,6 +549,13 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
                 case Launch::CHOL:
                     e = launch_chol(l.param, pl->d_insts, static_cast<const int *>(list), l.count, pl->acc, s);
                     break;
+                case Launch::TCW_PREP:
+                    e = launch_tcw_prep(l.param, pl->d_insts, static_cast<const int *>(list), l.count, s);
+                    break;
+                case Launch::PCG_TCW:
+                    e = launch_pcg_tcw(l.param, ctx->cfg.variant, pl->d_insts, static_cast<const int2 *>(list),
+                                       l.count, pl->acc, s, 0);
+                    break;
             }
             if (e != cudaSuccess) return cuda_fail(ctx, e);
             ++nl;
@@ -537,6 +581,10 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
                         e = launch_pcg_tc64(ctx->cfg.variant, pl->d_insts,
                                             reinterpret_cast<const int *>(pl->dev + l.list_off), l.count,
                                             pl->acc, &ctx->amap, ctx->arena.base, s, 1);
+                    else if (l.kind == Launch::PCG_TCW)
+                        e = launch_pcg_tcw(l.param, ctx->cfg.variant, pl->d_insts,
+                                           reinterpret_cast<const int2 *>(pl->dev + l.list_off), l.count,
+                                           pl->acc, s, 1);
                     else
                         continue;
                     if (e != cudaSuccess) return cuda_fail(ctx, e);
@@ -573,7 +621,7 @@ jacpcg_status make_plan(jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, int
     jacpcg_status st = validate(ctx, inst, n);
     if (st != JACPCG_OK) return st;
     const bool refine = ctx->cfg.refine_sweeps > 0;
-    Layout L = make_layout(inst, n, refine, ctx->pcg_shape_idx);
+    Layout L = make_layout(ctx->cfg, inst, n, refine, ctx->pcg_shape_idx);
     size_t off;
     if (!ctx->arena.alloc(L.total, &off)) return JACPCG_ENOMEM;
     jacpcg_plan *pl = new (std::nothrow) jacpcg_plan();
@@ -795,7 +843,7 @@ jacpcg_status jacpcg_create(const jacpcg_config *cfg, jacpcg_ctx **out) {
         q.K = cfg->max_K;
         std::vector<jacpcg_instance> v(cfg->max_instances, q);
         const int zero[6] = {0, 0, 0, 0, 0, 0};
-        bytes = 2 * make_layout(v.data(), cfg->max_instances, cfg->refine_sweeps > 0, zero).total;
+        bytes = 2 * make_layout(*cfg, v.data(), cfg->max_instances, cfg->refine_sweeps > 0, zero).total;
     }
     bytes = align_up(bytes);
     if (cudaMalloc(reinterpret_cast<void **>(&ctx->arena.base), bytes) != cudaSuccess) {
@@ -872,7 +920,7 @@ jacpcg_status jacpcg_plan_bytes(const jacpcg_ctx *ctx, const jacpcg_instance *in
     if (!bytes) return JACPCG_EINVAL;
     jacpcg_status st = validate(ctx, inst, n_inst);
     if (st != JACPCG_OK) return st;
-    *bytes = align_up(make_layout(inst, n_inst, ctx->cfg.refine_sweeps > 0, ctx->pcg_shape_idx).total);
+    *bytes = align_up(make_layout(ctx->cfg, inst, n_inst, ctx->cfg.refine_sweeps > 0, ctx->pcg_shape_idx).total);
     return JACPCG_OK;
 }
 

@@ -60,6 +60,12 @@ cudaError_t launch_hx_tc_wide(const DevInst *insts, const int2 *list, int n, Dev
 // floats, box 64 x 128), arena: its base address
 cudaError_t launch_pcg_tc64(int variant, const DevInst *insts, const int *list, int n, DevAccum acc,
                             const CUtensorMap *amap, const char *arena, cudaStream_t s, int mode);
+// tensor-core iteration for the K = 128 and 256 classes (standard or plain CG):
+// launch_tcw_prep splits each listed instance's A into the streamed TF32 stages
+// (DevInst::As), launch_pcg_tcw iterates; jobs: (instance, first of 32 columns)
+cudaError_t launch_tcw_prep(int KC, const DevInst *insts, const int *list, int n, cudaStream_t s);
+cudaError_t launch_pcg_tcw(int KC, int variant, const DevInst *insts, const int2 *jobs, int n, DevAccum acc,
+                           cudaStream_t s, int mode);
 // direct solve (Cholesky, forward and back substitution) of the K = KC class;
 // list: instance ids.  Replaces the iteration for the JACPCG_DIRECT variant.
 cudaError_t launch_chol(int KC, const DevInst *insts, const int *list, int n, DevAccum acc, cudaStream_t s);

@@ -37,9 +37,10 @@
 //   3. works column-wise: thread (warp w, lane l) owns column 8 w + (l mod 8)
 //      and the 16 complex rows g, g + 4, .., g + 60 with g = l / 8, holding
 //      x, r, p for them in registers; the per-column dot products are
-//      in-thread pairwise sums over its 16 rows and two xor shuffles across
-//      the four lanes of the column (commutative, so all four lanes obtain
-//      bit-identical totals and take identical decisions).
+//      compensated (Dot2): in-thread error-free sums over its 16 rows and two
+//      xor shuffles across the four lanes of the column, combined with
+//      commutative or exact operations only, so all four lanes obtain
+//      bit-identical totals and take identical decisions.
 // The tile strides (128-byte core matrices, 68-float rows of the Q tile) make
 // every P store, Q store and Q load free of shared-memory bank conflicts.
 #include "common.cuh"
@@ -107,20 +108,50 @@ __device__ __forceinline__ int team_or(int id, int pred) {
         : "memory");
     return r;
 }
-// pairwise sum of the thread's 16 row terms, fixed order
-__device__ __forceinline__ float sum16(const float (&v)[RPT]) {
-    float a[8];
+// Compensated per-column dot products (Dot2: each product split exactly by
+// an FMA, each addition by TwoSum; Ogita, Rump and Oishi 2005).  A thread
+// accumulates its 16 rows in order; the four lanes that share a column (lane
+// bits 3 and 4) then combine as (s_a + s_b, (c_a + c_b) + e): every operation
+// is commutative or exact, so all four lanes hold bit-identical totals.
+__device__ __forceinline__ Comp col_total(Comp v) {
 #pragma unroll
-    for (int u = 0; u < 8; ++u) a[u] = v[u] + v[u + 8];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) a[u] += a[u + 4];
-    return (a[0] + a[2]) + (a[1] + a[3]);
-}
-// total over the four lanes that share a column (lane bits 3 and 4)
-__device__ __forceinline__ float col_total(float v) {
-    v += __shfl_xor_sync(0xffffffffu, v, 8);
-    v += __shfl_xor_sync(0xffffffffu, v, 16);
+    for (int o = 8; o <= 16; o <<= 1) {
+        const float ws = __shfl_xor_sync(0xffffffffu, v.s, o);
+        const float wc = __shfl_xor_sync(0xffffffffu, v.c, o);
+        float s, e;
+        two_sum(v.s, ws, s, e);
+        v.s = s;
+        v.c = (v.c + wc) + e;
+    }
     return v;
+}
+__device__ __forceinline__ float comp_value(Comp v) { return v.s + v.c; }
+// Re sum_k conj(a_k) b_k over the thread's 16 rows, compensated and in a tree:
+// every product is split exactly by an FMA (TwoProduct), the 16 partial sums
+// are combined pairwise by TwoSum in 4 levels, and the errors are summed
+// alongside.  The same error-free steps as a sequential Dot2, but with no
+// chain of 32 dependent TwoSums on the iteration's critical path.
+__device__ __forceinline__ Comp dot2_rows(const float2 (&a)[RPT], const float2 (&b)[RPT]) {
+    float s[RPT], c[RPT];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const float p1 = a[k].x * b[k].x, p2 = a[k].y * b[k].y;
+        const float e1 = fmaf(a[k].x, b[k].x, -p1), e2 = fmaf(a[k].y, b[k].y, -p2);
+        float e;
+        two_sum(p1, p2, s[k], e);
+        c[k] = (e1 + e2) + e;
+    }
+#pragma unroll
+    for (int h = RPT / 2; h > 0; h >>= 1) {
+#pragma unroll
+        for (int k = 0; k < h; ++k) {
+            float sk, e;
+            two_sum(s[k], s[k + h], sk, e);
+            s[k] = sk;
+            c[k] = (c[k] + c[k + h]) + e;
+        }
+    }
+    return Comp{s[0], c[0]};
 }
 
 // MODE 0 solves A X = B from X0 (or 0); MODE 1 is a refinement correction
@@ -246,7 +277,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
         int itmax = 0;                     // iterations in which the column updated
         int notHPD = 0;
         {
-            float t0[RPT], t1[RPT];
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
                 const int i = g + 4 * k;
@@ -264,11 +294,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
                 x[k] = (warm && i < K && j < NCOL) ? in.X0[i + (size_t)j * K] : make_float2(0.f, 0.f);
                 r[k] = b;
                 p[k] = make_float2(dv[k] * b.x, dv[k] * b.y);
-                t1[k] = fmaf(b.x, b.x, b.y * b.y);
-                t0[k] = dv[k] * t1[k];
             }
-            rho = col_total(sum16(t0));    // r^H z
-            res2 = col_total(sum16(t1));   // ||r||^2 = ||b||^2
+            rho = comp_value(col_total(dot2_rows(r, p)));    // r^H z
+            res2 = comp_value(col_total(dot2_rows(r, r)));   // ||r||^2 = ||b||^2
             bn2c = res2;                   // stopping and reporting stay relative to ||b||
             btol = tol2 * bn2c;
         }
@@ -345,48 +373,38 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
                 q[k] = make_float2(S.Q[(2 * i) * QLD + j], S.Q[(2 * i + 1) * QLD + j]);
             }
             if (init) {   // r = b - A X0, then Step 1 from there
-                float t0[RPT], t1[RPT];
 #pragma unroll
                 for (int k = 0; k < RPT; ++k) {
                     r[k] = make_float2(r[k].x - q[k].x, r[k].y - q[k].y);
                     p[k] = make_float2(dv[k] * r[k].x, dv[k] * r[k].y);
-                    t1[k] = fmaf(r[k].x, r[k].x, r[k].y * r[k].y);
-                    t0[k] = dv[k] * t1[k];
                 }
-                rho = col_total(sum16(t0));
-                res2 = col_total(sum16(t1));
+                rho = comp_value(col_total(dot2_rows(r, p)));
+                res2 = comp_value(col_total(dot2_rows(r, r)));
                 continue;
             }
-            // lambda = r^H z / p^H A p
-            float pAp;
-            {
-                float tv[RPT];
-#pragma unroll
-                for (int k = 0; k < RPT; ++k) tv[k] = fmaf(p[k].x, q[k].x, p[k].y * q[k].y);
-                pAp = col_total(sum16(tv));
-            }
+            // lambda = r^H z / p^H A p (p^H A p is real for Hermitian A: Re part only)
+            const float pAp = comp_value(col_total(dot2_rows(p, q)));
             float lam = 0.f;
             if (pAp > 0.f) lam = rho / pAp;
             else if (res2 != 0.f && !done) notHPD = 1;
             if (done) lam = 0.f;
-            float t0[RPT], t1[RPT];
+            float2 z[RPT];
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
                 x[k].x = fmaf(lam, p[k].x, x[k].x);
                 x[k].y = fmaf(lam, p[k].y, x[k].y);
                 r[k].x = fmaf(-lam, q[k].x, r[k].x);
                 r[k].y = fmaf(-lam, q[k].y, r[k].y);
-                t1[k] = fmaf(r[k].x, r[k].x, r[k].y * r[k].y);   // ||r||^2 term
-                t0[k] = dv[k] * t1[k];                            // r^H z term, z = D^{-1} r
+                z[k] = make_float2(dv[k] * r[k].x, dv[k] * r[k].y);   // z = D^{-1} r
             }
-            const float rz_new = col_total(sum16(t0));
-            const float rr_new = col_total(sum16(t1));
+            const float rz_new = comp_value(col_total(dot2_rows(r, z)));
+            const float rr_new = comp_value(col_total(dot2_rows(r, r)));
             if (!done) {
                 const float beta = rho != 0.f ? rz_new / rho : 0.f;
 #pragma unroll
                 for (int k = 0; k < RPT; ++k) {
-                    p[k].x = fmaf(beta, p[k].x, dv[k] * r[k].x);
-                    p[k].y = fmaf(beta, p[k].y, dv[k] * r[k].y);
+                    p[k].x = fmaf(beta, p[k].x, z[k].x);
+                    p[k].y = fmaf(beta, p[k].y, z[k].y);
                 }
                 rho = rz_new;
                 res2 = rr_new;

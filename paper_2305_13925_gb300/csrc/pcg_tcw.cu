@@ -1,0 +1,527 @@
+// pcg_tcw.cu -- the Jac-PCG iteration with Q = A P on the tcgen05 tensor
+// cores for the K = 128 and K = 256 classes (Sec. III-B Steps 1-4, Eqs. 12-14
+// and 19-21; standard and plain-CG forms; right-hand side B = I, the
+// caller's symbol vectors, or the refinement residual; warm start from X0),
+// as pcg_tc.cu does for the 64 class.
+//
+// At these sizes A does not fit on one SM (K = 256: 512 KB complex, 1 MB as
+// TF32 head and tail), so it is streamed: once per instance a prep kernel
+// splits A into TF32 heads and exact tails of its real and imaginary parts
+// and stores them as MMA-ready 16 KB stages -- for row tile rt (128 rows) and
+// k-step ks (8 columns): [Ar_h | Ar_t | Ai_h | Ai_t], each a 128 x 8 tile in
+// the canonical no-swizzle K-major layout -- and each iteration streams the
+// stages through a 5-deep shared-memory ring with bulk copies (the TMA unit,
+// cp.async.bulk), completion counted in bytes on an mbarrier.  Real and
+// imaginary parts are kept apart (planar), so each byte of A is streamed once
+// per iteration rather than twice as in the 2 x 2 real expansion.
+//
+// The columns of X are independent systems sharing A, so a CTA owns 32 of
+// them (NB) for one instance.  Their P is resident in shared memory as the
+// MMA's B operand, laid out as 4 NB rows [Pr_h | Pi_h | Pr_t | Pi_t] along N
+// (TF32 heads of Re p and Im p, then the exact tails).  Per k-step:
+//   U += Ar_h [P_h | P_t]  (N = 128),   U[64..] += Ar_t P_h  (N = 64),
+//   V += Ai_h [P_h | P_t],              V[64..] += Ai_t P_h,
+// so U = Ar [Pr | Pi] and V = Ai [Pr | Pi] to 3xTF32 accuracy (columns 0-63
+// head x head, 64-127 both corrections), and
+//   Re q = Ar Pr - Ai Pi,   Im q = Ai Pr + Ar Pi.
+// U and V of both row tiles take 4 x 128 TMEM columns (K = 256: all 512).
+// The accumulation chain of a row tile is its KC / 8 k-steps.
+//
+// Roles: 8 warps own the vectors; each iteration they publish P (split) into
+// the B operand and vote on continuing (one barrier reduction), then thread 0
+// streams the iteration's KC / 128 x KC / 8 stages (waiting on `empty`),
+// thread 32 issues the MMAs (waiting on `full`) and commits to `qfull`, and
+// the epilogue -- idle while the product runs, so the roles take no warps of
+// their own and every thread may hold 255 registers -- waits on `qfull`,
+// moves U and V out of TMEM -- as Re q and Im q planes, column-major, into
+// the ring, idle until the next vote -- and works column-wise: thread
+// (warp w, lane l) owns column 4 w + (l mod 4) and the complex rows g, g + 8,
+// ... with g = l / 4; r lives in registers, p is read back from the B
+// operand (head + tail is exact), x is accumulated in the instance's
+// workspace X (which is also where a refinement correction X += dX lands),
+// and the per-column dot products are compensated (TwoProduct by FMA and
+// TwoSum in a tree, then three xor shuffles combined with commutative or
+// exact operations, so all eight lanes of a column hold bit-identical
+// totals).  Every wait is bounded; a timeout sets the instance's ETIMEOUT
+// flag and ends its iteration.
+#include "common.cuh"
+#include "kernels.h"
+#include "tc.cuh"
+
+namespace jacpcg {
+
+namespace {
+
+constexpr int NB = 32;                        // right-hand-side columns per CTA
+constexpr int THREADS = 256;                  // 8 warps: 2 per SM sub-partition, up to 255 registers
+constexpr int EPI = THREADS;
+constexpr int RING = 5;                       // stages in flight
+constexpr int STAGE = 16384;                  // bytes: four 128 x 8 TF32 tiles
+constexpr int TILE = 4096;
+constexpr int QLD = 136;                      // floats per staged Q column (128 rows + 8)
+constexpr uint32_t WAIT_LIMIT = 1u << 22;
+constexpr int BAR_EPI = 1;                    // named barrier of the epilogue warps
+
+template <int KC>
+struct Cfg {
+    static constexpr int RT = KC / 128;                      // row tiles
+    static constexpr int KS = KC / 8;                        // k-steps per row tile
+    static constexpr int NSTAGE = RT * KS;                   // stages per iteration
+    static constexpr uint32_t SBO_B = (KC / 4) * 128;        // bytes between 8-row groups of B (N)
+    static constexpr int B_BYTES = 4 * NB * KC * 4;          // the B operand
+    static constexpr int MR = KC / 8;                        // complex rows per epilogue thread
+    static constexpr uint32_t TMEM_COLS = RT == 2 ? 512 : 256;
+    static constexpr int SMEM = B_BYTES + RING * STAGE + KC * 4 + 256;
+    static_assert(2 * RT * NB * QLD * 4 <= RING * STAGE, "Q staging fits the ring");
+    static_assert(SMEM <= 227 * 1024, "shared memory");
+};
+
+struct Ctl {
+    uint64_t full[RING], empty[RING];
+    uint64_t qfull;
+    uint32_t tmem;
+    volatile int err;
+};
+
+__device__ __forceinline__ void epi_sync() {
+    asm volatile("bar.sync %0, %1;\n" ::"r"(BAR_EPI), "r"(EPI) : "memory");
+}
+__device__ __forceinline__ int epi_or(int pred) {
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.s32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.s32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"(pred), "r"(BAR_EPI), "r"(EPI)
+        : "memory");
+    return r;
+}
+// bulk copy global -> shared (both 16-byte aligned, bytes a multiple of 16),
+// completion as transaction bytes on `bar`
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
+        : "memory");
+}
+
+// byte offset of element (n, k) in the B operand (K-major, no swizzle)
+template <int KC>
+__device__ __forceinline__ uint32_t b_off(int n, int k) {
+    return (uint32_t)(n >> 3) * Cfg<KC>::SBO_B + (uint32_t)(k >> 2) * 128u + (uint32_t)(n & 7) * 16u +
+           (uint32_t)(k & 3) * 4u;
+}
+
+// ---------------------------------------------------------------------------
+// A (complex, workspace ld KC) -> the streamed stages: one CTA per (instance,
+// stage); element (r, k) of a 128 x 8 tile at (r / 8) 256 + (k / 4) 128 +
+// (r mod 8) 16 + (k mod 4) 4 bytes (LBO 128 along K, SBO 256 along M).
+template <int KC>
+__global__ void __launch_bounds__(256) tcw_prep_kernel(const DevInst *__restrict__ insts,
+                                                      const int *__restrict__ list) {
+    using C = Cfg<KC>;
+    const int id = list[blockIdx.x / C::NSTAGE];
+    const int s = blockIdx.x % C::NSTAGE, rt = s / C::KS, ks = s % C::KS;
+    const DevInst &in = insts[id];
+    char *dst = reinterpret_cast<char *>(in.As) + (size_t)s * STAGE;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int e = threadIdx.x + 256 * u, r = e & 127, k = e >> 7;
+        const float2 v = in.A[(size_t)(rt * 128 + r) + (size_t)(ks * 8 + k) * KC];
+        float rh, rl, ih, il;
+        tc::split_tf32(v.x, rh, rl);
+        tc::split_tf32(v.y, ih, il);
+        const uint32_t o = (uint32_t)(r >> 3) * 256u + (uint32_t)(k >> 2) * 128u + (uint32_t)(r & 7) * 16u +
+                           (uint32_t)(k & 3) * 4u;
+        *reinterpret_cast<float *>(dst + o) = rh;
+        *reinterpret_cast<float *>(dst + TILE + o) = rl;
+        *reinterpret_cast<float *>(dst + 2 * TILE + o) = ih;
+        *reinterpret_cast<float *>(dst + 3 * TILE + o) = il;
+    }
+}
+
+// Compensated sum over the thread's MR rows of Re conj(a_m) b_m, where f(m,
+// a, b) yields the pair of row m: rows in chunks of 8, each chunk a TwoSum
+// tree over the TwoProduct-split products, the chunks combined the same way,
+// then the 8 lanes of the column (lane bits 2-4) by three xor shuffles.  Only
+// one chunk of operands is live at a time.
+template <int MR, typename F>
+__device__ __forceinline__ float col_sum2(F f) {
+    constexpr int CH = MR < 8 ? MR : 8;
+    constexpr int NCH = MR / CH;
+    float S[NCH], Cc[NCH];
+#pragma unroll
+    for (int u = 0; u < NCH; ++u) {
+        float s[CH], c[CH];
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+            float2 a, b;
+            f(u * CH + k, a, b);
+            const float p1 = a.x * b.x, p2 = a.y * b.y;
+            const float e1 = fmaf(a.x, b.x, -p1), e2 = fmaf(a.y, b.y, -p2);
+            float e;
+            two_sum(p1, p2, s[k], e);
+            c[k] = (e1 + e2) + e;
+        }
+#pragma unroll
+        for (int h = CH / 2; h > 0; h >>= 1) {
+#pragma unroll
+            for (int k = 0; k < h; ++k) {
+                float sk, e;
+                two_sum(s[k], s[k + h], sk, e);
+                s[k] = sk;
+                c[k] = (c[k] + c[k + h]) + e;
+            }
+        }
+        S[u] = s[0];
+        Cc[u] = c[0];
+    }
+#pragma unroll
+    for (int h = NCH / 2; h > 0; h >>= 1) {
+#pragma unroll
+        for (int k = 0; k < h; ++k) {
+            float sk, e;
+            two_sum(S[k], S[k + h], sk, e);
+            S[k] = sk;
+            Cc[k] = (Cc[k] + Cc[k + h]) + e;
+        }
+    }
+    float vs = S[0], vc = Cc[0];
+#pragma unroll
+    for (int o = 4; o <= 16; o <<= 1) {
+        const float ws = __shfl_xor_sync(0xffffffffu, vs, o);
+        const float wc = __shfl_xor_sync(0xffffffffu, vc, o);
+        float sn, e;
+        two_sum(vs, ws, sn, e);
+        vs = sn;
+        vc = (vc + wc) + e;
+    }
+    return vs + vc;
+}
+
+// MODE 0 solves A X = B from X0 (or 0); MODE 1 is a refinement correction
+// solve (right-hand side R, X += dX; instances that stopped refining are
+// skipped).  jobs: (instance, first column), NB columns each.
+template <int KC, int VAR, int MODE>
+__global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__restrict__ insts,
+                                                             const int2 *__restrict__ jobs, int n_jobs,
+                                                             DevAccum acc_out) {
+    using C = Cfg<KC>;
+    constexpr int MR = C::MR;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    float *dvs = reinterpret_cast<float *>(smem + C::B_BYTES + RING * STAGE);
+    Ctl &S = *reinterpret_cast<Ctl *>(smem + C::B_BYTES + RING * STAGE + KC * 4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < RING; ++i) {
+            tc::mbar_init(&S.full[i], 1);
+            tc::mbar_init(&S.empty[i], 1);
+        }
+        tc::mbar_init(&S.qfull, 1);
+        S.err = 0;
+        tc::mbar_init_fence();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(&S.tmem, C::TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = S.tmem;
+    const uint32_t b_base = tc::smem_u32(smem), r_base = b_base + C::B_BYTES;
+    uint32_t pc = 0, mc = 0;   // stages produced (thread 0) / consumed (thread 32)
+    // One iteration's A x P: thread 0 streams the KC / 128 x KC / 8 stages into the
+    // ring, thread 32 issues their MMAs (per stage: head x [P_h | P_t] and tail x
+    // P_h, Ar then Ai) and commits to qfull; the other threads go on to wait.
+    auto product = [&](const char *src) {
+        if (threadIdx.x == 0) {
+            for (int s = 0; s < C::NSTAGE; ++s, ++pc) {
+                const int slot = pc % RING;
+                if (!tc::mbar_wait(&S.empty[slot], ((pc / RING) & 1) ^ 1, WAIT_LIMIT)) S.err = 1;
+                tc::mbar_arrive_expect_tx(&S.full[slot], STAGE);
+                bulk_load(r_base + slot * STAGE, src + (size_t)s * STAGE, STAGE, &S.full[slot]);
+            }
+        } else if (threadIdx.x == 32) {
+            constexpr uint32_t id128 = tc::idesc_tf32(128, 4 * NB);
+            constexpr uint32_t id64 = tc::idesc_tf32(128, 2 * NB);
+            tc::tc_fence_after();
+            for (int s = 0; s < C::NSTAGE; ++s, ++mc) {
+                const int slot = mc % RING, rt = s / C::KS, ks = s % C::KS;
+                if (!tc::mbar_wait(&S.full[slot], (mc / RING) & 1, WAIT_LIMIT)) S.err = 1;
+                tc::tc_fence_after();
+                const uint32_t a0 = r_base + slot * STAGE;
+                const uint64_t bd = tc::smem_desc(b_base + ks * 256, 128, C::SBO_B);
+                const uint32_t du = tmem + rt * 256, dvv = du + 128;
+                const uint32_t acc = ks > 0 ? 1u : 0u;
+                tc::mma_tf32(du, tc::smem_desc(a0, 128, 256), bd, id128, acc);
+                tc::mma_tf32(du + 64, tc::smem_desc(a0 + TILE, 128, 256), bd, id64, 1u);
+                tc::mma_tf32(dvv, tc::smem_desc(a0 + 2 * TILE, 128, 256), bd, id128, acc);
+                tc::mma_tf32(dvv + 64, tc::smem_desc(a0 + 3 * TILE, 128, 256), bd, id64, 1u);
+                tc::mma_commit(&S.empty[slot]);   // the slot is free once these have read it
+            }
+            tc::mma_commit(&S.qfull);
+        }
+        __syncwarp();
+    };
+    {
+        // ---- epilogue: the vectors of 32 columns, column-wise ----
+        const int cl = 4 * warp + (lane & 3);   // local column
+        const int g = lane >> 2;                // rows g + 8 m
+        const int qw = warp & 3, hh = warp >> 2;   // TMEM lane quarter and column half of the readout
+        float *Qre = reinterpret_cast<float *>(smem + C::B_BYTES);
+        float *Qim = Qre + C::RT * NB * QLD;
+        unsigned char *Bop = smem;
+        auto bget = [&](int n, int k) { return *reinterpret_cast<const float *>(Bop + b_off<KC>(n, k)); };
+        auto bset = [&](int n, int k, float v) { *reinterpret_cast<float *>(Bop + b_off<KC>(n, k)) = v; };
+        // P (head and tail of Re and Im) of the owned rows into the B operand
+        auto publish = [&](int m, float2 v) {
+            const int i = g + 8 * m;
+            float h, l;
+            tc::split_tf32(v.x, h, l);
+            bset(cl, i, h);
+            bset(2 * NB + cl, i, l);
+            tc::split_tf32(v.y, h, l);
+            bset(NB + cl, i, h);
+            bset(3 * NB + cl, i, l);
+        };
+        auto pget = [&](int m) {   // head + tail: exactly the published value
+            const int i = g + 8 * m;
+            return make_float2(bget(cl, i) + bget(2 * NB + cl, i), bget(NB + cl, i) + bget(3 * NB + cl, i));
+        };
+        auto qget = [&](int m) {
+            const int i = g + 8 * m;
+            const int o = ((i >> 7) * NB + cl) * QLD + (i & 127);
+            return make_float2(Qre[o], Qim[o]);
+        };
+        uint32_t qp = 0;
+        int err = 0;
+        for (int jj = blockIdx.x; jj < n_jobs; jj += gridDim.x) {
+            const int2 job = jobs[jj];
+            const int id = job.x;
+            const DevInst &in = insts[id];
+            if (MODE == 1 && in.rctl[1] != 0.f) continue;   // uniform: every role skips it
+            const int K = in.K, T = in.max_iter, NCOL = in.ncols;
+            const int j = job.y + cl;
+            const bool valid = j < NCOL;
+            const bool warm = MODE == 0 && in.X0 != nullptr;
+            const float tl = (MODE == 1 && in.rsolve_tol > 0.f) ? in.rsolve_tol : in.tol;
+            const float tol2 = tl > 0.f ? tl * tl : -1.f;
+            float2 *X = in.X + (size_t)(valid ? j : 0) * KC;   // the iterate (workspace, ld KC)
+            epi_sync();   // the previous instance's readers of dvs are done
+            for (int i = threadIdx.x; i < KC; i += EPI) dvs[i] = (i < K) ? (VAR == 2 ? 1.f : in.dinv[i]) : 0.f;
+            epi_sync();
+            // ---- Step 1: r = b, x = x0 (mode 0), p = D^{-1} r ----
+            float2 r[MR];
+#pragma unroll
+            for (int m = 0; m < MR; ++m) {
+                const int i = g + 8 * m;
+                float2 b = make_float2(0.f, 0.f);
+                if (valid && i < K) {
+                    if (MODE == 1) b = in.R[i + (size_t)j * KC];                    // refinement residual
+                    else if (!in.B) b.x = (i == j) ? 1.f : 0.f;                      // B = I
+                    else b = in.B[i + (size_t)j * in.ldb];                           // symbol vectors
+                }
+                r[m] = b;
+                if (MODE == 0 && valid)
+                    X[i] = (warm && i < K) ? in.X0[i + (size_t)j * K] : make_float2(0.f, 0.f);
+                const float d = dvs[i];
+                // the warm pass forms A X0 first; columns beyond the right-hand sides carry 0
+                publish(m, !valid ? make_float2(0.f, 0.f) : warm ? X[i] : make_float2(d * b.x, d * b.y));
+            }
+            float rho = col_sum2<MR>([&](int m, float2 &a, float2 &b) {
+                const float d = dvs[g + 8 * m];
+                a = r[m];
+                b = make_float2(d * r[m].x, d * r[m].y);
+            });
+            float res2 = col_sum2<MR>([&](int m, float2 &a, float2 &b) { a = r[m]; b = r[m]; });
+            const float bn2 = res2;   // stopping and reporting stay relative to ||b||
+            const float btol = tol2 * bn2;
+            bool done = !valid;
+            int itmax = 0, notHPD = 0;
+            for (int t = warm ? -1 : 0;; ++t) {
+                const bool init = t < 0;
+                if (!init && tol2 > 0.f && res2 <= btol) done = true;
+                const int any = (init || (!done && t < T)) ? 1 : 0;
+                // P and the staging reads before the async proxy, the TMEM reads
+                // before the next MMAs; one decision for the whole CTA
+                tc::fence_proxy_async_smem();
+                tc::tc_fence_before();
+                const int cont = epi_or(any && !S.err);
+                if (!cont) break;
+                product(reinterpret_cast<const char *>(in.As));
+                // ---- Q = A P: U, V -> Re q, Im q planes in the ring ----
+                if (!tc::mbar_wait(&S.qfull, qp & 1, WAIT_LIMIT)) {
+                    err = 1;
+                    S.err = 1;
+                }
+                ++qp;
+                __syncwarp();   // the TMEM loads below are warp-collective
+                tc::tc_fence_after();
+#pragma unroll
+                for (int rt = 0; rt < C::RT; ++rt) {
+                    const uint32_t tb = tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)(rt * 256 + 16 * hh);
+                    const int o = (rt * NB + 16 * hh) * QLD + 32 * qw + lane;
+                    float a[16], b[16], c[16], d[16];
+                    // Re q = Ar Pr - Ai Pi
+                    tc::tmem_ld16(tb, a);
+                    tc::tmem_ld16(tb + 64, b);
+                    tc::tmem_ld16(tb + 128 + NB, c);
+                    tc::tmem_ld16(tb + 128 + 64 + NB, d);
+                    tc::tmem_ld_wait();
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) Qre[o + e * QLD] = (a[e] + b[e]) - (c[e] + d[e]);
+                    // Im q = Ai Pr + Ar Pi
+                    tc::tmem_ld16(tb + 128, a);
+                    tc::tmem_ld16(tb + 128 + 64, b);
+                    tc::tmem_ld16(tb + NB, c);
+                    tc::tmem_ld16(tb + 64 + NB, d);
+                    tc::tmem_ld_wait();
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) Qim[o + e * QLD] = (a[e] + b[e]) + (c[e] + d[e]);
+                }
+                epi_sync();
+                if (init) {   // r = b - A X0, then Step 1 from there
+#pragma unroll
+                    for (int m = 0; m < MR; ++m) {
+                        const float2 q = qget(m);
+                        const float d = dvs[g + 8 * m];
+                        r[m] = make_float2(r[m].x - q.x, r[m].y - q.y);
+                        publish(m, make_float2(d * r[m].x, d * r[m].y));
+                    }
+                    rho = col_sum2<MR>([&](int m, float2 &a, float2 &b) {
+                        const float d = dvs[g + 8 * m];
+                        a = r[m];
+                        b = make_float2(d * r[m].x, d * r[m].y);
+                    });
+                    res2 = col_sum2<MR>([&](int m, float2 &a, float2 &b) { a = r[m]; b = r[m]; });
+                    continue;
+                }
+                // ---- Steps 2-4: lambda = r^H z / p^H A p, x += lambda p, r -= lambda q ----
+                const float pAp = col_sum2<MR>([&](int m, float2 &a, float2 &b) { a = pget(m); b = qget(m); });
+                float lam = 0.f;
+                if (pAp > 0.f) lam = rho / pAp;
+                else if (res2 != 0.f && !done) notHPD = 1;
+                if (done) lam = 0.f;
+#pragma unroll
+                for (int m = 0; m < MR; ++m) {
+                    const float2 q = qget(m);
+                    r[m].x = fmaf(-lam, q.x, r[m].x);
+                    r[m].y = fmaf(-lam, q.y, r[m].y);
+                }
+                if (!done) {
+#pragma unroll
+                    for (int m = 0; m < MR; ++m) {
+                        const float2 pv = pget(m);
+                        float2 xv = X[g + 8 * m];
+                        xv.x = fmaf(lam, pv.x, xv.x);
+                        xv.y = fmaf(lam, pv.y, xv.y);
+                        X[g + 8 * m] = xv;
+                    }
+                }
+                const float rz_new = col_sum2<MR>([&](int m, float2 &a, float2 &b) {
+                    const float d = dvs[g + 8 * m];
+                    a = r[m];
+                    b = make_float2(d * r[m].x, d * r[m].y);
+                });
+                const float rr_new = col_sum2<MR>([&](int m, float2 &a, float2 &b) { a = r[m]; b = r[m]; });
+                if (!done) {   // p = z + beta p, published for the next product
+                    const float beta = rho != 0.f ? rz_new / rho : 0.f;
+#pragma unroll
+                    for (int m = 0; m < MR; ++m) {
+                        const float2 pv = pget(m);
+                        const float d = dvs[g + 8 * m];
+                        publish(m, make_float2(fmaf(beta, pv.x, d * r[m].x), fmaf(beta, pv.y, d * r[m].y)));
+                    }
+                    rho = rz_new;
+                    res2 = rr_new;
+                    itmax = t + 1;
+                }
+            }
+            // ---- outputs ----
+            if (valid && in.Xout) {
+#pragma unroll
+                for (int m = 0; m < MR; ++m) {
+                    const int i = g + 8 * m;
+                    if (i < K) in.Xout[i + (size_t)j * K] = X[i];
+                }
+            }
+            if (MODE == 0 && g == 0) {   // one thread per column
+                int f = (err || S.err) ? FLAG_TIMEOUT : 0;
+                if (valid) {
+                    if (itmax > 0) atomicMax(acc_out.iters + id, itmax);
+                    const float rr = fmaxf(res2, 0.f);
+                    const float res = sqrtf(bn2 > 0.f ? rr / bn2 : rr);   // relative to ||b||
+                    if (res > 0.f) atomicMax(acc_out.resid_bits + id, __float_as_uint(res));
+                    if (notHPD) f |= FLAG_NOTHPD;
+                    if (tol2 > 0.f && !(res2 <= btol)) f |= FLAG_NOTCONV;
+                }
+                if (f) atomicOr(acc_out.flags + id, f);
+            }
+        }
+
+    }
+    // the copies issued last have landed before the CTA may exit
+    if (threadIdx.x == 0)
+        for (uint32_t q = pc > RING ? pc - RING : 0; q < pc; ++q)
+            (void)tc::mbar_wait(&S.full[q % RING], (q / RING) & 1, WAIT_LIMIT);
+    // every MMA has completed (each qfull was waited for) and every copy landed
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    if (warp == 0) tc::tmem_dealloc(tmem, C::TMEM_COLS);
+}
+
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            n = v;
+        else
+            n = 148;
+    }
+    return n;
+}
+
+template <int KC, int VAR, int MODE>
+cudaError_t launch_main(const DevInst *insts, const int2 *jobs, int n, DevAccum acc, cudaStream_t s) {
+    auto kern = pcg_tcw_kernel<KC, VAR, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<KC>::SMEM);
+    if (e != cudaSuccess) return e;
+    kern<<<n < sm_count() ? n : sm_count(), THREADS, Cfg<KC>::SMEM, s>>>(insts, jobs, n, acc);
+    return cudaGetLastError();
+}
+
+template <int KC>
+cudaError_t launch_kc(int variant, const DevInst *insts, const int2 *jobs, int n, DevAccum acc, cudaStream_t s,
+                      int mode) {
+    if (variant == 0) return mode ? launch_main<KC, 0, 1>(insts, jobs, n, acc, s) : launch_main<KC, 0, 0>(insts, jobs, n, acc, s);
+    if (variant == 2) return mode ? launch_main<KC, 2, 1>(insts, jobs, n, acc, s) : launch_main<KC, 2, 0>(insts, jobs, n, acc, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_tcw_prep(int KC, const DevInst *insts, const int *list, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (KC == 128) tcw_prep_kernel<128><<<n * Cfg<128>::NSTAGE, 256, 0, s>>>(insts, list);
+    else if (KC == 256) tcw_prep_kernel<256><<<n * Cfg<256>::NSTAGE, 256, 0, s>>>(insts, list);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_tcw(int KC, int variant, const DevInst *insts, const int2 *jobs, int n, DevAccum acc,
+                           cudaStream_t s, int mode) {
+    if (n <= 0) return cudaSuccess;
+    if (KC == 128) return launch_kc<128>(variant, insts, jobs, n, acc, s, mode);
+    if (KC == 256) return launch_kc<256>(variant, insts, jobs, n, acc, s, mode);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace jacpcg
+
+

@@ -64,12 +64,12 @@ def test_tensor_ragged_mix_with_simt_classes():
 @pytest.mark.parametrize("simt_iteration", [False, True])
 def test_tensor_tolerance_mode_reaches_direct_rzf(simt_iteration):
     """tf32x3 with tol 1e-6: each column stops at its tolerance and W lands
-    within 2e-5 of the direct RZF; iteration counts near the oracle's."""
+    within 1e-5 of the direct RZF; iteration counts near the oracle's."""
     H, xi = C.generate_batch("batched_1024x64", 8, 11)
     out = run(list(H), list(xi), T=200, tol=1e-6, precision="tf32x3", simt_iteration=simt_iteration)
     for i in range(8):
         Wd, _, _ = O.rzf_direct(H[i], xi[i])
-        assert rel_fro(out["W"][i], Wd) < 2e-5
+        assert rel_fro(out["W"][i], Wd) < 1e-5
         ref = O.precode(H[i], xi[i], "standard", max_iter=200, tol=1e-6)
         assert abs(int(out["iters"][i]) - ref["iters"]) <= 2
         assert out["status"][i] == 0
