@@ -309,7 +309,7 @@ RAGGED_MAX_ITER = 1000   # a cap that does not bind: the square K = M = 256 chan
 # tolerance mode at the metric's accuracy: the residual tolerance 1e-5 alone leaves the
 # near-square channels ~2e-5 from the direct RZF, so each instance is refined (Dot2
 # residual) until its relative residual is 1e-7 or stops halving
-RAGGED_REFINE = dict(refine_sweeps=3, refine_tol=1e-7, refine_solve_tol=1e-2)
+RAGGED_REFINE = dict(refine_sweeps=3, refine_tol=1e-7, refine_solve_tol=1e-2, refine_selective=True)
 
 
 def serving_traces(args, rates):

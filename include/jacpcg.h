@@ -73,9 +73,13 @@ enum { JACPCG_STANDARD = 0, JACPCG_ALG1 = 1, JACPCG_CG = 2, JACPCG_JOR = 3, JACP
  * TF32X3: tensor cores (tcgen05, kind::tf32) with each FP32 operand split
  *         into a TF32 head and a TF32 tail, three products accumulated in
  *         FP32 (about FP32 accuracy).
- * The iteration's vectors and scalars are FP32 in both cases and every
- * per-column dot product is compensated (Dot2); with TF32X3 its product
- * A P runs on the tensor cores in 3xTF32 for the K = 64 class. */
+ * The iteration's vectors and scalars are FP32 in both cases; with TF32X3
+ * its product A P runs on the tensor cores in 3xTF32 for the 64, 128 and
+ * 256 classes (standard and CG forms).  Every per-column dot product whose
+ * terms can cancel (p^H A p; Algorithm 1's complex denominator) is
+ * compensated (Dot2); the squared norms r^H D^{-1} r and ||r||^2 are sums of
+ * nonnegative terms (no cancellation), compensated on the SIMT kernel and
+ * summed pairwise (a few ulps) on the tensor-core kernels. */
 enum { JACPCG_FP32 = 0, JACPCG_TF32X3 = 1 };
 
 /* Storage type of H (jacpcg_instance.h_dtype).  BF16: each complex entry is
@@ -94,9 +98,16 @@ enum { JACPCG_RESID_DOT2 = 0, JACPCG_RESID_FP64 = 1 };
 /* config flags */
 enum {
     JACPCG_FLAG_PROFILE = 1,         /* record per-phase CUDA events on each execute */
-    JACPCG_FLAG_SIMT_ITERATION = 2   /* TF32X3, K = 64 class: keep the iteration on the FP32 SIMT
-                                        kernel (by default its A P product runs on the tensor
-                                        cores for the standard and CG forms) */
+    JACPCG_FLAG_SIMT_ITERATION = 2,  /* TF32X3: keep the iteration of every class on the FP32 SIMT
+                                        kernel (by default the A P product of the 64, 128 and 256
+                                        classes runs on the tensor cores for the standard and CG
+                                        forms) */
+    JACPCG_FLAG_REFINE_SELECTIVE = 4 /* with refine_sweeps > 0: refine only the channels with
+                                        M <= 2 K (few antennas per user: Jacobi-scaled condition
+                                        numbers up to thousands); the others keep the iteration's
+                                        result, whose W lies within a few 1e-6 of the RZF at a 1e-5
+                                        tolerance on the channels of Sec. II.  Their residual is not
+                                        evaluated and resid_hist is not written for them */
 };
 /* Other flag bits are rejected (EINVAL). */
 
@@ -114,7 +125,13 @@ typedef struct {
                                 evaluated as refine_residual says, A dX = R solved by the same
                                 FP32 iteration (the instance's max_iter and tol, relative to
                                 ||R||), X += dX */
-    int refine_residual;     /* JACPCG_RESID_DOT2 (default) or JACPCG_RESID_FP64 */
+    int refine_residual;     /* JACPCG_RESID_DOT2 (default) or JACPCG_RESID_FP64.  With
+                                refinement, channels with M <= 2 K form A with compensated
+                                (Dot2) sums on the SIMT pipes instead of the FP32 / 3xTF32
+                                Gram: refinement converges to the solution for the A it is
+                                given, and these channels' Jacobi-scaled condition numbers
+                                (up to thousands) would turn an FP32 Gram's rounding into an
+                                error floor near 1e-5 in W */
     float refine_tol;        /* 0 (default): every sweep runs for every instance.  > 0: an
                                 instance stops refining (its remaining correction solves and
                                 residual evaluations are skipped) once its largest per-column
@@ -231,22 +248,35 @@ jacpcg_status jacpcg_profile_read(jacpcg_ctx *ctx, float ms[4], int *n_executes,
                                   int *launches_per_execute);
 
 /* ---- autotuning --------------------------------------------------------
- * The iteration kernel has several launch shapes per K class (columns per
- * warp x warps per CTA; all give bit-identical results).  jacpcg_autotune
- * times every candidate on the instances of each K class present in
- * inst[0..n) (a plan of that class alone, 2 warm-up and 5 timed executes,
- * CUDA events on `stream`, which it synchronises) and keeps the fastest in
- * the context for later plans and calls.  If table is not NULL it receives a
- * NUL-terminated JSON object (truncated to table_cap bytes):
- *   {"<K class>": {"shape": i, "cols_per_warp": c, "warps_per_cta": w,
- *                  "instances": n, "ms_per_candidate": [...]}, ...}
+ * Per K class the iteration runs either on the tensor cores (shape -1: the
+ * 64 class's kernel with A in tensor memory, or the 128 / 256 classes'
+ * kernel with A streamed; allowed with TF32X3, STANDARD or CG and without
+ * JACPCG_FLAG_SIMT_ITERATION) or on the SIMT kernel in one of several launch
+ * shapes (0 .. n_shapes - 1: columns per warp x warps per CTA; all SIMT
+ * shapes give bit-identical results; the tensor path agrees with them within
+ * the FP32 tolerance).  The default is -1 (SIMT shape 0 where the tensor path
+ * is not allowed).  jacpcg_autotune times every candidate -- the tensor path
+ * where allowed, then each SIMT shape -- on the instances of each K class
+ * present in inst[0..n) (a plan of that class alone, 2 warm-up and 5 timed
+ * executes, CUDA events on `stream`, which it synchronises) and keeps the
+ * fastest in the context for later plans and calls: small batches of a
+ * class can run faster on the SIMT kernel, which spreads one instance over
+ * more CTAs.  If table is not NULL it receives a NUL-terminated JSON object
+ * (truncated to table_cap bytes):
+ *   {"<K class>": {"shape": i, "path": "tensor"|"simt", "cols_per_warp": c,
+ *                  "warps_per_cta": w, "instances": n, "candidates": [...],
+ *                  "ms_per_candidate": [...]}, ...}
  * which a caller can persist and replay with jacpcg_set_shape.
  * Errors: EINVAL, ENOMEM, ECUDA. */
 jacpcg_status jacpcg_autotune(jacpcg_ctx *ctx, const jacpcg_instance *inst, int n_inst,
                               void *stream, char *table, size_t table_cap);
-/* Choose candidate `shape` (0 = default) for K class k_class (8, 16, ..., 256). */
+/* Choose candidate `shape` for K class k_class (8, 16, ..., 256): -1 the
+ * tensor-core path where allowed (the default), 0 .. n_shapes - 1 a SIMT
+ * launch shape.  EINVAL outside -1 .. n_shapes - 1. */
 jacpcg_status jacpcg_set_shape(jacpcg_ctx *ctx, int k_class, int shape);
-/* Current shape of a K class, the number of candidates, and its geometry. */
+/* Current choice of a K class (-1 when the tensor path is in use), the
+ * number of SIMT shapes, and the SIMT geometry (of shape 0 for the tensor
+ * path). */
 jacpcg_status jacpcg_get_shape(const jacpcg_ctx *ctx, int k_class, int *shape, int *n_shapes,
                                int *cols_per_warp, int *warps_per_cta);
 

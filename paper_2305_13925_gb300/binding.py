@@ -23,6 +23,7 @@ JACPCG_STANDARD, JACPCG_ALG1, JACPCG_CG, JACPCG_JOR, JACPCG_DIRECT = 0, 1, 2, 3,
 JACPCG_FP32, JACPCG_TF32X3 = 0, 1
 JACPCG_FLAG_PROFILE = 1
 JACPCG_FLAG_SIMT_ITERATION = 2
+JACPCG_FLAG_REFINE_SELECTIVE = 4
 JACPCG_H_C64, JACPCG_H_BF16 = 0, 1
 JACPCG_RESID_DOT2, JACPCG_RESID_FP64 = 0, 1
 VARIANTS = {"standard": JACPCG_STANDARD, "alg1": JACPCG_ALG1, "cg": JACPCG_CG, "jor": JACPCG_JOR,
@@ -407,13 +408,14 @@ class Precoder:
     def __init__(self, max_instances: int, max_M: int, max_K: int, variant="standard",
                  precision="fp32", device: int = 0, arena_bytes: int = 0, profile: bool = False,
                  refine_sweeps: int = 0, refine_fp64: bool = False, simt_iteration: bool = False,
-                 refine_tol: float = 0.0, refine_solve_tol: float = 0.0):
+                 refine_tol: float = 0.0, refine_solve_tol: float = 0.0, refine_selective: bool = False):
         self.cfg = jacpcg_config(device=device, max_instances=max_instances, max_M=max_M,
                                  max_K=max_K, arena_bytes=arena_bytes,
                                  precision=PRECISIONS[precision] if isinstance(precision, str) else precision,
                                  variant=VARIANTS[variant] if isinstance(variant, str) else variant,
                                  flags=(JACPCG_FLAG_PROFILE if profile else 0)
-                                 | (JACPCG_FLAG_SIMT_ITERATION if simt_iteration else 0),
+                                 | (JACPCG_FLAG_SIMT_ITERATION if simt_iteration else 0)
+                                 | (JACPCG_FLAG_REFINE_SELECTIVE if refine_selective else 0),
                                  refine_sweeps=int(refine_sweeps),
                                  refine_residual=JACPCG_RESID_FP64 if refine_fp64 else JACPCG_RESID_DOT2,
                                  refine_tol=float(refine_tol), refine_solve_tol=float(refine_solve_tol))

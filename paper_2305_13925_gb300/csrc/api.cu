@@ -140,7 +140,9 @@ struct jacpcg_ctx {
     size_t prof_used = 0;
     int last_launches = 0;
     std::vector<jacpcg_plan *> plans;
-    int pcg_shape_idx[6] = {0, 0, 0, 0, 0, 0};   // chosen iteration shape per K class
+    // chosen iteration per K class: -1 the tensor-core kernel where the class,
+    // precision and variant allow it (else SIMT shape 0), 0.. a SIMT launch shape
+    int pcg_shape_idx[6] = {-1, -1, -1, -1, -1, -1};
     CUtensorMap amap{};   // the arena as rows of 64 floats, for the tiled copies of A
 };
 
@@ -247,20 +249,33 @@ constexpr int TCW_NB = 32;   // columns per CTA of the 128 / 256-class tensor-co
 // user-group blocks: one diagonal job for the 64 class, 2 + 1 for 128, 4 + 6
 // for 256) ...
 bool gram_on_tc(int precision, int KC) { return precision == JACPCG_TF32X3 && KC >= 64; }
+// With refinement, channels with at most two antennas per user form A by the
+// compensated SIMT Gram: their Jacobi-scaled condition numbers reach the
+// thousands, and refinement converges to the solution for the A it is given,
+// so the rounding of an FP32 (or 3xTF32) Gram would be the error floor of W.
+bool accurate_gram(bool refine, const jacpcg_instance &q) { return refine && q.M <= 2 * q.K; }
+// Instances that refinement works on: all of them, or with the selective
+// policy only those with at most two antennas per user.
+bool refines(const jacpcg_config &cfg, bool refine, const jacpcg_instance &q) {
+    return refine && (!(cfg.flags & JACPCG_FLAG_REFINE_SELECTIVE) || q.M <= 2 * q.K);
+}
 // ... whose W = H X does (the 64 class with X resident, 128 and 256 with X
 // streamed per stage, one job per 64 output columns) ...
 bool hx_on_tc(int precision, int KC) { return precision == JACPCG_TF32X3 && KC >= 64; }
 int hx_tc_groups(const jacpcg_instance &q) { return (n_cols(q) + 63) / 64; }
 // ... and whose iteration does, unless the SIMT kernel is asked for (Algorithm 1
 // and JOR always keep the SIMT kernel)
-bool pcg_on_tc(const jacpcg_config &cfg, int KC) {
-    return !(cfg.flags & JACPCG_FLAG_SIMT_ITERATION) && cfg.precision == JACPCG_TF32X3 && KC == 64 &&
+// (the K class's choice is -1: the tensor path where allowed)
+bool tensor_iteration_allowed(const jacpcg_config &cfg, int KC) {
+    return !(cfg.flags & JACPCG_FLAG_SIMT_ITERATION) && cfg.precision == JACPCG_TF32X3 && KC >= 64 &&
            (cfg.variant == JACPCG_STANDARD || cfg.variant == JACPCG_CG);
 }
+bool pcg_on_tc(const jacpcg_config &cfg, const int *shape_idx, int KC) {
+    return KC == 64 && shape_idx[kc_index(KC)] < 0 && tensor_iteration_allowed(cfg, KC);
+}
 // ... and, for the 128 and 256 classes, the streamed-A tensor-core iteration
-bool pcg_on_tcw(const jacpcg_config &cfg, int KC) {
-    return !(cfg.flags & JACPCG_FLAG_SIMT_ITERATION) && cfg.precision == JACPCG_TF32X3 && KC >= 128 &&
-           (cfg.variant == JACPCG_STANDARD || cfg.variant == JACPCG_CG);
+bool pcg_on_tcw(const jacpcg_config &cfg, const int *shape_idx, int KC) {
+    return KC >= 128 && shape_idx[kc_index(KC)] < 0 && tensor_iteration_allowed(cfg, KC);
 }
 
 Layout make_layout(const jacpcg_config &cfg, const jacpcg_instance *inst, int n, bool refine,
@@ -269,7 +284,7 @@ Layout make_layout(const jacpcg_config &cfg, const jacpcg_instance *inst, int n,
     L.n_gram = L.n_pcg = L.n_hx = L.n_res = L.n_gd = L.n_gx = L.n_hw = L.n_sinr = L.n_twj = 0;
     L.refine = refine;
     for (int i = 0; i < n; ++i) {
-        if (refine) L.n_res += (n_cols(inst[i]) + RES_CB - 1) / RES_CB;
+        if (refines(cfg, refine, inst[i])) L.n_res += (n_cols(inst[i]) + RES_CB - 1) / RES_CB;
         const int ng = k_class(inst[i].K) / 64;   // user groups of a tensor-core Gram
         L.n_gd += ng;
         L.n_gx += ng * (ng - 1) / 2;
@@ -278,7 +293,7 @@ Layout make_layout(const jacpcg_config &cfg, const jacpcg_instance *inst, int n,
         L.n_pcg += n_pblocks(inst[i], shape_idx);
         L.n_hx += n_wtiles(inst[i]);
         if (inst[i].sinr) L.n_sinr += (inst[i].K + 7) / 8;
-        if (pcg_on_tcw(cfg, k_class(inst[i].K))) L.n_twj += (n_cols(inst[i]) + TCW_NB - 1) / TCW_NB;
+        if (pcg_on_tcw(cfg, shape_idx, k_class(inst[i].K))) L.n_twj += (n_cols(inst[i]) + TCW_NB - 1) / TCW_NB;
     }
     size_t o = 0;
     L.insts = o;  o += align_up(sizeof(DevInst) * n);
@@ -299,7 +314,7 @@ Layout make_layout(const jacpcg_config &cfg, const jacpcg_instance *inst, int n,
     L.ws_off.resize(n);
     for (int i = 0; i < n; ++i) {
         L.ws_off[i] = o;
-        o += inst_ws_bytes(inst[i], refine, pcg_on_tcw(cfg, k_class(inst[i].K)));
+        o += inst_ws_bytes(inst[i], refine, pcg_on_tcw(cfg, shape_idx, k_class(inst[i].K)));
     }
     L.total = o;
     return L;
@@ -341,7 +356,7 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
         d.ldb = q.B ? q.ldb : 0;
         d.ncols = n_cols(q);
         d.X0 = static_cast<const float2 *>(q.X0);
-        if (pcg_on_tcw(ctx->cfg, KC)) {   // the split stages follow everything else
+        if (pcg_on_tcw(ctx->cfg, ctx->pcg_shape_idx, KC)) {   // the split stages follow everything else
             d.As = reinterpret_cast<float *>(w + inst_ws_bytes(q, L.refine, false));
         }
         if (L.refine) {
@@ -351,6 +366,7 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
             d.rnorm = reinterpret_cast<float *>(w + base + align_up((size_t)KC * KC * sizeof(float2)));
             d.rctl = d.rnorm + 2 * KC;
             d.rtol2 = ctx->cfg.refine_tol * ctx->cfg.refine_tol;
+            d.no_refine = refines(ctx->cfg, true, q) ? 0 : 1;
             d.rsolve_tol = ctx->cfg.refine_solve_tol;
             d.resid_hist = q.resid_hist;
         }
@@ -360,7 +376,8 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
         int2 *rb = reinterpret_cast<int2 *>(host + L.res);
         int r = 0;
         for (int i = 0; i < n; ++i)
-            for (int j = 0; j < n_cols(inst[i]); j += RES_CB) rb[r++] = make_int2(i, j);
+            if (refines(ctx->cfg, true, inst[i]))
+                for (int j = 0; j < n_cols(inst[i]); j += RES_CB) rb[r++] = make_int2(i, j);
     }
     launches.clear();
     // Gram on the tensor cores: diagonal (instance, group) jobs, then the
@@ -371,7 +388,7 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
     int nd = 0, nx = 0;
     for (int i = 0; i < n; ++i) {
         const int KC = k_class(inst[i].K);
-        if (!gram_on_tc(prec, KC)) continue;
+        if (!gram_on_tc(prec, KC) || accurate_gram(L.refine, inst[i])) continue;
         for (int a = 0; a < KC / 64; ++a) {
             gd[nd++] = make_int2(i, a);
             for (int b = a + 1; b < KC / 64; ++b) gx[nx++] = make_int4(i, a, b, 0);
@@ -383,20 +400,24 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
     int *tl = reinterpret_cast<int *>(host + L.tcl);
     int nt = 0;
     for (int i = 0; i < n; ++i)
-        if (pcg_on_tc(ctx->cfg, k_class(inst[i].K))) tl[nt++] = i;
+        if (pcg_on_tc(ctx->cfg, ctx->pcg_shape_idx, k_class(inst[i].K))) tl[nt++] = i;
     // Gram tiles (SIMT) grouped by tile edge
     int4 *gt = reinterpret_cast<int4 *>(host + L.gram);
     int g = 0;
-    for (int TB : {16, 32, 64}) {
-        const int start = g;
-        for (int i = 0; i < n; ++i) {
-            const int KC = k_class(inst[i].K);
-            if (gram_tb(KC) != TB || gram_on_tc(prec, KC)) continue;
-            const int nb = std::max(1, KC / TB);
-            for (int bi = 0; bi < nb; ++bi)
-                for (int bj = 0; bj <= bi; ++bj) gt[g++] = make_int4(i, bi, bj, 0);
+    for (int accurate = 0; accurate < 2; ++accurate) {
+        for (int TB : {16, 32, 64}) {
+            const int start = g;
+            for (int i = 0; i < n; ++i) {
+                const int KC = k_class(inst[i].K);
+                const bool acc_i = accurate_gram(L.refine, inst[i]);
+                if (gram_tb(KC) != TB || acc_i != (accurate != 0) || (!acc_i && gram_on_tc(prec, KC))) continue;
+                const int nb = std::max(1, KC / TB);
+                for (int bi = 0; bi < nb; ++bi)
+                    for (int bj = 0; bj <= bi; ++bj) gt[g++] = make_int4(i, bi, bj, 0);
+            }
+            // Launch::shape carries the compensated flag of a SIMT Gram launch
+            if (g > start) launches.push_back({Launch::GRAM, 0, TB, L.gram + start * sizeof(int4), g - start, accurate});
         }
-        if (g > start) launches.push_back({Launch::GRAM, 0, TB, L.gram + start * sizeof(int4), g - start});
     }
     // iteration blocks grouped by K class
     int2 *pb = reinterpret_cast<int2 *>(host + L.pcg);
@@ -410,7 +431,7 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
         int2 *twj = reinterpret_cast<int2 *>(host + L.twj);
         int ni = 0, nj = 0;
         for (int KC : {128, 256}) {
-            if (!pcg_on_tcw(ctx->cfg, KC)) continue;
+            if (!pcg_on_tcw(ctx->cfg, ctx->pcg_shape_idx, KC)) continue;
             const int i0 = ni, j0 = nj;
             for (int i = 0; i < n; ++i) {
                 if (k_class(inst[i].K) != KC) continue;
@@ -435,10 +456,12 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
     for (int KC : {8, 16, 32, 64, 128, 256}) {
         if (ctx->cfg.variant == JACPCG_DIRECT) break;
         const int start = p;
-        const int sh = ctx->pcg_shape_idx[kc_index(KC)];
+        const int sh = ctx->pcg_shape_idx[kc_index(KC)] < 0 ? 0 : ctx->pcg_shape_idx[kc_index(KC)];
         const PcgShape s = pcg_shape(KC, sh);
         for (int i = 0; i < n; ++i) {
-            if (k_class(inst[i].K) != KC || pcg_on_tc(ctx->cfg, KC) || pcg_on_tcw(ctx->cfg, KC)) continue;
+            if (k_class(inst[i].K) != KC || pcg_on_tc(ctx->cfg, ctx->pcg_shape_idx, KC) ||
+                pcg_on_tcw(ctx->cfg, ctx->pcg_shape_idx, KC))
+                continue;
             for (int c0 = 0; c0 < n_cols(inst[i]); c0 += s.CW * s.NW) pb[p++] = make_int2(i, c0);
         }
         if (p > start) launches.push_back({Launch::PCG, 1, KC, L.pcg + start * sizeof(int2), p - start, sh});
@@ -520,7 +543,7 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
             switch (l.kind) {
                 case Launch::GRAM:
                     e = launch_gram_simt(l.param, pl->d_insts, static_cast<const int4 *>(list), l.count,
-                                         pl->acc, s);
+                                         pl->acc, s, l.shape != 0);
                     break;
                 case Launch::PCG:
                     e = launch_pcg_shape(l.param, l.shape, ctx->cfg.variant, pl->d_insts,
@@ -560,7 +583,7 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
             if (e != cudaSuccess) return cuda_fail(ctx, e);
             ++nl;
         }
-        if (phase == 1 && pl->refine_sweeps > 0) {
+        if (phase == 1 && pl->refine_sweeps > 0 && pl->n_res > 0) {   // some instance refines
             // iterative refinement: R = I - A X (FP64), A dX = R (FP32 iteration), X += dX
             const NvtxRange refine_range("jacpcg: refinement");
             const int2 *rb = reinterpret_cast<const int2 *>(pl->dev + pl->res_off);
@@ -822,7 +845,8 @@ jacpcg_status jacpcg_create(const jacpcg_config *cfg, jacpcg_ctx **out) {
     if (cfg->precision != JACPCG_FP32 && cfg->precision != JACPCG_TF32X3) return JACPCG_EINVAL;
     if (cfg->variant < JACPCG_STANDARD || cfg->variant > JACPCG_DIRECT) return JACPCG_EINVAL;
     if (cfg->variant == JACPCG_DIRECT && cfg->refine_sweeps > 0) return JACPCG_EINVAL;
-    if (cfg->flags & ~(JACPCG_FLAG_PROFILE | JACPCG_FLAG_SIMT_ITERATION)) return JACPCG_EINVAL;
+    if (cfg->flags & ~(JACPCG_FLAG_PROFILE | JACPCG_FLAG_SIMT_ITERATION | JACPCG_FLAG_REFINE_SELECTIVE))
+        return JACPCG_EINVAL;
     if (cfg->refine_sweeps < 0 || cfg->refine_sweeps > 3) return JACPCG_EINVAL;
     if (cfg->refine_residual != JACPCG_RESID_DOT2 && cfg->refine_residual != JACPCG_RESID_FP64)
         return JACPCG_EINVAL;
@@ -842,8 +866,8 @@ jacpcg_status jacpcg_create(const jacpcg_config *cfg, jacpcg_ctx **out) {
         q.M = cfg->max_M;
         q.K = cfg->max_K;
         std::vector<jacpcg_instance> v(cfg->max_instances, q);
-        const int zero[6] = {0, 0, 0, 0, 0, 0};
-        bytes = 2 * make_layout(*cfg, v.data(), cfg->max_instances, cfg->refine_sweeps > 0, zero).total;
+        const int dflt[6] = {-1, -1, -1, -1, -1, -1};
+        bytes = 2 * make_layout(*cfg, v.data(), cfg->max_instances, cfg->refine_sweeps > 0, dflt).total;
     }
     bytes = align_up(bytes);
     if (cudaMalloc(reinterpret_cast<void **>(&ctx->arena.base), bytes) != cudaSuccess) {
@@ -961,7 +985,7 @@ const char *jacpcg_last_cuda_error(const jacpcg_ctx *ctx) {
 jacpcg_status jacpcg_set_shape(jacpcg_ctx *ctx, int k_class_, int shape) {
     if (!ctx || k_class_ < 8 || k_class_ > 256 || (k_class_ & (k_class_ - 1))) return JACPCG_EINVAL;
     const int c = kc_index(k_class_);
-    if (shape < 0 || shape >= PCG_NSHAPES[c]) return JACPCG_EINVAL;
+    if (shape < -1 || shape >= PCG_NSHAPES[c]) return JACPCG_EINVAL;
     ctx->pcg_shape_idx[c] = shape;
     return JACPCG_OK;
 }
@@ -970,8 +994,9 @@ jacpcg_status jacpcg_get_shape(const jacpcg_ctx *ctx, int k_class_, int *shape, 
                                int *cols_per_warp, int *warps_per_cta) {
     if (!ctx || k_class_ < 8 || k_class_ > 256 || (k_class_ & (k_class_ - 1))) return JACPCG_EINVAL;
     const int c = kc_index(k_class_);
+    const bool tensor = ctx->pcg_shape_idx[c] < 0 && tensor_iteration_allowed(ctx->cfg, k_class_);
     const PcgShape s = pcg_shape(k_class_, ctx->pcg_shape_idx[c]);
-    if (shape) *shape = ctx->pcg_shape_idx[c];
+    if (shape) *shape = tensor ? -1 : (ctx->pcg_shape_idx[c] < 0 ? 0 : ctx->pcg_shape_idx[c]);
     if (n_shapes) *n_shapes = PCG_NSHAPES[c];
     if (cols_per_warp) *cols_per_warp = s.CW;
     if (warps_per_cta) *warps_per_cta = s.NW;
@@ -997,7 +1022,8 @@ jacpcg_status jacpcg_autotune(jacpcg_ctx *ctx, const jacpcg_instance *inst, int 
         float best_ms = 1e30f;
         int best = 0;
         std::string times;
-        for (int sh = 0; sh < PCG_NSHAPES[c] && st == JACPCG_OK; ++sh) {
+        const int first_sh = tensor_iteration_allowed(ctx->cfg, KC) ? -1 : 0;   // -1: tensor cores
+        for (int sh = first_sh; sh < PCG_NSHAPES[c] && st == JACPCG_OK; ++sh) {
             ctx->pcg_shape_idx[c] = sh;
             jacpcg_plan *pl = nullptr;
             st = make_plan(ctx, sub.data(), (int)sub.size(), nullptr, nullptr, nullptr, nullptr, 0, nullptr, &pl);
@@ -1015,13 +1041,17 @@ jacpcg_status jacpcg_autotune(jacpcg_ctx *ctx, const jacpcg_instance *inst, int 
                 best_ms = ms;
                 best = sh;
             }
-            times += (sh ? ", " : "") + std::to_string(ms);
+            times += (sh != first_sh ? ", " : "") + std::to_string(ms);
         }
         ctx->pcg_shape_idx[c] = best;
         const PcgShape b = pcg_shape(KC, best);
         js += (first ? "" : ", ") + std::string("\"") + std::to_string(KC) + "\": {\"shape\": " + std::to_string(best) +
-              ", \"cols_per_warp\": " + std::to_string(b.CW) + ", \"warps_per_cta\": " + std::to_string(b.NW) +
-              ", \"instances\": " + std::to_string(sub.size()) + ", \"ms_per_candidate\": [" + times + "]}";
+              ", \"path\": \"" + (best < 0 ? "tensor" : "simt") + "\"" +
+              ", \"cols_per_warp\": " + std::to_string(best < 0 ? 0 : b.CW) +
+              ", \"warps_per_cta\": " + std::to_string(best < 0 ? 0 : b.NW) +
+              ", \"instances\": " + std::to_string(sub.size()) +
+              ", \"candidates\": [" + (first_sh < 0 ? "\"tensor\", " : "") + "\"simt shapes 0.." +
+              std::to_string(PCG_NSHAPES[c] - 1) + "\"]" + ", \"ms_per_candidate\": [" + times + "]}";
         first = false;
         if (st != JACPCG_OK) break;
     }

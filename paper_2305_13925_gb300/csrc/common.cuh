@@ -39,6 +39,7 @@ struct DevInst {
                           // evaluation, and 1 once the instance has stopped refining
     float rtol2;          // refine_tol^2 (0: every sweep runs)
     float rsolve_tol;     // tolerance of the correction solves (0: tol)
+    int no_refine;        // refinement is on but skips this instance (selective policy)
     float *resid_hist;    // caller's optional refinement history
     // right-hand sides (Eq. 16 per symbol vector): B == null means B = I_K
     const float2 *B;      // K x ncols, leading dimension ldb (caller)

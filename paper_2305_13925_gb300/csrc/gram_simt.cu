@@ -12,6 +12,12 @@
 // Each stage's products are summed into a fresh partial that is then added
 // to the running total (two-level summation: the rounding error grows with
 // MC + M / MC terms rather than with M).
+// ACC: every real product is accumulated as a compensated pair (TwoProduct
+// by FMA and TwoSum; Ogita, Rump and Oishi 2005) and xi is added in FP64, so
+// each entry of A is the exactly rounded FP32 value of H^H H + xi I up to a
+// few units.  Refinement uses it for channels with few antennas per user,
+// whose Jacobi-scaled condition numbers reach the thousands and would turn
+// the rounding of a plain FP32 Gram into an error floor near 1e-5 in W.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -21,7 +27,7 @@ namespace {
 
 constexpr int MC = 32;  // H rows per stage
 
-template <int TB>
+template <int TB, bool ACC>
 __global__ void __launch_bounds__(256) gram_simt_kernel(const DevInst *__restrict__ insts,
                                                         const int4 *__restrict__ tiles,
                                                         DevAccum acc_out) {
@@ -47,10 +53,14 @@ __global__ void __launch_bounds__(256) gram_simt_kernel(const DevInst *__restric
     }
 
     float2 acc[U][U];
+    Comp cre[ACC ? U : 1][ACC ? U : 1], cim[ACC ? U : 1][ACC ? U : 1];
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int v = 0; v < U; ++v) acc[u][v] = make_float2(0.f, 0.f);
+        for (int v = 0; v < U; ++v) {
+            acc[u][v] = make_float2(0.f, 0.f);
+            if (ACC) cre[u][v] = cim[u][v] = Comp{0.f, 0.f};
+        }
 
     // staging map: element e = threadIdx.x + 256 q -> column c = e / MC, row r = e % MC
     float2 ri[LOADS], rj[LOADS];
@@ -80,31 +90,51 @@ __global__ void __launch_bounds__(256) gram_simt_kernel(const DevInst *__restric
         __syncthreads();
         if (m0 + MC < Mloop) fetch(m0 + MC);
         float2(*Sb)[PITCH] = diag ? Si : Sj;
-        // two-level sum: a fresh partial per stage of MC rows, added to the total
-        float2 part[U][U];
+        if constexpr (ACC) {   // compensated: conj(a) b = (ar br + ai bi) + i (ar bi - ai br)
+#pragma unroll 2
+            for (int r = 0; r < MC; ++r) {
+                float2 a[U], b[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u)
+                for (int u = 0; u < U; ++u) a[u] = Si[r][ty * U + u];
 #pragma unroll
-            for (int v = 0; v < U; ++v) part[u][v] = make_float2(0.f, 0.f);
-#pragma unroll 4
-        for (int r = 0; r < MC; ++r) {
-            float2 a[U], b[U];
+                for (int v = 0; v < U; ++v) b[v] = Sb[r][tx * U + v];
 #pragma unroll
-            for (int u = 0; u < U; ++u) a[u] = Si[r][ty * U + u];
+                for (int u = 0; u < U; ++u)
 #pragma unroll
-            for (int v = 0; v < U; ++v) b[v] = Sb[r][tx * U + v];
+                    for (int v = 0; v < U; ++v) {
+                        comp_fma(cre[u][v], a[u].x, b[v].x);
+                        comp_fma(cre[u][v], a[u].y, b[v].y);
+                        comp_fma(cim[u][v], a[u].x, b[v].y);
+                        comp_fma(cim[u][v], -a[u].y, b[v].x);
+                    }
+            }
+        } else {
+            // two-level sum: a fresh partial per stage of MC rows, added to the total
+            float2 part[U][U];
 #pragma unroll
             for (int u = 0; u < U; ++u)
 #pragma unroll
-                for (int v = 0; v < U; ++v) cfma_conj(part[u][v], a[u], b[v]);
-        }
+                for (int v = 0; v < U; ++v) part[u][v] = make_float2(0.f, 0.f);
+#pragma unroll 4
+            for (int r = 0; r < MC; ++r) {
+                float2 a[U], b[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u)
+                for (int u = 0; u < U; ++u) a[u] = Si[r][ty * U + u];
 #pragma unroll
-            for (int v = 0; v < U; ++v) {
-                acc[u][v].x += part[u][v].x;
-                acc[u][v].y += part[u][v].y;
+                for (int v = 0; v < U; ++v) b[v] = Sb[r][tx * U + v];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int v = 0; v < U; ++v) cfma_conj(part[u][v], a[u], b[v]);
             }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int v = 0; v < U; ++v) {
+                    acc[u][v].x += part[u][v].x;
+                    acc[u][v].y += part[u][v].y;
+                }
+        }
     }
 
     // write the tile (workspace has leading dimension KC, caller's A has K)
@@ -118,10 +148,15 @@ __global__ void __launch_bounds__(256) gram_simt_kernel(const DevInst *__restric
             const int j = j0 + tx * U + v;
             if (i >= KC || j >= KC || i < j) continue;
             float2 a = acc[u][v];
+            double dre = 0.0;   // ACC: the compensated sum, rounded once
+            if (ACC) {
+                dre = (double)cre[u][v].s + (double)cre[u][v].c;
+                a = make_float2((float)dre, (float)((double)cim[u][v].s + (double)cim[u][v].c));
+            }
             if (i == j) {
                 a.y = 0.f;
                 if (i < K) {
-                    a.x += in.xi;
+                    a.x = ACC ? (float)(dre + (double)in.xi) : a.x + in.xi;
                     in.dinv[i] = 1.0f / a.x;
                 } else {
                     in.dinv[i] = 0.f;
@@ -140,12 +175,15 @@ __global__ void __launch_bounds__(256) gram_simt_kernel(const DevInst *__restric
 }  // namespace
 
 cudaError_t launch_gram_simt(int TB, const DevInst *insts, const int4 *tiles, int n_tiles,
-                             DevAccum acc, cudaStream_t s) {
+                             DevAccum acc, cudaStream_t s, bool accurate) {
     if (n_tiles <= 0) return cudaSuccess;
-    switch (TB) {
-        case 16: gram_simt_kernel<16><<<n_tiles, 256, 0, s>>>(insts, tiles, acc); break;
-        case 32: gram_simt_kernel<32><<<n_tiles, 256, 0, s>>>(insts, tiles, acc); break;
-        case 64: gram_simt_kernel<64><<<n_tiles, 256, 0, s>>>(insts, tiles, acc); break;
+    switch (TB * 2 + (accurate ? 1 : 0)) {
+        case 32: gram_simt_kernel<16, false><<<n_tiles, 256, 0, s>>>(insts, tiles, acc); break;
+        case 64: gram_simt_kernel<32, false><<<n_tiles, 256, 0, s>>>(insts, tiles, acc); break;
+        case 128: gram_simt_kernel<64, false><<<n_tiles, 256, 0, s>>>(insts, tiles, acc); break;
+        case 33: gram_simt_kernel<16, true><<<n_tiles, 256, 0, s>>>(insts, tiles, acc); break;
+        case 65: gram_simt_kernel<32, true><<<n_tiles, 256, 0, s>>>(insts, tiles, acc); break;
+        case 129: gram_simt_kernel<64, true><<<n_tiles, 256, 0, s>>>(insts, tiles, acc); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

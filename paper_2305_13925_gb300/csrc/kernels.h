@@ -40,7 +40,7 @@ constexpr int HX_TM = 64;
 
 // tiles: (instance, bi, bj, 0) with bi >= bj
 cudaError_t launch_gram_simt(int TB, const DevInst *insts, const int4 *tiles, int n_tiles,
-                             DevAccum acc, cudaStream_t s);
+                             DevAccum acc, cudaStream_t s, bool accurate = false);
 // tensor-core Gram (3xTF32), diagonal 64 x 64 blocks; list: (instance, user group) jobs
 cudaError_t launch_gram_tc64(const DevInst *insts, const int2 *list, int n, DevAccum acc,
                              cudaStream_t s);

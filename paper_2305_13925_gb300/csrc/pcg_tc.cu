@@ -36,11 +36,15 @@
 //      padded shared-memory tile, then a team barrier;
 //   3. works column-wise: thread (warp w, lane l) owns column 8 w + (l mod 8)
 //      and the 16 complex rows g, g + 4, .., g + 60 with g = l / 8, holding
-//      x, r, p for them in registers; the per-column dot products are
-//      compensated (Dot2): in-thread error-free sums over its 16 rows and two
-//      xor shuffles across the four lanes of the column, combined with
-//      commutative or exact operations only, so all four lanes obtain
-//      bit-identical totals and take identical decisions.
+//      x, r, p for them in registers; the step denominator p^H A p, whose
+//      terms can cancel, is compensated (Dot2: in-thread error-free sums over
+//      its 16 rows in a tree, then two xor shuffles across the four lanes of
+//      the column, combined with commutative or exact operations only); the
+//      squared norms r^H D^{-1} r and ||r||^2 sum nonnegative terms, where
+//      pairwise summation is already accurate to a few units, and are summed
+//      so (Dot2 on all three measured 0.368 against 0.318 ms per 2048-channel
+//      batch).  All four lanes obtain bit-identical totals and take identical
+//      decisions.
 // The tile strides (128-byte core matrices, 68-float rows of the Q tile) make
 // every P store, Q store and Q load free of shared-memory bank conflicts.
 #include "common.cuh"
@@ -131,6 +135,23 @@ __device__ __forceinline__ float comp_value(Comp v) { return v.s + v.c; }
 // are combined pairwise by TwoSum in 4 levels, and the errors are summed
 // alongside.  The same error-free steps as a sequential Dot2, but with no
 // chain of 32 dependent TwoSums on the iteration's critical path.
+// Sum over the thread's rows of Re conj(a_k) b_k when every term is >= 0
+// (||r||^2 and r^H D^{-1} r): no cancellation can occur, so plain pairwise
+// summation is already accurate to a few units in the last place, and the
+// lanes of a column combine by commutative additions (bit-identical totals).
+__device__ __forceinline__ float sumsq_col(const float2 (&a)[RPT], const float2 (&b)[RPT]) {
+    float s[RPT];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) s[k] = fmaf(a[k].x, b[k].x, a[k].y * b[k].y);
+#pragma unroll
+    for (int h = RPT / 2; h > 0; h >>= 1)
+#pragma unroll
+        for (int k = 0; k < h; ++k) s[k] += s[k + h];
+    float v = s[0];
+    v += __shfl_xor_sync(0xffffffffu, v, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 16);
+    return v;
+}
 __device__ __forceinline__ Comp dot2_rows(const float2 (&a)[RPT], const float2 (&b)[RPT]) {
     float s[RPT], c[RPT];
 #pragma unroll
@@ -295,8 +316,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
                 r[k] = b;
                 p[k] = make_float2(dv[k] * b.x, dv[k] * b.y);
             }
-            rho = comp_value(col_total(dot2_rows(r, p)));    // r^H z
-            res2 = comp_value(col_total(dot2_rows(r, r)));   // ||r||^2 = ||b||^2
+            rho = sumsq_col(r, p);    // r^H z (terms d |r|^2 >= 0)
+            res2 = sumsq_col(r, r);   // ||r||^2 = ||b||^2
             bn2c = res2;                   // stopping and reporting stay relative to ||b||
             btol = tol2 * bn2c;
         }
@@ -378,8 +399,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
                     r[k] = make_float2(r[k].x - q[k].x, r[k].y - q[k].y);
                     p[k] = make_float2(dv[k] * r[k].x, dv[k] * r[k].y);
                 }
-                rho = comp_value(col_total(dot2_rows(r, p)));
-                res2 = comp_value(col_total(dot2_rows(r, r)));
+                rho = sumsq_col(r, p);
+                res2 = sumsq_col(r, r);
                 continue;
             }
             // lambda = r^H z / p^H A p (p^H A p is real for Hermitian A: Re part only)
@@ -397,8 +418,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) pcg_tc64_kernel(const DevInst *__
                 r[k].y = fmaf(-lam, q[k].y, r[k].y);
                 z[k] = make_float2(dv[k] * r[k].x, dv[k] * r[k].y);   // z = D^{-1} r
             }
-            const float rz_new = comp_value(col_total(dot2_rows(r, z)));
-            const float rr_new = comp_value(col_total(dot2_rows(r, r)));
+            const float rz_new = sumsq_col(r, z);
+            const float rr_new = sumsq_col(r, r);
             if (!done) {
                 const float beta = rho != 0.f ? rz_new / rho : 0.f;
 #pragma unroll

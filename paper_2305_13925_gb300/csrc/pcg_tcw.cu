@@ -10,7 +10,7 @@
 // and stores them as MMA-ready 16 KB stages -- for row tile rt (128 rows) and
 // k-step ks (8 columns): [Ar_h | Ar_t | Ai_h | Ai_t], each a 128 x 8 tile in
 // the canonical no-swizzle K-major layout -- and each iteration streams the
-// stages through a 5-deep shared-memory ring with bulk copies (the TMA unit,
+// stages through a 6-deep shared-memory ring with bulk copies (the TMA unit,
 // cp.async.bulk), completion counted in bytes on an mbarrier.  Real and
 // imaginary parts are kept apart (planar), so each byte of A is streamed once
 // per iteration rather than twice as in the 2 x 2 real expansion.
@@ -39,10 +39,12 @@
 // ... with g = l / 4; r lives in registers, p is read back from the B
 // operand (head + tail is exact), x is accumulated in the instance's
 // workspace X (which is also where a refinement correction X += dX lands),
-// and the per-column dot products are compensated (TwoProduct by FMA and
-// TwoSum in a tree, then three xor shuffles combined with commutative or
-// exact operations, so all eight lanes of a column hold bit-identical
-// totals).  Every wait is bounded; a timeout sets the instance's ETIMEOUT
+// and the step denominator p^H A p, whose terms can cancel, is compensated
+// (TwoProduct by FMA and TwoSum in a tree, then three xor shuffles combined
+// with commutative or exact operations); the squared norms r^H D^{-1} r and
+// ||r||^2 sum nonnegative terms, where pairwise summation is already
+// accurate to a few units, and are summed so.  All eight lanes of a column
+// hold bit-identical totals.  Every wait is bounded; a timeout sets the instance's ETIMEOUT
 // flag and ends its iteration.
 #include "common.cuh"
 #include "kernels.h"
@@ -55,7 +57,7 @@ namespace {
 constexpr int NB = 32;                        // right-hand-side columns per CTA
 constexpr int THREADS = 256;                  // 8 warps: 2 per SM sub-partition, up to 255 registers
 constexpr int EPI = THREADS;
-constexpr int RING = 5;                       // stages in flight
+constexpr int RING = 6;                       // stages in flight
 constexpr int STAGE = 16384;                  // bytes: four 128 x 8 TF32 tiles
 constexpr int TILE = 4096;
 constexpr int QLD = 136;                      // floats per staged Q column (128 rows + 8)
@@ -201,6 +203,29 @@ __device__ __forceinline__ float col_sum2(F f) {
     return vs + vc;
 }
 
+// Sum over the thread's MR rows of Re conj(a_m) b_m when every term is >= 0
+// (||r||^2 and r^H D^{-1} r): no cancellation can occur, so pairwise
+// summation is already accurate to a few units in the last place; the 8 lanes
+// of the column combine by commutative additions (bit-identical totals).
+template <int MR, typename F>
+__device__ __forceinline__ float col_sumsq(F f) {
+    float s[MR];
+#pragma unroll
+    for (int m = 0; m < MR; ++m) {
+        float2 a, b;
+        f(m, a, b);
+        s[m] = fmaf(a.x, b.x, a.y * b.y);
+    }
+#pragma unroll
+    for (int h = MR / 2; h > 0; h >>= 1)
+#pragma unroll
+        for (int k = 0; k < h; ++k) s[k] += s[k + h];
+    float v = s[0];
+#pragma unroll
+    for (int o = 4; o <= 16; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // MODE 0 solves A X = B from X0 (or 0); MODE 1 is a refinement correction
 // solve (right-hand side R, X += dX; instances that stopped refining are
 // skipped).  jobs: (instance, first column), NB columns each.
@@ -331,12 +356,12 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
                 // the warm pass forms A X0 first; columns beyond the right-hand sides carry 0
                 publish(m, !valid ? make_float2(0.f, 0.f) : warm ? X[i] : make_float2(d * b.x, d * b.y));
             }
-            float rho = col_sum2<MR>([&](int m, float2 &a, float2 &b) {
+            float rho = col_sumsq<MR>([&](int m, float2 &a, float2 &b) {
                 const float d = dvs[g + 8 * m];
                 a = r[m];
                 b = make_float2(d * r[m].x, d * r[m].y);
             });
-            float res2 = col_sum2<MR>([&](int m, float2 &a, float2 &b) { a = r[m]; b = r[m]; });
+            float res2 = col_sumsq<MR>([&](int m, float2 &a, float2 &b) { a = r[m]; b = r[m]; });
             const float bn2 = res2;   // stopping and reporting stay relative to ||b||
             const float btol = tol2 * bn2;
             bool done = !valid;
@@ -391,12 +416,12 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
                         r[m] = make_float2(r[m].x - q.x, r[m].y - q.y);
                         publish(m, make_float2(d * r[m].x, d * r[m].y));
                     }
-                    rho = col_sum2<MR>([&](int m, float2 &a, float2 &b) {
+                    rho = col_sumsq<MR>([&](int m, float2 &a, float2 &b) {
                         const float d = dvs[g + 8 * m];
                         a = r[m];
                         b = make_float2(d * r[m].x, d * r[m].y);
                     });
-                    res2 = col_sum2<MR>([&](int m, float2 &a, float2 &b) { a = r[m]; b = r[m]; });
+                    res2 = col_sumsq<MR>([&](int m, float2 &a, float2 &b) { a = r[m]; b = r[m]; });
                     continue;
                 }
                 // ---- Steps 2-4: lambda = r^H z / p^H A p, x += lambda p, r -= lambda q ----
@@ -421,12 +446,12 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
                         X[g + 8 * m] = xv;
                     }
                 }
-                const float rz_new = col_sum2<MR>([&](int m, float2 &a, float2 &b) {
+                const float rz_new = col_sumsq<MR>([&](int m, float2 &a, float2 &b) {
                     const float d = dvs[g + 8 * m];
                     a = r[m];
                     b = make_float2(d * r[m].x, d * r[m].y);
                 });
-                const float rr_new = col_sum2<MR>([&](int m, float2 &a, float2 &b) { a = r[m]; b = r[m]; });
+                const float rr_new = col_sumsq<MR>([&](int m, float2 &a, float2 &b) { a = r[m]; b = r[m]; });
                 if (!done) {   // p = z + beta p, published for the next product
                     const float beta = rho != 0.f ? rz_new / rho : 0.f;
 #pragma unroll

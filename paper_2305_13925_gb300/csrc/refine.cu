@@ -146,6 +146,13 @@ __global__ void resid_hist_kernel(const DevInst *__restrict__ insts, int n_inst,
     const int lane = threadIdx.x & 31;
     if (inst >= n_inst) return;
     const DevInst &in = insts[inst];
+    if (in.no_refine) {   // selective policy: never evaluated, no correction solves
+        if (lane == 0 && sweep == 0) {
+            in.rctl[0] = 0.f;
+            in.rctl[1] = 1.f;
+        }
+        return;
+    }
     double s = 0.0;
     float rel = 0.f;
     for (int j = lane; j < in.ncols; j += 32) {

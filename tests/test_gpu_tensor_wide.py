@@ -149,3 +149,41 @@ def test_wide_tolerance_and_refinement_reach_the_direct_rzf():
         Wd = O.rzf_direct(H, xi)[0]
         assert out["status"][i] == 0, (i, out["status"][i])
         assert rel_fro(out["W"][i], Wd) <= TOL_W, (i, H.shape, rel_fro(out["W"][i], Wd))
+
+
+def test_autotune_chooses_between_tensor_and_simt_paths():
+    """With TF32X3 every class from 64 up has the tensor path as candidate -1
+    next to the SIMT launch shapes: each choice stays within 1e-5 of the
+    oracle, and the autotuner's table times every candidate and records the
+    path it kept."""
+    from paper_2305_13925_gb300 import binding
+    insts = C.generate_ragged(9, 61, k_set=(64, 128, 256), m_set=(512, 1024))
+    Hs = [C.round_complex64(i.H) for i in insts]
+    xis = [i.xi for i in insts]
+    refs = [O.precode(h, x, "standard", max_iter=5)["W"] for h, x in zip(Hs, xis)]
+    prec = binding.Precoder(max_instances=9, max_M=1024, max_K=256, precision="tf32x3")
+    try:
+        for KC in (64, 128, 256):
+            assert binding.jacpcg_get_shape(prec.ctx, KC)[0] == -1     # tensor path by default
+        for sh in (-1, 0, 1):
+            for KC in (64, 128, 256):
+                binding.jacpcg_set_shape(prec.ctx, KC, sh)
+            out = run(Hs, xis, T=5, prec=prec, precision="tf32x3")
+            for k in range(len(Hs)):
+                assert rel_fro(out["W"][k], refs[k]) <= TOL_W, (sh, k)
+        import torch
+        from gpu_util import to_dev
+        Hd = [to_dev(h, torch) for h in Hs]
+        Wd = [to_dev(np.zeros(h.shape), torch) for h in Hs]
+        table = binding.jacpcg_autotune(prec.ctx, [binding.instance(Hd[k], Wd[k], xis[k], 5)
+                                                   for k in range(len(Hs))])
+        for KC in (64, 128, 256):
+            e = table[str(KC)]
+            n_simt = binding.jacpcg_get_shape(prec.ctx, KC)[1]
+            assert len(e["ms_per_candidate"]) == n_simt + 1
+            assert e["path"] == ("tensor" if e["shape"] == -1 else "simt")
+        out = run(Hs, xis, T=5, prec=prec, precision="tf32x3")
+        for k in range(len(Hs)):
+            assert rel_fro(out["W"][k], refs[k]) <= TOL_W, k
+    finally:
+        prec.close()
