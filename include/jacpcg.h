@@ -124,7 +124,9 @@ typedef struct {
     int refine_sweeps;       /* 0..3 iterative-refinement sweeps after the solve: R = I - A X
                                 evaluated as refine_residual says, A dX = R solved by the same
                                 FP32 iteration (the instance's max_iter and tol, relative to
-                                ||R||), X += dX */
+                                ||R||), X += dX.  After the last sweep R is evaluated once more
+                                only when some instance of the call asks for resid_hist (it
+                                could change nothing else) */
     int refine_residual;     /* JACPCG_RESID_DOT2 (default) or JACPCG_RESID_FP64.  With
                                 refinement, channels with M <= 2 K form A with compensated
                                 (Dot2) sums on the SIMT pipes instead of the FP32 / 3xTF32

@@ -161,6 +161,7 @@ struct jacpcg_plan {
     cudaEvent_t done = nullptr;
     bool executed = false;
     int refine_sweeps = 0;
+    bool want_hist = false;       // some instance asked for its refinement residual history
     size_t res_off = 0;
     int n_res = 0;
     size_t acc_reset_bytes = 0;   // > 0: clear the accumulators before the Gram (multi-job instances)
@@ -588,6 +589,8 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
             const NvtxRange refine_range("jacpcg: refinement");
             const int2 *rb = reinterpret_cast<const int2 *>(pl->dev + pl->res_off);
             for (int sw = 0; sw <= pl->refine_sweeps; ++sw) {
+                // after the last correction the residual could only be reported
+                if (sw == pl->refine_sweeps && !pl->want_hist) break;
                 if (launch_residual(pl->d_insts, rb, pl->n_res, sw, s,
                                     ctx->cfg.refine_residual == JACPCG_RESID_FP64) != cudaSuccess ||
                     launch_resid_hist(pl->d_insts, pl->n_inst, sw, s) != cudaSuccess)
@@ -665,6 +668,7 @@ jacpcg_status make_plan(jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, int
     pl->out = DevOut{status_dev, iters_dev, resid_dev, beta_dev};
     pl->use_graph = use_graph;
     pl->refine_sweeps = ctx->cfg.refine_sweeps;
+    for (int i = 0; i < n; ++i) pl->want_hist = pl->want_hist || inst[i].resid_hist != nullptr;
     pl->res_off = L.res;
     pl->n_res = L.n_res;
     if (L.n_gx) pl->acc_reset_bytes = 3 * align_up(sizeof(int32_t) * n);
