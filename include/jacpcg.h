@@ -320,8 +320,10 @@ typedef struct {
  * (8 .. 64, 128, 256), with K = 256 split further into channels with
  * M >= 4 K and the rest (near-square channels, often ill-conditioned and
  * slow to converge) -- so cheap requests never wait inside an expensive
- * batch, and the classes overlap on the device in separate batches.  FIFO:
- * every waiting request in arrival order. */
+ * batch, and the classes overlap on the device in separate batches; the two
+ * 256-user classes hold at most max_inflight - 1 of the in-flight batches at
+ * once (with max_inflight >= 2), so a slot always stays for the cheaper
+ * classes.  FIFO: every waiting request in arrival order. */
 enum { JACPCG_BATCH_COST_CLASS = 0, JACPCG_BATCH_FIFO = 1 };
 
 jacpcg_status jacpcg_server_create(jacpcg_ctx *ctx, const jacpcg_server_config *cfg,

@@ -5,7 +5,8 @@
 // fewer than max_inflight batches are on the GPU it takes the waiting
 // requests of the oldest one's cost class (K class; K = 256 split by
 // M >= 4 K), so that a cheap request never waits inside a batch held up by
-// a slow one (up to max_batch), checks the arena for room (admission by free
+// a slow one (up to max_batch) -- the 256-user classes holding at most all
+// but one of the slots, which stays for the cheap ones -- checks the arena for room (admission by free
 // device memory; otherwise it waits for a batch to retire), builds a ragged
 // plan and launches it on its own stream, so requests that arrive while
 // other batches run are admitted as soon as a slot and memory free up and
@@ -52,6 +53,7 @@ struct Batch {
     int32_t *status_dev = nullptr;   // device, one per request
     int32_t *status_host = nullptr;  // pinned
     int slot = -1;
+    int cls = 0;                     // cost class of its requests
     std::atomic<int> done{0};
     double t_done = 0.0;
 };
@@ -80,6 +82,7 @@ struct jacpcg_server {
     size_t n_pending = 0;
     std::unordered_map<uint64_t, Result> results;
     std::vector<Batch *> inflight;
+    int slow_inflight = 0;                // in-flight batches of the 256-user classes
     uint64_t next_ticket = 1;
     bool stop = false;
     bool failed = false;
@@ -116,6 +119,7 @@ void reap(jacpcg_server *s) {
         s->n_done += b->tickets.size();
         if (b->plan) jacpcg_plan_destroy(b->plan);
         s->slot_busy[b->slot] = false;
+        if (b->cls >= 2) --s->slow_inflight;
         delete b;
         s->inflight.erase(s->inflight.begin() + i);
         s->cv_done.notify_all();
@@ -159,11 +163,20 @@ void scheduler(jacpcg_server *s) {
             s->cv_work.wait_for(lk, std::chrono::microseconds(20));
             continue;
         }
-        // the class of the oldest waiting request (tickets grow with arrival)
+        // the class of the oldest waiting request (tickets grow with arrival); under
+        // cost classes the 256-user classes (batches of milliseconds) may hold at
+        // most max_inflight - 1 slots, so one stays for the cheap classes
+        const bool reserve = s->cfg.batch_policy == JACPCG_BATCH_COST_CLASS && s->cfg.max_inflight >= 2 &&
+                             s->slow_inflight >= s->cfg.max_inflight - 1;
         int cls = -1;
         for (int c = 0; c < 4; ++c)
-            if (!s->queue[c].empty() && (cls < 0 || s->queue[c].front().ticket < s->queue[cls].front().ticket))
+            if (!s->queue[c].empty() && !(reserve && c >= 2) &&
+                (cls < 0 || s->queue[c].front().ticket < s->queue[cls].front().ticket))
                 cls = c;
+        if (cls < 0) {   // only slow requests wait and their share of the slots is taken
+            s->cv_work.wait_for(lk, std::chrono::microseconds(20));
+            continue;
+        }
         std::deque<Request> &q = s->queue[cls];
         // take up to max_batch of its requests, shrinking until the arena admits them
         size_t take = std::min<size_t>(q.size(), (size_t)s->cfg.max_batch);
@@ -210,6 +223,7 @@ void scheduler(jacpcg_server *s) {
         }
         b->srv = s;
         b->slot = slot;
+        b->cls = cls;
         b->status_dev = s->status_dev[slot];
         b->status_host = s->status_host[slot];
         for (auto &r : reqs) b->tickets.push_back(r.ticket);
@@ -239,6 +253,7 @@ void scheduler(jacpcg_server *s) {
             continue;
         }
         s->inflight.push_back(b);
+        if (cls >= 2) ++s->slow_inflight;
         s->n_batches += 1;
         s->sum_batch += (double)take;
     }
