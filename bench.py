@@ -1245,7 +1245,7 @@ def run_headline(args):
     f_it = float(sum(int(v) * K * (8.0 * K * K + 46.0 * K - 6.0) + 4.0 * K * K + 2.0 * K for v in it0))
     work = {"gram": 4.0 * M * K * (K + 1) * n, "pcg": f_it, "hx": 8.0 * M * K * K * n}
     hbytes = {"gram": (4.0 * M * K + 8.0 * K * K) * n, "hx": (4.0 * M * K + 8.0 * M * K + 8.0 * K * K) * n}
-    tf32 = peaks["tf32_tflops"] if peaks else mp["bf16_tflops"] * 1.1 / 2.25
+    bf16 = peaks["bf16_tflops"] if peaks else mp["bf16_tflops"]
     fp32 = peaks["fp32_fma_tflops"] if peaks else None
     per_kernel = {}
     for ph in ("gram", "pcg", "hx"):
@@ -1257,13 +1257,18 @@ def run_headline(args):
                    "peak_source": "measured in this run: FP32 FMA probe kernel (jacpcg_probe_fp32_fma)",
                    "kernel": "pcg_kernel<256, 2, 8> (SIMT, FP32 FMA)"}
         else:
-            rec = {"bound": "tensor", "achieved": tfl, "peak": tf32, "unit": "TFLOP/s", "frac": tfl / tf32,
-                   "kernel": {"gram": "gram_tc64 + gram_tc_cross", "pcg": "pcg_tcw_kernel<256> (A streamed in TF32 stages)",
-                              "hx": "hx_tc_wide"}[ph],
-                   "peak_source": ("measured in this run: cuBLAS TF32 GEMM burst (torch.matmul, FP32 with TF32 "
-                                   "allowed, 8192^3)" if peaks else "MEASURED_PEAKS bf16 burst x 1.1/2.25"),
-                   "note": "algorithmic flops; the 3xTF32 split executes 3x (Gram head x head, two "
-                           "corrections) as many tensor flops"}
+            rec = {"bound": "tensor", "achieved": tfl, "peak": bf16, "unit": "TFLOP/s", "frac": tfl / bf16,
+                   "kernel": {"gram": "gram_bf16_kernel (kind::f16, BF16 H by tiled TMA)",
+                              "pcg": "pcg_tcw_kernel<256> (kind::f16, A streamed as FP16 head and tail)",
+                              "hx": "hx_bf16_kernel (kind::f16, X as three BF16 terms)"}[ph],
+                   "peak_source": ("measured in this run: cuBLAS BF16 GEMM burst (torch.matmul, 8192^3)"
+                                   if peaks else "MEASURED_PEAKS bf16 burst"),
+                   "note": {"gram": "algorithmic flops (Hermitian half); the kernel executes the diagonal "
+                                    "blocks in full, 1.5x the algorithmic count",
+                            "pcg": "algorithmic flops (Appendix counts); the head/tail split executes 3x "
+                                   "as many tensor flops (head x head and both corrections)",
+                            "hx": "algorithmic flops; X enters as three exact bfloat16 terms, 3x as many "
+                                  "tensor flops"}[ph]}
             if ph in hbytes:
                 gbs = hbytes[ph] / (ms / 1e3) / 1e9
                 rec["hbm"] = {"achieved": gbs, "peak": mp["hbm_gbs"], "unit": "GB/s", "frac": gbs / mp["hbm_gbs"],
@@ -1303,7 +1308,7 @@ def run_headline(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
             "warmup": args.warmup, "ms_per_step": t_max / steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (H bf16; tf32x3 contractions)",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (H bf16; contractions on bf16/fp16 tensor cores, products exact)",
             "data": "synthetic", "config": xl_config(n, args),
             "latency_ms": lat,
             "step_ms": {"p50": step_ms[len(step_ms) // 2], "p99": step_ms[min(len(step_ms) - 1, int(0.99 * len(step_ms)))],
@@ -1325,16 +1330,17 @@ XL_ITER_TENSOR = True    # the K = 256 iteration runs on the tensor cores (pcg_t
 
 
 def measure_peaks(torch, binding):
-    """TF32 tensor roof (cuBLAS GEMM, FP32 inputs with TF32 allowed, 8192^3,
-    best of 10) and FP32 FMA roof (the library's FMA probe over 8 CTAs per SM,
-    best of 5), both timed with CUDA events on this GPU in this run."""
+    """BF16 and TF32 tensor roofs (cuBLAS GEMM 8192^3, bfloat16 inputs, and FP32
+    inputs with TF32 allowed; best of 12) and the FP32 FMA roof (the library's
+    FMA probe over 8 CTAs per SM, best of 6), all timed with CUDA events on
+    this GPU in this run.  The BF16 figure is the roof of the kind::f16 kernels
+    (BF16 and FP16 operands run at the same rate)."""
     s = torch.cuda.current_stream()
-    old = torch.backends.cuda.matmul.allow_tf32
-    torch.backends.cuda.matmul.allow_tf32 = True
-    try:
+
+    def gemm_tflops(dtype):
         N = 8192
-        a = torch.randn(N, N, device="cuda")
-        b = torch.randn(N, N, device="cuda")
+        a = torch.randn(N, N, device="cuda").to(dtype)
+        b = torch.randn(N, N, device="cuda").to(dtype)
         best = float("inf")
         for _ in range(12):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1343,10 +1349,16 @@ def measure_peaks(torch, binding):
             e1.record(s)
             torch.cuda.synchronize()
             best = min(best, e0.elapsed_time(e1))
-        tf32 = 2.0 * N ** 3 / (best / 1e3) / 1e12
         del a, b
+        return 2.0 * N ** 3 / (best / 1e3) / 1e12
+
+    old = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        tf32 = gemm_tflops(torch.float32)
     finally:
         torch.backends.cuda.matmul.allow_tf32 = old
+    bf16 = gemm_tflops(torch.bfloat16)
     scratch = torch.zeros(152 * 8, device="cuda")
     best = float("inf")
     flops = 0.0
@@ -1357,9 +1369,9 @@ def measure_peaks(torch, binding):
         e1.record(s)
         torch.cuda.synchronize()
         best = min(best, e0.elapsed_time(e1))
-    return {"tf32_tflops": tf32, "fp32_fma_tflops": flops / (best / 1e3) / 1e12,
-            "how": "TF32: torch.matmul 8192^3 FP32 with TF32 allowed, best of 12; FP32: "
-                   "jacpcg_probe_fp32_fma, 1216 CTAs x 256 threads x 8 independent FMA chains, best of 6"}
+    return {"bf16_tflops": bf16, "tf32_tflops": tf32, "fp32_fma_tflops": flops / (best / 1e3) / 1e12,
+            "how": "BF16 / TF32: torch.matmul 8192^3 on bfloat16 / on FP32 with TF32 allowed, best of 12; "
+                   "FP32: jacpcg_probe_fp32_fma, 1216 CTAs x 256 threads x 8 independent FMA chains, best of 6"}
 
 
 def run_e2e_xl(args, binding, prec, Hst, xi, torch):

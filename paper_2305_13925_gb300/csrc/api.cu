@@ -113,7 +113,7 @@ struct Arena {
 
 // What one kernel launch of a plan covers.
 struct Launch {
-    enum Kind { GRAM, PCG, HX, GRAM_TC, GRAM_TCX, HX_TC, HX_TCW, PCG_TC, CHOL, SINR, TCW_PREP, PCG_TCW } kind;
+    enum Kind { GRAM, PCG, HX, GRAM_TC, GRAM_TCX, HX_TC, HX_TCW, PCG_TC, CHOL, SINR, TCW_PREP, PCG_TCW, GRAM_BF16, HX_BF16 } kind;
     int phase;        // 0 Gram, 1 iteration, 2 W = H X, 3 SINR (after the power factor)
     int param;        // TB (Gram), KC (iteration), TN (W = H X)
     size_t list_off;  // byte offset of its work list inside the plan block
@@ -144,6 +144,7 @@ struct jacpcg_ctx {
     // precision and variant allow it (else SIMT shape 0), 0.. a SIMT launch shape
     int pcg_shape_idx[6] = {-1, -1, -1, -1, -1, -1};
     CUtensorMap amap{};   // the arena as rows of 64 floats, for the tiled copies of A
+    void *encode = nullptr;   // the driver's tensor-map encoder (cuTensorMapEncodeTiled)
 };
 
 struct jacpcg_plan {
@@ -165,6 +166,7 @@ struct jacpcg_plan {
     size_t res_off = 0;
     int n_res = 0;
     size_t acc_reset_bytes = 0;   // > 0: clear the accumulators before the Gram (multi-job instances)
+    size_t tmap_off = 0;          // tensor maps over the bfloat16 channels' H
 };
 
 namespace {
@@ -212,8 +214,8 @@ int n_cols(const jacpcg_instance &q) { return q.B ? q.n_rhs : q.K; }
 
 // Byte layout of one plan block.
 struct Layout {
-    size_t insts, gram, tcl, gdl, gxl, pcg, hx, hxl, hwl, res, sinr, twl, twj, accum, ws, total;
-    int n_gram, n_pcg, n_hx, n_res, n_gd, n_gx, n_hw, n_sinr, n_twj;
+    size_t insts, gram, tcl, gdl, gxl, pcg, hx, hxl, hwl, res, sinr, twl, twj, tmaps, gbl, hbl, accum, ws, total;
+    int n_gram, n_pcg, n_hx, n_res, n_gd, n_gx, n_hw, n_sinr, n_twj, n_tm, n_gb, n_hb;
     bool refine;
     std::vector<size_t> ws_off;   // per instance
 };
@@ -233,15 +235,25 @@ int n_pblocks(const jacpcg_instance &q, const int *shape_idx) {
     const int per = s.CW * s.NW;
     return (n_cols(q) + per - 1) / per;
 }
+// bfloat16 channels of the 128 and 256 classes: the Gram and W = H X read H
+// through tiled tensor copies and run kind::f16 MMAs (gram_bf16.cu,
+// hx_bf16.cu); W = H X in jobs of 32 output columns, one ||W||^2 partial per
+// 64 antennas and job
+bool bf16_native(int precision, const jacpcg_instance &q) {
+    return precision == JACPCG_TF32X3 && q.h_dtype == JACPCG_H_BF16 && k_class(q.K) >= 128;
+}
+int hx_bf16_groups(const jacpcg_instance &q) { return (n_cols(q) + 31) / 32; }
+int hx_bf16_slots(const jacpcg_instance &q) { return ((q.M + 63) / 64) * hx_bf16_groups(q); }
+size_t wpart_slots(const jacpcg_instance &q) { return std::max(n_wtiles(q), hx_bf16_slots(q)); }
 // A, X, 1/diag, W partials; then R and its column norms for refinement; then,
-// for the 128 and 256 classes' tensor-core iteration, A split into its
-// streamed TF32 stages (4 KC^2 floats)
+// for the 128 and 256 classes' tensor-core iteration, A as its streamed FP16
+// stages (head and tail of real and imaginary parts: 8 KC^2 bytes)
 size_t inst_ws_bytes(const jacpcg_instance &q, bool refine, bool tcw) {
     const size_t KC = k_class(q.K);
     size_t b = align_up(KC * KC * sizeof(float2)) * 2 + align_up(KC * sizeof(float)) +
-               align_up(n_wtiles(q) * sizeof(float));
+               align_up(wpart_slots(q) * sizeof(float));
     if (refine) b += align_up(KC * KC * sizeof(float2)) + align_up((2 * KC + 2) * sizeof(float));
-    if (tcw) b += align_up(4 * KC * KC * sizeof(float));
+    if (tcw) b += align_up(4 * KC * KC * 2);
     return b;
 }
 constexpr int TCW_NB = 32;   // columns per CTA of the 128 / 256-class tensor-core iteration
@@ -283,6 +295,7 @@ Layout make_layout(const jacpcg_config &cfg, const jacpcg_instance *inst, int n,
                    const int *shape_idx) {
     Layout L{};
     L.n_gram = L.n_pcg = L.n_hx = L.n_res = L.n_gd = L.n_gx = L.n_hw = L.n_sinr = L.n_twj = 0;
+    L.n_tm = L.n_gb = L.n_hb = 0;
     L.refine = refine;
     for (int i = 0; i < n; ++i) {
         if (refines(cfg, refine, inst[i])) L.n_res += (n_cols(inst[i]) + RES_CB - 1) / RES_CB;
@@ -295,6 +308,11 @@ Layout make_layout(const jacpcg_config &cfg, const jacpcg_instance *inst, int n,
         L.n_hx += n_wtiles(inst[i]);
         if (inst[i].sinr) L.n_sinr += (inst[i].K + 7) / 8;
         if (pcg_on_tcw(cfg, shape_idx, k_class(inst[i].K))) L.n_twj += (n_cols(inst[i]) + TCW_NB - 1) / TCW_NB;
+        if (bf16_native(cfg.precision, inst[i])) {
+            L.n_tm += 2;   // the Gram's and W = H X's tensor maps
+            if (!accurate_gram(refine, inst[i])) L.n_gb += k_class(inst[i].K) == 256 ? 3 : 1;
+            L.n_hb += hx_bf16_groups(inst[i]);
+        }
     }
     size_t o = 0;
     L.insts = o;  o += align_up(sizeof(DevInst) * n);
@@ -310,6 +328,9 @@ Layout make_layout(const jacpcg_config &cfg, const jacpcg_instance *inst, int n,
     L.sinr = o;   o += align_up(sizeof(int2) * L.n_sinr);
     L.twl = o;    o += align_up(sizeof(int) * n);
     L.twj = o;    o += align_up(sizeof(int2) * L.n_twj);
+    L.tmaps = o;  o += align_up(sizeof(CUtensorMap) * L.n_tm);
+    L.gbl = o;    o += align_up(sizeof(int4) * L.n_gb);
+    L.hbl = o;    o += align_up(sizeof(int4) * L.n_hb);
     L.accum = o;  o += align_up(sizeof(int32_t) * n) * 3;
     L.ws = o;
     L.ws_off.resize(n);
@@ -323,7 +344,29 @@ Layout make_layout(const jacpcg_config &cfg, const jacpcg_instance *inst, int n,
 
 // Fill the host image of the table part ([0, L.accum)) for a block at `dev`
 // and the launch list of the plan.
-void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, const Layout &L,
+// Tensor maps over a bfloat16 channel's H read as K rows of 2M values (row
+// stride ldh * 4 bytes), 128-byte swizzle, zero fill past M and K: box 64 x 128
+// for the Gram (user tiles), 64 x 64 for W = H X.
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+bool encode_h_maps(const jacpcg_ctx *ctx, const jacpcg_instance &q, CUtensorMap *gram_map, CUtensorMap *hx_map) {
+    if (!ctx->encode) return false;
+    const EncodeTiled enc = reinterpret_cast<EncodeTiled>(ctx->encode);
+    const cuuint64_t dims[2] = {2 * (cuuint64_t)q.M, (cuuint64_t)q.K};
+    const cuuint64_t strides[1] = {4 * (cuuint64_t)q.ldh};
+    const cuuint32_t elem[2] = {1, 1};
+    const cuuint32_t gbox[2] = {64, 128}, hbox[2] = {64, 64};
+    void *base = const_cast<void *>(q.H);
+    return enc(gram_map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, gbox, elem,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS &&
+           enc(hx_map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, hbox, elem,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, const Layout &L,
                   char *dev, char *host, std::vector<Launch> &launches) {
     DevInst *hi = reinterpret_cast<DevInst *>(host + L.insts);
     for (int i = 0; i < n; ++i) {
@@ -342,9 +385,10 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
                                             align_up(KC * sizeof(float)));
         d.M = q.M; d.K = q.K; d.ldh = q.ldh; d.ldw = q.ldw; d.KC = KC;
         d.max_iter = q.max_iter;
-        d.n_wpart = !hx_on_tc(ctx->cfg.precision, KC) ? n_wtiles(q)
-                    : KC == 64                         ? (q.M + 127) / 128
-                                                       : ((q.M + 127) / 128) * hx_tc_groups(q);
+        d.n_wpart = !hx_on_tc(ctx->cfg.precision, KC)   ? n_wtiles(q)
+                    : bf16_native(ctx->cfg.precision, q) ? hx_bf16_slots(q)
+                    : KC == 64                           ? (q.M + 127) / 128
+                                                         : ((q.M + 127) / 128) * hx_tc_groups(q);
         d.variant = ctx->cfg.variant;
         d.omega = q.omega > 0.f ? q.omega : 1.f;
         d.sinr = q.sinr;
@@ -362,7 +406,7 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
         }
         if (L.refine) {
             const size_t base = 2 * align_up((size_t)KC * KC * sizeof(float2)) + align_up(KC * sizeof(float)) +
-                                align_up(n_wtiles(q) * sizeof(float));
+                                align_up(wpart_slots(q) * sizeof(float));
             d.R = reinterpret_cast<float2 *>(w + base);
             d.rnorm = reinterpret_cast<float *>(w + base + align_up((size_t)KC * KC * sizeof(float2)));
             d.rctl = d.rnorm + 2 * KC;
@@ -389,7 +433,7 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
     int nd = 0, nx = 0;
     for (int i = 0; i < n; ++i) {
         const int KC = k_class(inst[i].K);
-        if (!gram_on_tc(prec, KC) || accurate_gram(L.refine, inst[i])) continue;
+        if (!gram_on_tc(prec, KC) || accurate_gram(L.refine, inst[i]) || bf16_native(prec, inst[i])) continue;
         for (int a = 0; a < KC / 64; ++a) {
             gd[nd++] = make_int2(i, a);
             for (int b = a + 1; b < KC / 64; ++b) gx[nx++] = make_int4(i, a, b, 0);
@@ -397,6 +441,23 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
     }
     if (nd) launches.push_back({Launch::GRAM_TC, 0, 0, L.gdl, nd});
     if (nx) launches.push_back({Launch::GRAM_TCX, 0, 0, L.gxl, nx});
+    // bfloat16 channels of the 128 and 256 classes: two tensor maps each, the
+    // Gram's (instance, tile a, tile b >= a) jobs and W = H X's (instance, group) jobs
+    CUtensorMap *tm = reinterpret_cast<CUtensorMap *>(host + L.tmaps);
+    int4 *gb = reinterpret_cast<int4 *>(host + L.gbl);
+    int4 *hb = reinterpret_cast<int4 *>(host + L.hbl);
+    int nm = 0, ngb = 0, nhb = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!bf16_native(prec, inst[i])) continue;
+        if (!encode_h_maps(ctx, inst[i], tm + nm, tm + nm + 1)) return false;
+        const int nt = k_class(inst[i].K) / 128;
+        if (!accurate_gram(L.refine, inst[i]))
+            for (int a = 0; a < nt; ++a)
+                for (int b = a; b < nt; ++b) gb[ngb++] = make_int4(i, a, b, nm);
+        for (int g = 0; g < hx_bf16_groups(inst[i]); ++g) hb[nhb++] = make_int4(i, g, nm + 1, 0);
+        nm += 2;
+    }
+    if (ngb) launches.push_back({Launch::GRAM_BF16, 0, 0, L.gbl, ngb});
     // the K = 64 class's tensor-core iteration: instance list
     int *tl = reinterpret_cast<int *>(host + L.tcl);
     int nt = 0;
@@ -476,9 +537,10 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
     int2 *hw = reinterpret_cast<int2 *>(host + L.hwl);
     int nw = 0;
     for (int i = 0; i < n; ++i)
-        if (hx_on_tc(prec, k_class(inst[i].K)) && k_class(inst[i].K) > 64)
+        if (hx_on_tc(prec, k_class(inst[i].K)) && k_class(inst[i].K) > 64 && !bf16_native(prec, inst[i]))
             for (int b = 0; b < hx_tc_groups(inst[i]); ++b) hw[nw++] = make_int2(i, b);
     if (nw) launches.push_back({Launch::HX_TCW, 2, 0, L.hwl, nw});
+    if (nhb) launches.push_back({Launch::HX_BF16, 2, 0, L.hbl, nhb});
     // W = H X tiles (SIMT) grouped by tile width; slot = index of the tile in its instance
     int4 *ht = reinterpret_cast<int4 *>(host + L.hx);
     int h = 0;
@@ -504,6 +566,7 @@ void build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
                 for (int b = 0; b < (inst[i].K + 7) / 8; ++b) sj[ns++] = make_int2(i, b);
         if (ns > start) launches.push_back({Launch::SINR, 3, KC, L.sinr + start * sizeof(int2), ns - start});
     }
+    return true;
 }
 
 constexpr size_t MAX_PROFILED = 4096;
@@ -579,6 +642,14 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
                 case Launch::PCG_TCW:
                     e = launch_pcg_tcw(l.param, ctx->cfg.variant, pl->d_insts, static_cast<const int2 *>(list),
                                        l.count, pl->acc, s, 0);
+                    break;
+                case Launch::GRAM_BF16:
+                    e = launch_gram_bf16(pl->d_insts, static_cast<const int4 *>(list), l.count,
+                                         reinterpret_cast<const CUtensorMap *>(pl->dev + pl->tmap_off), pl->acc, s);
+                    break;
+                case Launch::HX_BF16:
+                    e = launch_hx_bf16(pl->d_insts, static_cast<const int4 *>(list), l.count,
+                                       reinterpret_cast<const CUtensorMap *>(pl->dev + pl->tmap_off), pl->acc, s);
                     break;
             }
             if (e != cudaSuccess) return cuda_fail(ctx, e);
@@ -671,7 +742,8 @@ jacpcg_status make_plan(jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, int
     for (int i = 0; i < n; ++i) pl->want_hist = pl->want_hist || inst[i].resid_hist != nullptr;
     pl->res_off = L.res;
     pl->n_res = L.n_res;
-    if (L.n_gx) pl->acc_reset_bytes = 3 * align_up(sizeof(int32_t) * n);
+    if (L.n_gx || L.n_gb) pl->acc_reset_bytes = 3 * align_up(sizeof(int32_t) * n);
+    pl->tmap_off = L.tmaps;
     const size_t tbytes = L.accum;   // tables occupy [0, accum)
     auto fail = [&](jacpcg_status s) {
         ctx->arena.release(pl->off, pl->bytes, nullptr);
@@ -695,7 +767,7 @@ jacpcg_status make_plan(jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, int
         ctx->staging_bytes = tbytes;
     }
     std::memset(ctx->staging, 0, tbytes);
-    build_tables(ctx, inst, n, L, pl->dev, ctx->staging, pl->launches);
+    if (!build_tables(ctx, inst, n, L, pl->dev, ctx->staging, pl->launches)) return fail(JACPCG_ECUDA);
     if (async_stream) {
         if (cudaMemcpyAsync(pl->dev, ctx->staging, tbytes, cudaMemcpyHostToDevice, async_stream) !=
                 cudaSuccess ||
@@ -777,6 +849,7 @@ bool encode_arena_map(jacpcg_ctx *ctx) {
     const cuuint64_t strides[1] = {ALIGN};
     const cuuint32_t box[2] = {64, 128};
     const cuuint32_t elem[2] = {1, 1};
+    ctx->encode = fn;
     return reinterpret_cast<Encode>(fn)(&ctx->amap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ctx->arena.base, dims,
                                         strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
                                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,

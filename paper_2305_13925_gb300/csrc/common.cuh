@@ -46,8 +46,8 @@ struct DevInst {
     const float2 *X0;     // optional initial point, K x ncols, ld K (caller)
     int ldb;
     int ncols;            // right-hand sides: K for B = I, else n_rhs (<= KC)
-    float *As;            // workspace: A split into the streamed TF32 stages of the K = 128 and
-                          // 256 tensor-core iteration (null when that iteration is not used)
+    float *As;            // workspace: A as the streamed FP16 stages of the K = 128 and 256
+                          // tensor-core iteration (null when that iteration is not used)
     float *sinr;          // optional per-user SINR out, K floats (caller); B = I only
     float noise;          // noise power sigma^2 of the SINR (0: 1)
 };

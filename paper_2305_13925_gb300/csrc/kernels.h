@@ -48,6 +48,17 @@ cudaError_t launch_gram_tc64(const DevInst *insts, const int2 *list, int n, DevA
 // 256 classes); list: (instance, a, b, 0) jobs
 cudaError_t launch_gram_tc_cross(const DevInst *insts, const int4 *list, int n, DevAccum acc,
                                  cudaStream_t s);
+// tensor-core Gram of bfloat16 channels of the K = 128 and 256 classes (kind::f16,
+// H read by tiled tensor copies); jobs: (instance, user tile a, user tile b >= a,
+// index into maps), 128-user tiles; maps: per instance a 2-D BF16 tensor map over
+// H as K rows of 2M values, box 64 x 128, 128-byte swizzle
+cudaError_t launch_gram_bf16(const DevInst *insts, const int4 *jobs, int n, const CUtensorMap *maps, DevAccum acc,
+                             cudaStream_t s);
+// tensor-core W = H X for bfloat16 channels of the K = 128 and 256 classes (kind::f16,
+// X as three exact bfloat16 terms); jobs: (instance, 32-column output group, index
+// into maps, 0); maps: per instance the same tensor over H with box 64 x 64
+cudaError_t launch_hx_bf16(const DevInst *insts, const int4 *jobs, int n, const CUtensorMap *maps, DevAccum acc,
+                           cudaStream_t s);
 // tensor-core W = H X for the K = 64 class (3xTF32); list: instance ids
 cudaError_t launch_hx_tc64(const DevInst *insts, const int *list, int n, DevAccum acc,
                            cudaStream_t s);
@@ -61,7 +72,7 @@ cudaError_t launch_hx_tc_wide(const DevInst *insts, const int2 *list, int n, Dev
 cudaError_t launch_pcg_tc64(int variant, const DevInst *insts, const int *list, int n, DevAccum acc,
                             const CUtensorMap *amap, const char *arena, cudaStream_t s, int mode);
 // tensor-core iteration for the K = 128 and 256 classes (standard or plain CG):
-// launch_tcw_prep splits each listed instance's A into the streamed TF32 stages
+// launch_tcw_prep stores each listed instance's A as the streamed FP16 stages
 // (DevInst::As), launch_pcg_tcw iterates; jobs: (instance, first of 32 columns)
 cudaError_t launch_tcw_prep(int KC, const DevInst *insts, const int *list, int n, cudaStream_t s);
 cudaError_t launch_pcg_tcw(int KC, int variant, const DevInst *insts, const int2 *jobs, int n, DevAccum acc,

@@ -4,28 +4,37 @@
 // caller's symbol vectors, or the refinement residual; warm start from X0),
 // as pcg_tc.cu does for the 64 class.
 //
-// At these sizes A does not fit on one SM (K = 256: 512 KB complex, 1 MB as
-// TF32 head and tail), so it is streamed: once per instance a prep kernel
-// splits A into TF32 heads and exact tails of its real and imaginary parts
-// and stores them as MMA-ready 16 KB stages -- for row tile rt (128 rows) and
-// k-step ks (8 columns): [Ar_h | Ar_t | Ai_h | Ai_t], each a 128 x 8 tile in
-// the canonical no-swizzle K-major layout -- and each iteration streams the
-// stages through a 6-deep shared-memory ring with bulk copies (the TMA unit,
+// At these sizes A does not fit on one SM (K = 256: 512 KB complex), so it
+// is streamed.  Once per instance a prep kernel stores it as MMA-ready FP16
+// stages, for row tile rt (128 rows) and k-step ks (16 columns): [Ar_h |
+// Ar_t | Ai_h | Ai_t], each a 128 x 16 tile in the canonical no-swizzle
+// K-major layout, of the scaled matrix
+//   Ah = 2^13 E^-1 A E^-1,   E = diag(2^e_i),  2^e_i <= sqrt(A_ii) < 2^(e_i + 1),
+// split into an FP16 head and the FP16 rounding of the rest.  Every scaling is
+// a power of two (exact), and |A_ij| <= sqrt(A_ii A_jj) bounds |Ah_ij| below
+// 2^15, inside FP16's range; head + tail carries 22 bits of every entry, as
+// the TF32 head and tail of the 3xTF32 split do, in half the bytes, and the
+// kind::f16 MMAs run at twice the kind::tf32 rate.  Each iteration streams the
+// stages through a shared-memory ring with bulk copies (the TMA unit,
 // cp.async.bulk), completion counted in bytes on an mbarrier.  Real and
 // imaginary parts are kept apart (planar), so each byte of A is streamed once
 // per iteration rather than twice as in the 2 x 2 real expansion.
 //
 // The columns of X are independent systems sharing A, so a CTA owns 32 of
 // them (NB) for one instance.  Their P is resident in shared memory as the
-// MMA's B operand, laid out as 4 NB rows [Pr_h | Pi_h | Pr_t | Pi_t] along N
-// (TF32 heads of Re p and Im p, then the exact tails).  Per k-step:
+// MMA's B operand, laid out as 4 NB rows [Pr_h | Pi_h | Pr_t | Pi_t] along N:
+// FP16 head and tail of s_j E p_j, s_j a power of two per column that puts
+// the column's largest entry in [2^14, 2^15).  Per k-step:
 //   U += Ar_h [P_h | P_t]  (N = 128),   U[64..] += Ar_t P_h  (N = 64),
 //   V += Ai_h [P_h | P_t],              V[64..] += Ai_t P_h,
-// so U = Ar [Pr | Pi] and V = Ai [Pr | Pi] to 3xTF32 accuracy (columns 0-63
-// head x head, 64-127 both corrections), and
-//   Re q = Ar Pr - Ai Pi,   Im q = Ai Pr + Ar Pi.
-// U and V of both row tiles take 4 x 128 TMEM columns (K = 256: all 512).
-// The accumulation chain of a row tile is its KC / 8 k-steps.
+// so U = Ar [Pr | Pi] and V = Ai [Pr | Pi] with every product exact (columns
+// 0-63 head x head, 64-127 both corrections), and
+//   Re q = Ar Pr - Ai Pi,   Im q = Ai Pr + Ar Pi,
+// each unscaled by 2^(e_i - 13) / s_j on its way out of TMEM.  U and V of both
+// row tiles take 4 x 128 TMEM columns (K = 256: all 512).  The accumulation
+// chain of a row tile is its KC / 16 k-steps.  The iteration uses p as
+// published (head + tail, unscaled: 22 bits), in the product and everywhere
+// else, so the recurrences stay consistent.
 //
 // Roles: 8 warps own the vectors; each iteration they publish P (split) into
 // the B operand and vote on continuing (one barrier reduction), then thread 0
@@ -46,6 +55,8 @@
 // accurate to a few units, and are summed so.  All eight lanes of a column
 // hold bit-identical totals.  Every wait is bounded; a timeout sets the instance's ETIMEOUT
 // flag and ends its iteration.
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "tc.cuh"
@@ -57,9 +68,11 @@ namespace {
 constexpr int NB = 32;                        // right-hand-side columns per CTA
 constexpr int THREADS = 256;                  // 8 warps: 2 per SM sub-partition, up to 255 registers
 constexpr int EPI = THREADS;
-constexpr int RING = 6;                       // stages in flight
-constexpr int STAGE = 16384;                  // bytes: four 128 x 8 TF32 tiles
+constexpr int RING = 9;                       // stages in flight
+constexpr int STAGE = 16384;                  // bytes: four 128 x 16 FP16 tiles
 constexpr int TILE = 4096;
+constexpr int SA = 13;                        // A is stored scaled by 2^SA (entries below 2^15)
+constexpr int SP = 14;                        // a column of P is scaled to a largest entry in [2^14, 2^15)
 constexpr int QLD = 136;                      // floats per staged Q column (128 rows + 8)
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 constexpr int BAR_EPI = 1;                    // named barrier of the epilogue warps
@@ -67,13 +80,14 @@ constexpr int BAR_EPI = 1;                    // named barrier of the epilogue w
 template <int KC>
 struct Cfg {
     static constexpr int RT = KC / 128;                      // row tiles
-    static constexpr int KS = KC / 8;                        // k-steps per row tile
+    static constexpr int KS = KC / 16;                       // k-steps per row tile
     static constexpr int NSTAGE = RT * KS;                   // stages per iteration
-    static constexpr uint32_t SBO_B = (KC / 4) * 128;        // bytes between 8-row groups of B (N)
-    static constexpr int B_BYTES = 4 * NB * KC * 4;          // the B operand
+    static constexpr uint32_t SBO_B = (KC / 8) * 128;        // bytes between 8-row groups of B (N)
+    static constexpr int B_BYTES = 4 * NB * KC * 2;          // the B operand
     static constexpr int MR = KC / 8;                        // complex rows per epilogue thread
     static constexpr uint32_t TMEM_COLS = RT == 2 ? 512 : 256;
-    static constexpr int SMEM = B_BYTES + RING * STAGE + KC * 4 + 256;
+    // B, ring, then per row 1 / d, 2^e, 2^-e; per column the readout factor
+    static constexpr int SMEM = B_BYTES + RING * STAGE + 3 * KC * 4 + NB * 4 + 256;
     static_assert(2 * RT * NB * QLD * 4 <= RING * STAGE, "Q staging fits the ring");
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
@@ -109,17 +123,34 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
         : "memory");
 }
 
-// byte offset of element (n, k) in the B operand (K-major, no swizzle)
+// byte offset of element (n, k) in the B operand (FP16, K-major, no swizzle)
 template <int KC>
 __device__ __forceinline__ uint32_t b_off(int n, int k) {
-    return (uint32_t)(n >> 3) * Cfg<KC>::SBO_B + (uint32_t)(k >> 2) * 128u + (uint32_t)(n & 7) * 16u +
-           (uint32_t)(k & 3) * 4u;
+    return (uint32_t)(n >> 3) * Cfg<KC>::SBO_B + (uint32_t)(k >> 3) * 128u + (uint32_t)(n & 7) * 16u +
+           (uint32_t)(k & 7) * 2u;
+}
+
+// 2^v as a float, v in [-126, 127]
+__device__ __forceinline__ float pow2f(int v) { return __uint_as_float((uint32_t)(v + 127) << 23); }
+// e with 2^e <= x < 2^(e + 1) for a normal x > 0
+__device__ __forceinline__ int exp2_of(float x) { return (int)((__float_as_uint(x) >> 23) & 0xFFu) - 127; }
+// the row exponent e_i of the scaling: 2^e_i <= sqrt(A_ii) < 2^(e_i + 1); 0 for
+// padding rows (A_ii = 0) and anything not positive
+__device__ __forceinline__ int row_exp(float aii) {
+    if (!(aii >= 1.2e-38f) || !(aii < 3.0e38f)) return 0;
+    return exp2_of(sqrtf(aii));
+}
+// x = h + t + (the rest), h and t FP16 (round to nearest); the FP32 sum h + t is exact
+__device__ __forceinline__ void split_f16(float x, __half &h, __half &t) {
+    h = __float2half_rn(x);
+    t = __float2half_rn(x - __half2float(h));
 }
 
 // ---------------------------------------------------------------------------
-// A (complex, workspace ld KC) -> the streamed stages: one CTA per (instance,
-// stage); element (r, k) of a 128 x 8 tile at (r / 8) 256 + (k / 4) 128 +
-// (r mod 8) 16 + (k mod 4) 4 bytes (LBO 128 along K, SBO 256 along M).
+// A (complex, workspace ld KC) -> the streamed FP16 stages of 2^SA E^-1 A E^-1:
+// one CTA per (instance, stage); element (r, k) of a 128 x 16 tile at
+// (r / 8) 256 + (k / 8) 128 + (r mod 8) 16 + (k mod 8) 2 bytes (LBO 128 along
+// K, SBO 256 along M).
 template <int KC>
 __global__ void __launch_bounds__(256) tcw_prep_kernel(const DevInst *__restrict__ insts,
                                                       const int *__restrict__ list) {
@@ -128,19 +159,24 @@ __global__ void __launch_bounds__(256) tcw_prep_kernel(const DevInst *__restrict
     const int s = blockIdx.x % C::NSTAGE, rt = s / C::KS, ks = s % C::KS;
     const DevInst &in = insts[id];
     char *dst = reinterpret_cast<char *>(in.As) + (size_t)s * STAGE;
+    const float2 *__restrict__ A = in.A;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 8; ++u) {
         const int e = threadIdx.x + 256 * u, r = e & 127, k = e >> 7;
-        const float2 v = in.A[(size_t)(rt * 128 + r) + (size_t)(ks * 8 + k) * KC];
-        float rh, rl, ih, il;
-        tc::split_tf32(v.x, rh, rl);
-        tc::split_tf32(v.y, ih, il);
-        const uint32_t o = (uint32_t)(r >> 3) * 256u + (uint32_t)(k >> 2) * 128u + (uint32_t)(r & 7) * 16u +
-                           (uint32_t)(k & 3) * 4u;
-        *reinterpret_cast<float *>(dst + o) = rh;
-        *reinterpret_cast<float *>(dst + TILE + o) = rl;
-        *reinterpret_cast<float *>(dst + 2 * TILE + o) = ih;
-        *reinterpret_cast<float *>(dst + 3 * TILE + o) = il;
+        const int gi = rt * 128 + r, gk = ks * 16 + k;
+        const float2 v = A[(size_t)gi + (size_t)gk * KC];
+        // two factors, each inside the float exponent range; every product exact
+        const float si = pow2f(SA - row_exp(A[(size_t)gi * (KC + 1)].x));
+        const float sk = pow2f(-row_exp(A[(size_t)gk * (KC + 1)].x));
+        __half rh, rl, ih, il;
+        split_f16((v.x * si) * sk, rh, rl);
+        split_f16((v.y * si) * sk, ih, il);
+        const uint32_t o = (uint32_t)(r >> 3) * 256u + (uint32_t)(k >> 3) * 128u + (uint32_t)(r & 7) * 16u +
+                           (uint32_t)(k & 7) * 2u;
+        *reinterpret_cast<__half *>(dst + o) = rh;
+        *reinterpret_cast<__half *>(dst + TILE + o) = rl;
+        *reinterpret_cast<__half *>(dst + 2 * TILE + o) = ih;
+        *reinterpret_cast<__half *>(dst + 3 * TILE + o) = il;
     }
 }
 
@@ -236,8 +272,11 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
     using C = Cfg<KC>;
     constexpr int MR = C::MR;
     extern __shared__ __align__(1024) unsigned char smem[];
-    float *dvs = reinterpret_cast<float *>(smem + C::B_BYTES + RING * STAGE);
-    Ctl &S = *reinterpret_cast<Ctl *>(smem + C::B_BYTES + RING * STAGE + KC * 4);
+    float *dvs = reinterpret_cast<float *>(smem + C::B_BYTES + RING * STAGE);   // 1 / A_ii
+    float *scv = dvs + KC;                                                         // 2^e_i
+    float *iscv = scv + KC;                                                        // 2^-e_i
+    float *colq = iscv + KC;   // per column 2^-SA / s_j: the readout's unscaling
+    Ctl &S = *reinterpret_cast<Ctl *>(smem + C::B_BYTES + RING * STAGE + 3 * KC * 4 + NB * 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int i = 0; i < RING; ++i) {
@@ -258,7 +297,7 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
     const uint32_t tmem = S.tmem;
     const uint32_t b_base = tc::smem_u32(smem), r_base = b_base + C::B_BYTES;
     uint32_t pc = 0, mc = 0;   // stages produced (thread 0) / consumed (thread 32)
-    // One iteration's A x P: thread 0 streams the KC / 128 x KC / 8 stages into the
+    // One iteration's A x P: thread 0 streams the KC / 128 x KC / 16 stages into the
     // ring, thread 32 issues their MMAs (per stage: head x [P_h | P_t] and tail x
     // P_h, Ar then Ai) and commits to qfull; the other threads go on to wait.
     auto product = [&](const char *src) {
@@ -270,8 +309,8 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
                 bulk_load(r_base + slot * STAGE, src + (size_t)s * STAGE, STAGE, &S.full[slot]);
             }
         } else if (threadIdx.x == 32) {
-            constexpr uint32_t id128 = tc::idesc_tf32(128, 4 * NB);
-            constexpr uint32_t id64 = tc::idesc_tf32(128, 2 * NB);
+            constexpr uint32_t id128 = tc::idesc_f16(128, 4 * NB, false);
+            constexpr uint32_t id64 = tc::idesc_f16(128, 2 * NB, false);
             tc::tc_fence_after();
             for (int s = 0; s < C::NSTAGE; ++s, ++mc) {
                 const int slot = mc % RING, rt = s / C::KS, ks = s % C::KS;
@@ -281,10 +320,10 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
                 const uint64_t bd = tc::smem_desc(b_base + ks * 256, 128, C::SBO_B);
                 const uint32_t du = tmem + rt * 256, dvv = du + 128;
                 const uint32_t acc = ks > 0 ? 1u : 0u;
-                tc::mma_tf32(du, tc::smem_desc(a0, 128, 256), bd, id128, acc);
-                tc::mma_tf32(du + 64, tc::smem_desc(a0 + TILE, 128, 256), bd, id64, 1u);
-                tc::mma_tf32(dvv, tc::smem_desc(a0 + 2 * TILE, 128, 256), bd, id128, acc);
-                tc::mma_tf32(dvv + 64, tc::smem_desc(a0 + 3 * TILE, 128, 256), bd, id64, 1u);
+                tc::mma_bf16(du, tc::smem_desc(a0, 128, 256), bd, id128, acc);   // FP16 by the descriptors
+                tc::mma_bf16(du + 64, tc::smem_desc(a0 + TILE, 128, 256), bd, id64, 1u);
+                tc::mma_bf16(dvv, tc::smem_desc(a0 + 2 * TILE, 128, 256), bd, id128, acc);
+                tc::mma_bf16(dvv + 64, tc::smem_desc(a0 + 3 * TILE, 128, 256), bd, id64, 1u);
                 tc::mma_commit(&S.empty[slot]);   // the slot is free once these have read it
             }
             tc::mma_commit(&S.qfull);
@@ -299,22 +338,49 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
         float *Qre = reinterpret_cast<float *>(smem + C::B_BYTES);
         float *Qim = Qre + C::RT * NB * QLD;
         unsigned char *Bop = smem;
-        auto bget = [&](int n, int k) { return *reinterpret_cast<const float *>(Bop + b_off<KC>(n, k)); };
-        auto bset = [&](int n, int k, float v) { *reinterpret_cast<float *>(Bop + b_off<KC>(n, k)) = v; };
-        // P (head and tail of Re and Im) of the owned rows into the B operand
-        auto publish = [&](int m, float2 v) {
-            const int i = g + 8 * m;
-            float h, l;
-            tc::split_tf32(v.x, h, l);
-            bset(cl, i, h);
-            bset(2 * NB + cl, i, l);
-            tc::split_tf32(v.y, h, l);
-            bset(NB + cl, i, h);
-            bset(3 * NB + cl, i, l);
+        auto bget = [&](int n, int k) { return __half2float(*reinterpret_cast<const __half *>(Bop + b_off<KC>(n, k))); };
+        auto bset = [&](int n, int k, __half v) { *reinterpret_cast<__half *>(Bop + b_off<KC>(n, k)) = v; };
+        float pinv = 1.f;   // 1 / s_j of the owned column, as last published
+        // P of the owned rows into the B operand: f(m) gives p at row g + 8 m; the
+        // column's largest |Re|, |Im| of E p (8 lanes) sets s_j, then s_j E p goes
+        // in as FP16 head and tail.  All lanes take part (shuffles); a column that
+        // is not `active` keeps its published p.  f is evaluated twice, so it
+        // must not depend on what the second pass writes at other rows.
+        auto publish_all = [&](bool active, auto f) {
+            float mx = 0.f;
+            if (active) {
+#pragma unroll
+                for (int m = 0; m < MR; ++m) {
+                    const float2 v = f(m);
+                    mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)) * scv[g + 8 * m]);
+                }
+            }
+#pragma unroll
+            for (int o = 4; o <= 16; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            // s_j = 2^(SP - ex); ex clamped so that s_j, 1 / s_j and 2^-SA / s_j are floats
+            const int ex = (mx >= 1.2e-38f && mx < 3.0e38f) ? min(max(exp2_of(mx), SA + SP - 126), SP + 126) : SP;
+            const float sj = pow2f(SP - ex);
+            if (active) {
+#pragma unroll
+                for (int m = 0; m < MR; ++m) {
+                    const int i = g + 8 * m;
+                    const float2 v = f(m);
+                    __half h, t;
+                    split_f16((v.x * scv[i]) * sj, h, t);
+                    bset(cl, i, h);
+                    bset(2 * NB + cl, i, t);
+                    split_f16((v.y * scv[i]) * sj, h, t);
+                    bset(NB + cl, i, h);
+                    bset(3 * NB + cl, i, t);
+                }
+                pinv = pow2f(ex - SP);
+                if (g == 0) colq[cl] = pow2f(ex - SP - SA);
+            }
         };
-        auto pget = [&](int m) {   // head + tail: exactly the published value
+        auto pget = [&](int m) {   // head + tail (exact in FP32), unscaled: p as published
             const int i = g + 8 * m;
-            return make_float2(bget(cl, i) + bget(2 * NB + cl, i), bget(NB + cl, i) + bget(3 * NB + cl, i));
+            return make_float2(((bget(cl, i) + bget(2 * NB + cl, i)) * pinv) * iscv[i],
+                               ((bget(NB + cl, i) + bget(3 * NB + cl, i)) * pinv) * iscv[i]);
         };
         auto qget = [&](int m) {
             const int i = g + 8 * m;
@@ -335,8 +401,13 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
             const float tl = (MODE == 1 && in.rsolve_tol > 0.f) ? in.rsolve_tol : in.tol;
             const float tol2 = tl > 0.f ? tl * tl : -1.f;
             float2 *X = in.X + (size_t)(valid ? j : 0) * KC;   // the iterate (workspace, ld KC)
-            epi_sync();   // the previous instance's readers of dvs are done
-            for (int i = threadIdx.x; i < KC; i += EPI) dvs[i] = (i < K) ? (VAR == 2 ? 1.f : in.dinv[i]) : 0.f;
+            epi_sync();   // the previous instance's readers of dvs, scv and iscv are done
+            for (int i = threadIdx.x; i < KC; i += EPI) {
+                dvs[i] = (i < K) ? (VAR == 2 ? 1.f : in.dinv[i]) : 0.f;
+                const int e = row_exp(in.A[(size_t)i * (KC + 1)].x);   // as the prep kernel scaled A
+                scv[i] = pow2f(e);
+                iscv[i] = pow2f(-e);
+            }
             epi_sync();
             // ---- Step 1: r = b, x = x0 (mode 0), p = D^{-1} r ----
             float2 r[MR];
@@ -352,10 +423,14 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
                 r[m] = b;
                 if (MODE == 0 && valid)
                     X[i] = (warm && i < K) ? in.X0[i + (size_t)j * K] : make_float2(0.f, 0.f);
-                const float d = dvs[i];
-                // the warm pass forms A X0 first; columns beyond the right-hand sides carry 0
-                publish(m, !valid ? make_float2(0.f, 0.f) : warm ? X[i] : make_float2(d * b.x, d * b.y));
             }
+            // the warm pass forms A X0 first; columns beyond the right-hand sides carry 0
+            pinv = 1.f;
+            publish_all(true, [&](int m) {
+                const int i = g + 8 * m;
+                const float d = dvs[i];
+                return !valid ? make_float2(0.f, 0.f) : warm ? X[i] : make_float2(d * r[m].x, d * r[m].y);
+            });
             float rho = col_sumsq<MR>([&](int m, float2 &a, float2 &b) {
                 const float d = dvs[g + 8 * m];
                 a = r[m];
@@ -389,6 +464,7 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
                 for (int rt = 0; rt < C::RT; ++rt) {
                     const uint32_t tb = tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)(rt * 256 + 16 * hh);
                     const int o = (rt * NB + 16 * hh) * QLD + 32 * qw + lane;
+                    const float rf = scv[rt * 128 + 32 * qw + lane];   // row factor 2^e_i
                     float a[16], b[16], c[16], d[16];
                     // Re q = Ar Pr - Ai Pi
                     tc::tmem_ld16(tb, a);
@@ -397,7 +473,8 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
                     tc::tmem_ld16(tb + 128 + 64 + NB, d);
                     tc::tmem_ld_wait();
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) Qre[o + e * QLD] = (a[e] + b[e]) - (c[e] + d[e]);
+                    for (int e = 0; e < 16; ++e)
+                        Qre[o + e * QLD] = ((a[e] + b[e]) - (c[e] + d[e])) * rf * colq[16 * hh + e];
                     // Im q = Ai Pr + Ar Pi
                     tc::tmem_ld16(tb + 128, a);
                     tc::tmem_ld16(tb + 128 + 64, b);
@@ -405,17 +482,20 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
                     tc::tmem_ld16(tb + 64 + NB, d);
                     tc::tmem_ld_wait();
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) Qim[o + e * QLD] = (a[e] + b[e]) + (c[e] + d[e]);
+                    for (int e = 0; e < 16; ++e)
+                        Qim[o + e * QLD] = ((a[e] + b[e]) + (c[e] + d[e])) * rf * colq[16 * hh + e];
                 }
                 epi_sync();
                 if (init) {   // r = b - A X0, then Step 1 from there
 #pragma unroll
                     for (int m = 0; m < MR; ++m) {
                         const float2 q = qget(m);
-                        const float d = dvs[g + 8 * m];
                         r[m] = make_float2(r[m].x - q.x, r[m].y - q.y);
-                        publish(m, make_float2(d * r[m].x, d * r[m].y));
                     }
+                    publish_all(true, [&](int m) {
+                        const float d = dvs[g + 8 * m];
+                        return make_float2(d * r[m].x, d * r[m].y);
+                    });
                     rho = col_sumsq<MR>([&](int m, float2 &a, float2 &b) {
                         const float d = dvs[g + 8 * m];
                         a = r[m];
@@ -452,14 +532,14 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
                     b = make_float2(d * r[m].x, d * r[m].y);
                 });
                 const float rr_new = col_sumsq<MR>([&](int m, float2 &a, float2 &b) { a = r[m]; b = r[m]; });
-                if (!done) {   // p = z + beta p, published for the next product
-                    const float beta = rho != 0.f ? rz_new / rho : 0.f;
-#pragma unroll
-                    for (int m = 0; m < MR; ++m) {
-                        const float2 pv = pget(m);
-                        const float d = dvs[g + 8 * m];
-                        publish(m, make_float2(fmaf(beta, pv.x, d * r[m].x), fmaf(beta, pv.y, d * r[m].y)));
-                    }
+                // p = z + beta p, published for the next product
+                const float beta = (!done && rho != 0.f) ? rz_new / rho : 0.f;
+                publish_all(!done, [&](int m) {
+                    const float2 pv = pget(m);
+                    const float d = dvs[g + 8 * m];
+                    return make_float2(fmaf(beta, pv.x, d * r[m].x), fmaf(beta, pv.y, d * r[m].y));
+                });
+                if (!done) {
                     rho = rz_new;
                     res2 = rr_new;
                     itmax = t + 1;

@@ -125,6 +125,32 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     d |= static_cast<uint64_t>(1) << 46;   // fixed 0b001 descriptor version
     return d;                              // base offset 0, swizzle none
 }
+// The same for a tile in the 128-byte swizzled layout that a tiled TMA copy
+// with CU_TENSOR_MAP_SWIZZLE_128B writes (tile base 1024-byte aligned; a
+// start address inside the first 128-byte row selects a K offset of a
+// K-major tile).  K-major: 128-byte rows along K, `sbo` = distance between
+// 8-row groups (1024 for dense rows), `lbo` unused.  MN-major (16-bit
+// values): 64 values along M / N per 128-byte row, one row per K index;
+// `lbo` = distance between 64-wide blocks along M / N, `sbo` = between
+// groups of 8 K rows.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return smem_desc(saddr, lbo, sbo) | (static_cast<uint64_t>(2) << 61);
+}
+// Instruction descriptor, kind::f16 with F16 (bf16 = false) or BF16 A and B
+// (one type for both) and F32 accumulate, shape M x N; a_mn / b_mn: that
+// operand is stored MN-major (else K-major).
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool bf16, bool a_mn = false, bool b_mn = false) {
+    return (1u << 4)                                   // D format F32
+           | ((bf16 ? 1u : 0u) << 7)                   // A format F16 / BF16
+           | ((bf16 ? 1u : 0u) << 10)                  // B format, the same
+           | (a_mn ? (1u << 15) : 0u)                  // A major-ness
+           | (b_mn ? (1u << 16) : 0u)                  // B major-ness
+           | (static_cast<uint32_t>(N >> 3) << 17)     // N / 8
+           | (static_cast<uint32_t>(M >> 4) << 24);    // M / 16
+}
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn = false, bool b_mn = false) {
+    return idesc_f16(M, N, true, a_mn, b_mn);
+}
 // Instruction descriptor, kind::tf32: F32 accumulate, TF32 A and B, both
 // K-major, optional negation of A, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N, bool negate_a = false) {
@@ -147,6 +173,24 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64
         "}\n" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
+}
+// D (+)= A B^T with F16 or BF16 operands from shared memory (kind::f16, K = 16;
+// the types are in the instruction descriptor)
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+        "}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// a tensor map in global memory, written before the launch, is read by the
+// tensor copies of this kernel: order its reads after that write
+__device__ __forceinline__ void tensormap_acquire(const void *tmap) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(tmap) : "memory");
 }
 // the same with A read from tensor memory: a_tmem addresses lane 0 of the
 // K = 8 columns (one TF32 value per 32-bit column, row m in lane m) of the
