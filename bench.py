@@ -65,6 +65,8 @@ def parse_args():
     ap.add_argument("--workload", default="headline",
                     choices=["headline", "batched", "serving", "single", "xl", "ragged", "symbols", "blocks"])
     ap.add_argument("--xl-inst", type=int, default=256, help="channels per GPU of the headline workload")
+    ap.add_argument("--refine-residual", default="sliced", choices=["sliced", "dot2", "fp64"],
+                    help="headline: the refinement residual (sliced tensor-core products, Dot2 or FP64)")
     ap.add_argument("--no-extras", action="store_true",
                     help="headline only: skip the batched, serving, LSE-curve and direct records")
     ap.add_argument("--rates", default="5000,20000,50000,100000,200000")
@@ -1111,18 +1113,21 @@ XL_PRESET = "xl_4096x256"
 XL_SEED = 2
 XL_MAX_ITER = 100
 XL_TOL = 1e-5
-# one Dot2 refinement sweep (of the configuration's "up to 3"): the residual of
-# every instance is evaluated, those above 1e-6 get one correction solve to 1e-2
-# of their residual; with three sweeps the instances stop after the first one
+# one refinement sweep (of the configuration's "up to 3"): the residual of every
+# instance is evaluated (by default with sliced products on the tensor cores,
+# see --refine-residual), those above 1e-6 get one correction solve to 1e-2 of
+# their residual; with three sweeps the instances stop after the first one
 # anyway, so the extra sweeps only cost their evaluations
 XL_REFINE = dict(refine_sweeps=1, refine_tol=1e-6, refine_solve_tol=1e-2)
+RESID_NAMES = {"sliced": "sliced tensor-core", "dot2": "Dot2", "fp64": "FP64"}
 
 
 def xl_config(n, args):
     return {"workload": (f"xl: {n} channels per GPU, M=4096 (16x256 subarrays), K=256, H bfloat16, "
                          f"standard Jac-PCG to tol {XL_TOL} (max {XL_MAX_ITER} iterations), one "
-                         "refinement sweep (Dot2 residual; instances above relative residual 1e-6 "
-                         "take a correction solve to 1e-2 of it), B=I_K"),
+                         f"refinement sweep ({RESID_NAMES[args.refine_residual]} residual; instances "
+                         "above relative residual 1e-6 take a correction solve to 1e-2 of it), B=I_K"),
+            "refine_residual": args.refine_residual,
             "instances_per_gpu": n, "M": 4096, "K": 256, "h_dtype": "bf16", "tol": XL_TOL,
             "precision": args.precision, "mode": args.mode,
             "l2": "inputs larger than L2 (H is 1.07 GB, W 2.15 GB per step), no flush needed",
@@ -1178,7 +1183,7 @@ def run_headline(args):
     resid = torch.empty(n, dtype=torch.float32, device="cuda")
     beta = torch.empty(n, dtype=torch.float32, device="cuda")
     prec = binding.Precoder(max_instances=n, max_M=M, max_K=K, precision=args.precision, device=local,
-                            profile=True, **XL_REFINE)
+                            profile=True, refine_residual=args.refine_residual, **XL_REFINE)
     insts = [binding.instance(Hb[i], Wd[i], float(xi[i]), XL_MAX_ITER, XL_TOL) for i in range(n)]
     arr = (binding.jacpcg_instance * n)(*insts)
     stream = torch.cuda.current_stream()

@@ -92,8 +92,19 @@ enum { JACPCG_H_C64 = 0, JACPCG_H_BF16 = 1 };
  * DOT2: FP32 error-free transformations (TwoProduct by FMA + TwoSum, the
  * compensated dot product of Ogita, Rump and Oishi, 2005), as accurate as
  * twice the working precision, on the FP32 pipes.  FP64: products and sums
- * in FP64 (exact products of the FP32 operands); slower on this GPU. */
-enum { JACPCG_RESID_DOT2 = 0, JACPCG_RESID_FP64 = 1 };
+ * in FP64 (exact products of the FP32 operands); slower on this GPU.
+ * SLICED: for the K = 128 and 256 classes, products on the FP16 tensor cores
+ * (the Ozaki scheme on tensor cores: Mukunoki, Ozaki, Ogita and Imamura, ISC
+ * 2020).  A and X are balanced by exact powers of two near sqrt(diag A), and
+ * each row of the balanced A and each column of the balanced X is cut into five
+ * 8-bit integer slices on fixed-point grids of their own; slice products are
+ * exact, the sums of the fifteen kept slice pairs are exact (the top class to
+ * one unit of 2^-46 of its grid), and the classes are combined with B by TwoSum
+ * pairs and rounded once.  On the bench channels R comes out within 1e-4 of its
+ * own size (Dot2: within FP32 rounding), far more than the FP32 correction
+ * solves can use.  The other classes, and channels with M <= 2 K, use DOT2.
+ * Requires the entries of A and X within 2^-60 .. 2^60 of magnitude. */
+enum { JACPCG_RESID_DOT2 = 0, JACPCG_RESID_FP64 = 1, JACPCG_RESID_SLICED = 2 };
 
 /* config flags */
 enum {
@@ -127,7 +138,8 @@ typedef struct {
                                 ||R||), X += dX.  After the last sweep R is evaluated once more
                                 only when some instance of the call asks for resid_hist (it
                                 could change nothing else) */
-    int refine_residual;     /* JACPCG_RESID_DOT2 (default) or JACPCG_RESID_FP64.  With
+    int refine_residual;     /* JACPCG_RESID_DOT2 (default), JACPCG_RESID_FP64 or
+                                JACPCG_RESID_SLICED.  With
                                 refinement, channels with M <= 2 K form A with compensated
                                 (Dot2) sums on the SIMT pipes instead of the FP32 / 3xTF32
                                 Gram: refinement converges to the solution for the A it is

@@ -25,7 +25,8 @@ JACPCG_FLAG_PROFILE = 1
 JACPCG_FLAG_SIMT_ITERATION = 2
 JACPCG_FLAG_REFINE_SELECTIVE = 4
 JACPCG_H_C64, JACPCG_H_BF16 = 0, 1
-JACPCG_RESID_DOT2, JACPCG_RESID_FP64 = 0, 1
+JACPCG_RESID_DOT2, JACPCG_RESID_FP64, JACPCG_RESID_SLICED = 0, 1, 2
+RESIDUALS = {"dot2": JACPCG_RESID_DOT2, "fp64": JACPCG_RESID_FP64, "sliced": JACPCG_RESID_SLICED}
 VARIANTS = {"standard": JACPCG_STANDARD, "alg1": JACPCG_ALG1, "cg": JACPCG_CG, "jor": JACPCG_JOR,
             "direct": JACPCG_DIRECT}
 PRECISIONS = {"fp32": JACPCG_FP32, "tf32x3": JACPCG_TF32X3}
@@ -408,7 +409,8 @@ class Precoder:
     def __init__(self, max_instances: int, max_M: int, max_K: int, variant="standard",
                  precision="fp32", device: int = 0, arena_bytes: int = 0, profile: bool = False,
                  refine_sweeps: int = 0, refine_fp64: bool = False, simt_iteration: bool = False,
-                 refine_tol: float = 0.0, refine_solve_tol: float = 0.0, refine_selective: bool = False):
+                 refine_tol: float = 0.0, refine_solve_tol: float = 0.0, refine_selective: bool = False,
+                 refine_residual: str | None = None):
         self.cfg = jacpcg_config(device=device, max_instances=max_instances, max_M=max_M,
                                  max_K=max_K, arena_bytes=arena_bytes,
                                  precision=PRECISIONS[precision] if isinstance(precision, str) else precision,
@@ -417,7 +419,8 @@ class Precoder:
                                  | (JACPCG_FLAG_SIMT_ITERATION if simt_iteration else 0)
                                  | (JACPCG_FLAG_REFINE_SELECTIVE if refine_selective else 0),
                                  refine_sweeps=int(refine_sweeps),
-                                 refine_residual=JACPCG_RESID_FP64 if refine_fp64 else JACPCG_RESID_DOT2,
+                                 refine_residual=(RESIDUALS[refine_residual] if refine_residual is not None
+                                                  else JACPCG_RESID_FP64 if refine_fp64 else JACPCG_RESID_DOT2),
                                  refine_tol=float(refine_tol), refine_solve_tol=float(refine_solve_tol))
         self.ctx = jacpcg_create(self.cfg)
 

@@ -113,12 +113,17 @@ struct Arena {
 
 // What one kernel launch of a plan covers.
 struct Launch {
-    enum Kind { GRAM, PCG, HX, GRAM_TC, GRAM_TCX, HX_TC, HX_TCW, PCG_TC, CHOL, SINR, TCW_PREP, PCG_TCW, GRAM_BF16, HX_BF16 } kind;
-    int phase;        // 0 Gram, 1 iteration, 2 W = H X, 3 SINR (after the power factor)
+    enum Kind {
+        GRAM, PCG, HX, GRAM_TC, GRAM_TCX, HX_TC, HX_TCW, PCG_TC, CHOL, SINR, TCW_PREP, PCG_TCW, GRAM_BF16, HX_BF16,
+        RESID_TC
+    } kind;
+    int phase;        // 0 Gram, 1 iteration, 2 W = H X, 3 SINR (after the power factor), 4 refinement
     int param;        // TB (Gram), KC (iteration), TN (W = H X)
     size_t list_off;  // byte offset of its work list inside the plan block
     int count;        // CTAs
     int shape = 0;    // iteration launch shape (index into PCG_SHAPES)
+    size_t list2_off = 0;   // RESID_TC: its (instance, column) jobs; list_off / count: the instances
+    int count2 = 0;
 };
 
 }  // namespace
@@ -165,6 +170,7 @@ struct jacpcg_plan {
     bool want_hist = false;       // some instance asked for its refinement residual history
     size_t res_off = 0;
     int n_res = 0;
+    int n_rtc = 0;                // instances on the sliced tensor-core residual
     size_t acc_reset_bytes = 0;   // > 0: clear the accumulators before the Gram (multi-job instances)
     size_t tmap_off = 0;          // tensor maps over the bfloat16 channels' H
 };
@@ -215,7 +221,8 @@ int n_cols(const jacpcg_instance &q) { return q.B ? q.n_rhs : q.K; }
 // Byte layout of one plan block.
 struct Layout {
     size_t insts, gram, tcl, gdl, gxl, pcg, hx, hxl, hwl, res, sinr, twl, twj, tmaps, gbl, hbl, accum, ws, total;
-    int n_gram, n_pcg, n_hx, n_res, n_gd, n_gx, n_hw, n_sinr, n_twj, n_tm, n_gb, n_hb;
+    int n_gram, n_pcg, n_hx, n_res, n_gd, n_gx, n_hw, n_sinr, n_twj, n_tm, n_gb, n_hb, n_rtl, n_rtj;
+    size_t rtl, rtj;
     bool refine;
     std::vector<size_t> ws_off;   // per instance
 };
@@ -248,14 +255,25 @@ size_t wpart_slots(const jacpcg_instance &q) { return std::max(n_wtiles(q), hx_b
 // A, X, 1/diag, W partials; then R and its column norms for refinement; then,
 // for the 128 and 256 classes' tensor-core iteration, A as its streamed FP16
 // stages (head and tail of real and imaginary parts: 8 KC^2 bytes)
-size_t inst_ws_bytes(const jacpcg_instance &q, bool refine, bool tcw) {
+// (and, for the sliced tensor-core residual, A's slices and their row exponents)
+size_t inst_ws_bytes(const jacpcg_instance &q, bool refine, bool tcw, bool sliced = false) {
     const size_t KC = k_class(q.K);
     size_t b = align_up(KC * KC * sizeof(float2)) * 2 + align_up(KC * sizeof(float)) +
                align_up(wpart_slots(q) * sizeof(float));
     if (refine) b += align_up(KC * KC * sizeof(float2)) + align_up((2 * KC + 2) * sizeof(float));
     if (tcw) b += align_up(4 * KC * KC * 2);
+    if (sliced) b += align_up(resid_tc_slice_bytes((int)KC)) + align_up(2 * KC * sizeof(float));
     return b;
 }
+// Refining instances of the 128 and 256 classes whose residual runs with sliced
+// products on the tensor cores (resid_tc.cu); the others keep the SIMT kernel.
+// The slices' error, about 2^-28 of |A| |X|, reaches X through A^-1 twice, so
+// channels with at most two antennas per user (Jacobi-scaled condition numbers
+// up to thousands) keep the Dot2 residual.
+bool sliced_resid(const jacpcg_config &cfg, bool refine, const jacpcg_instance &q) {
+    return refine && cfg.refine_residual == JACPCG_RESID_SLICED && k_class(q.K) >= 128 && q.M > 2 * q.K;
+}
+constexpr int RTC_NB = 24;   // columns per job of the sliced residual
 constexpr int TCW_NB = 32;   // columns per CTA of the 128 / 256-class tensor-core iteration
 
 // K classes whose Gram runs on the tensor cores at this precision (64 x 64
@@ -295,10 +313,17 @@ Layout make_layout(const jacpcg_config &cfg, const jacpcg_instance *inst, int n,
                    const int *shape_idx) {
     Layout L{};
     L.n_gram = L.n_pcg = L.n_hx = L.n_res = L.n_gd = L.n_gx = L.n_hw = L.n_sinr = L.n_twj = 0;
-    L.n_tm = L.n_gb = L.n_hb = 0;
+    L.n_tm = L.n_gb = L.n_hb = L.n_rtl = L.n_rtj = 0;
     L.refine = refine;
     for (int i = 0; i < n; ++i) {
-        if (refines(cfg, refine, inst[i])) L.n_res += (n_cols(inst[i]) + RES_CB - 1) / RES_CB;
+        if (refines(cfg, refine, inst[i])) {
+            if (sliced_resid(cfg, refine, inst[i])) {
+                ++L.n_rtl;
+                L.n_rtj += (n_cols(inst[i]) + RTC_NB - 1) / RTC_NB;
+            } else {
+                L.n_res += (n_cols(inst[i]) + RES_CB - 1) / RES_CB;
+            }
+        }
         const int ng = k_class(inst[i].K) / 64;   // user groups of a tensor-core Gram
         L.n_gd += ng;
         L.n_gx += ng * (ng - 1) / 2;
@@ -325,6 +350,8 @@ Layout make_layout(const jacpcg_config &cfg, const jacpcg_instance *inst, int n,
     L.hxl = o;    o += align_up(sizeof(int) * n);
     L.hwl = o;    o += align_up(sizeof(int2) * L.n_hw);
     L.res = o;    o += align_up(sizeof(int2) * L.n_res);
+    L.rtl = o;    o += align_up(sizeof(int) * L.n_rtl);
+    L.rtj = o;    o += align_up(sizeof(int2) * L.n_rtj);
     L.sinr = o;   o += align_up(sizeof(int2) * L.n_sinr);
     L.twl = o;    o += align_up(sizeof(int) * n);
     L.twj = o;    o += align_up(sizeof(int2) * L.n_twj);
@@ -336,7 +363,8 @@ Layout make_layout(const jacpcg_config &cfg, const jacpcg_instance *inst, int n,
     L.ws_off.resize(n);
     for (int i = 0; i < n; ++i) {
         L.ws_off[i] = o;
-        o += inst_ws_bytes(inst[i], refine, pcg_on_tcw(cfg, shape_idx, k_class(inst[i].K)));
+        o += inst_ws_bytes(inst[i], refine, pcg_on_tcw(cfg, shape_idx, k_class(inst[i].K)),
+                           refines(cfg, refine, inst[i]) && sliced_resid(cfg, refine, inst[i]));
     }
     L.total = o;
     return L;
@@ -401,8 +429,14 @@ bool build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
         d.ldb = q.B ? q.ldb : 0;
         d.ncols = n_cols(q);
         d.X0 = static_cast<const float2 *>(q.X0);
-        if (pcg_on_tcw(ctx->cfg, ctx->pcg_shape_idx, KC)) {   // the split stages follow everything else
+        const bool tcw_i = pcg_on_tcw(ctx->cfg, ctx->pcg_shape_idx, KC);
+        if (tcw_i) {   // the split stages follow everything else
             d.As = reinterpret_cast<float *>(w + inst_ws_bytes(q, L.refine, false));
+        }
+        if (refines(ctx->cfg, L.refine, q) && sliced_resid(ctx->cfg, L.refine, q)) {   // then A's slices
+            const size_t o = inst_ws_bytes(q, L.refine, tcw_i);
+            d.Asl = w + o;
+            d.rexp = reinterpret_cast<float *>(w + o + align_up(resid_tc_slice_bytes(KC)));
         }
         if (L.refine) {
             const size_t base = 2 * align_up((size_t)KC * KC * sizeof(float2)) + align_up(KC * sizeof(float)) +
@@ -417,14 +451,30 @@ bool build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
         }
         hi[i] = d;
     }
-    if (L.refine) {   // residual blocks: (instance, column)
+    launches.clear();
+    if (L.refine) {   // residual blocks: (instance, column); the sliced residual's lists per K class
         int2 *rb = reinterpret_cast<int2 *>(host + L.res);
         int r = 0;
         for (int i = 0; i < n; ++i)
-            if (refines(ctx->cfg, true, inst[i]))
+            if (refines(ctx->cfg, true, inst[i]) && !sliced_resid(ctx->cfg, true, inst[i]))
                 for (int j = 0; j < n_cols(inst[i]); j += RES_CB) rb[r++] = make_int2(i, j);
+        int *rl = reinterpret_cast<int *>(host + L.rtl);
+        int2 *rj = reinterpret_cast<int2 *>(host + L.rtj);
+        int nl = 0, nj = 0;
+        for (int KC : {128, 256}) {
+            const int l0 = nl, j0 = nj;
+            for (int i = 0; i < n; ++i) {
+                if (k_class(inst[i].K) != KC || !refines(ctx->cfg, true, inst[i]) ||
+                    !sliced_resid(ctx->cfg, true, inst[i]))
+                    continue;
+                rl[nl++] = i;
+                for (int c0 = 0; c0 < n_cols(inst[i]); c0 += RTC_NB) rj[nj++] = make_int2(i, c0);
+            }
+            if (nl > l0)
+                launches.push_back({Launch::RESID_TC, 4, KC, L.rtl + l0 * sizeof(int), nl - l0, 0,
+                                    L.rtj + j0 * sizeof(int2), nj - j0});
+        }
     }
-    launches.clear();
     // Gram on the tensor cores: diagonal (instance, group) jobs, then the
     // off-diagonal (instance, a, b) jobs of the 128 and 256 classes
     const int prec = ctx->cfg.precision;
@@ -651,22 +701,41 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
                     e = launch_hx_bf16(pl->d_insts, static_cast<const int4 *>(list), l.count,
                                        reinterpret_cast<const CUtensorMap *>(pl->dev + pl->tmap_off), pl->acc, s);
                     break;
+                case Launch::RESID_TC:   // phase 4: run by the refinement below
+                    break;
             }
             if (e != cudaSuccess) return cuda_fail(ctx, e);
             ++nl;
         }
-        if (phase == 1 && pl->refine_sweeps > 0 && pl->n_res > 0) {   // some instance refines
-            // iterative refinement: R = I - A X (FP64), A dX = R (FP32 iteration), X += dX
+        if (phase == 1 && pl->refine_sweeps > 0 && (pl->n_res > 0 || pl->n_rtc > 0)) {   // some instance refines
+            // iterative refinement: R = I - A X (Dot2, FP64 or sliced), A dX = R (FP32 iteration), X += dX
             const NvtxRange refine_range("jacpcg: refinement");
             const int2 *rb = reinterpret_cast<const int2 *>(pl->dev + pl->res_off);
+            for (const Launch &l : pl->launches) {   // A's slices, once per execute
+                if (l.kind != Launch::RESID_TC) continue;
+                if (launch_rtc_prep(l.param, pl->d_insts, reinterpret_cast<const int *>(pl->dev + l.list_off), l.count,
+                                    s) != cudaSuccess)
+                    return cuda_fail(ctx);
+                ++nl;
+            }
             for (int sw = 0; sw <= pl->refine_sweeps; ++sw) {
                 // after the last correction the residual could only be reported
                 if (sw == pl->refine_sweeps && !pl->want_hist) break;
-                if (launch_residual(pl->d_insts, rb, pl->n_res, sw, s,
-                                    ctx->cfg.refine_residual == JACPCG_RESID_FP64) != cudaSuccess ||
-                    launch_resid_hist(pl->d_insts, pl->n_inst, sw, s) != cudaSuccess)
-                    return cuda_fail(ctx);
-                nl += 2;
+                if (pl->n_res > 0) {
+                    if (launch_residual(pl->d_insts, rb, pl->n_res, sw, s,
+                                        ctx->cfg.refine_residual == JACPCG_RESID_FP64) != cudaSuccess)
+                        return cuda_fail(ctx);
+                    ++nl;
+                }
+                for (const Launch &l : pl->launches) {
+                    if (l.kind != Launch::RESID_TC) continue;
+                    if (launch_resid_tc(l.param, pl->d_insts, reinterpret_cast<const int2 *>(pl->dev + l.list2_off),
+                                        l.count2, sw, pl->acc, s) != cudaSuccess)
+                        return cuda_fail(ctx);
+                    ++nl;
+                }
+                if (launch_resid_hist(pl->d_insts, pl->n_inst, sw, s) != cudaSuccess) return cuda_fail(ctx);
+                ++nl;
                 if (sw == pl->refine_sweeps) break;
                 for (const Launch &l : pl->launches) {
                     cudaError_t e = cudaSuccess;
@@ -742,6 +811,7 @@ jacpcg_status make_plan(jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, int
     for (int i = 0; i < n; ++i) pl->want_hist = pl->want_hist || inst[i].resid_hist != nullptr;
     pl->res_off = L.res;
     pl->n_res = L.n_res;
+    pl->n_rtc = L.n_rtl;
     if (L.n_gx || L.n_gb) pl->acc_reset_bytes = 3 * align_up(sizeof(int32_t) * n);
     pl->tmap_off = L.tmaps;
     const size_t tbytes = L.accum;   // tables occupy [0, accum)
@@ -925,7 +995,8 @@ jacpcg_status jacpcg_create(const jacpcg_config *cfg, jacpcg_ctx **out) {
     if (cfg->flags & ~(JACPCG_FLAG_PROFILE | JACPCG_FLAG_SIMT_ITERATION | JACPCG_FLAG_REFINE_SELECTIVE))
         return JACPCG_EINVAL;
     if (cfg->refine_sweeps < 0 || cfg->refine_sweeps > 3) return JACPCG_EINVAL;
-    if (cfg->refine_residual != JACPCG_RESID_DOT2 && cfg->refine_residual != JACPCG_RESID_FP64)
+    if (cfg->refine_residual != JACPCG_RESID_DOT2 && cfg->refine_residual != JACPCG_RESID_FP64 &&
+        cfg->refine_residual != JACPCG_RESID_SLICED)
         return JACPCG_EINVAL;
     if (!(cfg->refine_tol >= 0.f) || cfg->refine_tol > 1e30f) return JACPCG_EINVAL;   // also NaN
     if (!(cfg->refine_solve_tol >= 0.f) || cfg->refine_solve_tol > 1e30f) return JACPCG_EINVAL;

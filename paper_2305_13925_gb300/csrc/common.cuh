@@ -50,6 +50,10 @@ struct DevInst {
                           // tensor-core iteration (null when that iteration is not used)
     float *sinr;          // optional per-user SINR out, K floats (caller); B = I only
     float noise;          // noise power sigma^2 of the SINR (0: 1)
+    void *Asl;            // workspace: A's 8-bit slices as FP16 stages for the sliced tensor-core
+                          // residual of the 128 and 256 classes (null when not used)
+    float *rexp;          // workspace 2 KC: per row the slices' output exponent, then the
+                          // balancing exponent e_i (2^e_i <= sqrt(A_ii) < 2^(e_i + 1))
 };
 
 // One entry of H as complex FP32 (bfloat16 converts exactly).

@@ -105,6 +105,14 @@ constexpr int RES_CB = 8;
 cudaError_t launch_residual(const DevInst *insts, const int2 *blocks, int n_blocks, int sweep,
                             cudaStream_t s, bool fp64);
 cudaError_t launch_resid_hist(const DevInst *insts, int n_inst, int sweep, cudaStream_t s);
+// the same residual with sliced products on the tensor cores (K = 128 and 256
+// classes): launch_rtc_prep slices A once per execute (list: instance ids;
+// DevInst::Asl, resid_tc_slice_bytes(KC) bytes, and DevInst::rexp), then each
+// evaluation runs launch_resid_tc over (instance, first of 24 columns) jobs
+size_t resid_tc_slice_bytes(int KC);
+cudaError_t launch_rtc_prep(int KC, const DevInst *insts, const int *list, int n, cudaStream_t s);
+cudaError_t launch_resid_tc(int KC, const DevInst *insts, const int2 *jobs, int n, int sweep, DevAccum acc,
+                            cudaStream_t s);
 // tiles: (instance, m tile, n tile, partial slot)
 cudaError_t launch_hx_simt(int TN, const DevInst *insts, const int4 *tiles, int n_tiles,
                            cudaStream_t s);

@@ -34,7 +34,7 @@ def to_dev_bf16(H: np.ndarray, torch):
 def run(Hs, xis, variant="standard", T=6, tol=0.0, want_X=False, want_A=False, power=1.0,
         plan=False, graph=False, repeats=1, precision="fp32", prec=None, bf16=False,
         refine_sweeps=0, want_hist=False, refine_fp64=False, simt_iteration=False, refine_tol=0.0,
-        refine_solve_tol=0.0, omegas=None, refine_selective=False):
+        refine_solve_tol=0.0, omegas=None, refine_selective=False, refine_residual=None):
     """Precode each (M_i, K_i) channel of ``Hs`` in one batch on the GPU."""
     import torch
     n = len(Hs)
@@ -59,7 +59,7 @@ def run(Hs, xis, variant="standard", T=6, tol=0.0, want_X=False, want_A=False, p
                                 precision=precision, refine_sweeps=refine_sweeps,
                                 refine_fp64=refine_fp64, simt_iteration=simt_iteration,
                                 refine_tol=refine_tol, refine_solve_tol=refine_solve_tol,
-                                refine_selective=refine_selective)
+                                refine_selective=refine_selective, refine_residual=refine_residual)
     try:
         if plan:
             p = prec.plan(insts, status, iters, resid, beta, use_graph=graph)
