@@ -68,8 +68,10 @@ namespace {
 constexpr int NB = 32;                        // right-hand-side columns per CTA
 constexpr int THREADS = 256;                  // 8 warps: 2 per SM sub-partition, up to 255 registers
 constexpr int EPI = THREADS;
-constexpr int RING = 9;                       // stages in flight
-constexpr int STAGE = 16384;                  // bytes: four 128 x 16 FP16 tiles
+constexpr int STAGE = 16384;                  // bytes of one k-step: four 128 x 16 FP16 tiles
+constexpr int SUB = 2;                        // k-steps per bulk copy (ring slot)
+constexpr int SLOT = SUB * STAGE;
+constexpr int RING = 4;                       // ring slots in flight
 constexpr int TILE = 4096;
 constexpr int SA = 13;                        // A is stored scaled by 2^SA (entries below 2^15)
 constexpr int SP = 14;                        // a column of P is scaled to a largest entry in [2^14, 2^15)
@@ -87,8 +89,9 @@ struct Cfg {
     static constexpr int MR = KC / 8;                        // complex rows per epilogue thread
     static constexpr uint32_t TMEM_COLS = RT == 2 ? 512 : 256;
     // B, ring, then per row 1 / d, 2^e, 2^-e; per column the readout factor
-    static constexpr int SMEM = B_BYTES + RING * STAGE + 3 * KC * 4 + NB * 4 + 256;
-    static_assert(2 * RT * NB * QLD * 4 <= RING * STAGE, "Q staging fits the ring");
+    static constexpr int SMEM = B_BYTES + RING * SLOT + 3 * KC * 4 + NB * 4 + 256;
+    static_assert(2 * RT * NB * QLD * 4 <= RING * SLOT, "Q staging fits the ring");
+    static_assert(NSTAGE % SUB == 0, "whole slots");
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
@@ -272,11 +275,11 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
     using C = Cfg<KC>;
     constexpr int MR = C::MR;
     extern __shared__ __align__(1024) unsigned char smem[];
-    float *dvs = reinterpret_cast<float *>(smem + C::B_BYTES + RING * STAGE);   // 1 / A_ii
+    float *dvs = reinterpret_cast<float *>(smem + C::B_BYTES + RING * SLOT);    // 1 / A_ii
     float *scv = dvs + KC;                                                         // 2^e_i
     float *iscv = scv + KC;                                                        // 2^-e_i
     float *colq = iscv + KC;   // per column 2^-SA / s_j: the readout's unscaling
-    Ctl &S = *reinterpret_cast<Ctl *>(smem + C::B_BYTES + RING * STAGE + 3 * KC * 4 + NB * 4);
+    Ctl &S = *reinterpret_cast<Ctl *>(smem + C::B_BYTES + RING * SLOT + 3 * KC * 4 + NB * 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int i = 0; i < RING; ++i) {
@@ -298,32 +301,37 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
     const uint32_t b_base = tc::smem_u32(smem), r_base = b_base + C::B_BYTES;
     uint32_t pc = 0, mc = 0;   // stages produced (thread 0) / consumed (thread 32)
     // One iteration's A x P: thread 0 streams the KC / 128 x KC / 16 stages into the
-    // ring, thread 32 issues their MMAs (per stage: head x [P_h | P_t] and tail x
-    // P_h, Ar then Ai) and commits to qfull; the other threads go on to wait.
+    // ring, SUB consecutive stages (k-steps) per bulk copy; thread 32 issues their
+    // MMAs (per stage: head x [P_h | P_t] and tail x P_h, Ar then Ai) and commits
+    // to qfull; the other threads go on to wait.
     auto product = [&](const char *src) {
         if (threadIdx.x == 0) {
-            for (int s = 0; s < C::NSTAGE; ++s, ++pc) {
+            for (int s = 0; s < C::NSTAGE / SUB; ++s, ++pc) {
                 const int slot = pc % RING;
                 if (!tc::mbar_wait(&S.empty[slot], ((pc / RING) & 1) ^ 1, WAIT_LIMIT)) S.err = 1;
-                tc::mbar_arrive_expect_tx(&S.full[slot], STAGE);
-                bulk_load(r_base + slot * STAGE, src + (size_t)s * STAGE, STAGE, &S.full[slot]);
+                tc::mbar_arrive_expect_tx(&S.full[slot], SLOT);
+                bulk_load(r_base + slot * SLOT, src + (size_t)s * SLOT, SLOT, &S.full[slot]);
             }
         } else if (threadIdx.x == 32) {
             constexpr uint32_t id128 = tc::idesc_f16(128, 4 * NB, false);
             constexpr uint32_t id64 = tc::idesc_f16(128, 2 * NB, false);
             tc::tc_fence_after();
-            for (int s = 0; s < C::NSTAGE; ++s, ++mc) {
-                const int slot = mc % RING, rt = s / C::KS, ks = s % C::KS;
+            for (int s = 0; s < C::NSTAGE / SUB; ++s, ++mc) {
+                const int slot = mc % RING;
                 if (!tc::mbar_wait(&S.full[slot], (mc / RING) & 1, WAIT_LIMIT)) S.err = 1;
                 tc::tc_fence_after();
-                const uint32_t a0 = r_base + slot * STAGE;
-                const uint64_t bd = tc::smem_desc(b_base + ks * 256, 128, C::SBO_B);
-                const uint32_t du = tmem + rt * 256, dvv = du + 128;
-                const uint32_t acc = ks > 0 ? 1u : 0u;
-                tc::mma_bf16(du, tc::smem_desc(a0, 128, 256), bd, id128, acc);   // FP16 by the descriptors
-                tc::mma_bf16(du + 64, tc::smem_desc(a0 + TILE, 128, 256), bd, id64, 1u);
-                tc::mma_bf16(dvv, tc::smem_desc(a0 + 2 * TILE, 128, 256), bd, id128, acc);
-                tc::mma_bf16(dvv + 64, tc::smem_desc(a0 + 3 * TILE, 128, 256), bd, id64, 1u);
+#pragma unroll
+                for (int u = 0; u < SUB; ++u) {
+                    const int g = s * SUB + u, rt = g / C::KS, ks = g % C::KS;
+                    const uint32_t a0 = r_base + slot * SLOT + u * STAGE;
+                    const uint64_t bd = tc::smem_desc(b_base + ks * 256, 128, C::SBO_B);
+                    const uint32_t du = tmem + rt * 256, dvv = du + 128;
+                    const uint32_t acc = ks > 0 ? 1u : 0u;
+                    tc::mma_bf16(du, tc::smem_desc(a0, 128, 256), bd, id128, acc);   // FP16 by the descriptors
+                    tc::mma_bf16(du + 64, tc::smem_desc(a0 + TILE, 128, 256), bd, id64, 1u);
+                    tc::mma_bf16(dvv, tc::smem_desc(a0 + 2 * TILE, 128, 256), bd, id128, acc);
+                    tc::mma_bf16(dvv + 64, tc::smem_desc(a0 + 3 * TILE, 128, 256), bd, id64, 1u);
+                }
                 tc::mma_commit(&S.empty[slot]);   // the slot is free once these have read it
             }
             tc::mma_commit(&S.qfull);
@@ -346,19 +354,17 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
         // in as FP16 head and tail.  All lanes take part (shuffles); a column that
         // is not `active` keeps its published p.  f is evaluated twice, so it
         // must not depend on what the second pass writes at other rows.
-        auto publish_all = [&](bool active, auto f) {
-            float mx = 0.f;
-            if (active) {
-#pragma unroll
-                for (int m = 0; m < MR; ++m) {
-                    const float2 v = f(m);
-                    mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)) * scv[g + 8 * m]);
-                }
-            }
+        int pex = SP;       // the column's exponent ex at the last publication
+        // col_exp: the exponent ex for a column whose largest |E p| is at most mx
+        // (a maximum over the column's 8 lanes), s_j = 2^(SP - ex); clamped so that
+        // s_j, 1 / s_j and 2^-SA / s_j are floats
+        auto col_exp = [&](float mx) {
 #pragma unroll
             for (int o = 4; o <= 16; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            // s_j = 2^(SP - ex); ex clamped so that s_j, 1 / s_j and 2^-SA / s_j are floats
-            const int ex = (mx >= 1.2e-38f && mx < 3.0e38f) ? min(max(exp2_of(mx), SA + SP - 126), SP + 126) : SP;
+            return (mx >= 1.2e-38f && mx < 3.0e38f) ? min(max(exp2_of(mx), SA + SP - 126), SP + 126) : SP;
+        };
+        // store s_j E p (p = f(m) at row g + 8 m) as FP16 head and tail, s_j = 2^(SP - ex)
+        auto publish_exp = [&](bool active, int ex, auto f) {
             const float sj = pow2f(SP - ex);
             if (active) {
 #pragma unroll
@@ -374,8 +380,20 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
                     bset(3 * NB + cl, i, t);
                 }
                 pinv = pow2f(ex - SP);
+                pex = ex;
                 if (g == 0) colq[cl] = pow2f(ex - SP - SA);
             }
+        };
+        auto publish_all = [&](bool active, auto f) {
+            float mx = 0.f;
+            if (active) {
+#pragma unroll
+                for (int m = 0; m < MR; ++m) {
+                    const float2 v = f(m);
+                    mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)) * scv[g + 8 * m]);
+                }
+            }
+            publish_exp(active, col_exp(mx), f);
         };
         auto pget = [&](int m) {   // head + tail (exact in FP32), unscaled: p as published
             const int i = g + 8 * m;
@@ -532,9 +550,18 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
                     b = make_float2(d * r[m].x, d * r[m].y);
                 });
                 const float rr_new = col_sumsq<MR>([&](int m, float2 &a, float2 &b) { a = r[m]; b = r[m]; });
-                // p = z + beta p, published for the next product
+                // p = z + beta p, published for the next product, its scale from the
+                // bound max |E p| <= max |E z| + beta max |E p_old| (< 2^(pex + 1)): one
+                // pass over the rows instead of two
                 const float beta = (!done && rho != 0.f) ? rz_new / rho : 0.f;
-                publish_all(!done, [&](int m) {
+                float mz = 0.f;
+#pragma unroll
+                for (int m = 0; m < MR; ++m) {
+                    const int i = g + 8 * m;
+                    mz = fmaxf(mz, fmaxf(fabsf(r[m].x), fabsf(r[m].y)) * (dvs[i] * scv[i]));
+                }
+                const int exn = col_exp(fmaf(beta, pow2f(min(pex + 1, 127)), mz));
+                publish_exp(!done, exn, [&](int m) {
                     const float2 pv = pget(m);
                     const float d = dvs[g + 8 * m];
                     return make_float2(fmaf(beta, pv.x, d * r[m].x), fmaf(beta, pv.y, d * r[m].y));

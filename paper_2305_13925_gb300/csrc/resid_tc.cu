@@ -60,8 +60,10 @@ constexpr int NSL = 5;                 // slices per row of Ah and per column of
 constexpr int NCLS = NSL;              // classes s + t = 0 .. 4
 constexpr int CPT = NB / 2;            // columns per epilogue thread
 constexpr int TILE = 128 * 16 * 2;     // one 128 x 16 FP16 tile (4 KB)
-constexpr int STAGE = 2 * TILE;        // [Ar^(s) | Ai^(s)]
-constexpr int RING = 10;
+constexpr int STAGE = 2 * TILE;        // [Ar^(s) | Ai^(s)] of one k-step
+constexpr int SUB = 4;                 // k-steps per bulk copy (ring slot)
+constexpr int SLOT = SUB * STAGE;      // 32 KB
+constexpr int RING = 3;
 constexpr int NEW = 8;                 // epilogue warps
 constexpr int TMA_WARP = NEW, MMA_WARP = NEW + 1;
 constexpr int NTHREADS = (NEW + 2) * 32;
@@ -71,6 +73,7 @@ constexpr int BAR_EPI = 1;
 
 template <int KC>
 struct RCfg {
+    static_assert(KC / 16 % SUB == 0, "whole slots per slice");
     static constexpr int RT = KC / 128;                  // row tiles
     static constexpr int KS = KC / 16;                   // k-steps per row tile
     static constexpr uint32_t SBO_B = (KC / 8) * 128;    // bytes between 8-row groups of B
@@ -79,8 +82,8 @@ struct RCfg {
 
 struct __align__(128) RSmem {
     unsigned char B[NSL][BR * 256 * 2];    // sized for K = 256
-    unsigned char ring[RING][STAGE];
-    float cmax[NEW][32];                   // column maxima of E X, per epilogue warp
+    unsigned char ring[RING][SLOT];
+    float cmax[NEW][NB];                   // column maxima of E X, per epilogue warp
     float xs[NB];                          // 2^-(gx_j - e_j): the column's output scale, inverted
     float xsi[NB];                         // 2^(gx_j - e_j)
     float xe[NB];                          // 2^e_j
@@ -150,6 +153,7 @@ __global__ void __launch_bounds__(256) rtc_prep_kernel(const DevInst *__restrict
     const int gi = rt * 128 + r;
     const float ri = p2(-bal_exp(A[(size_t)gi * (KC + 1)].x));
     float m = 0.f;
+#pragma unroll 8
     for (int k = half * (KC / 2); k < (half + 1) * (KC / 2); ++k) {
         const float2 v = A[(size_t)gi + (size_t)k * KC];
         m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)) * ri * cinv[k]);   // exact scalings
@@ -164,25 +168,36 @@ __global__ void __launch_bounds__(256) rtc_prep_kernel(const DevInst *__restrict
         in.rexp[KC + rt * 128 + t] = (float)e;
     }
     __syncthreads();
+    // thread t: row rr = t mod 128 and the 8 columns 8 kh .. of each 16-column
+    // k-step, one 16-byte store per slice and part (rows of a core matrix)
     char *dst0 = reinterpret_cast<char *>(in.Asl) + (size_t)rt * NSL * C::KS * STAGE;
+    const int rr = t & 127, kh = t >> 7;
+    const float rs0 = p2(-eb[rr]), g = p2(-ga[rr]);
+    const uint32_t o = (uint32_t)(rr >> 3) * 256u + (uint32_t)kh * 128u + (uint32_t)(rr & 7) * 16u;
     for (int ks = 0; ks < C::KS; ++ks) {
-#pragma unroll 2
-        for (int u = 0; u < 8; ++u) {
-            const int e = t + 256 * u, rr = e & 127, k = e >> 7;
-            const float2 v = A[(size_t)(rt * 128 + rr) + (size_t)(ks * 16 + k) * KC];
-            const float rs = p2(-eb[rr]) * cinv[ks * 16 + k];   // 2^(-e_i - e_k), a float for |e| <= 63
-            const float g = p2(-ga[rr]);
-            __half sr[NSL], si[NSL];
-            slice5(v.x * rs, g, 1.f, sr);
-            slice5(v.y * rs, g, 1.f, si);
-            const uint32_t o = (uint32_t)(rr >> 3) * 256u + (uint32_t)(k >> 3) * 128u + (uint32_t)(rr & 7) * 16u +
-                               (uint32_t)(k & 7) * 2u;
+        uint32_t wr[NSL][4], wi[NSL][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k0 = ks * 16 + 8 * kh + 2 * q;
+            const float2 v0 = A[(size_t)(rt * 128 + rr) + (size_t)k0 * KC];
+            const float2 v1 = A[(size_t)(rt * 128 + rr) + (size_t)(k0 + 1) * KC];
+            const float s0 = rs0 * cinv[k0], s1 = rs0 * cinv[k0 + 1];   // 2^(-e_i - e_k)
+            __half a0[NSL], a1[NSL], b0[NSL], b1[NSL];
+            slice5(v0.x * s0, g, 1.f, a0);
+            slice5(v1.x * s1, g, 1.f, a1);
+            slice5(v0.y * s0, g, 1.f, b0);
+            slice5(v1.y * s1, g, 1.f, b1);
 #pragma unroll
             for (int s = 0; s < NSL; ++s) {
-                char *st = dst0 + ((size_t)s * C::KS + ks) * STAGE;
-                *reinterpret_cast<__half *>(st + o) = sr[s];
-                *reinterpret_cast<__half *>(st + TILE + o) = si[s];
+                wr[s][q] = (uint32_t)__half_as_ushort(a0[s]) | ((uint32_t)__half_as_ushort(a1[s]) << 16);
+                wi[s][q] = (uint32_t)__half_as_ushort(b0[s]) | ((uint32_t)__half_as_ushort(b1[s]) << 16);
             }
+        }
+#pragma unroll
+        for (int s = 0; s < NSL; ++s) {
+            char *st = dst0 + ((size_t)s * C::KS + ks) * STAGE + o;
+            *reinterpret_cast<uint4 *>(st) = make_uint4(wr[s][0], wr[s][1], wr[s][2], wr[s][3]);
+            *reinterpret_cast<uint4 *>(st + TILE) = make_uint4(wi[s][0], wi[s][1], wi[s][2], wi[s][3]);
         }
     }
 }
@@ -232,16 +247,28 @@ __global__ void __launch_bounds__(NTHREADS, 1) resid_tc_kernel(const DevInst *__
             const int K = in.K, ncols = in.ncols, j0 = job.y;
             const float2 *__restrict__ X = in.X;
             const float *__restrict__ eks = in.rexp + KC;   // e_k of every row
-            // column maxima of E X over the K rows (the job's columns)
+            // column maxima of E X over the K rows (the job's columns): thread t takes
+            // rows t, t + 256, ... of every column (coalesced), then the warp's and
+            // the eight warps' maxima
             {
-                const int jl = t & 31, rg = t >> 5;
-                float m = 0.f;
-                if (jl < NB && j0 + jl < ncols)
-                    for (int k = rg; k < K; k += NEW) {
-                        const float2 v = X[k + (size_t)(j0 + jl) * KC];
-                        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)) * p2((int)eks[k]));
-                    }
-                S.cmax[rg][jl] = m;
+                float m[NB];
+#pragma unroll
+                for (int jl = 0; jl < NB; ++jl) m[jl] = 0.f;
+                for (int k = t; k < K; k += NEW * 32) {
+                    const float ek = p2((int)eks[k]);
+#pragma unroll
+                    for (int jl = 0; jl < NB; ++jl)
+                        if (j0 + jl < ncols) {
+                            const float2 v = X[k + (size_t)(j0 + jl) * KC];
+                            m[jl] = fmaxf(m[jl], fmaxf(fabsf(v.x), fabsf(v.y)) * ek);
+                        }
+                }
+#pragma unroll
+                for (int jl = 0; jl < NB; ++jl) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) m[jl] = fmaxf(m[jl], __shfl_xor_sync(0xffffffffu, m[jl], o));
+                    if (lane == 0) S.cmax[warp][jl] = m[jl];
+                }
             }
             asm volatile("bar.sync %0, %1;\n" ::"r"(BAR_EPI), "r"(NEW * 32) : "memory");
             if (t < NB) {
@@ -404,14 +431,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) resid_tc_kernel(const DevInst *__
                 const DevInst &in = insts[job.x];
                 if (sweep > 0 && in.rctl[1] != 0.f) continue;
                 const char *src = reinterpret_cast<const char *>(in.Asl);
-                for (int st = 0; st < C::RT * NSL * C::KS && !S.err; ++st, ++seq) {   // (rt, s, ks) order
+                // (rt, s, ks) order, SUB consecutive k-steps per copy
+                for (int st = 0; st < C::RT * NSL * C::KS / SUB && !S.err; ++st, ++seq) {
                     const int slot = seq % RING;
                     if (seq >= RING && !tc::mbar_wait(&S.empty[slot], ((seq / RING) - 1) & 1, WAIT_LIMIT)) {
                         S.err = 1;
                         break;
                     }
-                    tc::mbar_arrive_expect_tx(&S.full[slot], STAGE);
-                    bulk_load(ring0 + slot * STAGE, src + (size_t)st * STAGE, STAGE, &S.full[slot]);
+                    tc::mbar_arrive_expect_tx(&S.full[slot], SLOT);
+                    bulk_load(ring0 + slot * SLOT, src + (size_t)st * SLOT, SLOT, &S.full[slot]);
                 }
             }
             for (uint32_t q = seq > RING ? seq - RING : 0; q < seq; ++q)
@@ -433,14 +461,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) resid_tc_kernel(const DevInst *__
                 tc::tc_fence_after();
                 for (int rt = 0; rt < C::RT && !S.err; ++rt, ++use) {
                     for (int s = 0; s < NSL && !S.err; ++s) {          // slice s + 1 of A
-                        for (int ks = 0; ks < C::KS && !S.err; ++ks, ++seq) {
+                        for (int kq = 0; kq < C::KS / SUB && !S.err; ++kq, ++seq) {
                             const int slot = seq % RING;
                             if (!tc::mbar_wait(&S.full[slot], (seq / RING) & 1, WAIT_LIMIT)) {
                                 S.err = 1;
                                 break;
                             }
                             tc::tc_fence_after();
-                            const uint32_t a = ring0 + slot * STAGE;
+                            for (int u = 0; u < SUB; ++u) {
+                            const int ks = kq * SUB + u;
+                            const uint32_t a = ring0 + slot * SLOT + u * STAGE;
                             const uint64_t ad = tc::smem_desc(a, 128, 256), vd = tc::smem_desc(a + TILE, 128, 256);
                             for (int tt = 0; tt < NSL - s; ++tt) {       // X slice tt + 1: class s + tt
                                 const int ci = s + tt;
@@ -456,6 +486,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) resid_tc_kernel(const DevInst *__
                                 const uint32_t accum = (s == 0 && ks == 0) ? 0u : 1u;
                                 tc::mma_bf16(d, ad, bd, idesc, accum);        // FP16 by the descriptor
                                 tc::mma_bf16(d + BR, vd, bd, idesc, accum);
+                            }
                             }
                             tc::mma_commit(&S.empty[slot]);
                         }
