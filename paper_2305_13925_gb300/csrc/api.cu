@@ -747,10 +747,10 @@ jacpcg_status enqueue(jacpcg_plan *pl, cudaStream_t s, bool profile, int *n_laun
                         e = launch_pcg_tc64(ctx->cfg.variant, pl->d_insts,
                                             reinterpret_cast<const int *>(pl->dev + l.list_off), l.count,
                                             pl->acc, &ctx->amap, ctx->arena.base, s, 1);
-                    else if (l.kind == Launch::PCG_TCW)
+                    else if (l.kind == Launch::PCG_TCW)   // loose corrections: heads only (mode 2)
                         e = launch_pcg_tcw(l.param, ctx->cfg.variant, pl->d_insts,
                                            reinterpret_cast<const int2 *>(pl->dev + l.list_off), l.count,
-                                           pl->acc, s, 1);
+                                           pl->acc, s, ctx->cfg.refine_solve_tol >= 5e-3f ? 2 : 1);
                     else
                         continue;
                     if (e != cudaSuccess) return cuda_fail(ctx, e);

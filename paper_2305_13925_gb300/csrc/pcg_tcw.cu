@@ -176,9 +176,9 @@ __global__ void __launch_bounds__(256) tcw_prep_kernel(const DevInst *__restrict
         split_f16((v.y * si) * sk, ih, il);
         const uint32_t o = (uint32_t)(r >> 3) * 256u + (uint32_t)(k >> 3) * 128u + (uint32_t)(r & 7) * 16u +
                            (uint32_t)(k & 7) * 2u;
-        *reinterpret_cast<__half *>(dst + o) = rh;
-        *reinterpret_cast<__half *>(dst + TILE + o) = rl;
-        *reinterpret_cast<__half *>(dst + 2 * TILE + o) = ih;
+        *reinterpret_cast<__half *>(dst + o) = rh;              // [Ar_h | Ai_h | Ar_t | Ai_t]:
+        *reinterpret_cast<__half *>(dst + TILE + o) = ih;       // the heads lead, so a light
+        *reinterpret_cast<__half *>(dst + 2 * TILE + o) = rl;   // correction streams half
         *reinterpret_cast<__half *>(dst + 3 * TILE + o) = il;
     }
 }
@@ -267,7 +267,12 @@ __device__ __forceinline__ float col_sumsq(F f) {
 
 // MODE 0 solves A X = B from X0 (or 0); MODE 1 is a refinement correction
 // solve (right-hand side R, X += dX; instances that stopped refining are
-// skipped).  jobs: (instance, first column), NB columns each.
+// skipped); MODE 2 is the same with the heads of A and P only (FP16, 11 bits:
+// A off by 2^-12 of its entries, the correction's solution by about kappa
+// 2^-12, far inside the loose tolerance such solves run to -- the host asks
+// for it only when refine_solve_tol >= 5e-3): half the bytes streamed, two
+// MMAs per k-step instead of four.  jobs: (instance, first column), NB
+// columns each.
 template <int KC, int VAR, int MODE>
 __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__restrict__ insts,
                                                              const int2 *__restrict__ jobs, int n_jobs,
@@ -304,14 +309,43 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
     // ring, SUB consecutive stages (k-steps) per bulk copy; thread 32 issues their
     // MMAs (per stage: head x [P_h | P_t] and tail x P_h, Ar then Ai) and commits
     // to qfull; the other threads go on to wait.
+    constexpr bool LIGHT = MODE == 2;
+    constexpr int KPS = LIGHT ? 2 * SUB : SUB;       // k-steps per ring slot (heads: 8 KB each)
     auto product = [&](const char *src) {
         if (threadIdx.x == 0) {
-            for (int s = 0; s < C::NSTAGE / SUB; ++s, ++pc) {
+            for (int s = 0; s < C::NSTAGE / KPS; ++s, ++pc) {
                 const int slot = pc % RING;
                 if (!tc::mbar_wait(&S.empty[slot], ((pc / RING) & 1) ^ 1, WAIT_LIMIT)) S.err = 1;
                 tc::mbar_arrive_expect_tx(&S.full[slot], SLOT);
-                bulk_load(r_base + slot * SLOT, src + (size_t)s * SLOT, SLOT, &S.full[slot]);
+                if (LIGHT) {   // the leading [Ar_h | Ai_h] half of each k-step
+#pragma unroll
+                    for (int u = 0; u < KPS; ++u)
+                        bulk_load(r_base + slot * SLOT + u * (STAGE / 2), src + (size_t)(s * KPS + u) * STAGE,
+                                  STAGE / 2, &S.full[slot]);
+                } else {
+                    bulk_load(r_base + slot * SLOT, src + (size_t)s * SLOT, SLOT, &S.full[slot]);
+                }
             }
+        } else if (threadIdx.x == 32 && LIGHT) {
+            constexpr uint32_t id64 = tc::idesc_f16(128, 2 * NB, false);
+            tc::tc_fence_after();
+            for (int s = 0; s < C::NSTAGE / KPS; ++s, ++mc) {
+                const int slot = mc % RING;
+                if (!tc::mbar_wait(&S.full[slot], (mc / RING) & 1, WAIT_LIMIT)) S.err = 1;
+                tc::tc_fence_after();
+#pragma unroll
+                for (int u = 0; u < KPS; ++u) {
+                    const int g = s * KPS + u, rt = g / C::KS, ks = g % C::KS;
+                    const uint32_t a0 = r_base + slot * SLOT + u * (STAGE / 2);
+                    const uint64_t bd = tc::smem_desc(b_base + ks * 256, 128, C::SBO_B);   // [Pr_h | Pi_h]
+                    const uint32_t du = tmem + rt * 256, dvv = du + 128;
+                    const uint32_t acc = ks > 0 ? 1u : 0u;
+                    tc::mma_bf16(du, tc::smem_desc(a0, 128, 256), bd, id64, acc);
+                    tc::mma_bf16(dvv, tc::smem_desc(a0 + TILE, 128, 256), bd, id64, acc);
+                }
+                tc::mma_commit(&S.empty[slot]);
+            }
+            tc::mma_commit(&S.qfull);
         } else if (threadIdx.x == 32) {
             constexpr uint32_t id128 = tc::idesc_f16(128, 4 * NB, false);
             constexpr uint32_t id64 = tc::idesc_f16(128, 2 * NB, false);
@@ -328,8 +362,8 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
                     const uint32_t du = tmem + rt * 256, dvv = du + 128;
                     const uint32_t acc = ks > 0 ? 1u : 0u;
                     tc::mma_bf16(du, tc::smem_desc(a0, 128, 256), bd, id128, acc);   // FP16 by the descriptors
-                    tc::mma_bf16(du + 64, tc::smem_desc(a0 + TILE, 128, 256), bd, id64, 1u);
-                    tc::mma_bf16(dvv, tc::smem_desc(a0 + 2 * TILE, 128, 256), bd, id128, acc);
+                    tc::mma_bf16(du + 64, tc::smem_desc(a0 + 2 * TILE, 128, 256), bd, id64, 1u);
+                    tc::mma_bf16(dvv, tc::smem_desc(a0 + TILE, 128, 256), bd, id128, acc);
                     tc::mma_bf16(dvv + 64, tc::smem_desc(a0 + 3 * TILE, 128, 256), bd, id64, 1u);
                 }
                 tc::mma_commit(&S.empty[slot]);   // the slot is free once these have read it
@@ -354,7 +388,7 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
         // in as FP16 head and tail.  All lanes take part (shuffles); a column that
         // is not `active` keeps its published p.  f is evaluated twice, so it
         // must not depend on what the second pass writes at other rows.
-        int pex = SP;       // the column's exponent ex at the last publication
+        int pex = SP;       // exponent of the column's largest |E p| as last published
         // col_exp: the exponent ex for a column whose largest |E p| is at most mx
         // (a maximum over the column's 8 lanes), s_j = 2^(SP - ex); clamped so that
         // s_j, 1 / s_j and 2^-SA / s_j are floats
@@ -363,26 +397,30 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
             for (int o = 4; o <= 16; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
             return (mx >= 1.2e-38f && mx < 3.0e38f) ? min(max(exp2_of(mx), SA + SP - 126), SP + 126) : SP;
         };
-        // store s_j E p (p = f(m) at row g + 8 m) as FP16 head and tail, s_j = 2^(SP - ex)
+        // store s_j E p (p = f(m) at row g + 8 m) as FP16 head and tail, s_j = 2^(SP - ex);
+        // all lanes take part (shuffles)
         auto publish_exp = [&](bool active, int ex, auto f) {
             const float sj = pow2f(SP - ex);
+            float mx = 0.f;   // the published column's largest |E p| (tightens the next bound)
             if (active) {
 #pragma unroll
                 for (int m = 0; m < MR; ++m) {
                     const int i = g + 8 * m;
                     const float2 v = f(m);
+                    mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)) * scv[i]);
                     __half h, t;
                     split_f16((v.x * scv[i]) * sj, h, t);
                     bset(cl, i, h);
-                    bset(2 * NB + cl, i, t);
+                    if (!LIGHT) bset(2 * NB + cl, i, t);   // a light correction uses the heads only
                     split_f16((v.y * scv[i]) * sj, h, t);
                     bset(NB + cl, i, h);
-                    bset(3 * NB + cl, i, t);
+                    if (!LIGHT) bset(3 * NB + cl, i, t);
                 }
                 pinv = pow2f(ex - SP);
-                pex = ex;
                 if (g == 0) colq[cl] = pow2f(ex - SP - SA);
             }
+            const int ea = col_exp(mx);
+            if (active) pex = ea;
         };
         auto publish_all = [&](bool active, auto f) {
             float mx = 0.f;
@@ -397,6 +435,7 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
         };
         auto pget = [&](int m) {   // head + tail (exact in FP32), unscaled: p as published
             const int i = g + 8 * m;
+            if (LIGHT) return make_float2((bget(cl, i) * pinv) * iscv[i], (bget(NB + cl, i) * pinv) * iscv[i]);
             return make_float2(((bget(cl, i) + bget(2 * NB + cl, i)) * pinv) * iscv[i],
                                ((bget(NB + cl, i) + bget(3 * NB + cl, i)) * pinv) * iscv[i]);
         };
@@ -411,12 +450,12 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
             const int2 job = jobs[jj];
             const int id = job.x;
             const DevInst &in = insts[id];
-            if (MODE == 1 && in.rctl[1] != 0.f) continue;   // uniform: every role skips it
+            if (MODE >= 1 && in.rctl[1] != 0.f) continue;   // uniform: every role skips it
             const int K = in.K, T = in.max_iter, NCOL = in.ncols;
             const int j = job.y + cl;
             const bool valid = j < NCOL;
             const bool warm = MODE == 0 && in.X0 != nullptr;
-            const float tl = (MODE == 1 && in.rsolve_tol > 0.f) ? in.rsolve_tol : in.tol;
+            const float tl = (MODE >= 1 && in.rsolve_tol > 0.f) ? in.rsolve_tol : in.tol;
             const float tol2 = tl > 0.f ? tl * tl : -1.f;
             float2 *X = in.X + (size_t)(valid ? j : 0) * KC;   // the iterate (workspace, ld KC)
             epi_sync();   // the previous instance's readers of dvs, scv and iscv are done
@@ -434,7 +473,7 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
                 const int i = g + 8 * m;
                 float2 b = make_float2(0.f, 0.f);
                 if (valid && i < K) {
-                    if (MODE == 1) b = in.R[i + (size_t)j * KC];                    // refinement residual
+                    if (MODE >= 1) b = in.R[i + (size_t)j * KC];                    // refinement residual
                     else if (!in.B) b.x = (i == j) ? 1.f : 0.f;                      // B = I
                     else b = in.B[i + (size_t)j * in.ldb];                           // symbol vectors
                 }
@@ -484,6 +523,19 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
                     const int o = (rt * NB + 16 * hh) * QLD + 32 * qw + lane;
                     const float rf = scv[rt * 128 + 32 * qw + lane];   // row factor 2^e_i
                     float a[16], b[16], c[16], d[16];
+                    if (LIGHT) {   // heads only: no correction columns
+                        tc::tmem_ld16(tb, a);
+                        tc::tmem_ld16(tb + 128 + NB, c);
+                        tc::tmem_ld_wait();
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) Qre[o + e * QLD] = (a[e] - c[e]) * rf * colq[16 * hh + e];
+                        tc::tmem_ld16(tb + 128, a);
+                        tc::tmem_ld16(tb + NB, c);
+                        tc::tmem_ld_wait();
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) Qim[o + e * QLD] = (a[e] + c[e]) * rf * colq[16 * hh + e];
+                        continue;
+                    }
                     // Re q = Ar Pr - Ai Pi
                     tc::tmem_ld16(tb, a);
                     tc::tmem_ld16(tb + 64, b);
@@ -551,8 +603,9 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
                 });
                 const float rr_new = col_sumsq<MR>([&](int m, float2 &a, float2 &b) { a = r[m]; b = r[m]; });
                 // p = z + beta p, published for the next product, its scale from the
-                // bound max |E p| <= max |E z| + beta max |E p_old| (< 2^(pex + 1)): one
-                // pass over the rows instead of two
+                // bound max |E p| <= max |E z| + beta max |E p_old| (< 2^(pex + 1), the
+                // maximum of what was published, so bounds do not compound): one pass
+                // over the rows instead of two
                 const float beta = (!done && rho != 0.f) ? rz_new / rho : 0.f;
                 float mz = 0.f;
 #pragma unroll
@@ -631,8 +684,14 @@ cudaError_t launch_main(const DevInst *insts, const int2 *jobs, int n, DevAccum 
 template <int KC>
 cudaError_t launch_kc(int variant, const DevInst *insts, const int2 *jobs, int n, DevAccum acc, cudaStream_t s,
                       int mode) {
-    if (variant == 0) return mode ? launch_main<KC, 0, 1>(insts, jobs, n, acc, s) : launch_main<KC, 0, 0>(insts, jobs, n, acc, s);
-    if (variant == 2) return mode ? launch_main<KC, 2, 1>(insts, jobs, n, acc, s) : launch_main<KC, 2, 0>(insts, jobs, n, acc, s);
+    if (variant == 0)
+        return mode == 2 ? launch_main<KC, 0, 2>(insts, jobs, n, acc, s)
+               : mode    ? launch_main<KC, 0, 1>(insts, jobs, n, acc, s)
+                         : launch_main<KC, 0, 0>(insts, jobs, n, acc, s);
+    if (variant == 2)
+        return mode == 2 ? launch_main<KC, 2, 2>(insts, jobs, n, acc, s)
+               : mode    ? launch_main<KC, 2, 1>(insts, jobs, n, acc, s)
+                         : launch_main<KC, 2, 0>(insts, jobs, n, acc, s);
     return cudaErrorInvalidValue;
 }
 
