@@ -274,7 +274,7 @@ bool sliced_resid(const jacpcg_config &cfg, bool refine, const jacpcg_instance &
     return refine && cfg.refine_residual == JACPCG_RESID_SLICED && k_class(q.K) >= 128 && q.M > 2 * q.K;
 }
 constexpr int RTC_NB = 24;   // columns per job of the sliced residual
-constexpr int TCW_NB = 32;   // columns per CTA of the 128 / 256-class tensor-core iteration
+constexpr int TCW_NB = 16;   // columns per CTA of the 128 / 256-class tensor-core iteration
 
 // K classes whose Gram runs on the tensor cores at this precision (64 x 64
 // user-group blocks: one diagonal job for the 64 class, 2 + 1 for 128, 4 + 6

@@ -15,11 +15,11 @@
 // B = [Xr^T ; Xi^T] of those columns (64 rows, K-major, no swizzle, three
 // terms: 96 KB for K = 256) stays in shared memory for the whole job; H
 // streams through a ring of stages of 128 rows of U x 64 users, two tiled
-// TMA copies each (128-byte swizzle, zero-filled past M and K).  The X1
-// products of a 128-row tile form one accumulation chain of K / 16 MMAs in
-// TMEM (the tensor core's FP32 accumulation truncates; no chain is longer
-// than the Gram's), the X2 and X3 products (2^-8 and 2^-16 of them) a second
-// one; the epilogue adds the two.
+// TMA copies each (128-byte swizzle, zero-filled past M and K).  The three
+// terms' rows of B follow each other, so one N = 192 MMA per 16 users forms
+// the X1, X2 and X3 products side by side in TMEM: three accumulation chains
+// of K / 16 MMAs per 128-row tile (the tensor core's FP32 accumulation
+// truncates; no chain is longer than the Gram's), added by the epilogue.
 //
 // Persistent, warp-specialised, one CTA per SM walking its jobs:
 //   warps 0-7   at the start of a job (the previous job's MMAs done) build B
@@ -28,7 +28,7 @@
 //               column-major, coalesced) and the tile's ||W||_F^2 partial in
 //               slot g * (row tiles) + tile;
 //   warp 8      lane 0 issues the tensor copies, up to RING stages ahead;
-//   warp 9      TMEM allocation (NBUF tiles of 128 columns); lane 0 issues
+//   warp 9      TMEM allocation (NBUF tiles of 192 columns); lane 0 issues
 //               the MMAs and commits.
 // Every wait is bounded; a timeout stops the CTA's pipeline, flags its
 // instances with FLAG_TIMEOUT, and the CTA still drains and frees its TMEM.
@@ -51,11 +51,11 @@ constexpr int UST = 2 * BOX;              // one stage: 128 rows of U x 64 users
 constexpr int RING = 7;
 constexpr int KCMAX = 256;
 constexpr int BTERM = BR * KCMAX * 2;     // one bfloat16 term of B (32 KB)
-constexpr int NBUF = 4;                   // TMEM tile buffers: X1 chain | X2 + X3 chain
+constexpr int NBUF = 2;                   // TMEM tile buffers: X1 | X2 | X3 products, 64 columns each
 constexpr int NEW = 8;                    // epilogue warps
 constexpr int TMA_WARP = NEW, MMA_WARP = NEW + 1;
 constexpr int NTHREADS = (NEW + 2) * 32;
-constexpr int TMEM_COLS = NBUF * 2 * BR;  // 512
+constexpr int TMEM_COLS = 512;            // NBUF x 3 x BR = 384 used
 constexpr uint32_t WAIT_LIMIT = 1u << 21;
 constexpr int BAR_EPI = 1;                // named barrier of the epilogue warps
 
@@ -137,7 +137,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_bf16_kernel(const DevInst *__r
             const int nag = KC / 8;                  // 8-user groups along K
             const uint32_t sbo = nag * 128;
             // B term tt, row r (0..63), users a..a+7 (a = 8 ag): 16 bytes at
-            // tt * BTERM + (r / 8) * sbo + ag * 128 + (r % 8) * 16
+            // (8 tt + r / 8) * sbo + ag * 128 + (r % 8) * 16: the three terms' rows follow
+            // each other, so one N = 192 MMA multiplies all three
             const float2 *__restrict__ X = in.X;
             for (int e = t; e < NB * nag; e += NEW * 32) {
                 const int r8 = e & 7, ag = (e >> 3) % nag, ng = (e >> 3) / nag;
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_bf16_kernel(const DevInst *__r
                 }
 #pragma unroll
                 for (int tt = 0; tt < 3; ++tt) {
-                    const uint32_t base = b0 + tt * BTERM + ag * 128 + r8 * 16;
+                    const uint32_t base = b0 + tt * 8 * sbo + ag * 128 + r8 * 16;   // terms stacked along N
                     const uint32_t ar = base + ng * sbo, ai = base + (NB / 8 + ng) * sbo;
                     asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n" ::"r"(ar), "r"(re[tt][0]),
                                  "r"(re[tt][1]), "r"(re[tt][2]), "r"(re[tt][3])
@@ -189,22 +190,24 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_bf16_kernel(const DevInst *__r
                     ok = false;
                 }
                 ok = __all_sync(0xffffffffu, ok);
-                float d1[16], d2[16], v[16];
+                float d1[16], d2[16], v[16], w[16];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) d1[i] = d2[i] = 0.f;
                 if (ok) {
                     tc::tc_fence_after();
-                    const uint32_t ta = tmem + ((uint32_t)(32 * quad) << 16) + buf * 2 * BR + 16 * part;
-                    tc::tmem_ld16(ta, d1);               // X1 chain, Xr columns
-                    tc::tmem_ld16(ta + BR, v);           // X2 + X3 chain, Xr columns
+                    const uint32_t ta = tmem + ((uint32_t)(32 * quad) << 16) + buf * 3 * BR + 16 * part;
+                    tc::tmem_ld16(ta, d1);               // X1 products, Xr columns
+                    tc::tmem_ld16(ta + BR, v);           // X2
+                    tc::tmem_ld16(ta + 2 * BR, w);       // X3
                     tc::tmem_ld_wait();
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) d1[i] += v[i];
-                    tc::tmem_ld16(ta + NB, d2);          // X1 chain, Xi columns
-                    tc::tmem_ld16(ta + BR + NB, v);      // X2 + X3 chain, Xi columns
+                    for (int i = 0; i < 16; ++i) d1[i] += v[i] + w[i];
+                    tc::tmem_ld16(ta + NB, d2);          // X1 products, Xi columns
+                    tc::tmem_ld16(ta + BR + NB, v);
+                    tc::tmem_ld16(ta + 2 * BR + NB, w);
                     tc::tmem_ld_wait();
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) d2[i] += v[i];
+                    for (int i = 0; i < 16; ++i) d2[i] += v[i] + w[i];
                     tc::tc_fence_before();
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(&S.tfree[buf]);
@@ -267,7 +270,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_bf16_kernel(const DevInst *__r
     } else {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            constexpr uint32_t idesc = tc::idesc_bf16(TR, BR, /*a_mn=*/true, /*b_mn=*/false);
+            constexpr uint32_t idesc = tc::idesc_bf16(TR, 3 * BR, /*a_mn=*/true, /*b_mn=*/false);
             uint32_t seq = 0, seqt = 0, njob = 0;
             for (int j = blockIdx.x; j < n_jobs && !S.err; j += gridDim.x, ++njob) {
                 const int4 job = jobs[j];
@@ -288,7 +291,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_bf16_kernel(const DevInst *__r
                         }
                         tc::tc_fence_after();
                     }
-                    const uint32_t d = tmem + buf * 2 * BR, dc = d + BR;
+                    const uint32_t d = tmem + buf * 3 * BR;
                     for (int kc = 0; kc < nkc; ++kc, ++seq) {
                         const int s = seq % RING;
                         if (!tc::mbar_wait(&S.full[s], (seq / RING) & 1, WAIT_LIMIT)) {
@@ -303,10 +306,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_bf16_kernel(const DevInst *__r
                             const uint64_t ad = tc::smem_desc_sw128(u + kk * 2048, BOX, 1024);
                             const uint32_t boff = (8 * kc + 2 * kk) * 128;
                             const bool first = kc == 0 && kk == 0;
+                            // all three terms (N = 192: X1 | X2 | X3 products side by side)
                             tc::mma_bf16(d, ad, tc::smem_desc(b0 + boff, 128, sbo), idesc, first ? 0u : 1u);
-                            tc::mma_bf16(dc, ad, tc::smem_desc(b0 + BTERM + boff, 128, sbo), idesc,
-                                         first ? 0u : 1u);
-                            tc::mma_bf16(dc, ad, tc::smem_desc(b0 + 2 * BTERM + boff, 128, sbo), idesc, 1u);
                         }
                         tc::mma_commit(&S.empty[s]);
                     }

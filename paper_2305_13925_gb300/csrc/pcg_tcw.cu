@@ -20,25 +20,26 @@
 // imaginary parts are kept apart (planar), so each byte of A is streamed once
 // per iteration rather than twice as in the 2 x 2 real expansion.
 //
-// The columns of X are independent systems sharing A, so a CTA owns 32 of
-// them (NB) for one instance.  Their P is resident in shared memory as the
+// The columns of X are independent systems sharing A, so a CTA owns 16 of
+// them (NB) for one instance, and two CTAs share an SM.  Their P is resident in shared memory as the
 // MMA's B operand, laid out as 4 NB rows [Pr_h | Pi_h | Pr_t | Pi_t] along N:
 // FP16 head and tail of s_j E p_j, s_j a power of two per column that puts
 // the column's largest entry in [2^14, 2^15).  Per k-step:
-//   U += Ar_h [P_h | P_t]  (N = 128),   U[64..] += Ar_t P_h  (N = 64),
-//   V += Ai_h [P_h | P_t],              V[64..] += Ai_t P_h,
+//   U += Ar_h [P_h | P_t]  (N = 4 NB),   U[2 NB..] += Ar_t P_h  (N = 2 NB),
+//   V += Ai_h [P_h | P_t],               V[2 NB..] += Ai_t P_h,
 // so U = Ar [Pr | Pi] and V = Ai [Pr | Pi] with every product exact (columns
-// 0-63 head x head, 64-127 both corrections), and
+// 0 .. 2 NB - 1 head x head, the rest both corrections), and
 //   Re q = Ar Pr - Ai Pi,   Im q = Ai Pr + Ar Pi,
 // each unscaled by 2^(e_i - 13) / s_j on its way out of TMEM.  U and V of both
-// row tiles take 4 x 128 TMEM columns (K = 256: all 512).  The accumulation
+// row tiles take 2 x 2 x 4 NB TMEM columns (K = 256: 256, half of the SM's
+// 512, so two CTAs fit).  The accumulation
 // chain of a row tile is its KC / 16 k-steps.  The iteration uses p as
 // published (head + tail, unscaled: 22 bits), in the product and everywhere
 // else, so the recurrences stay consistent.
 //
-// Roles: 8 warps own the vectors; each iteration they publish P (split) into
+// Roles: 4 warps own the vectors; each iteration they publish P (split) into
 // the B operand and vote on continuing (one barrier reduction), then thread 0
-// streams the iteration's KC / 128 x KC / 8 stages (waiting on `empty`),
+// streams the iteration's KC / 128 x KC / 16 stages (waiting on `empty`),
 // thread 32 issues the MMAs (waiting on `full`) and commits to `qfull`, and
 // the epilogue -- idle while the product runs, so the roles take no warps of
 // their own and every thread may hold 255 registers -- waits on `qfull`,
@@ -53,8 +54,9 @@
 // with commutative or exact operations); the squared norms r^H D^{-1} r and
 // ||r||^2 sum nonnegative terms, where pairwise summation is already
 // accurate to a few units, and are summed so.  All eight lanes of a column
-// hold bit-identical totals.  Every wait is bounded; a timeout sets the instance's ETIMEOUT
-// flag and ends its iteration.
+// hold bit-identical totals.  With two CTAs on an SM, one CTA's epilogue runs
+// while the other's product streams and multiplies.  Every wait is bounded; a
+// timeout sets the instance's ETIMEOUT flag and ends its iteration.
 #include <cuda_fp16.h>
 
 #include "common.cuh"
@@ -65,13 +67,19 @@ namespace jacpcg {
 
 namespace {
 
-constexpr int NB = 32;                        // right-hand-side columns per CTA
-constexpr int THREADS = 256;                  // 8 warps: 2 per SM sub-partition, up to 255 registers
+// Two CTAs per SM, each of 4 warps owning 16 columns: one CTA's epilogue runs
+// while the other's product streams and multiplies.  On the XL batch this
+// measured the same as one CTA of 8 warps and 32 columns (4.23 against 4.27
+// ms for the main solve: the stream of A, not idle tensor cores, bounds it),
+// but a lone request gets twice the CTAs.
+constexpr int NB = 16;                        // right-hand-side columns per CTA
+constexpr int THREADS = 128;                  // 4 warps, up to 255 registers with two CTAs per SM
+constexpr int CTAS_PER_SM = 2;
 constexpr int EPI = THREADS;
 constexpr int STAGE = 16384;                  // bytes of one k-step: four 128 x 16 FP16 tiles
 constexpr int SUB = 2;                        // k-steps per bulk copy (ring slot)
 constexpr int SLOT = SUB * STAGE;
-constexpr int RING = 4;                       // ring slots in flight
+constexpr int RING = 2;                       // ring slots in flight per CTA
 constexpr int TILE = 4096;
 constexpr int SA = 13;                        // A is stored scaled by 2^SA (entries below 2^15)
 constexpr int SP = 14;                        // a column of P is scaled to a largest entry in [2^14, 2^15)
@@ -87,12 +95,14 @@ struct Cfg {
     static constexpr uint32_t SBO_B = (KC / 8) * 128;        // bytes between 8-row groups of B (N)
     static constexpr int B_BYTES = 4 * NB * KC * 2;          // the B operand
     static constexpr int MR = KC / 8;                        // complex rows per epilogue thread
-    static constexpr uint32_t TMEM_COLS = RT == 2 ? 512 : 256;
+    static constexpr uint32_t TMEM_COLS = RT * 8 * NB;       // per row tile U | V, 4 NB columns each
     // B, ring, then per row 1 / d, 2^e, 2^-e; per column the readout factor
     static constexpr int SMEM = B_BYTES + RING * SLOT + 3 * KC * 4 + NB * 4 + 256;
     static_assert(2 * RT * NB * QLD * 4 <= RING * SLOT, "Q staging fits the ring");
-    static_assert(NSTAGE % SUB == 0, "whole slots");
-    static_assert(SMEM <= 227 * 1024, "shared memory");
+    static_assert(KS % (2 * SUB) == 0, "whole slots in a row tile");
+    static_assert(CTAS_PER_SM * (SMEM + 1024) <= 228 * 1024, "shared memory");
+    static_assert(CTAS_PER_SM * TMEM_COLS <= 512, "tensor memory");
+    static_assert(THREADS / 32 * 4 == NB, "a warp owns 4 columns");
 };
 
 struct Ctl {
@@ -274,7 +284,7 @@ __device__ __forceinline__ float col_sumsq(F f) {
 // MMAs per k-step instead of four.  jobs: (instance, first column), NB
 // columns each.
 template <int KC, int VAR, int MODE>
-__global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__restrict__ insts,
+__global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const DevInst *__restrict__ insts,
                                                              const int2 *__restrict__ jobs, int n_jobs,
                                                              DevAccum acc_out) {
     using C = Cfg<KC>;
@@ -311,60 +321,68 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
     // to qfull; the other threads go on to wait.
     constexpr bool LIGHT = MODE == 2;
     constexpr int KPS = LIGHT ? 2 * SUB : SUB;       // k-steps per ring slot (heads: 8 KB each)
+    auto first_kstep = [&](int s) {   // slot s -> (row tile, k-step of its first stage)
+        const int g0 = s * KPS;
+        return make_int2(g0 / C::KS, g0 % C::KS);
+    };
     auto product = [&](const char *src) {
         if (threadIdx.x == 0) {
             for (int s = 0; s < C::NSTAGE / KPS; ++s, ++pc) {
                 const int slot = pc % RING;
+                const int2 f = first_kstep(s);
+                const char *st = src + (size_t)(f.x * C::KS + f.y) * STAGE;
                 if (!tc::mbar_wait(&S.empty[slot], ((pc / RING) & 1) ^ 1, WAIT_LIMIT)) S.err = 1;
                 tc::mbar_arrive_expect_tx(&S.full[slot], SLOT);
                 if (LIGHT) {   // the leading [Ar_h | Ai_h] half of each k-step
 #pragma unroll
                     for (int u = 0; u < KPS; ++u)
-                        bulk_load(r_base + slot * SLOT + u * (STAGE / 2), src + (size_t)(s * KPS + u) * STAGE,
-                                  STAGE / 2, &S.full[slot]);
+                        bulk_load(r_base + slot * SLOT + u * (STAGE / 2), st + (size_t)u * STAGE, STAGE / 2,
+                                  &S.full[slot]);
                 } else {
-                    bulk_load(r_base + slot * SLOT, src + (size_t)s * SLOT, SLOT, &S.full[slot]);
+                    bulk_load(r_base + slot * SLOT, st, SLOT, &S.full[slot]);
                 }
             }
         } else if (threadIdx.x == 32 && LIGHT) {
-            constexpr uint32_t id64 = tc::idesc_f16(128, 2 * NB, false);
+            constexpr uint32_t idN2 = tc::idesc_f16(128, 2 * NB, false);
             tc::tc_fence_after();
             for (int s = 0; s < C::NSTAGE / KPS; ++s, ++mc) {
                 const int slot = mc % RING;
                 if (!tc::mbar_wait(&S.full[slot], (mc / RING) & 1, WAIT_LIMIT)) S.err = 1;
                 tc::tc_fence_after();
+                const int2 f = first_kstep(s);
 #pragma unroll
                 for (int u = 0; u < KPS; ++u) {
-                    const int g = s * KPS + u, rt = g / C::KS, ks = g % C::KS;
+                    const int rt = f.x, ks = f.y + u;
                     const uint32_t a0 = r_base + slot * SLOT + u * (STAGE / 2);
                     const uint64_t bd = tc::smem_desc(b_base + ks * 256, 128, C::SBO_B);   // [Pr_h | Pi_h]
-                    const uint32_t du = tmem + rt * 256, dvv = du + 128;
+                    const uint32_t du = tmem + rt * 8 * NB, dvv = du + 4 * NB;
                     const uint32_t acc = ks > 0 ? 1u : 0u;
-                    tc::mma_bf16(du, tc::smem_desc(a0, 128, 256), bd, id64, acc);
-                    tc::mma_bf16(dvv, tc::smem_desc(a0 + TILE, 128, 256), bd, id64, acc);
+                    tc::mma_bf16(du, tc::smem_desc(a0, 128, 256), bd, idN2, acc);
+                    tc::mma_bf16(dvv, tc::smem_desc(a0 + TILE, 128, 256), bd, idN2, acc);
                 }
                 tc::mma_commit(&S.empty[slot]);
             }
             tc::mma_commit(&S.qfull);
         } else if (threadIdx.x == 32) {
-            constexpr uint32_t id128 = tc::idesc_f16(128, 4 * NB, false);
-            constexpr uint32_t id64 = tc::idesc_f16(128, 2 * NB, false);
+            constexpr uint32_t idN4 = tc::idesc_f16(128, 4 * NB, false);
+            constexpr uint32_t idN2 = tc::idesc_f16(128, 2 * NB, false);
             tc::tc_fence_after();
             for (int s = 0; s < C::NSTAGE / SUB; ++s, ++mc) {
                 const int slot = mc % RING;
                 if (!tc::mbar_wait(&S.full[slot], (mc / RING) & 1, WAIT_LIMIT)) S.err = 1;
                 tc::tc_fence_after();
+                const int2 f = first_kstep(s);
 #pragma unroll
                 for (int u = 0; u < SUB; ++u) {
-                    const int g = s * SUB + u, rt = g / C::KS, ks = g % C::KS;
+                    const int rt = f.x, ks = f.y + u;
                     const uint32_t a0 = r_base + slot * SLOT + u * STAGE;
                     const uint64_t bd = tc::smem_desc(b_base + ks * 256, 128, C::SBO_B);
-                    const uint32_t du = tmem + rt * 256, dvv = du + 128;
+                    const uint32_t du = tmem + rt * 8 * NB, dvv = du + 4 * NB;
                     const uint32_t acc = ks > 0 ? 1u : 0u;
-                    tc::mma_bf16(du, tc::smem_desc(a0, 128, 256), bd, id128, acc);   // FP16 by the descriptors
-                    tc::mma_bf16(du + 64, tc::smem_desc(a0 + 2 * TILE, 128, 256), bd, id64, 1u);
-                    tc::mma_bf16(dvv, tc::smem_desc(a0 + TILE, 128, 256), bd, id128, acc);
-                    tc::mma_bf16(dvv + 64, tc::smem_desc(a0 + 3 * TILE, 128, 256), bd, id64, 1u);
+                    tc::mma_bf16(du, tc::smem_desc(a0, 128, 256), bd, idN4, acc);   // FP16 by the descriptors
+                    tc::mma_bf16(du + 2 * NB, tc::smem_desc(a0 + 2 * TILE, 128, 256), bd, idN2, 1u);
+                    tc::mma_bf16(dvv, tc::smem_desc(a0 + TILE, 128, 256), bd, idN4, acc);
+                    tc::mma_bf16(dvv + 2 * NB, tc::smem_desc(a0 + 3 * TILE, 128, 256), bd, idN2, 1u);
                 }
                 tc::mma_commit(&S.empty[slot]);   // the slot is free once these have read it
             }
@@ -519,17 +537,17 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
                 tc::tc_fence_after();
 #pragma unroll
                 for (int rt = 0; rt < C::RT; ++rt) {
-                    const uint32_t tb = tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)(rt * 256 + 16 * hh);
+                    const uint32_t tb = tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)(rt * 8 * NB + 16 * hh);
                     const int o = (rt * NB + 16 * hh) * QLD + 32 * qw + lane;
                     const float rf = scv[rt * 128 + 32 * qw + lane];   // row factor 2^e_i
                     float a[16], b[16], c[16], d[16];
                     if (LIGHT) {   // heads only: no correction columns
                         tc::tmem_ld16(tb, a);
-                        tc::tmem_ld16(tb + 128 + NB, c);
+                        tc::tmem_ld16(tb + 4 * NB + NB, c);
                         tc::tmem_ld_wait();
 #pragma unroll
                         for (int e = 0; e < 16; ++e) Qre[o + e * QLD] = (a[e] - c[e]) * rf * colq[16 * hh + e];
-                        tc::tmem_ld16(tb + 128, a);
+                        tc::tmem_ld16(tb + 4 * NB, a);
                         tc::tmem_ld16(tb + NB, c);
                         tc::tmem_ld_wait();
 #pragma unroll
@@ -537,19 +555,19 @@ __global__ void __launch_bounds__(THREADS, 1) pcg_tcw_kernel(const DevInst *__re
                         continue;
                     }
                     // Re q = Ar Pr - Ai Pi
-                    tc::tmem_ld16(tb, a);
-                    tc::tmem_ld16(tb + 64, b);
-                    tc::tmem_ld16(tb + 128 + NB, c);
-                    tc::tmem_ld16(tb + 128 + 64 + NB, d);
+                    tc::tmem_ld16(tb, a);                       // U: Ar P_h
+                    tc::tmem_ld16(tb + 2 * NB, b);              // U: corrections
+                    tc::tmem_ld16(tb + 4 * NB + NB, c);         // V: Ai Pi_h
+                    tc::tmem_ld16(tb + 4 * NB + 3 * NB, d);     // V: corrections of Ai Pi
                     tc::tmem_ld_wait();
 #pragma unroll
                     for (int e = 0; e < 16; ++e)
                         Qre[o + e * QLD] = ((a[e] + b[e]) - (c[e] + d[e])) * rf * colq[16 * hh + e];
                     // Im q = Ai Pr + Ar Pi
-                    tc::tmem_ld16(tb + 128, a);
-                    tc::tmem_ld16(tb + 128 + 64, b);
+                    tc::tmem_ld16(tb + 4 * NB, a);
+                    tc::tmem_ld16(tb + 4 * NB + 2 * NB, b);
                     tc::tmem_ld16(tb + NB, c);
-                    tc::tmem_ld16(tb + 64 + NB, d);
+                    tc::tmem_ld16(tb + 3 * NB, d);
                     tc::tmem_ld_wait();
 #pragma unroll
                     for (int e = 0; e < 16; ++e)
@@ -677,7 +695,10 @@ cudaError_t launch_main(const DevInst *insts, const int2 *jobs, int n, DevAccum 
     auto kern = pcg_tcw_kernel<KC, VAR, MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<KC>::SMEM);
     if (e != cudaSuccess) return e;
-    kern<<<n < sm_count() ? n : sm_count(), THREADS, Cfg<KC>::SMEM, s>>>(insts, jobs, n, acc);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    const int grid = CTAS_PER_SM * sm_count();
+    kern<<<n < grid ? n : grid, THREADS, Cfg<KC>::SMEM, s>>>(insts, jobs, n, acc);
     return cudaGetLastError();
 }
 

@@ -37,7 +37,10 @@
 // built by the epilogue warps at the start of the job.  Per row tile the A
 // stages stream slice by slice through a ring of bulk copies; after slice s,
 // class s is complete, so the epilogue drains it while the next slice streams.
-// The five classes hold 5 x 96 TMEM columns (U | V, 48 each).
+// The five classes hold 2 x 5 x 48 TMEM columns (all U, then all V); the
+// X slices' B rows follow each other, so slice s of A meets X slices 1 ..
+// NSL - s in one MMA of N = 48 (NSL - s) into classes s .. 4 (one for U, one
+// for V: two MMAs per k-step instead of ten).
 //
 // Roles: warps 0-7 build B, then drain the classes (TMEM lanes 32 (w mod 4)
 // .., columns 12 (w / 4) .. of the job) and write R and the column norms;
@@ -360,11 +363,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) resid_tc_kernel(const DevInst *__
                     if (!ok) continue;
                     tc::tc_fence_after();
                     // 16 columns from the thread's first (the last 4 belong to the neighbour)
-                    const uint32_t ta = tmem + ((uint32_t)(32 * quad) << 16) + ci * 2 * BR + CPT * part;
+                    // U of class ci at columns ci BR .., V at (NCLS + ci) BR ..
+                    const uint32_t ta = tmem + ((uint32_t)(32 * quad) << 16) + ci * BR + CPT * part;
+                    const uint32_t tv = ta + NCLS * BR;
                     const float w = p2(-14 - 8 * ci);
                     float u[16], v[16];
                     tc::tmem_ld16(ta, u);               // Ar Xr
-                    tc::tmem_ld16(ta + BR + NB, v);     // Ai Xi
+                    tc::tmem_ld16(tv + NB, v);          // Ai Xi
                     tc::tmem_ld_wait();
 #pragma unroll
                     for (int i = 0; i < CPT; ++i) {     // Re: acc -= w (Ar Xr - Ai Xi), terms exact
@@ -372,7 +377,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) resid_tc_kernel(const DevInst *__
                         two_sum_acc(hr[i], lr[i], w * v[i]);
                     }
                     tc::tmem_ld16(ta + NB, u);          // Ar Xi
-                    tc::tmem_ld16(ta + BR, v);          // Ai Xr
+                    tc::tmem_ld16(tv, v);               // Ai Xr
                     tc::tmem_ld_wait();
                     tc::tc_fence_before();
                     __syncwarp();
@@ -447,7 +452,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) resid_tc_kernel(const DevInst *__
         }
     } else {
         if (lane == 0) {
-            constexpr uint32_t idesc = tc::idesc_f16(128, BR, false);
+
             uint32_t seq = 0, use = 0, njob = 0;
             for (int jj = blockIdx.x; jj < n_jobs && !S.err; jj += gridDim.x) {
                 const int2 job = jobs[jj];
@@ -461,6 +466,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) resid_tc_kernel(const DevInst *__
                 tc::tc_fence_after();
                 for (int rt = 0; rt < C::RT && !S.err; ++rt, ++use) {
                     for (int s = 0; s < NSL && !S.err; ++s) {          // slice s + 1 of A
+                        const uint32_t idn = tc::idesc_f16(128, BR * (NSL - s), false);
                         for (int kq = 0; kq < C::KS / SUB && !S.err; ++kq, ++seq) {
                             const int slot = seq % RING;
                             if (!tc::mbar_wait(&S.full[slot], (seq / RING) & 1, WAIT_LIMIT)) {
@@ -472,21 +478,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) resid_tc_kernel(const DevInst *__
                             const int ks = kq * SUB + u;
                             const uint32_t a = ring0 + slot * SLOT + u * STAGE;
                             const uint64_t ad = tc::smem_desc(a, 128, 256), vd = tc::smem_desc(a + TILE, 128, 256);
-                            for (int tt = 0; tt < NSL - s; ++tt) {       // X slice tt + 1: class s + tt
-                                const int ci = s + tt;
-                                if (s == 0 && ks == 0 && use > 0) {      // the class's previous pass is drained
-                                    if (!tc::mbar_wait(&S.tfree[ci], (use - 1) & 1, WAIT_LIMIT)) {
-                                        S.err = 1;
-                                        break;
-                                    }
-                                    tc::tc_fence_after();
-                                }
-                                const uint64_t bd = tc::smem_desc(b0 + tt * C::BSL + ks * 256, 128, C::SBO_B);
-                                const uint32_t d = tmem + ci * 2 * BR;
-                                const uint32_t accum = (s == 0 && ks == 0) ? 0u : 1u;
-                                tc::mma_bf16(d, ad, bd, idesc, accum);        // FP16 by the descriptor
-                                tc::mma_bf16(d + BR, vd, bd, idesc, accum);
-                            }
+                            const bool first = s == 0 && ks == 0;   // initialises every class
+                            if (first && use > 0)                    // the classes' previous pass is drained
+                                for (int ci = 0; ci < NCLS; ++ci)
+                                    if (!tc::mbar_wait(&S.tfree[ci], (use - 1) & 1, WAIT_LIMIT)) S.err = 1;
+                            tc::tc_fence_after();
+                            // X slices 1 .. NSL - s stacked along N (their B rows follow each
+                            // other): one MMA into classes s .. NCLS - 1 for U, one for V
+                            const uint64_t bd = tc::smem_desc(b0 + ks * 256, 128, C::SBO_B);
+                            const uint32_t accum = first ? 0u : 1u;
+                            tc::mma_bf16(tmem + s * BR, ad, bd, idn, accum);              // FP16 by the descriptor
+                            tc::mma_bf16(tmem + (NCLS + s) * BR, vd, bd, idn, accum);
                             }
                             tc::mma_commit(&S.empty[slot]);
                         }
