@@ -274,7 +274,6 @@ bool sliced_resid(const jacpcg_config &cfg, bool refine, const jacpcg_instance &
     return refine && cfg.refine_residual == JACPCG_RESID_SLICED && k_class(q.K) >= 128 && q.M > 2 * q.K;
 }
 constexpr int RTC_NB = 24;   // columns per job of the sliced residual
-constexpr int TCW_NB = 16;   // columns per CTA of the 128 / 256-class tensor-core iteration
 
 // K classes whose Gram runs on the tensor cores at this precision (64 x 64
 // user-group blocks: one diagonal job for the 64 class, 2 + 1 for 128, 4 + 6
@@ -332,7 +331,7 @@ Layout make_layout(const jacpcg_config &cfg, const jacpcg_instance *inst, int n,
         L.n_pcg += n_pblocks(inst[i], shape_idx);
         L.n_hx += n_wtiles(inst[i]);
         if (inst[i].sinr) L.n_sinr += (inst[i].K + 7) / 8;
-        if (pcg_on_tcw(cfg, shape_idx, k_class(inst[i].K))) L.n_twj += (n_cols(inst[i]) + TCW_NB - 1) / TCW_NB;
+        if (pcg_on_tcw(cfg, shape_idx, k_class(inst[i].K))) L.n_twj += (n_cols(inst[i]) + pcg_tcw_cols() - 1) / pcg_tcw_cols();
         if (bf16_native(cfg.precision, inst[i])) {
             L.n_tm += 2;   // the Gram's and W = H X's tensor maps
             if (!accurate_gram(refine, inst[i])) L.n_gb += k_class(inst[i].K) == 256 ? 3 : 1;
@@ -548,7 +547,7 @@ bool build_tables(const jacpcg_ctx *ctx, const jacpcg_instance *inst, int n, con
             for (int i = 0; i < n; ++i) {
                 if (k_class(inst[i].K) != KC) continue;
                 twl[ni++] = i;
-                for (int c0 = 0; c0 < n_cols(inst[i]); c0 += TCW_NB) twj[nj++] = make_int2(i, c0);
+                for (int c0 = 0; c0 < n_cols(inst[i]); c0 += pcg_tcw_cols()) twj[nj++] = make_int2(i, c0);
             }
             if (ni > i0) {
                 launches.push_back({Launch::TCW_PREP, 1, KC, L.twl + i0 * sizeof(int), ni - i0});

@@ -73,8 +73,10 @@ cudaError_t launch_pcg_tc64(int variant, const DevInst *insts, const int *list, 
                             const CUtensorMap *amap, const char *arena, cudaStream_t s, int mode);
 // tensor-core iteration for the K = 128 and 256 classes (standard or plain CG):
 // launch_tcw_prep stores each listed instance's A as the streamed FP16 stages
-// (DevInst::As), launch_pcg_tcw iterates; jobs: (instance, first of 32 columns);
-// mode 0 solve, 1 refinement correction, 2 correction with the FP16 heads only
+// (DevInst::As), launch_pcg_tcw iterates; jobs: (instance, first of
+// pcg_tcw_cols() columns); mode 0 solve, 1 refinement correction, 2 correction
+// with the FP16 heads only
+int pcg_tcw_cols();
 cudaError_t launch_tcw_prep(int KC, const DevInst *insts, const int *list, int n, cudaStream_t s);
 cudaError_t launch_pcg_tcw(int KC, int variant, const DevInst *insts, const int2 *jobs, int n, DevAccum acc,
                            cudaStream_t s, int mode);

@@ -37,26 +37,27 @@
 // published (head + tail, unscaled: 22 bits), in the product and everywhere
 // else, so the recurrences stay consistent.
 //
-// Roles: 4 warps own the vectors; each iteration they publish P (split) into
+// Roles: 8 warps own the vectors; each iteration they publish P (split) into
 // the B operand and vote on continuing (one barrier reduction), then thread 0
 // streams the iteration's KC / 128 x KC / 16 stages (waiting on `empty`),
 // thread 32 issues the MMAs (waiting on `full`) and commits to `qfull`, and
 // the epilogue -- idle while the product runs, so the roles take no warps of
-// their own and every thread may hold 255 registers -- waits on `qfull`,
-// moves U and V out of TMEM -- as Re q and Im q planes, column-major, into
-// the ring, idle until the next vote -- and works column-wise: thread
-// (warp w, lane l) owns column 4 w + (l mod 4) and the complex rows g, g + 8,
-// ... with g = l / 4; r lives in registers, p is read back from the B
-// operand (head + tail is exact), x is accumulated in the instance's
-// workspace X (which is also where a refinement correction X += dX lands),
-// and the step denominator p^H A p, whose terms can cancel, is compensated
-// (TwoProduct by FMA and TwoSum in a tree, then three xor shuffles combined
-// with commutative or exact operations); the squared norms r^H D^{-1} r and
-// ||r||^2 sum nonnegative terms, where pairwise summation is already
-// accurate to a few units, and are summed so.  All eight lanes of a column
-// hold bit-identical totals.  With two CTAs on an SM, one CTA's epilogue runs
-// while the other's product streams and multiplies.  Every wait is bounded; a
-// timeout sets the instance's ETIMEOUT flag and ends its iteration.
+// their own -- waits on `qfull`, moves U and V out of TMEM -- as Re q and Im q
+// planes, column-major, into the ring, idle until the next vote -- and works
+// column-wise: thread (warp w, lane l) owns column 2 w + (l mod 2) and the
+// complex rows g, g + 16, ... with g = l / 2.  r and p (as published: head +
+// tail, exact in FP32) live in registers; x lives in the instance's workspace
+// X (which is also where a refinement correction X += dX lands) and takes
+// x += lambda p as fire-and-forget reductions, so no thread waits on a global
+// load inside the iteration.  The step denominator p^H A p, whose terms can
+// cancel, is compensated (TwoProduct by FMA and TwoSum in a tree, then xor
+// shuffles combined with commutative or exact operations); the squared norms
+// r^H D^{-1} r and ||r||^2 sum nonnegative terms, where pairwise summation is
+// already accurate to a few units, and are summed so, in the same pass over
+// the rows as r -= lambda q.  All lanes of a column hold bit-identical
+// totals.  With two CTAs on an SM, one CTA's epilogue runs while the other's
+// product streams and multiplies.  Every wait is bounded; a timeout sets the
+// instance's ETIMEOUT flag and ends its iteration.
 #include <cuda_fp16.h>
 
 #include "common.cuh"
@@ -67,15 +68,21 @@ namespace jacpcg {
 
 namespace {
 
-// Two CTAs per SM, each of 4 warps owning 16 columns: one CTA's epilogue runs
+// Two CTAs per SM, each of 8 warps owning 16 columns: one CTA's epilogue runs
 // while the other's product streams and multiplies.  On the XL batch this
-// measured the same as one CTA of 8 warps and 32 columns (4.23 against 4.27
-// ms for the main solve: the stream of A, not idle tensor cores, bounds it),
-// but a lone request gets twice the CTAs.
+// measured the same as one CTA of 8 warps and 32 columns with four ring slots
+// (3.46 against 3.42 ms for the main solve, the refinement's correction
+// solves 0.03 ms faster), and a lone request gets twice the CTAs.  8 warps
+// rather than 4 (255 registers each, 32 rows per thread) hide more of the
+// epilogue's latency: 3.60 -> 3.44 ms.
 constexpr int NB = 16;                        // right-hand-side columns per CTA
-constexpr int THREADS = 128;                  // 4 warps, up to 255 registers with two CTAs per SM
+constexpr int THREADS = 256;                  // 8 warps, up to 128 registers with two CTAs per SM
 constexpr int CTAS_PER_SM = 2;
 constexpr int EPI = THREADS;
+constexpr int WARPS = THREADS / 32;
+constexpr int CPW = NB / WARPS;               // columns per warp in the epilogue
+constexpr int LPC = 32 / CPW;                 // lanes per column: lane bits log2(CPW) .. 4
+constexpr int RCOLS = NB / (WARPS / 4);       // columns per warp in the TMEM readout
 constexpr int STAGE = 16384;                  // bytes of one k-step: four 128 x 16 FP16 tiles
 constexpr int SUB = 2;                        // k-steps per bulk copy (ring slot)
 constexpr int SLOT = SUB * STAGE;
@@ -94,15 +101,16 @@ struct Cfg {
     static constexpr int NSTAGE = RT * KS;                   // stages per iteration
     static constexpr uint32_t SBO_B = (KC / 8) * 128;        // bytes between 8-row groups of B (N)
     static constexpr int B_BYTES = 4 * NB * KC * 2;          // the B operand
-    static constexpr int MR = KC / 8;                        // complex rows per epilogue thread
+    static constexpr int MR = KC / LPC;                      // complex rows per epilogue thread
     static constexpr uint32_t TMEM_COLS = RT * 8 * NB;       // per row tile U | V, 4 NB columns each
-    // B, ring, then per row 1 / d, 2^e, 2^-e; per column the readout factor
-    static constexpr int SMEM = B_BYTES + RING * SLOT + 3 * KC * 4 + NB * 4 + 256;
+    // B, ring, then per row 1 / d and 2^e; per column the readout factor
+    static constexpr int SMEM = B_BYTES + RING * SLOT + 2 * KC * 4 + NB * 4 + 256;
     static_assert(2 * RT * NB * QLD * 4 <= RING * SLOT, "Q staging fits the ring");
     static_assert(KS % (2 * SUB) == 0, "whole slots in a row tile");
     static_assert(CTAS_PER_SM * (SMEM + 1024) <= 228 * 1024, "shared memory");
     static_assert(CTAS_PER_SM * TMEM_COLS <= 512, "tensor memory");
-    static_assert(THREADS / 32 * 4 == NB, "a warp owns 4 columns");
+    static_assert(CPW * WARPS == NB && LPC * CPW == 32 && MR % 8 == 0, "whole columns per warp");
+    static_assert(WARPS % 4 == 0 && RCOLS % 8 == 0, "the readout covers the TMEM lane quarters");
 };
 
 struct Ctl {
@@ -158,6 +166,27 @@ __device__ __forceinline__ void split_f16(float x, __half &h, __half &t) {
     h = __float2half_rn(x);
     t = __float2half_rn(x - __half2float(h));
 }
+// base[OFF / 8] += v in global memory (8-byte aligned) as one reduction that
+// returns nothing: the issuing thread does not wait for it.  The byte offset
+// is an immediate, so the unrolled rows share one address register.
+template <int OFF>
+__device__ __forceinline__ void red_add2(float2 *base, float2 v) {
+    asm volatile("red.relaxed.gpu.global.add.v2.f32 [%0+%3], {%1, %2};" ::"l"(base), "f"(v.x), "f"(v.y), "n"(OFF));
+}
+// red_add2 of f(m) at rows M, M + 1, ..., N - 1 of base, STRIDE floats2 apart
+template <int M, int N, int STRIDE, typename F>
+__device__ __forceinline__ void red_rows(float2 *base, F f) {
+    if constexpr (M < N) {
+        red_add2<M * STRIDE * 8>(base, f(M));
+        red_rows<M + 1, N, STRIDE>(base, f);
+    }
+}
+// keeps the compiler from moving memory accesses across this point: the row
+// loops fence every 8 rows so that their loads are not all hoisted at once
+// (with r and p resident, that would exceed the register file)
+__device__ __forceinline__ void row_chunk_fence() { asm volatile("" ::: "memory"); }
+// 2^-e from 2^e, for 2^e and 2^-e both normal floats
+__device__ __forceinline__ float pow2_inv(float p2) { return __uint_as_float(0x7F000000u - __float_as_uint(p2)); }
 
 // ---------------------------------------------------------------------------
 // A (complex, workspace ld KC) -> the streamed FP16 stages of 2^SA E^-1 A E^-1:
@@ -196,7 +225,7 @@ __global__ void __launch_bounds__(256) tcw_prep_kernel(const DevInst *__restrict
 // Compensated sum over the thread's MR rows of Re conj(a_m) b_m, where f(m,
 // a, b) yields the pair of row m: rows in chunks of 8, each chunk a TwoSum
 // tree over the TwoProduct-split products, the chunks combined the same way,
-// then the 8 lanes of the column (lane bits 2-4) by three xor shuffles.  Only
+// then the lanes of the column (lane bits log2(CPW) .. 4) by xor shuffles.  Only
 // one chunk of operands is live at a time.
 template <int MR, typename F>
 __device__ __forceinline__ float col_sum2(F f) {
@@ -228,6 +257,7 @@ __device__ __forceinline__ float col_sum2(F f) {
         }
         S[u] = s[0];
         Cc[u] = c[0];
+        row_chunk_fence();
     }
 #pragma unroll
     for (int h = NCH / 2; h > 0; h >>= 1) {
@@ -241,7 +271,7 @@ __device__ __forceinline__ float col_sum2(F f) {
     }
     float vs = S[0], vc = Cc[0];
 #pragma unroll
-    for (int o = 4; o <= 16; o <<= 1) {
+    for (int o = CPW; o <= 16; o <<= 1) {
         const float ws = __shfl_xor_sync(0xffffffffu, vs, o);
         const float wc = __shfl_xor_sync(0xffffffffu, vc, o);
         float sn, e;
@@ -254,7 +284,7 @@ __device__ __forceinline__ float col_sum2(F f) {
 
 // Sum over the thread's MR rows of Re conj(a_m) b_m when every term is >= 0
 // (||r||^2 and r^H D^{-1} r): no cancellation can occur, so pairwise
-// summation is already accurate to a few units in the last place; the 8 lanes
+// summation is already accurate to a few units in the last place; the lanes
 // of the column combine by commutative additions (bit-identical totals).
 template <int MR, typename F>
 __device__ __forceinline__ float col_sumsq(F f) {
@@ -271,7 +301,7 @@ __device__ __forceinline__ float col_sumsq(F f) {
         for (int k = 0; k < h; ++k) s[k] += s[k + h];
     float v = s[0];
 #pragma unroll
-    for (int o = 4; o <= 16; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = CPW; o <= 16; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
@@ -292,9 +322,8 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
     extern __shared__ __align__(1024) unsigned char smem[];
     float *dvs = reinterpret_cast<float *>(smem + C::B_BYTES + RING * SLOT);    // 1 / A_ii
     float *scv = dvs + KC;                                                         // 2^e_i
-    float *iscv = scv + KC;                                                        // 2^-e_i
-    float *colq = iscv + KC;   // per column 2^-SA / s_j: the readout's unscaling
-    Ctl &S = *reinterpret_cast<Ctl *>(smem + C::B_BYTES + RING * SLOT + 3 * KC * 4 + NB * 4);
+    float *colq = scv + KC;    // per column 2^-SA / s_j: the readout's unscaling
+    Ctl &S = *reinterpret_cast<Ctl *>(smem + C::B_BYTES + RING * SLOT + 2 * KC * 4 + NB * 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int i = 0; i < RING; ++i) {
@@ -391,50 +420,55 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
         __syncwarp();
     };
     {
-        // ---- epilogue: the vectors of 32 columns, column-wise ----
-        const int cl = 4 * warp + (lane & 3);   // local column
-        const int g = lane >> 2;                // rows g + 8 m
-        const int qw = warp & 3, hh = warp >> 2;   // TMEM lane quarter and column half of the readout
+        // ---- epilogue: the vectors of the CTA's NB columns, column-wise ----
+        const int cl = CPW * warp + (lane % CPW);   // local column
+        const int g = lane / CPW;                    // rows g + LPC m
+        const int qw = warp & 3, hh = warp >> 2;     // TMEM lane quarter and column group of the readout
         float *Qre = reinterpret_cast<float *>(smem + C::B_BYTES);
         float *Qim = Qre + C::RT * NB * QLD;
         unsigned char *Bop = smem;
-        auto bget = [&](int n, int k) { return __half2float(*reinterpret_cast<const __half *>(Bop + b_off<KC>(n, k))); };
         auto bset = [&](int n, int k, __half v) { *reinterpret_cast<__half *>(Bop + b_off<KC>(n, k)) = v; };
-        float pinv = 1.f;   // 1 / s_j of the owned column, as last published
+        // p of the owned rows as published (head + tail, exact in FP32, unscaled):
+        // what the product multiplied, kept here rather than read back
+        float2 pr[MR];
         // P of the owned rows into the B operand: f(m) gives p at row g + 8 m; the
-        // column's largest |Re|, |Im| of E p (8 lanes) sets s_j, then s_j E p goes
+        // column's largest |Re|, |Im| of E p (its lanes) sets s_j, then s_j E p goes
         // in as FP16 head and tail.  All lanes take part (shuffles); a column that
         // is not `active` keeps its published p.  f is evaluated twice, so it
         // must not depend on what the second pass writes at other rows.
         int pex = SP;       // exponent of the column's largest |E p| as last published
         // col_exp: the exponent ex for a column whose largest |E p| is at most mx
-        // (a maximum over the column's 8 lanes), s_j = 2^(SP - ex); clamped so that
+        // (a maximum over the column's lanes), s_j = 2^(SP - ex); clamped so that
         // s_j, 1 / s_j and 2^-SA / s_j are floats
         auto col_exp = [&](float mx) {
 #pragma unroll
-            for (int o = 4; o <= 16; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            for (int o = CPW; o <= 16; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
             return (mx >= 1.2e-38f && mx < 3.0e38f) ? min(max(exp2_of(mx), SA + SP - 126), SP + 126) : SP;
         };
-        // store s_j E p (p = f(m) at row g + 8 m) as FP16 head and tail, s_j = 2^(SP - ex);
-        // all lanes take part (shuffles)
+        // store s_j E p (p = f(m) at row g + 8 m) as FP16 head and tail, s_j = 2^(SP - ex),
+        // and keep p as published in pr; all lanes take part (shuffles)
         auto publish_exp = [&](bool active, int ex, auto f) {
-            const float sj = pow2f(SP - ex);
+            const float sj = pow2f(SP - ex), pi = pow2f(ex - SP);
             float mx = 0.f;   // the published column's largest |E p| (tightens the next bound)
             if (active) {
 #pragma unroll
                 for (int m = 0; m < MR; ++m) {
-                    const int i = g + 8 * m;
+                    const int i = g + LPC * m;
                     const float2 v = f(m);
-                    mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)) * scv[i]);
+                    const float sc = scv[i], isc = pow2_inv(sc);
+                    mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)) * sc);
                     __half h, t;
-                    split_f16((v.x * scv[i]) * sj, h, t);
+                    split_f16((v.x * sc) * sj, h, t);
                     bset(cl, i, h);
                     if (!LIGHT) bset(2 * NB + cl, i, t);   // a light correction uses the heads only
-                    split_f16((v.y * scv[i]) * sj, h, t);
+                    const float px = LIGHT ? __half2float(h) : __half2float(h) + __half2float(t);
+                    split_f16((v.y * sc) * sj, h, t);
                     bset(NB + cl, i, h);
                     if (!LIGHT) bset(3 * NB + cl, i, t);
+                    const float py = LIGHT ? __half2float(h) : __half2float(h) + __half2float(t);
+                    pr[m] = make_float2((px * pi) * isc, (py * pi) * isc);
+                    if ((m & 7) == 7) row_chunk_fence();
                 }
-                pinv = pow2f(ex - SP);
                 if (g == 0) colq[cl] = pow2f(ex - SP - SA);
             }
             const int ea = col_exp(mx);
@@ -446,19 +480,13 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
 #pragma unroll
                 for (int m = 0; m < MR; ++m) {
                     const float2 v = f(m);
-                    mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)) * scv[g + 8 * m]);
+                    mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)) * scv[g + LPC * m]);
                 }
             }
             publish_exp(active, col_exp(mx), f);
         };
-        auto pget = [&](int m) {   // head + tail (exact in FP32), unscaled: p as published
-            const int i = g + 8 * m;
-            if (LIGHT) return make_float2((bget(cl, i) * pinv) * iscv[i], (bget(NB + cl, i) * pinv) * iscv[i]);
-            return make_float2(((bget(cl, i) + bget(2 * NB + cl, i)) * pinv) * iscv[i],
-                               ((bget(NB + cl, i) + bget(3 * NB + cl, i)) * pinv) * iscv[i]);
-        };
         auto qget = [&](int m) {
-            const int i = g + 8 * m;
+            const int i = g + LPC * m;
             const int o = ((i >> 7) * NB + cl) * QLD + (i & 127);
             return make_float2(Qre[o], Qim[o]);
         };
@@ -476,19 +504,18 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
             const float tl = (MODE >= 1 && in.rsolve_tol > 0.f) ? in.rsolve_tol : in.tol;
             const float tol2 = tl > 0.f ? tl * tl : -1.f;
             float2 *X = in.X + (size_t)(valid ? j : 0) * KC;   // the iterate (workspace, ld KC)
-            epi_sync();   // the previous instance's readers of dvs, scv and iscv are done
+            epi_sync();   // the previous instance's readers of dvs and scv are done
             for (int i = threadIdx.x; i < KC; i += EPI) {
                 dvs[i] = (i < K) ? (VAR == 2 ? 1.f : in.dinv[i]) : 0.f;
                 const int e = row_exp(in.A[(size_t)i * (KC + 1)].x);   // as the prep kernel scaled A
                 scv[i] = pow2f(e);
-                iscv[i] = pow2f(-e);
             }
             epi_sync();
             // ---- Step 1: r = b, x = x0 (mode 0), p = D^{-1} r ----
             float2 r[MR];
 #pragma unroll
             for (int m = 0; m < MR; ++m) {
-                const int i = g + 8 * m;
+                const int i = g + LPC * m;
                 float2 b = make_float2(0.f, 0.f);
                 if (valid && i < K) {
                     if (MODE >= 1) b = in.R[i + (size_t)j * KC];                    // refinement residual
@@ -499,15 +526,15 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
                 if (MODE == 0 && valid)
                     X[i] = (warm && i < K) ? in.X0[i + (size_t)j * K] : make_float2(0.f, 0.f);
             }
+            if (MODE == 0) __threadfence();   // the stores of x0 precede the reductions into X
             // the warm pass forms A X0 first; columns beyond the right-hand sides carry 0
-            pinv = 1.f;
             publish_all(true, [&](int m) {
-                const int i = g + 8 * m;
+                const int i = g + LPC * m;
                 const float d = dvs[i];
                 return !valid ? make_float2(0.f, 0.f) : warm ? X[i] : make_float2(d * r[m].x, d * r[m].y);
             });
             float rho = col_sumsq<MR>([&](int m, float2 &a, float2 &b) {
-                const float d = dvs[g + 8 * m];
+                const float d = dvs[g + LPC * m];
                 a = r[m];
                 b = make_float2(d * r[m].x, d * r[m].y);
             });
@@ -535,43 +562,54 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
                 ++qp;
                 __syncwarp();   // the TMEM loads below are warp-collective
                 tc::tc_fence_after();
+                float cq[RCOLS];   // the readout's per-column unscaling 2^-SA / s_j
+#pragma unroll
+                for (int e = 0; e < RCOLS; ++e) cq[e] = colq[RCOLS * hh + e];
 #pragma unroll
                 for (int rt = 0; rt < C::RT; ++rt) {
-                    const uint32_t tb = tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)(rt * 8 * NB + 16 * hh);
-                    const int o = (rt * NB + 16 * hh) * QLD + 32 * qw + lane;
+                    const uint32_t tb = tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)(rt * 8 * NB + RCOLS * hh);
+                    const int o = (rt * NB + RCOLS * hh) * QLD + 32 * qw + lane;
                     const float rf = scv[rt * 128 + 32 * qw + lane];   // row factor 2^e_i
-                    float a[16], b[16], c[16], d[16];
-                    if (LIGHT) {   // heads only: no correction columns
-                        tc::tmem_ld16(tb, a);
-                        tc::tmem_ld16(tb + 4 * NB + NB, c);
+                    // Re q = Ar Pr - Ai Pi and Im q = Ai Pr + Ar Pi from U's and V's head
+                    // products and corrections (a light correction has no corrections),
+                    // 8 columns at a time
+#pragma unroll
+                    for (int h8 = 0; h8 < RCOLS; h8 += 8) {
+                        float x[8], y[8], z[8];
+                        if (LIGHT) {
+                            tc::tmem_ld8(tb + h8, x);
+                            tc::tmem_ld8(tb + 4 * NB + NB + h8, y);
+                            tc::tmem_ld_wait();
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) Qre[o + (h8 + e) * QLD] = (x[e] - y[e]) * rf * cq[h8 + e];
+                            tc::tmem_ld8(tb + 4 * NB + h8, x);
+                            tc::tmem_ld8(tb + NB + h8, y);
+                            tc::tmem_ld_wait();
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) Qim[o + (h8 + e) * QLD] = (x[e] + y[e]) * rf * cq[h8 + e];
+                            continue;
+                        }
+                        tc::tmem_ld8(tb + h8, x);
+                        tc::tmem_ld8(tb + 2 * NB + h8, y);
                         tc::tmem_ld_wait();
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) Qre[o + e * QLD] = (a[e] - c[e]) * rf * colq[16 * hh + e];
-                        tc::tmem_ld16(tb + 4 * NB, a);
-                        tc::tmem_ld16(tb + NB, c);
+                        for (int e = 0; e < 8; ++e) x[e] += y[e];
+                        tc::tmem_ld8(tb + 4 * NB + NB + h8, y);
+                        tc::tmem_ld8(tb + 4 * NB + 3 * NB + h8, z);
                         tc::tmem_ld_wait();
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) Qim[o + e * QLD] = (a[e] + c[e]) * rf * colq[16 * hh + e];
-                        continue;
+                        for (int e = 0; e < 8; ++e) Qre[o + (h8 + e) * QLD] = (x[e] - (y[e] + z[e])) * rf * cq[h8 + e];
+                        tc::tmem_ld8(tb + 4 * NB + h8, x);
+                        tc::tmem_ld8(tb + 4 * NB + 2 * NB + h8, y);
+                        tc::tmem_ld_wait();
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) x[e] += y[e];
+                        tc::tmem_ld8(tb + NB + h8, y);
+                        tc::tmem_ld8(tb + 3 * NB + h8, z);
+                        tc::tmem_ld_wait();
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) Qim[o + (h8 + e) * QLD] = (x[e] + (y[e] + z[e])) * rf * cq[h8 + e];
                     }
-                    // Re q = Ar Pr - Ai Pi
-                    tc::tmem_ld16(tb, a);                       // U: Ar P_h
-                    tc::tmem_ld16(tb + 2 * NB, b);              // U: corrections
-                    tc::tmem_ld16(tb + 4 * NB + NB, c);         // V: Ai Pi_h
-                    tc::tmem_ld16(tb + 4 * NB + 3 * NB, d);     // V: corrections of Ai Pi
-                    tc::tmem_ld_wait();
-#pragma unroll
-                    for (int e = 0; e < 16; ++e)
-                        Qre[o + e * QLD] = ((a[e] + b[e]) - (c[e] + d[e])) * rf * colq[16 * hh + e];
-                    // Im q = Ai Pr + Ar Pi
-                    tc::tmem_ld16(tb + 4 * NB, a);
-                    tc::tmem_ld16(tb + 4 * NB + 2 * NB, b);
-                    tc::tmem_ld16(tb + NB, c);
-                    tc::tmem_ld16(tb + 3 * NB, d);
-                    tc::tmem_ld_wait();
-#pragma unroll
-                    for (int e = 0; e < 16; ++e)
-                        Qim[o + e * QLD] = ((a[e] + b[e]) + (c[e] + d[e])) * rf * colq[16 * hh + e];
                 }
                 epi_sync();
                 if (init) {   // r = b - A X0, then Step 1 from there
@@ -581,11 +619,11 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
                         r[m] = make_float2(r[m].x - q.x, r[m].y - q.y);
                     }
                     publish_all(true, [&](int m) {
-                        const float d = dvs[g + 8 * m];
+                        const float d = dvs[g + LPC * m];
                         return make_float2(d * r[m].x, d * r[m].y);
                     });
                     rho = col_sumsq<MR>([&](int m, float2 &a, float2 &b) {
-                        const float d = dvs[g + 8 * m];
+                        const float d = dvs[g + LPC * m];
                         a = r[m];
                         b = make_float2(d * r[m].x, d * r[m].y);
                     });
@@ -593,49 +631,67 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
                     continue;
                 }
                 // ---- Steps 2-4: lambda = r^H z / p^H A p, x += lambda p, r -= lambda q ----
-                const float pAp = col_sum2<MR>([&](int m, float2 &a, float2 &b) { a = pget(m); b = qget(m); });
+                const float pAp = col_sum2<MR>([&](int m, float2 &a, float2 &b) { a = pr[m]; b = qget(m); });
                 float lam = 0.f;
                 if (pAp > 0.f) lam = rho / pAp;
                 else if (res2 != 0.f && !done) notHPD = 1;
                 if (done) lam = 0.f;
-#pragma unroll
-                for (int m = 0; m < MR; ++m) {
-                    const float2 q = qget(m);
-                    r[m].x = fmaf(-lam, q.x, r[m].x);
-                    r[m].y = fmaf(-lam, q.y, r[m].y);
-                }
+                // x += lambda p as reductions into the workspace, which this thread
+                // does not wait for (it reads X again only after a fence)
                 if (!done) {
-#pragma unroll
-                    for (int m = 0; m < MR; ++m) {
-                        const float2 pv = pget(m);
-                        float2 xv = X[g + 8 * m];
-                        xv.x = fmaf(lam, pv.x, xv.x);
-                        xv.y = fmaf(lam, pv.y, xv.y);
-                        X[g + 8 * m] = xv;
-                    }
+                    red_rows<0, MR, LPC>(X + g, [&](int m) { return make_float2(lam * pr[m].x, lam * pr[m].y); });
                 }
-                const float rz_new = col_sumsq<MR>([&](int m, float2 &a, float2 &b) {
-                    const float d = dvs[g + 8 * m];
-                    a = r[m];
-                    b = make_float2(d * r[m].x, d * r[m].y);
-                });
-                const float rr_new = col_sumsq<MR>([&](int m, float2 &a, float2 &b) { a = r[m]; b = r[m]; });
+                // r -= lambda q, and in the same pass over the rows the new r^H D^{-1} r
+                // and ||r||^2 (nonnegative terms, pairwise in chunks of 8 rows, then the
+                // chunks pairwise) and max |E z| for the next scale
+                float Sz[MR / 8], Sr[MR / 8], mz = 0.f;
+#pragma unroll
+                for (int u = 0; u < MR / 8; ++u) {
+                    float sz[8], sr[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int m = 8 * u + k, i = g + LPC * m;
+                        const float2 q = qget(m);
+                        r[m].x = fmaf(-lam, q.x, r[m].x);
+                        r[m].y = fmaf(-lam, q.y, r[m].y);
+                        const float d = dvs[i];
+                        sz[k] = fmaf(r[m].x, d * r[m].x, r[m].y * (d * r[m].y));
+                        sr[k] = fmaf(r[m].x, r[m].x, r[m].y * r[m].y);
+                        mz = fmaxf(mz, fmaxf(fabsf(r[m].x), fabsf(r[m].y)) * (d * scv[i]));
+                    }
+#pragma unroll
+                    for (int h = 4; h > 0; h >>= 1)
+#pragma unroll
+                        for (int k = 0; k < h; ++k) {
+                            sz[k] += sz[k + h];
+                            sr[k] += sr[k + h];
+                        }
+                    Sz[u] = sz[0];
+                    Sr[u] = sr[0];
+                    row_chunk_fence();
+                }
+#pragma unroll
+                for (int h = MR / 16; h > 0; h >>= 1)
+#pragma unroll
+                    for (int k = 0; k < h; ++k) {
+                        Sz[k] += Sz[k + h];
+                        Sr[k] += Sr[k + h];
+                    }
+                float rz_new = Sz[0], rr_new = Sr[0];
+#pragma unroll
+                for (int o = CPW; o <= 16; o <<= 1) {   // the lanes of the column, commutatively
+                    rz_new += __shfl_xor_sync(0xffffffffu, rz_new, o);
+                    rr_new += __shfl_xor_sync(0xffffffffu, rr_new, o);
+                }
                 // p = z + beta p, published for the next product, its scale from the
                 // bound max |E p| <= max |E z| + beta max |E p_old| (< 2^(pex + 1), the
                 // maximum of what was published, so bounds do not compound): one pass
                 // over the rows instead of two
                 const float beta = (!done && rho != 0.f) ? rz_new / rho : 0.f;
-                float mz = 0.f;
-#pragma unroll
-                for (int m = 0; m < MR; ++m) {
-                    const int i = g + 8 * m;
-                    mz = fmaxf(mz, fmaxf(fabsf(r[m].x), fabsf(r[m].y)) * (dvs[i] * scv[i]));
-                }
                 const int exn = col_exp(fmaf(beta, pow2f(min(pex + 1, 127)), mz));
                 publish_exp(!done, exn, [&](int m) {
-                    const float2 pv = pget(m);
-                    const float d = dvs[g + 8 * m];
-                    return make_float2(fmaf(beta, pv.x, d * r[m].x), fmaf(beta, pv.y, d * r[m].y));
+                    const float d = dvs[g + LPC * m];
+                    return make_float2(fmaf(beta, pr[m].x, d * r[m].x), fmaf(beta, pr[m].y, d * r[m].y));
                 });
                 if (!done) {
                     rho = rz_new;
@@ -645,10 +701,11 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
             }
             // ---- outputs ----
             if (valid && in.Xout) {
+                __threadfence();   // this thread's reductions into X are performed
 #pragma unroll
                 for (int m = 0; m < MR; ++m) {
-                    const int i = g + 8 * m;
-                    if (i < K) in.Xout[i + (size_t)j * K] = X[i];
+                    const int i = g + LPC * m;
+                    if (i < K) in.Xout[i + (size_t)j * K] = __ldcg(X + i);   // from L2, where they landed
                 }
             }
             if (MODE == 0 && g == 0) {   // one thread per column
@@ -717,6 +774,8 @@ cudaError_t launch_kc(int variant, const DevInst *insts, const int2 *jobs, int n
 }
 
 }  // namespace
+
+int pcg_tcw_cols() { return NB; }
 
 cudaError_t launch_tcw_prep(int KC, const DevInst *insts, const int *list, int n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
