@@ -6,22 +6,24 @@
 //
 // At these sizes A does not fit on one SM (K = 256: 512 KB complex), so it
 // is streamed.  Once per instance a prep kernel stores it as MMA-ready FP16
-// stages, for row tile rt (128 rows) and k-step ks (16 columns): [Ar_h |
-// Ar_t | Ai_h | Ai_t], each a 128 x 16 tile in the canonical no-swizzle
-// K-major layout, of the scaled matrix
+// tiles, for row tile rt (128 rows) and k-step ks (16 columns): Ar_h, Ai_h,
+// Ar_t, Ai_t, each a 128 x 16 tile in the canonical no-swizzle K-major
+// layout, in groups of SUB k-steps [heads of the group | tails of the group],
+// of the scaled matrix
 //   Ah = 2^13 E^-1 A E^-1,   E = diag(2^e_i),  2^e_i <= sqrt(A_ii) < 2^(e_i + 1),
 // split into an FP16 head and the FP16 rounding of the rest.  Every scaling is
 // a power of two (exact), and |A_ij| <= sqrt(A_ii A_jj) bounds |Ah_ij| below
 // 2^15, inside FP16's range; head + tail carries 22 bits of every entry, as
 // the TF32 head and tail of the 3xTF32 split do, in half the bytes, and the
 // kind::f16 MMAs run at twice the kind::tf32 rate.  Each iteration streams the
-// stages through a shared-memory ring with bulk copies (the TMA unit,
-// cp.async.bulk), completion counted in bytes on an mbarrier.  Real and
+// groups through a shared-memory ring with bulk copies (the TMA unit,
+// cp.async.bulk), one 64 KB copy per group (a light correction: the heads of
+// two groups), completion counted in bytes on an mbarrier.  Real and
 // imaginary parts are kept apart (planar), so each byte of A is streamed once
 // per iteration rather than twice as in the 2 x 2 real expansion.
 //
-// The columns of X are independent systems sharing A, so a CTA owns 16 of
-// them (NB) for one instance, and two CTAs share an SM.  Their P is resident in shared memory as the
+// The columns of X are independent systems sharing A, so a CTA owns 32 of
+// them (NB) for one instance, one CTA per SM.  Their P is resident in shared memory as the
 // MMA's B operand, laid out as 4 NB rows [Pr_h | Pi_h | Pr_t | Pi_t] along N:
 // FP16 head and tail of s_j E p_j, s_j a power of two per column that puts
 // the column's largest entry in [2^14, 2^15).  Per k-step:
@@ -31,13 +33,13 @@
 // 0 .. 2 NB - 1 head x head, the rest both corrections), and
 //   Re q = Ar Pr - Ai Pi,   Im q = Ai Pr + Ar Pi,
 // each unscaled by 2^(e_i - 13) / s_j on its way out of TMEM.  U and V of both
-// row tiles take 2 x 2 x 4 NB TMEM columns (K = 256: 256, half of the SM's
-// 512, so two CTAs fit).  The accumulation
+// row tiles take 2 x 2 x 4 NB TMEM columns (K = 256: all 512 of the SM's).
+// The accumulation
 // chain of a row tile is its KC / 16 k-steps.  The iteration uses p as
 // published (head + tail, unscaled: 22 bits), in the product and everywhere
 // else, so the recurrences stay consistent.
 //
-// Roles: 8 warps own the vectors; each iteration they publish P (split) into
+// Roles: 16 warps own the vectors; each iteration they publish P (split) into
 // the B operand and vote on continuing (one barrier reduction), then thread 0
 // streams the iteration's KC / 128 x KC / 16 stages (waiting on `empty`),
 // thread 32 issues the MMAs (waiting on `full`) and commits to `qfull`, and
@@ -45,7 +47,7 @@
 // their own -- waits on `qfull`, moves U and V out of TMEM -- as Re q and Im q
 // planes, column-major, into the ring, idle until the next vote -- and works
 // column-wise: thread (warp w, lane l) owns column 2 w + (l mod 2) and the
-// complex rows g, g + 16, ... with g = l / 2.  r and p (as published: head +
+// complex rows g, g + 16, ... with g = l / 2 (16 rows at K = 256).  r and p (as published: head +
 // tail, exact in FP32) live in registers; x lives in the instance's workspace
 // X (which is also where a refinement correction X += dX lands) and takes
 // x += lambda p as fire-and-forget reductions, so no thread waits on a global
@@ -55,9 +57,8 @@
 // r^H D^{-1} r and ||r||^2 sum nonnegative terms, where pairwise summation is
 // already accurate to a few units, and are summed so, in the same pass over
 // the rows as r -= lambda q.  All lanes of a column hold bit-identical
-// totals.  With two CTAs on an SM, one CTA's epilogue runs while the other's
-// product streams and multiplies.  Every wait is bounded; a timeout sets the
-// instance's ETIMEOUT flag and ends its iteration.
+// totals.  Every wait is bounded; a timeout sets the instance's ETIMEOUT flag
+// and ends its iteration.
 #include <cuda_fp16.h>
 
 #include "common.cuh"
@@ -68,29 +69,36 @@ namespace jacpcg {
 
 namespace {
 
-// Two CTAs per SM, each of 8 warps owning 16 columns: one CTA's epilogue runs
-// while the other's product streams and multiplies.  On the XL batch this
-// measured the same as one CTA of 8 warps and 32 columns with four ring slots
-// (3.46 against 3.42 ms for the main solve, the refinement's correction
-// solves 0.03 ms faster), and a lone request gets twice the CTAs.  8 warps
-// rather than 4 (255 registers each, 32 rows per thread) hide more of the
-// epilogue's latency: 3.60 -> 3.44 ms.
-constexpr int NB = 16;                        // right-hand-side columns per CTA
-constexpr int THREADS = 256;                  // 8 warps, up to 128 registers with two CTAs per SM
-constexpr int CTAS_PER_SM = 2;
+// One CTA per SM of 16 warps owning 32 columns, two ring slots of one 64 KB
+// group each.  Measured on the XL batch's main solve (K = 256): two CTAs per
+// SM of 8 warps and 16 columns each, 32 KB slots (one CTA's epilogue
+// overlapping the other's product, but twice the bytes of A streamed per
+// column): 3.41 ms; one CTA, 32 columns, 16 warps, four 32 KB slots: 3.29;
+// two 64 KB slots: 3.09 (four 32 KB slots, even with a second copy-issuing
+// thread, 3.28; eight 16 KB slots 3.75: the fewer, larger copies the
+// better).  The three MMAs per k-step of the head / tail split take about 4 us
+// of an iteration's 6 us product at the measured tensor peak.  16 warps (128
+// registers, 16 rows per thread) rather than 8 (255, 32 rows) hide more of the
+// epilogue's latency.
+constexpr int NB = 32;                        // right-hand-side columns per CTA
+constexpr int THREADS = 512;                  // 16 warps, up to 128 registers each
+constexpr int CTAS_PER_SM = 1;
 constexpr int EPI = THREADS;
 constexpr int WARPS = THREADS / 32;
 constexpr int CPW = NB / WARPS;               // columns per warp in the epilogue
 constexpr int LPC = 32 / CPW;                 // lanes per column: lane bits log2(CPW) .. 4
 constexpr int RCOLS = NB / (WARPS / 4);       // columns per warp in the TMEM readout
 constexpr int STAGE = 16384;                  // bytes of one k-step: four 128 x 16 FP16 tiles
-constexpr int SUB = 2;                        // k-steps per bulk copy (ring slot)
+constexpr int SUB = 4;                        // k-steps per group: one bulk copy per ring slot
 constexpr int SLOT = SUB * STAGE;
 constexpr int RING = 2;                       // ring slots in flight per CTA
+constexpr int NPROD = 1;                      // copy-issuing threads (0, 64, ...), each owning RING / NPROD slots
+                                              // (two measured the same with two 64 KB slots)
 constexpr int TILE = 4096;
 constexpr int SA = 13;                        // A is stored scaled by 2^SA (entries below 2^15)
 constexpr int SP = 14;                        // a column of P is scaled to a largest entry in [2^14, 2^15)
-constexpr int QLD = 136;                      // floats per staged Q column (128 rows + 8)
+constexpr int QLD = 144;                      // floats per staged Q column (128 rows + 16: the two
+                                              // columns of a warp's row reads fall on disjoint banks)
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 constexpr int BAR_EPI = 1;                    // named barrier of the epilogue warps
 
@@ -107,6 +115,7 @@ struct Cfg {
     static constexpr int SMEM = B_BYTES + RING * SLOT + 2 * KC * 4 + NB * 4 + 256;
     static_assert(2 * RT * NB * QLD * 4 <= RING * SLOT, "Q staging fits the ring");
     static_assert(KS % (2 * SUB) == 0, "whole slots in a row tile");
+    static_assert(RING % NPROD == 0 && THREADS >= 64 * NPROD, "each slot has one producer");
     static_assert(CTAS_PER_SM * (SMEM + 1024) <= 228 * 1024, "shared memory");
     static_assert(CTAS_PER_SM * TMEM_COLS <= 512, "tensor memory");
     static_assert(CPW * WARPS == NB && LPC * CPW == 32 && MR % 8 == 0, "whole columns per warp");
@@ -200,7 +209,11 @@ __global__ void __launch_bounds__(256) tcw_prep_kernel(const DevInst *__restrict
     const int id = list[blockIdx.x / C::NSTAGE];
     const int s = blockIdx.x % C::NSTAGE, rt = s / C::KS, ks = s % C::KS;
     const DevInst &in = insts[id];
-    char *dst = reinterpret_cast<char *>(in.As) + (size_t)s * STAGE;
+    // groups of SUB k-steps, [heads of the SUB k-steps | their tails], so that a
+    // ring slot is one bulk copy, and a light correction's slot (heads only) two
+    const int u0 = ks % SUB;
+    char *dh = reinterpret_cast<char *>(in.As) + (size_t)(s - u0) * STAGE + (size_t)u0 * (STAGE / 2);
+    char *dt = dh + SUB * (STAGE / 2);
     const float2 *__restrict__ A = in.A;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
@@ -215,10 +228,10 @@ __global__ void __launch_bounds__(256) tcw_prep_kernel(const DevInst *__restrict
         split_f16((v.y * si) * sk, ih, il);
         const uint32_t o = (uint32_t)(r >> 3) * 256u + (uint32_t)(k >> 3) * 128u + (uint32_t)(r & 7) * 16u +
                            (uint32_t)(k & 7) * 2u;
-        *reinterpret_cast<__half *>(dst + o) = rh;              // [Ar_h | Ai_h | Ar_t | Ai_t]:
-        *reinterpret_cast<__half *>(dst + TILE + o) = ih;       // the heads lead, so a light
-        *reinterpret_cast<__half *>(dst + 2 * TILE + o) = rl;   // correction streams half
-        *reinterpret_cast<__half *>(dst + 3 * TILE + o) = il;
+        *reinterpret_cast<__half *>(dh + o) = rh;          // [Ar_h | Ai_h] of the k-step
+        *reinterpret_cast<__half *>(dh + TILE + o) = ih;
+        *reinterpret_cast<__half *>(dt + o) = rl;          // [Ar_t | Ai_t]
+        *reinterpret_cast<__half *>(dt + TILE + o) = il;
     }
 }
 
@@ -344,10 +357,12 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
     const uint32_t tmem = S.tmem;
     const uint32_t b_base = tc::smem_u32(smem), r_base = b_base + C::B_BYTES;
     uint32_t pc = 0, mc = 0;   // stages produced (thread 0) / consumed (thread 32)
-    // One iteration's A x P: thread 0 streams the KC / 128 x KC / 16 stages into the
-    // ring, SUB consecutive stages (k-steps) per bulk copy; thread 32 issues their
-    // MMAs (per stage: head x [P_h | P_t] and tail x P_h, Ar then Ai) and commits
-    // to qfull; the other threads go on to wait.
+    // One iteration's A x P: threads 0, 64, ... (NPROD of them, each owning every
+    // NPROD-th slot) stream the KC / 128 x KC / 16 stages into the ring, one group
+    // of SUB k-steps per bulk copy (a light correction: the heads
+    // of two groups, two copies); thread 32 issues their MMAs (per k-step: head x
+    // [P_h | P_t] and tail x P_h, Ar then Ai) and commits to qfull; the other
+    // threads go on to wait.
     constexpr bool LIGHT = MODE == 2;
     constexpr int KPS = LIGHT ? 2 * SUB : SUB;       // k-steps per ring slot (heads: 8 KB each)
     auto first_kstep = [&](int s) {   // slot s -> (row tile, k-step of its first stage)
@@ -355,18 +370,18 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
         return make_int2(g0 / C::KS, g0 % C::KS);
     };
     auto product = [&](const char *src) {
-        if (threadIdx.x == 0) {
+        if ((threadIdx.x & 63) == 0 && (int)(threadIdx.x >> 6) < NPROD) {
+            const int who = threadIdx.x >> 6;   // this producer's slots: slot mod NPROD == who
             for (int s = 0; s < C::NSTAGE / KPS; ++s, ++pc) {
                 const int slot = pc % RING;
+                if (slot % NPROD != who) continue;
                 const int2 f = first_kstep(s);
                 const char *st = src + (size_t)(f.x * C::KS + f.y) * STAGE;
                 if (!tc::mbar_wait(&S.empty[slot], ((pc / RING) & 1) ^ 1, WAIT_LIMIT)) S.err = 1;
                 tc::mbar_arrive_expect_tx(&S.full[slot], SLOT);
-                if (LIGHT) {   // the leading [Ar_h | Ai_h] half of each k-step
-#pragma unroll
-                    for (int u = 0; u < KPS; ++u)
-                        bulk_load(r_base + slot * SLOT + u * (STAGE / 2), st + (size_t)u * STAGE, STAGE / 2,
-                                  &S.full[slot]);
+                if (LIGHT) {   // the leading heads half of two groups
+                    bulk_load(r_base + slot * SLOT, st, SLOT / 2, &S.full[slot]);
+                    bulk_load(r_base + slot * SLOT + SLOT / 2, st + SLOT, SLOT / 2, &S.full[slot]);
                 } else {
                     bulk_load(r_base + slot * SLOT, st, SLOT, &S.full[slot]);
                 }
@@ -404,14 +419,15 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
 #pragma unroll
                 for (int u = 0; u < SUB; ++u) {
                     const int rt = f.x, ks = f.y + u;
-                    const uint32_t a0 = r_base + slot * SLOT + u * STAGE;
+                    const uint32_t a0 = r_base + slot * SLOT + u * (STAGE / 2);   // [Ar_h | Ai_h]
+                    const uint32_t a1 = a0 + SLOT / 2;                              // [Ar_t | Ai_t]
                     const uint64_t bd = tc::smem_desc(b_base + ks * 256, 128, C::SBO_B);
                     const uint32_t du = tmem + rt * 8 * NB, dvv = du + 4 * NB;
                     const uint32_t acc = ks > 0 ? 1u : 0u;
                     tc::mma_bf16(du, tc::smem_desc(a0, 128, 256), bd, idN4, acc);   // FP16 by the descriptors
-                    tc::mma_bf16(du + 2 * NB, tc::smem_desc(a0 + 2 * TILE, 128, 256), bd, idN2, 1u);
+                    tc::mma_bf16(du + 2 * NB, tc::smem_desc(a1, 128, 256), bd, idN2, 1u);
                     tc::mma_bf16(dvv, tc::smem_desc(a0 + TILE, 128, 256), bd, idN4, acc);
-                    tc::mma_bf16(dvv + 2 * NB, tc::smem_desc(a0 + 3 * TILE, 128, 256), bd, idN2, 1u);
+                    tc::mma_bf16(dvv + 2 * NB, tc::smem_desc(a1 + TILE, 128, 256), bd, idN2, 1u);
                 }
                 tc::mma_commit(&S.empty[slot]);   // the slot is free once these have read it
             }
@@ -436,43 +452,49 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
         // in as FP16 head and tail.  All lanes take part (shuffles); a column that
         // is not `active` keeps its published p.  f is evaluated twice, so it
         // must not depend on what the second pass writes at other rows.
-        int pex = SP;       // exponent of the column's largest |E p| as last published
-        // col_exp: the exponent ex for a column whose largest |E p| is at most mx
-        // (a maximum over the column's lanes), s_j = 2^(SP - ex); clamped so that
-        // s_j, 1 / s_j and 2^-SA / s_j are floats
-        auto col_exp = [&](float mx) {
-#pragma unroll
-            for (int o = CPW; o <= 16; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        // the largest |E p| over the owned rows as last published; the column's
+        // maximum (over its lanes) bounds the next publication's scale
+        float pmx = 0.f;
+        // the exponent ex for a column whose largest |E p| is at most mx, s_j =
+        // 2^(SP - ex); clamped so that s_j, 1 / s_j and 2^-SA / s_j are floats
+        auto exp_of = [&](float mx) {
             return (mx >= 1.2e-38f && mx < 3.0e38f) ? min(max(exp2_of(mx), SA + SP - 126), SP + 126) : SP;
         };
-        // store s_j E p (p = f(m) at row g + 8 m) as FP16 head and tail, s_j = 2^(SP - ex),
-        // and keep p as published in pr; all lanes take part (shuffles)
-        auto publish_exp = [&](bool active, int ex, auto f) {
-            const float sj = pow2f(SP - ex), pi = pow2f(ex - SP);
-            float mx = 0.f;   // the published column's largest |E p| (tightens the next bound)
-            if (active) {
+        auto col_max = [&](float mx) {   // over the column's lanes
 #pragma unroll
-                for (int m = 0; m < MR; ++m) {
-                    const int i = g + LPC * m;
-                    const float2 v = f(m);
-                    const float sc = scv[i], isc = pow2_inv(sc);
-                    mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)) * sc);
-                    __half h, t;
-                    split_f16((v.x * sc) * sj, h, t);
-                    bset(cl, i, h);
-                    if (!LIGHT) bset(2 * NB + cl, i, t);   // a light correction uses the heads only
-                    const float px = LIGHT ? __half2float(h) : __half2float(h) + __half2float(t);
-                    split_f16((v.y * sc) * sj, h, t);
-                    bset(NB + cl, i, h);
-                    if (!LIGHT) bset(3 * NB + cl, i, t);
-                    const float py = LIGHT ? __half2float(h) : __half2float(h) + __half2float(t);
-                    pr[m] = make_float2((px * pi) * isc, (py * pi) * isc);
-                    if ((m & 7) == 7) row_chunk_fence();
+            for (int o = CPW; o <= 16; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            return mx;
+        };
+        // store s_j E p (p = f(m) at row g + LPC m) as FP16 head and tail (Re and Im
+        // rounded as a pair), s_j = 2^(SP - ex), and keep p as published in pr
+        auto publish_exp = [&](bool active, int ex, auto f) {
+            if (!active) return;
+            const float sj = pow2f(SP - ex), pi = pow2f(ex - SP);
+            float mx = 0.f;
+#pragma unroll
+            for (int m = 0; m < MR; ++m) {
+                const int i = g + LPC * m;
+                const float2 v = f(m);
+                const float sc = scv[i], isc = pow2_inv(sc);
+                mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)) * sc);
+                const float sx = (v.x * sc) * sj, sy = (v.y * sc) * sj;
+                const __half2 h2 = __floats2half2_rn(sx, sy);
+                const float2 hf = __half22float2(h2);
+                bset(cl, i, __low2half(h2));
+                bset(NB + cl, i, __high2half(h2));
+                float2 pf = hf;
+                if (!LIGHT) {   // a light correction uses the heads only
+                    const __half2 t2 = __floats2half2_rn(sx - hf.x, sy - hf.y);
+                    const float2 tf = __half22float2(t2);
+                    bset(2 * NB + cl, i, __low2half(t2));
+                    bset(3 * NB + cl, i, __high2half(t2));
+                    pf = make_float2(hf.x + tf.x, hf.y + tf.y);   // exact
                 }
-                if (g == 0) colq[cl] = pow2f(ex - SP - SA);
+                pr[m] = make_float2((pf.x * pi) * isc, (pf.y * pi) * isc);
+                if ((m & 7) == 7) row_chunk_fence();
             }
-            const int ea = col_exp(mx);
-            if (active) pex = ea;
+            if (g == 0) colq[cl] = pow2f(ex - SP - SA);
+            pmx = mx;
         };
         auto publish_all = [&](bool active, auto f) {
             float mx = 0.f;
@@ -483,7 +505,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
                     mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)) * scv[g + LPC * m]);
                 }
             }
-            publish_exp(active, col_exp(mx), f);
+            publish_exp(active, exp_of(col_max(mx)), f);   // all lanes take part (shuffles)
         };
         auto qget = [&](int m) {
             const int i = g + LPC * m;
@@ -677,18 +699,24 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
                         Sz[k] += Sz[k + h];
                         Sr[k] += Sr[k + h];
                     }
-                float rz_new = Sz[0], rr_new = Sr[0];
+                // the lanes of the column: the sums commutatively, with the maxima
+                // of |E z| and of the last published |E p| in the same independent
+                // shuffle rounds
+                float rz_new = Sz[0], rr_new = Sr[0], pm = pmx;
 #pragma unroll
-                for (int o = CPW; o <= 16; o <<= 1) {   // the lanes of the column, commutatively
+                for (int o = CPW; o <= 16; o <<= 1) {
                     rz_new += __shfl_xor_sync(0xffffffffu, rz_new, o);
                     rr_new += __shfl_xor_sync(0xffffffffu, rr_new, o);
+                    mz = fmaxf(mz, __shfl_xor_sync(0xffffffffu, mz, o));
+                    pm = fmaxf(pm, __shfl_xor_sync(0xffffffffu, pm, o));
                 }
                 // p = z + beta p, published for the next product, its scale from the
-                // bound max |E p| <= max |E z| + beta max |E p_old| (< 2^(pex + 1), the
-                // maximum of what was published, so bounds do not compound): one pass
-                // over the rows instead of two
+                // bound max |E p| <= max |E z| + beta max |E p_old| (< 2^(pex + 1), pex
+                // the exponent of the maximum of what was published, so bounds do not
+                // compound): one pass over the rows instead of two
                 const float beta = (!done && rho != 0.f) ? rz_new / rho : 0.f;
-                const int exn = col_exp(fmaf(beta, pow2f(min(pex + 1, 127)), mz));
+                const int pex = exp_of(pm);
+                const int exn = exp_of(fmaf(beta, pow2f(min(pex + 1, 127)), mz));
                 publish_exp(!done, exn, [&](int m) {
                     const float d = dvs[g + LPC * m];
                     return make_float2(fmaf(beta, pr[m].x, d * r[m].x), fmaf(beta, pr[m].y, d * r[m].y));
@@ -724,9 +752,10 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
 
     }
     // the copies issued last have landed before the CTA may exit
-    if (threadIdx.x == 0)
+    if ((threadIdx.x & 63) == 0 && (int)(threadIdx.x >> 6) < NPROD)
         for (uint32_t q = pc > RING ? pc - RING : 0; q < pc; ++q)
-            (void)tc::mbar_wait(&S.full[q % RING], (q / RING) & 1, WAIT_LIMIT);
+            if ((int)(q % RING) % NPROD == (int)(threadIdx.x >> 6))
+                (void)tc::mbar_wait(&S.full[q % RING], (q / RING) & 1, WAIT_LIMIT);
     // every MMA has completed (each qfull was waited for) and every copy landed
     tc::tc_fence_before();
     __syncthreads();
