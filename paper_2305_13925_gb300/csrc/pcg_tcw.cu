@@ -47,16 +47,18 @@
 // their own -- waits on `qfull`, moves U and V out of TMEM -- as Re q and Im q
 // planes, column-major, into the ring, idle until the next vote -- and works
 // column-wise: thread (warp w, lane l) owns column 2 w + (l mod 2) and the
-// complex rows g, g + 16, ... with g = l / 2 (16 rows at K = 256).  r and p (as published: head +
-// tail, exact in FP32) live in registers; x lives in the instance's workspace
-// X (which is also where a refinement correction X += dX lands) and takes
-// x += lambda p as fire-and-forget reductions, so no thread waits on a global
-// load inside the iteration.  The step denominator p^H A p, whose terms can
-// cancel, is compensated (TwoProduct by FMA and TwoSum in a tree, then xor
+// complex row pairs 2 g + 32 n, 2 g + 32 n + 1 with g = l / 2 (16 rows at K =
+// 256), so that its staging reads, B stores and reductions are two rows wide.
+// It works in the Jacobi-scaled variables of the product (r' = E^-1 r, u = s_j
+// E p), where the row factors cancel from every step but the update of x.  r'
+// and u (as published: head + tail, exact in FP32) live in registers; x lives
+// in the instance's workspace X (which is also where a refinement correction
+// X += dX lands) and takes x += lambda p as fire-and-forget reductions, so no
+// thread waits on a global load inside the iteration.  The step denominator
+// p^H A p, whose terms can cancel, is compensated (TwoProduct by FMA and TwoSum in a tree, then xor
 // shuffles combined with commutative or exact operations); the squared norms
 // r^H D^{-1} r and ||r||^2 sum nonnegative terms, where pairwise summation is
-// already accurate to a few units, and are summed so, in the same pass over
-// the rows as r -= lambda q.  All lanes of a column hold bit-identical
+// already accurate to a few units, and are summed so.  All lanes of a column hold bit-identical
 // totals.  Every wait is bounded; a timeout sets the instance's ETIMEOUT flag
 // and ends its iteration.
 #include <cuda_fp16.h>
@@ -111,8 +113,9 @@ struct Cfg {
     static constexpr int B_BYTES = 4 * NB * KC * 2;          // the B operand
     static constexpr int MR = KC / LPC;                      // complex rows per epilogue thread
     static constexpr uint32_t TMEM_COLS = RT * 8 * NB;       // per row tile U | V, 4 NB columns each
-    // B, ring, then per row 1 / d and 2^e; per column the readout factor
-    static constexpr int SMEM = B_BYTES + RING * SLOT + 2 * KC * 4 + NB * 4 + 256;
+    // B, ring, then per row {2^(2e) / A_ii, 2^(2e)} and {2^e, 2^-e}; per column the
+    // readout factor
+    static constexpr int SMEM = B_BYTES + RING * SLOT + 4 * KC * 4 + NB * 4 + 256;
     static_assert(2 * RT * NB * QLD * 4 <= RING * SLOT, "Q staging fits the ring");
     static_assert(KS % (2 * SUB) == 0, "whole slots in a row tile");
     static_assert(RING % NPROD == 0 && THREADS >= 64 * NPROD, "each slot has one producer");
@@ -175,27 +178,32 @@ __device__ __forceinline__ void split_f16(float x, __half &h, __half &t) {
     h = __float2half_rn(x);
     t = __float2half_rn(x - __half2float(h));
 }
-// base[OFF / 8] += v in global memory (8-byte aligned) as one reduction that
-// returns nothing: the issuing thread does not wait for it.  The byte offset
-// is an immediate, so the unrolled rows share one address register.
-template <int OFF>
-__device__ __forceinline__ void red_add2(float2 *base, float2 v) {
-    asm volatile("red.relaxed.gpu.global.add.v2.f32 [%0+%3], {%1, %2};" ::"l"(base), "f"(v.x), "f"(v.y), "n"(OFF));
+// *dst = v as a relaxed store at GPU scope (8-byte aligned)
+__device__ __forceinline__ void st_relaxed2(float2 *dst, float2 v) {
+    asm volatile("st.relaxed.gpu.global.v2.f32 [%0], {%1, %2};" ::"l"(dst), "f"(v.x), "f"(v.y) : "memory");
 }
-// red_add2 of f(m) at rows M, M + 1, ..., N - 1 of base, STRIDE floats2 apart
+// base[OFF / 16] += v in global memory (two complex values, 16-byte aligned)
+// as one reduction that returns nothing: the issuing thread does not wait for
+// it.  The byte offset is an immediate, so the unrolled rows share one address
+// register.
+template <int OFF>
+__device__ __forceinline__ void red_add4(float2 *base, float4 v) {
+    asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0+%5], {%1, %2, %3, %4};" ::"l"(base), "f"(v.x), "f"(v.y),
+                 "f"(v.z), "f"(v.w), "n"(OFF));
+}
+// red_add4 of f(n) at the row pairs n = M, M + 1, ..., N - 1 of base, STRIDE
+// float2 apart
 template <int M, int N, int STRIDE, typename F>
-__device__ __forceinline__ void red_rows(float2 *base, F f) {
+__device__ __forceinline__ void red_pairs(float2 *base, F f) {
     if constexpr (M < N) {
-        red_add2<M * STRIDE * 8>(base, f(M));
-        red_rows<M + 1, N, STRIDE>(base, f);
+        red_add4<M * STRIDE * 8>(base, f(M));
+        red_pairs<M + 1, N, STRIDE>(base, f);
     }
 }
 // keeps the compiler from moving memory accesses across this point: the row
 // loops fence every 8 rows so that their loads are not all hoisted at once
 // (with r and p resident, that would exceed the register file)
 __device__ __forceinline__ void row_chunk_fence() { asm volatile("" ::: "memory"); }
-// 2^-e from 2^e, for 2^e and 2^-e both normal floats
-__device__ __forceinline__ float pow2_inv(float p2) { return __uint_as_float(0x7F000000u - __float_as_uint(p2)); }
 
 // ---------------------------------------------------------------------------
 // A (complex, workspace ld KC) -> the streamed FP16 stages of 2^SA E^-1 A E^-1:
@@ -235,25 +243,26 @@ __global__ void __launch_bounds__(256) tcw_prep_kernel(const DevInst *__restrict
     }
 }
 
-// Compensated sum over the thread's MR rows of Re conj(a_m) b_m, where f(m,
-// a, b) yields the pair of row m: rows in chunks of 8, each chunk a TwoSum
-// tree over the TwoProduct-split products, the chunks combined the same way,
-// then the lanes of the column (lane bits log2(CPW) .. 4) by xor shuffles.  Only
-// one chunk of operands is live at a time.
+// Compensated sum over the thread's MR rows of Re conj(a_m) b_m: rows in
+// chunks of 8, f(u, a, b) filling the operand pairs of chunk u, each chunk a
+// TwoSum tree over the TwoProduct-split products, the chunks combined the same
+// way, then the lanes of the column (lane bits log2(CPW) .. 4) by xor
+// shuffles.  Only one chunk of operands is live at a time.
 template <int MR, typename F>
 __device__ __forceinline__ float col_sum2(F f) {
-    constexpr int CH = MR < 8 ? MR : 8;
+    constexpr int CH = 8;
     constexpr int NCH = MR / CH;
+    static_assert(MR % CH == 0, "whole chunks");
     float S[NCH], Cc[NCH];
 #pragma unroll
     for (int u = 0; u < NCH; ++u) {
+        float2 a[CH], b[CH];
+        f(u, a, b);
         float s[CH], c[CH];
 #pragma unroll
         for (int k = 0; k < CH; ++k) {
-            float2 a, b;
-            f(u * CH + k, a, b);
-            const float p1 = a.x * b.x, p2 = a.y * b.y;
-            const float e1 = fmaf(a.x, b.x, -p1), e2 = fmaf(a.y, b.y, -p2);
+            const float p1 = a[k].x * b[k].x, p2 = a[k].y * b[k].y;
+            const float e1 = fmaf(a[k].x, b[k].x, -p1), e2 = fmaf(a[k].y, b[k].y, -p2);
             float e;
             two_sum(p1, p2, s[k], e);
             c[k] = (e1 + e2) + e;
@@ -295,29 +304,6 @@ __device__ __forceinline__ float col_sum2(F f) {
     return vs + vc;
 }
 
-// Sum over the thread's MR rows of Re conj(a_m) b_m when every term is >= 0
-// (||r||^2 and r^H D^{-1} r): no cancellation can occur, so pairwise
-// summation is already accurate to a few units in the last place; the lanes
-// of the column combine by commutative additions (bit-identical totals).
-template <int MR, typename F>
-__device__ __forceinline__ float col_sumsq(F f) {
-    float s[MR];
-#pragma unroll
-    for (int m = 0; m < MR; ++m) {
-        float2 a, b;
-        f(m, a, b);
-        s[m] = fmaf(a.x, b.x, a.y * b.y);
-    }
-#pragma unroll
-    for (int h = MR / 2; h > 0; h >>= 1)
-#pragma unroll
-        for (int k = 0; k < h; ++k) s[k] += s[k + h];
-    float v = s[0];
-#pragma unroll
-    for (int o = CPW; o <= 16; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 // MODE 0 solves A X = B from X0 (or 0); MODE 1 is a refinement correction
 // solve (right-hand side R, X += dX; instances that stopped refining are
 // skipped); MODE 2 is the same with the heads of A and P only (FP16, 11 bits:
@@ -333,10 +319,12 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
     using C = Cfg<KC>;
     constexpr int MR = C::MR;
     extern __shared__ __align__(1024) unsigned char smem[];
-    float *dvs = reinterpret_cast<float *>(smem + C::B_BYTES + RING * SLOT);    // 1 / A_ii
-    float *scv = dvs + KC;                                                         // 2^e_i
-    float *colq = scv + KC;    // per column 2^-SA / s_j: the readout's unscaling
-    Ctl &S = *reinterpret_cast<Ctl *>(smem + C::B_BYTES + RING * SLOT + 2 * KC * 4 + NB * 4);
+    // per row i: rowc = {d'_i = 2^(2 e_i) d_i, 2^(2 e_i)} (d_i the Jacobi factor
+    // 1 / A_ii, or 1 for plain CG), rowe = {2^e_i, 2^-e_i}
+    float *rowc = reinterpret_cast<float *>(smem + C::B_BYTES + RING * SLOT);
+    float *rowe = rowc + 2 * KC;
+    float *colq = rowe + 2 * KC;   // per column 2^-SA / s_j: the readout's unscaling
+    Ctl &S = *reinterpret_cast<Ctl *>(smem + C::B_BYTES + RING * SLOT + 4 * KC * 4 + NB * 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int i = 0; i < RING; ++i) {
@@ -437,24 +425,29 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
     };
     {
         // ---- epilogue: the vectors of the CTA's NB columns, column-wise ----
+        // It works in the Jacobi-scaled variables of the product, E = diag(2^e_i):
+        //   r' = E^-1 r,  w = E^-1 q (the readout),  u = s_j E p (P as published),
+        // where the row factors cancel from every step but the update of x:
+        //   p^H A p = Re u^H w / s_j,   r' -= lambda w,   x += (lambda / s_j) E^-1 u,
+        //   r^H z = sum d'_i |r'_i|^2,  ||r||^2 = sum 2^(2 e_i) |r'_i|^2,  E z = d' r',
+        //   E p_new = d' r' + (beta / s_j) u,      d'_i = 2^(2 e_i) d_i.
+        // Every factor is a power of two, so the values are those of the unscaled
+        // recurrences.
         const int cl = CPW * warp + (lane % CPW);   // local column
-        const int g = lane / CPW;                    // rows g + LPC m
+        const int g = lane / CPW;                    // row pairs 2 g + 2 LPC n, n < MR / 2
         const int qw = warp & 3, hh = warp >> 2;     // TMEM lane quarter and column group of the readout
         float *Qre = reinterpret_cast<float *>(smem + C::B_BYTES);
         float *Qim = Qre + C::RT * NB * QLD;
         unsigned char *Bop = smem;
-        auto bset = [&](int n, int k, __half v) { *reinterpret_cast<__half *>(Bop + b_off<KC>(n, k)) = v; };
-        // p of the owned rows as published (head + tail, exact in FP32, unscaled):
-        // what the product multiplied, kept here rather than read back
-        float2 pr[MR];
-        // P of the owned rows into the B operand: f(m) gives p at row g + 8 m; the
-        // column's largest |Re|, |Im| of E p (its lanes) sets s_j, then s_j E p goes
-        // in as FP16 head and tail.  All lanes take part (shuffles); a column that
-        // is not `active` keeps its published p.  f is evaluated twice, so it
-        // must not depend on what the second pass writes at other rows.
-        // the largest |E p| over the owned rows as last published; the column's
-        // maximum (over its lanes) bounds the next publication's scale
-        float pmx = 0.f;
+        auto row = [&](int m) { return 2 * g + 2 * LPC * (m >> 1) + (m & 1); };   // the thread's row m
+        // rows row(m), row(m) + 1 (m even) of B's plane pl: 0 Pr_h, 1 Pi_h, 2 Pr_t, 3 Pi_t
+        auto bset2 = [&](int pl, int m, __half2 v) {
+            *reinterpret_cast<__half2 *>(Bop + b_off<KC>(pl * NB + cl, row(m))) = v;
+        };
+        float2 r[MR];        // r' at the owned rows
+        float2 u[MR];        // u at the owned rows, as published (head + tail, exact in FP32)
+        float pinv = 1.f;    // 1 / s_j of the last publication
+        float pmx = 0.f;     // the owned rows' largest |E p| as last published
         // the exponent ex for a column whose largest |E p| is at most mx, s_j =
         // 2^(SP - ex); clamped so that s_j, 1 / s_j and 2^-SA / s_j are floats
         auto exp_of = [&](float mx) {
@@ -465,52 +458,99 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
             for (int o = CPW; o <= 16; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
             return mx;
         };
-        // store s_j E p (p = f(m) at row g + LPC m) as FP16 head and tail (Re and Im
-        // rounded as a pair), s_j = 2^(SP - ex), and keep p as published in pr
+        // store s_j v (v = f(m) = E p at row(m)) into B as FP16 head and tail, two
+        // rows per 32-bit store, and keep u = s_j v as published
         auto publish_exp = [&](bool active, int ex, auto f) {
             if (!active) return;
-            const float sj = pow2f(SP - ex), pi = pow2f(ex - SP);
+            const float sj = pow2f(SP - ex);
             float mx = 0.f;
 #pragma unroll
-            for (int m = 0; m < MR; ++m) {
-                const int i = g + LPC * m;
-                const float2 v = f(m);
-                const float sc = scv[i], isc = pow2_inv(sc);
-                mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)) * sc);
-                const float sx = (v.x * sc) * sj, sy = (v.y * sc) * sj;
-                const __half2 h2 = __floats2half2_rn(sx, sy);
-                const float2 hf = __half22float2(h2);
-                bset(cl, i, __low2half(h2));
-                bset(NB + cl, i, __high2half(h2));
-                float2 pf = hf;
-                if (!LIGHT) {   // a light correction uses the heads only
-                    const __half2 t2 = __floats2half2_rn(sx - hf.x, sy - hf.y);
-                    const float2 tf = __half22float2(t2);
-                    bset(2 * NB + cl, i, __low2half(t2));
-                    bset(3 * NB + cl, i, __high2half(t2));
-                    pf = make_float2(hf.x + tf.x, hf.y + tf.y);   // exact
+            for (int m = 0; m < MR; m += 2) {
+                const float2 v0 = f(m), v1 = f(m + 1);
+                mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v0.x), fabsf(v0.y)), fmaxf(fabsf(v1.x), fabsf(v1.y))));
+                const float ar = v0.x * sj, br = v1.x * sj, ai = v0.y * sj, bi = v1.y * sj;
+                const __half2 hr = __floats2half2_rn(ar, br), hi = __floats2half2_rn(ai, bi);
+                const float2 fr = __half22float2(hr), fi = __half22float2(hi);
+                bset2(0, m, hr);
+                bset2(1, m, hi);
+                if (LIGHT) {   // a light correction uses the heads only
+                    u[m] = make_float2(fr.x, fi.x);
+                    u[m + 1] = make_float2(fr.y, fi.y);
+                } else {
+                    const __half2 tr = __floats2half2_rn(ar - fr.x, br - fr.y);
+                    const __half2 ti = __floats2half2_rn(ai - fi.x, bi - fi.y);
+                    const float2 gr = __half22float2(tr), gi = __half22float2(ti);
+                    bset2(2, m, tr);
+                    bset2(3, m, ti);
+                    u[m] = make_float2(fr.x + gr.x, fi.x + gi.x);   // exact
+                    u[m + 1] = make_float2(fr.y + gr.y, fi.y + gi.y);
                 }
-                pr[m] = make_float2((pf.x * pi) * isc, (pf.y * pi) * isc);
-                if ((m & 7) == 7) row_chunk_fence();
+                if ((m & 7) == 6) row_chunk_fence();
             }
+            pinv = pow2f(ex - SP);
             if (g == 0) colq[cl] = pow2f(ex - SP - SA);
             pmx = mx;
         };
-        auto publish_all = [&](bool active, auto f) {
+        // a publication whose scale comes from the column's maximum (two passes
+        // over f; all lanes take part)
+        auto publish_all = [&](auto f) {
             float mx = 0.f;
-            if (active) {
 #pragma unroll
-                for (int m = 0; m < MR; ++m) {
-                    const float2 v = f(m);
-                    mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)) * scv[g + LPC * m]);
-                }
+            for (int m = 0; m < MR; ++m) {
+                const float2 v = f(m);
+                mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
             }
-            publish_exp(active, exp_of(col_max(mx)), f);   // all lanes take part (shuffles)
+            publish_exp(true, exp_of(col_max(mx)), f);
         };
-        auto qget = [&](int m) {
-            const int i = g + LPC * m;
+        // w at rows row(m), row(m) + 1 (m even): {Re, Re}, {Im, Im}
+        auto wpair = [&](int m, float2 &re, float2 &im) {
+            const int i = row(m);
             const int o = ((i >> 7) * NB + cl) * QLD + (i & 127);
-            return make_float2(Qre[o], Qim[o]);
+            re = *reinterpret_cast<const float2 *>(Qre + o);
+            im = *reinterpret_cast<const float2 *>(Qim + o);
+        };
+        // rowc of rows row(m), row(m) + 1 (m even): {d', 2^2e, d', 2^2e}
+        auto rcpair = [&](int m) { return *reinterpret_cast<const float4 *>(rowc + 2 * row(m)); };
+        // the new r^H z and ||r||^2 (nonnegative terms, pairwise in chunks of 8
+        // rows, then the chunks pairwise) and max |E z| over the owned rows
+        auto norms = [&](float &rz, float &rr, float &mz) {
+            float Sz[MR / 8], Sr[MR / 8];
+            mz = 0.f;
+#pragma unroll
+            for (int c8 = 0; c8 < MR / 8; ++c8) {
+                float sz[8], sr[8];
+#pragma unroll
+                for (int k = 0; k < 8; k += 2) {
+                    const int m = 8 * c8 + k;
+                    const float4 rc = rcpair(m);
+                    const float zx0 = rc.x * r[m].x, zy0 = rc.x * r[m].y;
+                    const float zx1 = rc.z * r[m + 1].x, zy1 = rc.z * r[m + 1].y;
+                    sz[k] = fmaf(r[m].x, zx0, r[m].y * zy0);
+                    sz[k + 1] = fmaf(r[m + 1].x, zx1, r[m + 1].y * zy1);
+                    sr[k] = fmaf(r[m].x, r[m].x, r[m].y * r[m].y) * rc.y;
+                    sr[k + 1] = fmaf(r[m + 1].x, r[m + 1].x, r[m + 1].y * r[m + 1].y) * rc.w;
+                    mz = fmaxf(mz, fmaxf(fmaxf(fabsf(zx0), fabsf(zy0)), fmaxf(fabsf(zx1), fabsf(zy1))));
+                }
+#pragma unroll
+                for (int h = 4; h > 0; h >>= 1)
+#pragma unroll
+                    for (int k = 0; k < h; ++k) {
+                        sz[k] += sz[k + h];
+                        sr[k] += sr[k + h];
+                    }
+                Sz[c8] = sz[0];
+                Sr[c8] = sr[0];
+                row_chunk_fence();
+            }
+#pragma unroll
+            for (int h = MR / 16; h > 0; h >>= 1)
+#pragma unroll
+                for (int k = 0; k < h; ++k) {
+                    Sz[k] += Sz[k + h];
+                    Sr[k] += Sr[k + h];
+                }
+            rz = Sz[0];
+            rr = Sr[0];
         };
         uint32_t qp = 0;
         int err = 0;
@@ -526,41 +566,61 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
             const float tl = (MODE >= 1 && in.rsolve_tol > 0.f) ? in.rsolve_tol : in.tol;
             const float tol2 = tl > 0.f ? tl * tl : -1.f;
             float2 *X = in.X + (size_t)(valid ? j : 0) * KC;   // the iterate (workspace, ld KC)
-            epi_sync();   // the previous instance's readers of dvs and scv are done
-            for (int i = threadIdx.x; i < KC; i += EPI) {
-                dvs[i] = (i < K) ? (VAR == 2 ? 1.f : in.dinv[i]) : 0.f;
-                const int e = row_exp(in.A[(size_t)i * (KC + 1)].x);   // as the prep kernel scaled A
-                scv[i] = pow2f(e);
-            }
-            epi_sync();
-            // ---- Step 1: r = b, x = x0 (mode 0), p = D^{-1} r ----
-            float2 r[MR];
+            // the owned rows' right-hand side (and x0, kept in u until the first
+            // publication reads it): loads in flight across the table build
 #pragma unroll
             for (int m = 0; m < MR; ++m) {
-                const int i = g + LPC * m;
-                float2 b = make_float2(0.f, 0.f);
+                const int i = row(m);
+                float2 b = make_float2(0.f, 0.f), x0 = make_float2(0.f, 0.f);
                 if (valid && i < K) {
                     if (MODE >= 1) b = in.R[i + (size_t)j * KC];                    // refinement residual
                     else if (!in.B) b.x = (i == j) ? 1.f : 0.f;                      // B = I
                     else b = in.B[i + (size_t)j * in.ldb];                           // symbol vectors
+                    if (warm) x0 = in.X0[i + (size_t)j * K];
                 }
                 r[m] = b;
-                if (MODE == 0 && valid)
-                    X[i] = (warm && i < K) ? in.X0[i + (size_t)j * K] : make_float2(0.f, 0.f);
+                u[m] = x0;
             }
-            if (MODE == 0) __threadfence();   // the stores of x0 precede the reductions into X
+            epi_sync();   // the previous instance's readers of rowc and rowe are done
+            for (int i = threadIdx.x; i < KC; i += EPI) {
+                const int e = row_exp(in.A[(size_t)i * (KC + 1)].x);   // as the prep kernel scaled A
+                const float d = (i < K) ? (VAR == 2 ? 1.f : in.dinv[i]) : 0.f;
+                rowc[2 * i] = d * pow2f(2 * e);
+                rowc[2 * i + 1] = pow2f(2 * e);
+                rowe[2 * i] = pow2f(e);
+                rowe[2 * i + 1] = pow2f(-e);
+            }
+            epi_sync();
+            // ---- Step 1: r' = E^-1 b, x = x0 (mode 0; a correction adds to x as it
+            // stands), p = D^{-1} r ----
+#pragma unroll
+            for (int m = 0; m < MR; ++m) {
+                const int i = row(m);
+                const float is = rowe[2 * i + 1];
+                r[m] = make_float2(r[m].x * is, r[m].y * is);
+                // x0 as a relaxed store at GPU scope, like the reductions that follow
+                // it to the same address: the same thread's strong accesses to one
+                // location are ordered without a fence
+                if (MODE == 0 && valid) st_relaxed2(X + i, u[m]);
+            }
             // the warm pass forms A X0 first; columns beyond the right-hand sides carry 0
-            publish_all(true, [&](int m) {
-                const int i = g + LPC * m;
-                const float d = dvs[i];
-                return !valid ? make_float2(0.f, 0.f) : warm ? X[i] : make_float2(d * r[m].x, d * r[m].y);
+            publish_all([&](int m) {
+                const int i = row(m);
+                if (!valid) return make_float2(0.f, 0.f);
+                if (warm) {
+                    const float sc = rowe[2 * i];
+                    return make_float2(sc * u[m].x, sc * u[m].y);   // E x0
+                }
+                const float dp = rowc[2 * i];
+                return make_float2(dp * r[m].x, dp * r[m].y);
             });
-            float rho = col_sumsq<MR>([&](int m, float2 &a, float2 &b) {
-                const float d = dvs[g + LPC * m];
-                a = r[m];
-                b = make_float2(d * r[m].x, d * r[m].y);
-            });
-            float res2 = col_sumsq<MR>([&](int m, float2 &a, float2 &b) { a = r[m]; b = r[m]; });
+            float rho, res2, mz0;
+            norms(rho, res2, mz0);
+#pragma unroll
+            for (int o = CPW; o <= 16; o <<= 1) {   // the lanes of the column, commutatively
+                rho += __shfl_xor_sync(0xffffffffu, rho, o);
+                res2 += __shfl_xor_sync(0xffffffffu, res2, o);
+            }
             const float bn2 = res2;   // stopping and reporting stay relative to ||b||
             const float btol = tol2 * bn2;
             bool done = !valid;
@@ -576,7 +636,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
                 const int cont = epi_or(any && !S.err);
                 if (!cont) break;
                 product(reinterpret_cast<const char *>(in.As));
-                // ---- Q = A P: U, V -> Re q, Im q planes in the ring ----
+                // ---- w = E^-1 A p: U, V -> Re w, Im w planes in the ring ----
                 if (!tc::mbar_wait(&S.qfull, qp & 1, WAIT_LIMIT)) {
                     err = 1;
                     S.err = 1;
@@ -591,10 +651,9 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
                 for (int rt = 0; rt < C::RT; ++rt) {
                     const uint32_t tb = tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)(rt * 8 * NB + RCOLS * hh);
                     const int o = (rt * NB + RCOLS * hh) * QLD + 32 * qw + lane;
-                    const float rf = scv[rt * 128 + 32 * qw + lane];   // row factor 2^e_i
-                    // Re q = Ar Pr - Ai Pi and Im q = Ai Pr + Ar Pi from U's and V's head
-                    // products and corrections (a light correction has no corrections),
-                    // 8 columns at a time
+                    // Re w = (Ar Pr - Ai Pi) and Im w = (Ai Pr + Ar Pi) from U's and V's
+                    // head products and corrections (a light correction has no
+                    // corrections), 8 columns at a time
 #pragma unroll
                     for (int h8 = 0; h8 < RCOLS; h8 += 8) {
                         float x[8], y[8], z[8];
@@ -603,12 +662,12 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
                             tc::tmem_ld8(tb + 4 * NB + NB + h8, y);
                             tc::tmem_ld_wait();
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) Qre[o + (h8 + e) * QLD] = (x[e] - y[e]) * rf * cq[h8 + e];
+                            for (int e = 0; e < 8; ++e) Qre[o + (h8 + e) * QLD] = (x[e] - y[e]) * cq[h8 + e];
                             tc::tmem_ld8(tb + 4 * NB + h8, x);
                             tc::tmem_ld8(tb + NB + h8, y);
                             tc::tmem_ld_wait();
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) Qim[o + (h8 + e) * QLD] = (x[e] + y[e]) * rf * cq[h8 + e];
+                            for (int e = 0; e < 8; ++e) Qim[o + (h8 + e) * QLD] = (x[e] + y[e]) * cq[h8 + e];
                             continue;
                         }
                         tc::tmem_ld8(tb + h8, x);
@@ -620,7 +679,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
                         tc::tmem_ld8(tb + 4 * NB + 3 * NB + h8, z);
                         tc::tmem_ld_wait();
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) Qre[o + (h8 + e) * QLD] = (x[e] - (y[e] + z[e])) * rf * cq[h8 + e];
+                        for (int e = 0; e < 8; ++e) Qre[o + (h8 + e) * QLD] = (x[e] - (y[e] + z[e])) * cq[h8 + e];
                         tc::tmem_ld8(tb + 4 * NB + h8, x);
                         tc::tmem_ld8(tb + 4 * NB + 2 * NB + h8, y);
                         tc::tmem_ld_wait();
@@ -630,79 +689,76 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
                         tc::tmem_ld8(tb + 3 * NB + h8, z);
                         tc::tmem_ld_wait();
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) Qim[o + (h8 + e) * QLD] = (x[e] + (y[e] + z[e])) * rf * cq[h8 + e];
+                        for (int e = 0; e < 8; ++e) Qim[o + (h8 + e) * QLD] = (x[e] + (y[e] + z[e])) * cq[h8 + e];
                     }
                 }
                 epi_sync();
                 if (init) {   // r = b - A X0, then Step 1 from there
 #pragma unroll
-                    for (int m = 0; m < MR; ++m) {
-                        const float2 q = qget(m);
-                        r[m] = make_float2(r[m].x - q.x, r[m].y - q.y);
+                    for (int m = 0; m < MR; m += 2) {
+                        float2 re, im;
+                        wpair(m, re, im);
+                        r[m] = make_float2(r[m].x - re.x, r[m].y - im.x);
+                        r[m + 1] = make_float2(r[m + 1].x - re.y, r[m + 1].y - im.y);
                     }
-                    publish_all(true, [&](int m) {
-                        const float d = dvs[g + LPC * m];
-                        return make_float2(d * r[m].x, d * r[m].y);
+                    publish_all([&](int m) {
+                        const float dp = rowc[2 * row(m)];
+                        return make_float2(dp * r[m].x, dp * r[m].y);
                     });
-                    rho = col_sumsq<MR>([&](int m, float2 &a, float2 &b) {
-                        const float d = dvs[g + LPC * m];
-                        a = r[m];
-                        b = make_float2(d * r[m].x, d * r[m].y);
-                    });
-                    res2 = col_sumsq<MR>([&](int m, float2 &a, float2 &b) { a = r[m]; b = r[m]; });
+                    float mzi;
+                    norms(rho, res2, mzi);
+#pragma unroll
+                    for (int o = CPW; o <= 16; o <<= 1) {
+                        rho += __shfl_xor_sync(0xffffffffu, rho, o);
+                        res2 += __shfl_xor_sync(0xffffffffu, res2, o);
+                    }
                     continue;
                 }
                 // ---- Steps 2-4: lambda = r^H z / p^H A p, x += lambda p, r -= lambda q ----
-                const float pAp = col_sum2<MR>([&](int m, float2 &a, float2 &b) { a = pr[m]; b = qget(m); });
+                const float pAp = pinv * col_sum2<MR>([&](int c8, float2(&a)[8], float2(&b)[8]) {
+#pragma unroll
+                    for (int k = 0; k < 8; k += 2) {
+                        const int m = 8 * c8 + k;
+                        float2 re, im;
+                        wpair(m, re, im);
+                        a[k] = u[m];
+                        a[k + 1] = u[m + 1];
+                        b[k] = make_float2(re.x, im.x);
+                        b[k + 1] = make_float2(re.y, im.y);
+                    }
+                });
                 float lam = 0.f;
                 if (pAp > 0.f) lam = rho / pAp;
                 else if (res2 != 0.f && !done) notHPD = 1;
                 if (done) lam = 0.f;
-                // x += lambda p as reductions into the workspace, which this thread
-                // does not wait for (it reads X again only after a fence)
+                // x += lambda p = (lambda / s_j) E^-1 u as reductions into the
+                // workspace, two rows each, which this thread does not wait for (it
+                // reads X again only after a fence)
                 if (!done) {
-                    red_rows<0, MR, LPC>(X + g, [&](int m) { return make_float2(lam * pr[m].x, lam * pr[m].y); });
+                    const float lp = lam * pinv;
+                    red_pairs<0, MR / 2, 2 * LPC>(X + 2 * g, [&](int n) {
+                        const float4 ee = *reinterpret_cast<const float4 *>(rowe + 2 * row(2 * n));
+                        const float a0 = lp * ee.y, a1 = lp * ee.w;   // times 2^-e of the two rows
+                        return make_float4(a0 * u[2 * n].x, a0 * u[2 * n].y, a1 * u[2 * n + 1].x, a1 * u[2 * n + 1].y);
+                    });
                 }
-                // r -= lambda q, and in the same pass over the rows the new r^H D^{-1} r
-                // and ||r||^2 (nonnegative terms, pairwise in chunks of 8 rows, then the
-                // chunks pairwise) and max |E z| for the next scale
-                float Sz[MR / 8], Sr[MR / 8], mz = 0.f;
+                // r' -= lambda w
 #pragma unroll
-                for (int u = 0; u < MR / 8; ++u) {
-                    float sz[8], sr[8];
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        const int m = 8 * u + k, i = g + LPC * m;
-                        const float2 q = qget(m);
-                        r[m].x = fmaf(-lam, q.x, r[m].x);
-                        r[m].y = fmaf(-lam, q.y, r[m].y);
-                        const float d = dvs[i];
-                        sz[k] = fmaf(r[m].x, d * r[m].x, r[m].y * (d * r[m].y));
-                        sr[k] = fmaf(r[m].x, r[m].x, r[m].y * r[m].y);
-                        mz = fmaxf(mz, fmaxf(fabsf(r[m].x), fabsf(r[m].y)) * (d * scv[i]));
-                    }
-#pragma unroll
-                    for (int h = 4; h > 0; h >>= 1)
-#pragma unroll
-                        for (int k = 0; k < h; ++k) {
-                            sz[k] += sz[k + h];
-                            sr[k] += sr[k + h];
-                        }
-                    Sz[u] = sz[0];
-                    Sr[u] = sr[0];
-                    row_chunk_fence();
+                for (int m = 0; m < MR; m += 2) {
+                    float2 re, im;
+                    wpair(m, re, im);
+                    r[m].x = fmaf(-lam, re.x, r[m].x);
+                    r[m].y = fmaf(-lam, im.x, r[m].y);
+                    r[m + 1].x = fmaf(-lam, re.y, r[m + 1].x);
+                    r[m + 1].y = fmaf(-lam, im.y, r[m + 1].y);
+                    if ((m & 7) == 6) row_chunk_fence();
                 }
-#pragma unroll
-                for (int h = MR / 16; h > 0; h >>= 1)
-#pragma unroll
-                    for (int k = 0; k < h; ++k) {
-                        Sz[k] += Sz[k + h];
-                        Sr[k] += Sr[k + h];
-                    }
+                float rz_new, rr_new, mz;
+                norms(rz_new, rr_new, mz);
                 // the lanes of the column: the sums commutatively, with the maxima
                 // of |E z| and of the last published |E p| in the same independent
                 // shuffle rounds
-                float rz_new = Sz[0], rr_new = Sr[0], pm = pmx;
+                float pm = pmx;
 #pragma unroll
                 for (int o = CPW; o <= 16; o <<= 1) {
                     rz_new += __shfl_xor_sync(0xffffffffu, rz_new, o);
@@ -717,9 +773,10 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
                 const float beta = (!done && rho != 0.f) ? rz_new / rho : 0.f;
                 const int pex = exp_of(pm);
                 const int exn = exp_of(fmaf(beta, pow2f(min(pex + 1, 127)), mz));
+                const float bp = beta * pinv;
                 publish_exp(!done, exn, [&](int m) {
-                    const float d = dvs[g + LPC * m];
-                    return make_float2(fmaf(beta, pr[m].x, d * r[m].x), fmaf(beta, pr[m].y, d * r[m].y));
+                    const float dp = rowc[2 * row(m)];
+                    return make_float2(fmaf(bp, u[m].x, dp * r[m].x), fmaf(bp, u[m].y, dp * r[m].y));
                 });
                 if (!done) {
                     rho = rz_new;
@@ -732,7 +789,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
                 __threadfence();   // this thread's reductions into X are performed
 #pragma unroll
                 for (int m = 0; m < MR; ++m) {
-                    const int i = g + LPC * m;
+                    const int i = row(m);
                     if (i < K) in.Xout[i + (size_t)j * K] = __ldcg(X + i);   // from L2, where they landed
                 }
             }
@@ -749,7 +806,6 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
                 if (f) atomicOr(acc_out.flags + id, f);
             }
         }
-
     }
     // the copies issued last have landed before the CTA may exit
     if ((threadIdx.x & 63) == 0 && (int)(threadIdx.x >> 6) < NPROD)
