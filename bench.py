@@ -134,7 +134,9 @@ def algorithmic_bytes(phase, M, K):
 
 KERNEL_FILES = {("fp32", "gram"): ["gram_simt.cu"], ("fp32", "pcg"): ["pcg_kernel.cuh"],
                 ("fp32", "hx"): ["hx_simt.cu"], ("tf32x3", "gram"): ["gram_tc.cu", "tc.cuh"],
-                ("tf32x3", "pcg"): ["pcg_tc.cu", "tc.cuh"], ("tf32x3", "hx"): ["hx_tc.cu", "tc.cuh"]}
+                ("tf32x3", "pcg"): ["pcg_tc.cu", "tc.cuh"], ("tf32x3", "hx"): ["hx_tc.cu", "tc.cuh"],
+                ("xl", "gram"): ["gram_bf16.cu", "tc.cuh"], ("xl", "pcg"): ["pcg_tcw.cu", "tc.cuh"],
+                ("xl", "hx"): ["hx_bf16.cu", "tc.cuh"]}
 
 
 def kernel_source_hash(phase, precision="fp32"):
@@ -1278,7 +1280,8 @@ def run_headline(args):
                 gbs = hbytes[ph] / (ms / 1e3) / 1e9
                 rec["hbm"] = {"achieved": gbs, "peak": mp["hbm_gbs"], "unit": "GB/s", "frac": gbs / mp["hbm_gbs"],
                               "algorithmic_bytes_per_launch": hbytes[ph]}
-        rec.update({"kernel_ms": ms, "algorithmic_flops_per_launch": work[ph], "traffic": None})
+        rec.update({"kernel_ms": ms, "algorithmic_flops_per_launch": work[ph],
+                    "traffic": ncu_traffic(ph, "xl") if n == 256 and M == 4096 and K == 256 else None})
         per_kernel[ph] = rec
     dom = max(("gram", "pcg", "hx"), key=lambda k: ph0[names.index(k)])
     roofline = dict(per_kernel[dom])
