@@ -94,13 +94,9 @@ constexpr int STAGE = 16384;                  // bytes of one k-step: four 128 x
 constexpr int SUB = 4;                        // k-steps per group: one bulk copy per ring slot
 constexpr int SLOT = SUB * STAGE;
 constexpr int RING = 2;                       // ring slots in flight per CTA
-constexpr int NPROD = 1;                      // copy-issuing threads (0, 64, ...), each owning RING / NPROD slots
-                                              // (two measured the same with two 64 KB slots)
 constexpr int TILE = 4096;
 constexpr int SA = 13;                        // A is stored scaled by 2^SA (entries below 2^15)
 constexpr int SP = 14;                        // a column of P is scaled to a largest entry in [2^14, 2^15)
-constexpr int QLD = 144;                      // floats per staged Q column (128 rows + 16: the two
-                                              // columns of a warp's row reads fall on disjoint banks)
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 constexpr int BAR_EPI = 1;                    // named barrier of the epilogue warps
 
@@ -116,9 +112,9 @@ struct Cfg {
     // B, ring, then per row {2^(2e) / A_ii, 2^(2e)} and {2^e, 2^-e}; per column the
     // readout factor
     static constexpr int SMEM = B_BYTES + RING * SLOT + 4 * KC * 4 + NB * 4 + 256;
-    static_assert(2 * RT * NB * QLD * 4 <= RING * SLOT, "Q staging fits the ring");
+    static_assert(2 * RT * NB * 128 * 4 <= SLOT, "the readout staging fits one ring slot");
     static_assert(KS % (2 * SUB) == 0, "whole slots in a row tile");
-    static_assert(RING % NPROD == 0 && THREADS >= 64 * NPROD, "each slot has one producer");
+    static_assert(RING == 2, "group s of an iteration goes to slot s mod 2");
     static_assert(CTAS_PER_SM * (SMEM + 1024) <= 228 * 1024, "shared memory");
     static_assert(CTAS_PER_SM * TMEM_COLS <= 512, "tensor memory");
     static_assert(CPW * WARPS == NB && LPC * CPW == 32 && MR % 8 == 0, "whole columns per warp");
@@ -344,42 +340,50 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
     tc::tc_fence_after();
     const uint32_t tmem = S.tmem;
     const uint32_t b_base = tc::smem_u32(smem), r_base = b_base + C::B_BYTES;
-    uint32_t pc = 0, mc = 0;   // stages produced (thread 0) / consumed (thread 32)
-    // One iteration's A x P: threads 0, 64, ... (NPROD of them, each owning every
-    // NPROD-th slot) stream the KC / 128 x KC / 16 stages into the ring, one group
-    // of SUB k-steps per bulk copy (a light correction: the heads
-    // of two groups, two copies); thread 32 issues their MMAs (per k-step: head x
-    // [P_h | P_t] and tail x P_h, Ar then Ai) and commits to qfull; the other
-    // threads go on to wait.
+    // One iteration's A x P: thread 0 streams the KC / 128 x KC / 16 stages into
+    // the ring, one group of SUB k-steps per bulk copy (a light correction: the
+    // heads of two groups, two copies); thread 32 issues their MMAs (per k-step:
+    // head x [P_h | P_t] and tail x P_h, Ar then Ai) and commits to qfull; the
+    // other threads go on to wait.
     constexpr bool LIGHT = MODE == 2;
     constexpr int KPS = LIGHT ? 2 * SUB : SUB;       // k-steps per ring slot (heads: 8 KB each)
     auto first_kstep = [&](int s) {   // slot s -> (row tile, k-step of its first stage)
         const int g0 = s * KPS;
         return make_int2(g0 / C::KS, g0 % C::KS);
     };
+    // Group s of an iteration goes to ring slot s mod 2, so that slot 0 can take
+    // the next iteration's first group while the epilogue stages its readout in
+    // slot 1.  fills[k] counts the fills of slot k (thread 0: issued; thread 32:
+    // consumed), which gives the parity of each wait.
+    int fills[RING] = {0, 0};
+    bool pref = false;   // group 0 of the current instance is already in slot 0
+    auto issue = [&](const char *src, int s) {   // thread 0: group s into slot s mod 2
+        const int slot = s & 1;
+        const int2 f = first_kstep(s);
+        const char *st = src + (size_t)(f.x * C::KS + f.y) * STAGE;
+        if (!tc::mbar_wait(&S.empty[slot], (fills[slot] & 1) ^ 1, WAIT_LIMIT)) S.err = 1;
+        ++fills[slot];
+        tc::mbar_arrive_expect_tx(&S.full[slot], SLOT);
+        if (LIGHT) {   // the leading heads half of two groups
+            bulk_load(r_base + slot * SLOT, st, SLOT / 2, &S.full[slot]);
+            bulk_load(r_base + slot * SLOT + SLOT / 2, st + SLOT, SLOT / 2, &S.full[slot]);
+        } else {
+            bulk_load(r_base + slot * SLOT, st, SLOT, &S.full[slot]);
+        }
+    };
     auto product = [&](const char *src) {
-        if ((threadIdx.x & 63) == 0 && (int)(threadIdx.x >> 6) < NPROD) {
-            const int who = threadIdx.x >> 6;   // this producer's slots: slot mod NPROD == who
-            for (int s = 0; s < C::NSTAGE / KPS; ++s, ++pc) {
-                const int slot = pc % RING;
-                if (slot % NPROD != who) continue;
-                const int2 f = first_kstep(s);
-                const char *st = src + (size_t)(f.x * C::KS + f.y) * STAGE;
-                if (!tc::mbar_wait(&S.empty[slot], ((pc / RING) & 1) ^ 1, WAIT_LIMIT)) S.err = 1;
-                tc::mbar_arrive_expect_tx(&S.full[slot], SLOT);
-                if (LIGHT) {   // the leading heads half of two groups
-                    bulk_load(r_base + slot * SLOT, st, SLOT / 2, &S.full[slot]);
-                    bulk_load(r_base + slot * SLOT + SLOT / 2, st + SLOT, SLOT / 2, &S.full[slot]);
-                } else {
-                    bulk_load(r_base + slot * SLOT, st, SLOT, &S.full[slot]);
-                }
-            }
+        if (threadIdx.x == 0) {
+            for (int s = pref ? 1 : 0; s < C::NSTAGE / KPS; ++s) issue(src, s);
+            // the next iteration's first group, on the chance that the job goes on:
+            // its copy then overlaps the epilogue
+            issue(src, 0);
         } else if (threadIdx.x == 32 && LIGHT) {
             constexpr uint32_t idN2 = tc::idesc_f16(128, 2 * NB, false);
             tc::tc_fence_after();
-            for (int s = 0; s < C::NSTAGE / KPS; ++s, ++mc) {
-                const int slot = mc % RING;
-                if (!tc::mbar_wait(&S.full[slot], (mc / RING) & 1, WAIT_LIMIT)) S.err = 1;
+            for (int s = 0; s < C::NSTAGE / KPS; ++s) {
+                const int slot = s & 1;
+                if (!tc::mbar_wait(&S.full[slot], fills[slot] & 1, WAIT_LIMIT)) S.err = 1;
+                ++fills[slot];
                 tc::tc_fence_after();
                 const int2 f = first_kstep(s);
 #pragma unroll
@@ -399,9 +403,10 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
             constexpr uint32_t idN4 = tc::idesc_f16(128, 4 * NB, false);
             constexpr uint32_t idN2 = tc::idesc_f16(128, 2 * NB, false);
             tc::tc_fence_after();
-            for (int s = 0; s < C::NSTAGE / SUB; ++s, ++mc) {
-                const int slot = mc % RING;
-                if (!tc::mbar_wait(&S.full[slot], (mc / RING) & 1, WAIT_LIMIT)) S.err = 1;
+            for (int s = 0; s < C::NSTAGE / SUB; ++s) {
+                const int slot = s & 1;
+                if (!tc::mbar_wait(&S.full[slot], fills[slot] & 1, WAIT_LIMIT)) S.err = 1;
+                ++fills[slot];
                 tc::tc_fence_after();
                 const int2 f = first_kstep(s);
 #pragma unroll
@@ -421,6 +426,22 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
             }
             tc::mma_commit(&S.qfull);
         }
+        pref = true;
+        __syncwarp();
+    };
+    // the vote ended the job: the look-ahead group in slot 0 goes unused; thread
+    // 32 takes it off the ring (its fill landed, the slot is free again)
+    auto discard = [&]() {
+        if (pref && threadIdx.x == 32) {
+            if (!tc::mbar_wait(&S.full[0], fills[0] & 1, WAIT_LIMIT)) S.err = 1;
+            ++fills[0];
+            tc::tc_fence_after();
+            tc::mma_commit(&S.empty[0]);
+            // the commit's arrival has landed before anything else may touch the slot
+            // (or the CTA exit): the phase it completes is the (fills[0] - 1)-th
+            if (!tc::mbar_wait(&S.empty[0], (fills[0] - 1) & 1, WAIT_LIMIT)) S.err = 1;
+        }
+        pref = false;
         __syncwarp();
     };
     {
@@ -436,8 +457,12 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
         const int cl = CPW * warp + (lane % CPW);   // local column
         const int g = lane / CPW;                    // row pairs 2 g + 2 LPC n, n < MR / 2
         const int qw = warp & 3, hh = warp >> 2;     // TMEM lane quarter and column group of the readout
-        float *Qre = reinterpret_cast<float *>(smem + C::B_BYTES);
-        float *Qim = Qre + C::RT * NB * QLD;
+        // the readout staging: ring slot 1 (slot 0 may hold the next iteration's
+        // first group), Re and Im planes, column c's row i at
+        // (i / 128 NB + c) 128 + (i mod 128 xor 16 (c mod 2)), so that the two
+        // columns of a warp's row-pair reads fall on disjoint banks
+        float *Qre = reinterpret_cast<float *>(smem + C::B_BYTES + SLOT);
+        float *Qim = Qre + C::RT * NB * 128;
         unsigned char *Bop = smem;
         auto row = [&](int m) { return 2 * g + 2 * LPC * (m >> 1) + (m & 1); };   // the thread's row m
         // rows row(m), row(m) + 1 (m even) of B's plane pl: 0 Pr_h, 1 Pi_h, 2 Pr_t, 3 Pi_t
@@ -505,7 +530,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
         // w at rows row(m), row(m) + 1 (m even): {Re, Re}, {Im, Im}
         auto wpair = [&](int m, float2 &re, float2 &im) {
             const int i = row(m);
-            const int o = ((i >> 7) * NB + cl) * QLD + (i & 127);
+            const int o = ((i >> 7) * NB + cl) * 128 + ((i & 127) ^ ((cl & 1) << 4));
             re = *reinterpret_cast<const float2 *>(Qre + o);
             im = *reinterpret_cast<const float2 *>(Qim + o);
         };
@@ -634,7 +659,10 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
                 tc::fence_proxy_async_smem();
                 tc::tc_fence_before();
                 const int cont = epi_or(any && !S.err);
-                if (!cont) break;
+                if (!cont) {
+                    discard();
+                    break;
+                }
                 product(reinterpret_cast<const char *>(in.As));
                 // ---- w = E^-1 A p: U, V -> Re w, Im w planes in the ring ----
                 if (!tc::mbar_wait(&S.qfull, qp & 1, WAIT_LIMIT)) {
@@ -650,7 +678,8 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
 #pragma unroll
                 for (int rt = 0; rt < C::RT; ++rt) {
                     const uint32_t tb = tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)(rt * 8 * NB + RCOLS * hh);
-                    const int o = (rt * NB + RCOLS * hh) * QLD + 32 * qw + lane;
+                    const int o = (rt * NB + RCOLS * hh) * 128;   // + column * 128 + row, swizzled
+                    const int rl = 32 * qw + lane;
                     // Re w = (Ar Pr - Ai Pi) and Im w = (Ai Pr + Ar Pi) from U's and V's
                     // head products and corrections (a light correction has no
                     // corrections), 8 columns at a time
@@ -662,12 +691,12 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
                             tc::tmem_ld8(tb + 4 * NB + NB + h8, y);
                             tc::tmem_ld_wait();
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) Qre[o + (h8 + e) * QLD] = (x[e] - y[e]) * cq[h8 + e];
+                            for (int e = 0; e < 8; ++e) Qre[o + (h8 + e) * 128 + (rl ^ ((e & 1) << 4))] = (x[e] - y[e]) * cq[h8 + e];
                             tc::tmem_ld8(tb + 4 * NB + h8, x);
                             tc::tmem_ld8(tb + NB + h8, y);
                             tc::tmem_ld_wait();
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) Qim[o + (h8 + e) * QLD] = (x[e] + y[e]) * cq[h8 + e];
+                            for (int e = 0; e < 8; ++e) Qim[o + (h8 + e) * 128 + (rl ^ ((e & 1) << 4))] = (x[e] + y[e]) * cq[h8 + e];
                             continue;
                         }
                         tc::tmem_ld8(tb + h8, x);
@@ -679,7 +708,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
                         tc::tmem_ld8(tb + 4 * NB + 3 * NB + h8, z);
                         tc::tmem_ld_wait();
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) Qre[o + (h8 + e) * QLD] = (x[e] - (y[e] + z[e])) * cq[h8 + e];
+                        for (int e = 0; e < 8; ++e) Qre[o + (h8 + e) * 128 + (rl ^ ((e & 1) << 4))] = (x[e] - (y[e] + z[e])) * cq[h8 + e];
                         tc::tmem_ld8(tb + 4 * NB + h8, x);
                         tc::tmem_ld8(tb + 4 * NB + 2 * NB + h8, y);
                         tc::tmem_ld_wait();
@@ -689,7 +718,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
                         tc::tmem_ld8(tb + 3 * NB + h8, z);
                         tc::tmem_ld_wait();
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) Qim[o + (h8 + e) * QLD] = (x[e] + (y[e] + z[e])) * cq[h8 + e];
+                        for (int e = 0; e < 8; ++e) Qim[o + (h8 + e) * 128 + (rl ^ ((e & 1) << 4))] = (x[e] + (y[e] + z[e])) * cq[h8 + e];
                     }
                 }
                 epi_sync();
@@ -808,10 +837,9 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
         }
     }
     // the copies issued last have landed before the CTA may exit
-    if ((threadIdx.x & 63) == 0 && (int)(threadIdx.x >> 6) < NPROD)
-        for (uint32_t q = pc > RING ? pc - RING : 0; q < pc; ++q)
-            if ((int)(q % RING) % NPROD == (int)(threadIdx.x >> 6))
-                (void)tc::mbar_wait(&S.full[q % RING], (q / RING) & 1, WAIT_LIMIT);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < RING; ++k)
+            if (fills[k] > 0) (void)tc::mbar_wait(&S.full[k], (fills[k] - 1) & 1, WAIT_LIMIT);
     // every MMA has completed (each qfull was waited for) and every copy landed
     tc::tc_fence_before();
     __syncthreads();
