@@ -109,10 +109,16 @@ struct Cfg {
     static constexpr int B_BYTES = 4 * NB * KC * 2;          // the B operand
     static constexpr int MR = KC / LPC;                      // complex rows per epilogue thread
     static constexpr uint32_t TMEM_COLS = RT * 8 * NB;       // per row tile U | V, 4 NB columns each
-    // B, ring, then per row {2^(2e) / A_ii, 2^(2e)} and {2^e, 2^-e}; per column the
-    // readout factor
-    static constexpr int SMEM = B_BYTES + RING * SLOT + 4 * KC * 4 + NB * 4 + 256;
-    static_assert(2 * RT * NB * 128 * 4 <= SLOT, "the readout staging fits one ring slot");
+    // A's stages fit the ring (K = 128: 128 KB): they stay resident for the job,
+    // copied in by its first product, and the readout is staged after the ring
+    static constexpr bool RES = NSTAGE * STAGE <= RING * SLOT;
+    static constexpr int STG_BYTES = 2 * RT * NB * 128 * 4;   // Re, Im staging planes
+    static constexpr int STG_OFF = RES ? B_BYTES + RING * SLOT : B_BYTES + SLOT;   // else ring slot 1
+    static constexpr int TAB_OFF = B_BYTES + RING * SLOT + (RES ? STG_BYTES : 0);
+    // B, ring, [staging], then per row {2^(2e) / A_ii, 2^(2e)} and {2^e, 2^-e}; per
+    // column the readout factor
+    static constexpr int SMEM = TAB_OFF + 4 * KC * 4 + NB * 4 + 256;
+    static_assert(STG_BYTES <= SLOT, "the readout staging fits one ring slot");
     static_assert(KS % (2 * SUB) == 0, "whole slots in a row tile");
     static_assert(RING == 2, "group s of an iteration goes to slot s mod 2");
     static_assert(CTAS_PER_SM * (SMEM + 1024) <= 228 * 1024, "shared memory");
@@ -317,10 +323,10 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
     extern __shared__ __align__(1024) unsigned char smem[];
     // per row i: rowc = {d'_i = 2^(2 e_i) d_i, 2^(2 e_i)} (d_i the Jacobi factor
     // 1 / A_ii, or 1 for plain CG), rowe = {2^e_i, 2^-e_i}
-    float *rowc = reinterpret_cast<float *>(smem + C::B_BYTES + RING * SLOT);
+    float *rowc = reinterpret_cast<float *>(smem + C::TAB_OFF);
     float *rowe = rowc + 2 * KC;
     float *colq = rowe + 2 * KC;   // per column 2^-SA / s_j: the readout's unscaling
-    Ctl &S = *reinterpret_cast<Ctl *>(smem + C::B_BYTES + RING * SLOT + 4 * KC * 4 + NB * 4);
+    Ctl &S = *reinterpret_cast<Ctl *>(smem + C::TAB_OFF + 4 * KC * 4 + NB * 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int i = 0; i < RING; ++i) {
@@ -355,8 +361,10 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
     // the next iteration's first group while the epilogue stages its readout in
     // slot 1.  fills[k] counts the fills of slot k (thread 0: issued; thread 32:
     // consumed), which gives the parity of each wait.
+    // With A resident (C::RES) the job's first product fills the slots once and
+    // later products multiply what is there.
     int fills[RING] = {0, 0};
-    bool pref = false;   // group 0 of the current instance is already in slot 0
+    bool pref = false;   // group 0 (resident: all of A) of the current instance is already in the ring
     auto issue = [&](const char *src, int s) {   // thread 0: group s into slot s mod 2
         const int slot = s & 1;
         const int2 f = first_kstep(s);
@@ -373,17 +381,24 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
     };
     auto product = [&](const char *src) {
         if (threadIdx.x == 0) {
-            for (int s = pref ? 1 : 0; s < C::NSTAGE / KPS; ++s) issue(src, s);
-            // the next iteration's first group, on the chance that the job goes on:
-            // its copy then overlaps the epilogue
-            issue(src, 0);
+            if (C::RES) {
+                if (!pref)
+                    for (int s = 0; s < C::NSTAGE / KPS; ++s) issue(src, s);
+            } else {
+                for (int s = pref ? 1 : 0; s < C::NSTAGE / KPS; ++s) issue(src, s);
+                // the next iteration's first group, on the chance that the job goes
+                // on: its copy then overlaps the epilogue
+                issue(src, 0);
+            }
         } else if (threadIdx.x == 32 && LIGHT) {
             constexpr uint32_t idN2 = tc::idesc_f16(128, 2 * NB, false);
             tc::tc_fence_after();
             for (int s = 0; s < C::NSTAGE / KPS; ++s) {
                 const int slot = s & 1;
-                if (!tc::mbar_wait(&S.full[slot], fills[slot] & 1, WAIT_LIMIT)) S.err = 1;
-                ++fills[slot];
+                if (!C::RES || !pref) {
+                    if (!tc::mbar_wait(&S.full[slot], fills[slot] & 1, WAIT_LIMIT)) S.err = 1;
+                    ++fills[slot];
+                }
                 tc::tc_fence_after();
                 const int2 f = first_kstep(s);
 #pragma unroll
@@ -396,7 +411,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
                     tc::mma_bf16(du, tc::smem_desc(a0, 128, 256), bd, idN2, acc);
                     tc::mma_bf16(dvv, tc::smem_desc(a0 + TILE, 128, 256), bd, idN2, acc);
                 }
-                tc::mma_commit(&S.empty[slot]);
+                if (!C::RES) tc::mma_commit(&S.empty[slot]);
             }
             tc::mma_commit(&S.qfull);
         } else if (threadIdx.x == 32) {
@@ -405,8 +420,10 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
             tc::tc_fence_after();
             for (int s = 0; s < C::NSTAGE / SUB; ++s) {
                 const int slot = s & 1;
-                if (!tc::mbar_wait(&S.full[slot], fills[slot] & 1, WAIT_LIMIT)) S.err = 1;
-                ++fills[slot];
+                if (!C::RES || !pref) {
+                    if (!tc::mbar_wait(&S.full[slot], fills[slot] & 1, WAIT_LIMIT)) S.err = 1;
+                    ++fills[slot];
+                }
                 tc::tc_fence_after();
                 const int2 f = first_kstep(s);
 #pragma unroll
@@ -422,24 +439,30 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
                     tc::mma_bf16(dvv, tc::smem_desc(a0 + TILE, 128, 256), bd, idN4, acc);
                     tc::mma_bf16(dvv + 2 * NB, tc::smem_desc(a1 + TILE, 128, 256), bd, idN2, 1u);
                 }
-                tc::mma_commit(&S.empty[slot]);   // the slot is free once these have read it
+                if (!C::RES) tc::mma_commit(&S.empty[slot]);   // the slot is free once these have read it
             }
             tc::mma_commit(&S.qfull);
         }
         pref = true;
         __syncwarp();
     };
-    // the vote ended the job: the look-ahead group in slot 0 goes unused; thread
-    // 32 takes it off the ring (its fill landed, the slot is free again)
+    // the vote ended the job: the look-ahead group in slot 0 goes unused (resident:
+    // A leaves the ring); thread 32 takes it off (its fill landed, the slot is free
+    // again) and waits for the release to land before anything else may touch the
+    // slot (or the CTA exit)
+    auto release = [&](int k, bool landed) {
+        if (!landed && !tc::mbar_wait(&S.full[k], fills[k] & 1, WAIT_LIMIT)) S.err = 1;
+        if (!landed) ++fills[k];
+        tc::tc_fence_after();
+        tc::mma_commit(&S.empty[k]);
+        if (!tc::mbar_wait(&S.empty[k], (fills[k] - 1) & 1, WAIT_LIMIT)) S.err = 1;   // phase fills - 1
+    };
     auto discard = [&]() {
         if (pref && threadIdx.x == 32) {
-            if (!tc::mbar_wait(&S.full[0], fills[0] & 1, WAIT_LIMIT)) S.err = 1;
-            ++fills[0];
-            tc::tc_fence_after();
-            tc::mma_commit(&S.empty[0]);
-            // the commit's arrival has landed before anything else may touch the slot
-            // (or the CTA exit): the phase it completes is the (fills[0] - 1)-th
-            if (!tc::mbar_wait(&S.empty[0], (fills[0] - 1) & 1, WAIT_LIMIT)) S.err = 1;
+            if (C::RES)
+                for (int k = 0; k < RING && k < C::NSTAGE / KPS; ++k) release(k, true);
+            else
+                release(0, false);
         }
         pref = false;
         __syncwarp();
@@ -458,10 +481,10 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
         const int g = lane / CPW;                    // row pairs 2 g + 2 LPC n, n < MR / 2
         const int qw = warp & 3, hh = warp >> 2;     // TMEM lane quarter and column group of the readout
         // the readout staging: ring slot 1 (slot 0 may hold the next iteration's
-        // first group), Re and Im planes, column c's row i at
+        // first group), or after the ring when A is resident; Re and Im planes, column c's row i at
         // (i / 128 NB + c) 128 + (i mod 128 xor 16 (c mod 2)), so that the two
         // columns of a warp's row-pair reads fall on disjoint banks
-        float *Qre = reinterpret_cast<float *>(smem + C::B_BYTES + SLOT);
+        float *Qre = reinterpret_cast<float *>(smem + C::STG_OFF);
         float *Qim = Qre + C::RT * NB * 128;
         unsigned char *Bop = smem;
         auto row = [&](int m) { return 2 * g + 2 * LPC * (m >> 1) + (m & 1); };   // the thread's row m
