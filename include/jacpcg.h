@@ -74,12 +74,17 @@ enum { JACPCG_STANDARD = 0, JACPCG_ALG1 = 1, JACPCG_CG = 2, JACPCG_JOR = 3, JACP
  *         into a TF32 head and a TF32 tail, three products accumulated in
  *         FP32 (about FP32 accuracy).
  * The iteration's vectors and scalars are FP32 in both cases; with TF32X3
- * its product A P runs on the tensor cores in 3xTF32 for the 64, 128 and
- * 256 classes (standard and CG forms).  Every per-column dot product whose
- * terms can cancel (p^H A p; Algorithm 1's complex denominator) is
- * compensated (Dot2); the squared norms r^H D^{-1} r and ||r||^2 are sums of
- * nonnegative terms (no cancellation), compensated on the SIMT kernel and
- * summed pairwise (a few ulps) on the tensor-core kernels. */
+ * its product A P runs on the tensor cores (standard and CG forms): in
+ * 3xTF32 for the 64 class, and for the 128 and 256 classes as FP16 heads and
+ * tails of A and P scaled by exact powers of two (22 bits per entry, every
+ * product exact).  Every per-column dot product whose terms can cancel (p^H A
+ * p; Algorithm 1's complex denominator) is compensated (Dot2); the squared
+ * norms r^H D^{-1} r and ||r||^2 are sums of nonnegative terms (no
+ * cancellation), compensated on the SIMT kernel and summed pairwise (a few
+ * ulps) on the tensor-core kernels.  Refinement correction solves of the 128
+ * and 256 classes run with refine_solve_tol >= 5e-3 on the FP16 heads alone
+ * (11 bits) with plain pairwise p^H A p: the next accurate residual corrects
+ * what such a loose solve leaves. */
 enum { JACPCG_FP32 = 0, JACPCG_TF32X3 = 1 };
 
 /* Storage type of H (jacpcg_instance.h_dtype).  BF16: each complex entry is

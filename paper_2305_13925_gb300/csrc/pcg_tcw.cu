@@ -55,7 +55,8 @@
 // in the instance's workspace X (which is also where a refinement correction
 // X += dX lands) and takes x += lambda p as fire-and-forget reductions, so no
 // thread waits on a global load inside the iteration.  The step denominator
-// p^H A p, whose terms can cancel, is compensated (TwoProduct by FMA and TwoSum in a tree, then xor
+// p^H A p, whose terms can cancel, is compensated (a light correction, which
+// only has to cut the error by a fixed factor, sums it plainly) (TwoProduct by FMA and TwoSum in a tree, then xor
 // shuffles combined with commutative or exact operations); the squared norms
 // r^H D^{-1} r and ||r||^2 sum nonnegative terms, where pairwise summation is
 // already accurate to a few units, and are summed so.  All lanes of a column hold bit-identical
@@ -304,6 +305,38 @@ __device__ __forceinline__ float col_sum2(F f) {
         vc = (vc + wc) + e;
     }
     return vs + vc;
+}
+
+// Plain pairwise sum over the thread's MR rows of Re conj(a_m) b_m (chunks as
+// in col_sum2), the lanes of the column combined commutatively: for the light
+// correction solves, whose 1e-2 tolerance leaves FP32 rounding of the
+// denominator far behind
+template <int MR, typename F>
+__device__ __forceinline__ float col_sum_plain(F f) {
+    constexpr int CH = 8, NCH = MR / CH;
+    float S[NCH];
+#pragma unroll
+    for (int u = 0; u < NCH; ++u) {
+        float2 a[CH], b[CH];
+        f(u, a, b);
+        float s[CH];
+#pragma unroll
+        for (int k = 0; k < CH; ++k) s[k] = fmaf(a[k].x, b[k].x, a[k].y * b[k].y);
+#pragma unroll
+        for (int h = CH / 2; h > 0; h >>= 1)
+#pragma unroll
+            for (int k = 0; k < h; ++k) s[k] += s[k + h];
+        S[u] = s[0];
+        row_chunk_fence();
+    }
+#pragma unroll
+    for (int h = NCH / 2; h > 0; h >>= 1)
+#pragma unroll
+        for (int k = 0; k < h; ++k) S[k] += S[k + h];
+    float v = S[0];
+#pragma unroll
+    for (int o = CPW; o <= 16; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
 // MODE 0 solves A X = B from X0 (or 0); MODE 1 is a refinement correction
@@ -767,7 +800,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
                     continue;
                 }
                 // ---- Steps 2-4: lambda = r^H z / p^H A p, x += lambda p, r -= lambda q ----
-                const float pAp = pinv * col_sum2<MR>([&](int c8, float2(&a)[8], float2(&b)[8]) {
+                auto wchunk = [&](int c8, float2(&a)[8], float2(&b)[8]) {
 #pragma unroll
                     for (int k = 0; k < 8; k += 2) {
                         const int m = 8 * c8 + k;
@@ -778,7 +811,9 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
                         b[k] = make_float2(re.x, im.x);
                         b[k + 1] = make_float2(re.y, im.y);
                     }
-                });
+                };
+                // p^H A p: compensated in the solve, plain in a light correction
+                const float pAp = pinv * (LIGHT ? col_sum_plain<MR>(wchunk) : col_sum2<MR>(wchunk));
                 float lam = 0.f;
                 if (pAp > 0.f) lam = rho / pAp;
                 else if (res2 != 0.f && !done) notHPD = 1;
