@@ -4,8 +4,8 @@
 // caller's symbol vectors, or the refinement residual; warm start from X0),
 // as pcg_tc.cu does for the 64 class.
 //
-// At these sizes A does not fit on one SM (K = 256: 512 KB complex), so it
-// is streamed.  Once per instance a prep kernel stores it as MMA-ready FP16
+// At K = 256 A does not fit on one SM (512 KB complex), so it is streamed
+// (at K = 128 its 128 KB of stages stay resident for a job).  Once per instance a prep kernel stores it as MMA-ready FP16
 // tiles, for row tile rt (128 rows) and k-step ks (16 columns): Ar_h, Ai_h,
 // Ar_t, Ai_t, each a 128 x 16 tile in the canonical no-swizzle K-major
 // layout, in groups of SUB k-steps [heads of the group | tails of the group],
@@ -23,45 +23,45 @@
 // per iteration rather than twice as in the 2 x 2 real expansion.
 //
 // The columns of X are independent systems sharing A, so a CTA owns 32 of
-// them (NB) for one instance, one CTA per SM.  Their P is resident in shared memory as the
-// MMA's B operand, laid out as 4 NB rows [Pr_h | Pi_h | Pr_t | Pi_t] along N:
+// them (NB) for one instance, one CTA per SM.  Their P is resident in shared
+// memory as the MMA's B operand, laid out as 4 NB rows [Pr_h | Pi_h | Pr_t | Pi_t] along N:
 // FP16 head and tail of s_j E p_j, s_j a power of two per column that puts
 // the column's largest entry in [2^14, 2^15).  Per k-step:
 //   U += Ar_h [P_h | P_t]  (N = 4 NB),   U[2 NB..] += Ar_t P_h  (N = 2 NB),
 //   V += Ai_h [P_h | P_t],               V[2 NB..] += Ai_t P_h,
 // so U = Ar [Pr | Pi] and V = Ai [Pr | Pi] with every product exact (columns
 // 0 .. 2 NB - 1 head x head, the rest both corrections), and
-//   Re q = Ar Pr - Ai Pi,   Im q = Ai Pr + Ar Pi,
-// each unscaled by 2^(e_i - 13) / s_j on its way out of TMEM.  U and V of both
-// row tiles take 2 x 2 x 4 NB TMEM columns (K = 256: all 512 of the SM's).
-// The accumulation
-// chain of a row tile is its KC / 16 k-steps.  The iteration uses p as
-// published (head + tail, unscaled: 22 bits), in the product and everywhere
-// else, so the recurrences stay consistent.
+//   Re w = Ar Pr - Ai Pi,   Im w = Ai Pr + Ar Pi,   w = E^-1 A p,
+// each scaled by 2^-13 / s_j on its way out of TMEM.  U and V of both row
+// tiles take 2 x 2 x 4 NB TMEM columns (K = 256: all 512 of the SM's).  The
+// accumulation chain of a row tile is its KC / 16 k-steps.  The iteration uses
+// p as published (head + tail, 22 bits), in the product and everywhere else,
+// so the recurrences stay consistent.
 //
 // Roles: 16 warps own the vectors; each iteration they publish P (split) into
 // the B operand and vote on continuing (one barrier reduction), then thread 0
-// streams the iteration's KC / 128 x KC / 16 stages (waiting on `empty`),
-// thread 32 issues the MMAs (waiting on `full`) and commits to `qfull`, and
-// the epilogue -- idle while the product runs, so the roles take no warps of
-// their own -- waits on `qfull`, moves U and V out of TMEM -- as Re q and Im q
-// planes, column-major, into the ring, idle until the next vote -- and works
-// column-wise: thread (warp w, lane l) owns column 2 w + (l mod 2) and the
-// complex row pairs 2 g + 32 n, 2 g + 32 n + 1 with g = l / 2 (16 rows at K =
-// 256), so that its staging reads, B stores and reductions are two rows wide.
-// It works in the Jacobi-scaled variables of the product (r' = E^-1 r, u = s_j
-// E p), where the row factors cancel from every step but the update of x.  r'
-// and u (as published: head + tail, exact in FP32) live in registers; x lives
-// in the instance's workspace X (which is also where a refinement correction
-// X += dX lands) and takes x += lambda p as fire-and-forget reductions, so no
-// thread waits on a global load inside the iteration.  The step denominator
-// p^H A p, whose terms can cancel, is compensated (a light correction, which
-// only has to cut the error by a fixed factor, sums it plainly) (TwoProduct by FMA and TwoSum in a tree, then xor
-// shuffles combined with commutative or exact operations); the squared norms
-// r^H D^{-1} r and ||r||^2 sum nonnegative terms, where pairwise summation is
-// already accurate to a few units, and are summed so.  All lanes of a column hold bit-identical
-// totals.  Every wait is bounded; a timeout sets the instance's ETIMEOUT flag
-// and ends its iteration.
+// streams the iteration's groups (waiting on `empty`), thread 32 issues the
+// MMAs (waiting on `full`) and commits to `qfull`, and the epilogue -- idle
+// while the product runs, so the roles take no warps of their own -- waits on
+// `qfull`, moves U and V out of TMEM as Re w and Im w planes, column-major,
+// into a staging area (ring slot 1, or after the ring when A stays resident),
+// and works column-wise: thread (warp w, lane l) owns column 2 w + (l mod 2)
+// and the complex row pairs 2 g + 32 n, 2 g + 32 n + 1 with g = l / 2 (16 rows
+// at K = 256), so that its staging reads, B stores and reductions are two rows
+// wide.  It works in the Jacobi-scaled variables of the product (r' = E^-1 r,
+// u = s_j E p), where the row factors cancel from every step but the update
+// of x.  r' and u (as published: head + tail, exact in FP32) live in
+// registers; x lives in the instance's workspace X (which is also where a
+// refinement correction X += dX lands) and takes x += lambda p as
+// fire-and-forget reductions, so no thread waits on a global load inside the
+// iteration.  The step denominator p^H A p, whose terms can cancel, is
+// compensated (TwoProduct by FMA and TwoSum in a tree, then xor shuffles
+// combined with commutative or exact operations); a light correction, which
+// only has to cut the error by a fixed factor, sums it plainly.  The squared
+// norms r^H D^{-1} r and ||r||^2 sum nonnegative terms, where pairwise
+// summation is already accurate to a few units, and are summed so.  All lanes
+// of a column hold bit-identical totals.  Every wait is bounded; a timeout
+// sets the instance's ETIMEOUT flag and ends its iteration.
 #include <cuda_fp16.h>
 
 #include "common.cuh"
@@ -79,7 +79,8 @@ namespace {
 // column): 3.41 ms; one CTA, 32 columns, 16 warps, four 32 KB slots: 3.29;
 // two 64 KB slots: 3.09 (four 32 KB slots, even with a second copy-issuing
 // thread, 3.28; eight 16 KB slots 3.75: the fewer, larger copies the
-// better).  The three MMAs per k-step of the head / tail split take about 4 us
+// better); the next iteration's first group copied during the epilogue:
+// 2.84.  The three MMAs per k-step of the head / tail split take about 4 us
 // of an iteration's 6 us product at the measured tensor peak.  16 warps (128
 // registers, 16 rows per thread) rather than 8 (255, 32 rows) hide more of the
 // epilogue's latency.
@@ -720,7 +721,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) pcg_tcw_kernel(const Dev
                     break;
                 }
                 product(reinterpret_cast<const char *>(in.As));
-                // ---- w = E^-1 A p: U, V -> Re w, Im w planes in the ring ----
+                // ---- w = E^-1 A p: U, V -> Re w, Im w staging planes ----
                 if (!tc::mbar_wait(&S.qfull, qp & 1, WAIT_LIMIT)) {
                     err = 1;
                     S.err = 1;
