@@ -383,7 +383,7 @@ bool encode_h_maps(const jacpcg_ctx *ctx, const jacpcg_instance &q, CUtensorMap 
     const cuuint64_t dims[2] = {2 * (cuuint64_t)q.M, (cuuint64_t)q.K};
     const cuuint64_t strides[1] = {4 * (cuuint64_t)q.ldh};
     const cuuint32_t elem[2] = {1, 1};
-    const cuuint32_t gbox[2] = {64, 128}, hbox[2] = {64, 64};
+    const cuuint32_t gbox[2] = {64, 128}, hbox[2] = {64, 128};   // the same box: 64 values x 128 users
     void *base = const_cast<void *>(q.H);
     return enc(gram_map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, gbox, elem,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,

@@ -14,7 +14,7 @@
 // A job is (instance, output group g): the 32 columns 32 g .. 32 g + 31 of W.
 // B = [Xr^T ; Xi^T] of those columns (64 rows, K-major, no swizzle, three
 // terms: 96 KB for K = 256) stays in shared memory for the whole job; H
-// streams through a ring of stages of 128 rows of U x 64 users, two tiled
+// streams through a ring of stages of 128 rows of U x 128 users, two tiled
 // TMA copies each (128-byte swizzle, zero-filled past M and K).  The three
 // terms' rows of B follow each other, so one N = 192 MMA per 16 users forms
 // the X1, X2 and X3 products side by side in TMEM: three accumulation chains
@@ -45,10 +45,12 @@ namespace {
 constexpr int NB = 32;                    // output columns per job
 constexpr int BR = 2 * NB;                // B rows: Xr^T then Xi^T
 constexpr int TR = 128;                   // rows of U (64 antennas) per tile: MMA M
-constexpr int KU = 64;                    // users per stage
-constexpr int BOX = KU * 128;             // one tensor copy: 64 users x 64 values (8 KB)
-constexpr int UST = 2 * BOX;              // one stage: 128 rows of U x 64 users
-constexpr int RING = 7;
+constexpr int KU = 128;                   // users per stage: fewer, larger tensor copies (two per
+                                          // stage) -- 64-user stages, twice the copies from one
+                                          // issuing thread, took 1.34 against 1.17 ms on the XL batch
+constexpr int BOX = KU * 128;             // one tensor copy: 128 users x 64 values (16 KB)
+constexpr int UST = 2 * BOX;              // one stage: 128 rows of U x 128 users
+constexpr int RING = 3;
 constexpr int KCMAX = 256;
 constexpr int BTERM = BR * KCMAX * 2;     // one bfloat16 term of B (32 KB)
 constexpr int NBUF = 2;                   // TMEM tile buffers: X1 | X2 | X3 products, 64 columns each
@@ -304,7 +306,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) hx_bf16_kernel(const DevInst *__r
                         for (int kk = 0; kk < KU / 16; ++kk) {
                             // 16 users: rows 16 kk .. of both boxes; B columns (8 kc + 2 kk) .. of 8 users
                             const uint64_t ad = tc::smem_desc_sw128(u + kk * 2048, BOX, 1024);
-                            const uint32_t boff = (8 * kc + 2 * kk) * 128;
+                            const uint32_t boff = ((KU / 8) * kc + 2 * kk) * 128;
                             const bool first = kc == 0 && kk == 0;
                             // all three terms (N = 192: X1 | X2 | X3 products side by side)
                             tc::mma_bf16(d, ad, tc::smem_desc(b0 + boff, 128, sbo), idesc, first ? 0u : 1u);
