@@ -50,7 +50,7 @@ constexpr int KU = 128;                   // users per stage: fewer, larger tens
                                           // issuing thread, took 1.34 against 1.17 ms on the XL batch
 constexpr int BOX = KU * 128;             // one tensor copy: 128 users x 64 values (16 KB)
 constexpr int UST = 2 * BOX;              // one stage: 128 rows of U x 128 users
-constexpr int RING = 3;
+constexpr int RING = 4;
 constexpr int KCMAX = 256;
 constexpr int BTERM = BR * KCMAX * 2;     // one bfloat16 term of B (32 KB)
 constexpr int NBUF = 2;                   // TMEM tile buffers: X1 | X2 | X3 products, 64 columns each
