@@ -373,7 +373,7 @@ Layout make_layout(const jacpcg_config &cfg, const jacpcg_instance *inst, int n,
 // and the launch list of the plan.
 // Tensor maps over a bfloat16 channel's H read as K rows of 2M values (row
 // stride ldh * 4 bytes), 128-byte swizzle, zero fill past M and K: box 64 x 128
-// for the Gram (user tiles), 64 x 64 for W = H X.
+// (64 values of 128 users) for the Gram's user tiles and W = H X's stages.
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
